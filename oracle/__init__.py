@@ -1,0 +1,217 @@
+"""Plain FP64 CPU oracle for the fused D2Q9 stream + collide + kinetic-sensor step.
+
+TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` may import this package.  The oracle is the
+C library ``orc.c`` (plain scalar double-precision loops, one function per definition
+of arXiv 2603.13618), loaded here with ctypes; it shares no code with the CUDA
+library in ``paper_2603_13618_gb300``.
+
+Arrays are numpy float64: populations ``f[9, ny, nx]``, fields ``[ny, nx]``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "liborc.so")
+
+NSENS = 13
+SENSOR_NAMES = ("tau_ns", "c", "s", "e", "qh", "kn", "neq", "qe", "hr", "kl",
+                "sigma_h", "sigma_kl", "alpha")
+SENSOR_ID = {n: k for k, n in enumerate(SENSOR_NAMES)}
+
+
+def build(verbose: bool = False) -> str:
+    """Compile orc.c into _build/liborc.so with gcc (plain -O2, no fast-math)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    src = os.path.join(_HERE, "orc.c")
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
+           "-ffp-contract=off", "-Wall", "-Wextra", "-o", _LIB_PATH, src, "-lm"]
+    if verbose:
+        print(" ".join(cmd))
+    subprocess.run(cmd, check=True)
+    return _LIB_PATH
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        src = os.path.join(_HERE, "orc.c")
+        if (not os.path.exists(_LIB_PATH)
+                or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src)):
+            build()
+        L = ctypes.CDLL(_LIB_PATH)
+        dp = ctypes.POINTER(ctypes.c_double)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        ci, cd = ctypes.c_int, ctypes.c_double
+        sig = {
+            "orc_equilibrium": (None, [cd, cd, cd, dp]),
+            "orc_init_equilibrium": (None, [ci, ci, dp, dp, dp, dp]),
+            "orc_stream": (None, [ci, ci, dp, dp]),
+            "orc_collide": (None, [ci, ci, cd, dp, dp]),
+            "orc_step": (None, [ci, ci, cd, dp, dp]),
+            "orc_moments": (None, [ci, ci, dp, dp, dp, dp]),
+            "orc_cell_sensors": (ci, [dp, cd, dp]),
+            "orc_cell_log_sensors_literal": (None, [dp, cd, dp, dp]),
+            "orc_alpha_poly": (cd, [dp, dp]),
+            "orc_alpha_exact": (cd, [dp]),
+            "orc_sensor_fields": (None, [ci, ci, cd, dp, ci, dp, u8p]),
+            "orc_flags": (None, [ci, ci, dp, cd, dp, cd, u8p, ci, u8p, i32p, i64p]),
+            "orc_sums": (None, [ci, ci, dp, dp]),
+            "orc_mac_sensors": (None, [ci, ci, cd, dp, dp, dp, dp]),
+            "orc_run": (ctypes.c_int64, [ci, ci, cd, dp, dp, ci, ci, cd, ci, cd, ci,
+                                          dp, u8p, i32p, i64p, dp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray, ct=ctypes.c_double):
+    assert a.flags["C_CONTIGUOUS"], "oracle arrays must be C-contiguous"
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def equilibrium(rho: float, ux: float, uy: float) -> np.ndarray:
+    out = np.empty(9)
+    lib().orc_equilibrium(rho, ux, uy, _p(out))
+    return out
+
+
+def init_equilibrium(rho, ux, uy) -> np.ndarray:
+    rho, ux, uy = _f64(rho), _f64(ux), _f64(uy)
+    ny, nx = rho.shape
+    f = np.empty((9, ny, nx))
+    lib().orc_init_equilibrium(nx, ny, _p(rho), _p(ux), _p(uy), _p(f))
+    return f
+
+
+def stream(f) -> np.ndarray:
+    f = _f64(f)
+    out = np.empty_like(f)
+    lib().orc_stream(f.shape[2], f.shape[1], _p(f), _p(out))
+    return out
+
+
+def collide(ft, tau: float) -> np.ndarray:
+    ft = _f64(ft)
+    out = np.empty_like(ft)
+    lib().orc_collide(ft.shape[2], ft.shape[1], tau, _p(ft), _p(out))
+    return out
+
+
+def step(f, tau: float, nsteps: int = 1) -> np.ndarray:
+    f = _f64(f).copy()
+    g = np.empty_like(f)
+    for _ in range(nsteps):
+        lib().orc_step(f.shape[2], f.shape[1], tau, _p(f), _p(g))
+        f, g = g, f
+    return f
+
+
+def moments(f):
+    f = _f64(f)
+    ny, nx = f.shape[1:]
+    rho, ux, uy = np.empty((ny, nx)), np.empty((ny, nx)), np.empty((ny, nx))
+    lib().orc_moments(nx, ny, _p(f), _p(rho), _p(ux), _p(uy))
+    return rho, ux, uy
+
+
+def cell_sensors(ft, tau: float):
+    ft = _f64(ft)
+    out = np.empty(NSENS)
+    nonpos = lib().orc_cell_sensors(_p(ft), tau, _p(out))
+    return out, bool(nonpos)
+
+
+def cell_log_sensors_literal(ft, tau: float):
+    ft = _f64(ft)
+    out, scale = np.empty(4), np.empty(4)
+    lib().orc_cell_log_sensors_literal(_p(ft), tau, _p(out), _p(scale))
+    return out, scale
+
+
+def alpha_poly(ft):
+    ft = _f64(ft)
+    a = np.empty(4)
+    alpha = lib().orc_alpha_poly(_p(ft), _p(a))
+    return alpha, a
+
+
+def alpha_exact(ft) -> float:
+    return lib().orc_alpha_exact(_p(_f64(ft)))
+
+
+def sensor_fields(f, tau: float, pull: bool = True):
+    """All sensors of the state (streamed first when pull=True): ([13, ny, nx], nonpos)."""
+    f = _f64(f)
+    ny, nx = f.shape[1:]
+    out = np.empty((NSENS, ny, nx))
+    nonpos = np.empty((ny, nx), dtype=np.uint8)
+    lib().orc_sensor_fields(nx, ny, tau, _p(f), int(pull), _p(out),
+                            _p(nonpos, ctypes.c_uint8))
+    return out, nonpos
+
+
+def flags(eps_r, thr_r: float, eps_s, thr_s: float, nonpos, tile: int):
+    eps_r, eps_s = _f64(eps_r), _f64(eps_s)
+    nonpos = np.ascontiguousarray(nonpos, dtype=np.uint8)
+    ny, nx = eps_r.shape
+    ntx, nty = -(-nx // tile), -(-ny // tile)
+    fl = np.empty((ny, nx), dtype=np.uint8)
+    tiles = np.empty((2, nty, ntx), dtype=np.int32)
+    counts = np.empty(3, dtype=np.int64)
+    lib().orc_flags(nx, ny, _p(eps_r), thr_r, _p(eps_s), thr_s,
+                    _p(nonpos, ctypes.c_uint8), tile, _p(fl, ctypes.c_uint8),
+                    _p(tiles, ctypes.c_int32), _p(counts, ctypes.c_int64))
+    return fl, tiles, counts
+
+
+def sums(f) -> np.ndarray:
+    f = _f64(f)
+    out = np.empty(3)
+    lib().orc_sums(f.shape[2], f.shape[1], _p(f), _p(out))
+    return out
+
+
+def mac_sensors(rho, ux, uy, tau: float) -> np.ndarray:
+    rho, ux, uy = _f64(rho), _f64(ux), _f64(uy)
+    ny, nx = rho.shape
+    out = np.empty((4, ny, nx))
+    lib().orc_mac_sensors(nx, ny, tau, _p(rho), _p(ux), _p(uy), _p(out))
+    return out
+
+
+def run(f, tau: float, nsteps: int, sensor_r: int, thr_r: float, sensor_s: int,
+        thr_s: float, tile: int = 16):
+    """nsteps fused reference steps in place on a copy of f; returns a dict."""
+    f = _f64(f).copy()
+    ny, nx = f.shape[1:]
+    work = np.empty_like(f)
+    rec = np.empty((ny, nx))
+    fl = np.empty((ny, nx), dtype=np.uint8)
+    ntx, nty = -(-nx // tile), -(-ny // tile)
+    tiles = np.empty((2, nty, ntx), dtype=np.int32)
+    counts = np.empty(3, dtype=np.int64)
+    sm = np.empty(3)
+    lib().orc_run(nx, ny, tau, _p(f), _p(work), nsteps, sensor_r, thr_r, sensor_s,
+                  thr_s, tile, _p(rec), _p(fl, ctypes.c_uint8),
+                  _p(tiles, ctypes.c_int32), _p(counts, ctypes.c_int64), _p(sm))
+    return {"f": f, "eps_r": rec, "flags": fl, "tiles": tiles, "counts": counts,
+            "sums": sm}

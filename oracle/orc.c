@@ -1,0 +1,476 @@
+/*
+ * orc.c -- plain FP64 CPU oracle (see orc.h).  TEST INFRASTRUCTURE ONLY.
+ *
+ * Everything here is a direct transcription of a definition of the paper
+ * (arXiv 2603.13618), cell by cell, in scalar double precision, with no
+ * blocking, fusion or vectorisation.  Each function names the passage it
+ * follows.  Readings where the paper is silent (D2Q9 lattice, the mu/lambda
+ * of the class-1 sensors, the non-positive convention, the cancellation-free
+ * form of the logarithmic sensors) are stated at the point of use.
+ */
+#include "orc.h"
+
+#include <math.h>
+#include <stddef.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* D2Q9 velocity set and Gauss-Hermite weights (section "Discrete kinetic
+ * model": discrete velocities v_i with weights w_i). */
+static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                            1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+/* Reference temperature of the lattice, R T_ref = c_s^2 = 1/3. */
+static const double CS2 = 1.0 / 3.0;
+
+static size_t at(int nx, int ny, int q, int i, int j) {
+  return ((size_t)q * (size_t)ny + (size_t)j) * (size_t)nx + (size_t)i;
+}
+
+static int wrap(int a, int n) {
+  int r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+/* Grad-Hermite equilibrium to order N = 2: f^eq_i = w_i sum_n
+ * a_n : H_n(v_i) / (n! (R T_ref)^n) with a_0 = rho, a_1 = rho u,
+ * a_2 = rho u u (isothermal, T = T_ref) and H_0 = 1, H_1 = v,
+ * H_2 = v v - R T_ref I. */
+void orc_equilibrium(double rho, double ux, double uy, double feq[9]) {
+  const double a1[2] = {rho * ux, rho * uy};
+  const double a2[2][2] = {{rho * ux * ux, rho * ux * uy}, {rho * uy * ux, rho * uy * uy}};
+  for (int q = 0; q < 9; ++q) {
+    const double v[2] = {(double)CX[q], (double)CY[q]};
+    double h1 = 0.0;
+    for (int a = 0; a < 2; ++a) h1 += a1[a] * v[a];
+    double h2 = 0.0;
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) h2 += a2[a][b] * (v[a] * v[b] - (a == b ? CS2 : 0.0));
+    feq[q] = W[q] * (rho + h1 / CS2 + h2 / (2.0 * CS2 * CS2));
+  }
+}
+
+void orc_init_equilibrium(int nx, int ny, const double* rho, const double* ux,
+                          const double* uy, double* f) {
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const size_t c = (size_t)j * nx + i;
+      double feq[9];
+      orc_equilibrium(rho[c], ux[c], uy[c], feq);
+      for (int q = 0; q < 9; ++q) f[at(nx, ny, q, i, j)] = feq[q];
+    }
+}
+
+/* Streaming term v_i . grad f_i of the discrete kinetic equations, in its
+ * lattice form with dt = dx = 1: pull every population from the neighbour
+ * it comes from, periodic in both directions. */
+void orc_stream(int nx, int ny, const double* f, double* ft) {
+  for (int q = 0; q < 9; ++q)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i)
+        ft[at(nx, ny, q, i, j)] = f[at(nx, ny, q, wrap(i - CX[q], nx), wrap(j - CY[q], ny))];
+}
+
+/* Moments as quadratures, Eqs. eq_quadratur1-2. */
+static void cell_moments(const double ft[9], double* rho, double* ux, double* uy) {
+  double r = 0.0, jx = 0.0, jy = 0.0;
+  for (int q = 0; q < 9; ++q) {
+    r += ft[q];
+    jx += CX[q] * ft[q];
+    jy += CY[q] * ft[q];
+  }
+  *rho = r;
+  *ux = jx / r;
+  *uy = jy / r;
+}
+
+/* Eq. new_collision_fi with tau1 = tau2 = tau (f* = f^eq): the discrete
+ * collision operator Omega_i = -(f_i - f^eq_i)/tau, added with dt = 1. */
+void orc_collide(int nx, int ny, double tau, const double* ft, double* fnext) {
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      double c[9], feq[9], rho, ux, uy;
+      for (int q = 0; q < 9; ++q) c[q] = ft[at(nx, ny, q, i, j)];
+      cell_moments(c, &rho, &ux, &uy);
+      orc_equilibrium(rho, ux, uy, feq);
+      for (int q = 0; q < 9; ++q) {
+        const double omega = -(c[q] - feq[q]) / tau;
+        fnext[at(nx, ny, q, i, j)] = c[q] + omega;
+      }
+    }
+}
+
+void orc_step(int nx, int ny, double tau, const double* f, double* fnext) {
+  double* ft = (double*)malloc(sizeof(double) * 9 * (size_t)nx * ny);
+  orc_stream(nx, ny, f, ft);
+  orc_collide(nx, ny, tau, ft, fnext);
+  free(ft);
+}
+
+void orc_moments(int nx, int ny, const double* f, double* rho, double* ux, double* uy) {
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      double c[9];
+      for (int q = 0; q < 9; ++q) c[q] = f[at(nx, ny, q, i, j)];
+      const size_t k = (size_t)j * nx + i;
+      cell_moments(c, &rho[k], &ux[k], &uy[k]);
+    }
+}
+
+/* phi(x) = (1 + x) ln(1 + x) - x.  For |x| < 1/16 its Maclaurin series
+ * sum_{n>=2} (-1)^n x^n / (n (n - 1)) (from the series of ln(1 + x)),
+ * summed to n = 18; otherwise the closed form with log1p. */
+static double phi(double x) {
+  if (fabs(x) < 0.0625) {
+    double s = 0.0, p = x * x;
+    for (int n = 2; n <= 18; ++n) {
+      s += ((n % 2 == 0) ? 1.0 : -1.0) * p / (double)(n * (n - 1));
+      p *= x;
+    }
+    return s;
+  }
+  return (1.0 + x) * log1p(x) - x;
+}
+
+static double frob2(double a, double b, double c, double d) {
+  return sqrt(a * a + b * b + c * c + d * d);
+}
+
+/* Entropic estimate, Eqs. alpha-polynomial-1/-2, read literally: f^neq =
+ * f - f^eq (as defined at the start of section "Refinement sensors") and the
+ * current populations f in the denominators.  a_1 = 0 (equilibrium) gives
+ * alpha := 2. */
+double orc_alpha_poly(const double ft[9], double a[4]) {
+  double rho, ux, uy, feq[9];
+  cell_moments(ft, &rho, &ux, &uy);
+  orc_equilibrium(rho, ux, uy, feq);
+  for (int n = 1; n <= 4; ++n) {
+    double s = 0.0;
+    for (int q = 0; q < 9; ++q) {
+      const double fneq = ft[q] - feq[q];
+      s += pow(fneq, n + 1) / pow(ft[q], n);
+    }
+    const double sign = (n % 2 == 1) ? 1.0 : -1.0; /* (-1)^(n-1) */
+    a[n - 1] = sign * s / (double)(n * (n + 1));
+  }
+  const double a1 = a[0], a2 = a[1], a3 = a[2], a4 = a[3];
+  if (a1 == 0.0) return 2.0;
+  return 2.0 - 4.0 * a2 / a1 + 16.0 * a2 * a2 / (a1 * a1) - 8.0 * a3 / a1 +
+         80.0 * a2 * a3 / (a1 * a1) - 80.0 * a2 * a2 * a2 / (a1 * a1 * a1) - 16.0 * a4 / a1;
+}
+
+/* g(alpha) = H(f + alpha (f^eq - f)) - H(f) with H of Eq.
+ * H-function-discrete, written without cancellation: with D = f^eq - f,
+ * y = D/f, and sum D = 0, g = alpha sum D ln(f/(w rho)) + sum f phi(alpha y). */
+static double mirror_gap(const double ft[9], const double feq[9], double rho, double alpha) {
+  double g = 0.0;
+  for (int q = 0; q < 9; ++q) {
+    const double d = feq[q] - ft[q];
+    g += alpha * d * log(ft[q] / (W[q] * rho)) + ft[q] * phi(alpha * d / ft[q]);
+  }
+  return g;
+}
+
+/* Positive root of Eq. H-mirr-equal by bisection (diagnostic only). */
+double orc_alpha_exact(const double ft[9]) {
+  double rho, ux, uy, feq[9];
+  cell_moments(ft, &rho, &ux, &uy);
+  orc_equilibrium(rho, ux, uy, feq);
+  double amax = INFINITY;
+  int moved = 0;
+  for (int q = 0; q < 9; ++q) {
+    if (ft[q] <= 0.0 || feq[q] <= 0.0) return NAN;
+    const double d = feq[q] - ft[q];
+    if (d != 0.0) moved = 1;
+    if (d < 0.0) {
+      const double lim = ft[q] / (-d);
+      if (lim < amax) amax = lim;
+    }
+  }
+  if (!moved) return 2.0;
+  double lo = 1.0e-3, hi = 2.0;
+  if (mirror_gap(ft, feq, rho, lo) >= 0.0) return NAN;
+  while (mirror_gap(ft, feq, rho, hi) < 0.0) {
+    if (hi >= 0.999999 * amax || hi > 1.0e6) return NAN;
+    hi = fmin(2.0 * hi, 0.5 * (hi + amax));
+  }
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid == lo || mid == hi) break;
+    if (mirror_gap(ft, feq, rho, mid) < 0.0)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+/* All sensors of Table 1 for a single distribution (the g-terms dropped,
+ * section "Overview and further considerations": the sensors apply to a
+ * single distribution function), on the pre-collision populations ft.
+ *
+ * Class-1 reading for the isothermal D2Q9 BGK model: its first-order stress
+ * is P^neq = -rho c_s^2 tau (grad u + grad u^T) with no separate bulk part,
+ * i.e. in the notation of Eq. tauNS-1: mu = rho c_s^2 tau, lambda = 0 and
+ * eta = 2 mu / D + lambda = mu.
+ *
+ * Logarithmic sensors: f ln(f/f^eq) = f^eq phi(x) + f^neq with x = f^neq/f^eq,
+ * and sum f^neq = 0 exactly (rho of f and of f^eq coincide, Eq.
+ * eq_quadratur1), so the sums are evaluated term-by-term without the O(1)
+ * cancellation of the printed form:
+ *   KL       = |sum f^eq phi(x)|
+ *   HR       = |sum f^neq L + sum f^eq phi(x)|,     L = ln(f^eq/(w rho))
+ *   sigma_H  = (1/tau) (sum f^neq L + sum f^neq ln(1 + x))
+ *   sigma_KL = (1/tau) sum f^neq ln(1 + x)
+ * (the constant ln(rho) parts multiply sum f^neq = 0).  The printed forms
+ * are kept in orc_cell_log_sensors_literal and checked against these.
+ *
+ * Non-positive populations (section "Overview and further considerations":
+ * positivity is not guaranteed by Grad-Hermite equilibria): if any ft_q <= 0
+ * or f^eq_q <= 0, Kn and the five entropy-based sensors are +Inf.        */
+int orc_cell_sensors(const double ft[9], double tau, double out[ORC_NSENS]) {
+  double rho, ux, uy, feq[9], fneq[9];
+  cell_moments(ft, &rho, &ux, &uy);
+  orc_equilibrium(rho, ux, uy, feq);
+  int nonpos = 0;
+  for (int q = 0; q < 9; ++q) {
+    fneq[q] = ft[q] - feq[q];
+    if (ft[q] <= 0.0 || feq[q] <= 0.0) nonpos = 1;
+  }
+
+  /* Non-equilibrium pressure tensor P^neq = sum v v f^neq. */
+  double P[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int q = 0; q < 9; ++q) {
+    const double v[2] = {(double)CX[q], (double)CY[q]};
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) P[a][b] += v[a] * v[b] * fneq[q];
+  }
+  const double D = 2.0;
+  const double mu = rho * CS2 * tau;
+  const double lambda = 0.0;
+  const double eta = 2.0 * mu / D + lambda;
+  const double trP = P[0][0] + P[1][1];
+
+  out[ORC_TAU_NS] = frob2(P[0][0], P[0][1], P[1][0], P[1][1]);
+  out[ORC_C] = sqrt(D) * fabs(-trP / (2.0 * mu + D * lambda));
+  {
+    double M[2][2];
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) M[a][b] = ((a == b ? trP / D : 0.0) - P[a][b]) / mu;
+    out[ORC_S] = frob2(M[0][0], M[0][1], M[1][0], M[1][1]);
+  }
+  {
+    double M[2][2];
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        M[a][b] = ((a == b ? lambda / (D * eta) * trP : 0.0) - P[a][b]) / (2.0 * mu);
+    out[ORC_E] = frob2(M[0][0], M[0][1], M[1][0], M[1][1]);
+  }
+  {
+    /* (sum v f / sum f) . P^neq */
+    double jx = 0.0, jy = 0.0, r = 0.0;
+    for (int q = 0; q < 9; ++q) {
+      r += ft[q];
+      jx += CX[q] * ft[q];
+      jy += CY[q] * ft[q];
+    }
+    const double u[2] = {jx / r, jy / r};
+    double qh[2] = {0.0, 0.0};
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) qh[b] += u[a] * P[a][b];
+    out[ORC_QH] = sqrt(qh[0] * qh[0] + qh[1] * qh[1]);
+  }
+  {
+    double kn = 0.0, neq = 0.0, qe = 0.0;
+    for (int q = 0; q < 9; ++q) {
+      kn += fabs(fneq[q] / feq[q]);
+      neq += fabs(fneq[q]);
+      const double fstar = feq[q]; /* BGK: the quasi-equilibrium is the equilibrium */
+      qe += fabs(fstar - feq[q]);
+    }
+    out[ORC_KN] = kn;
+    out[ORC_NEQ] = neq;
+    out[ORC_QE] = qe;
+  }
+  {
+    double kl = 0.0, lin = 0.0, sig = 0.0;
+    for (int q = 0; q < 9; ++q) {
+      const double x = fneq[q] / feq[q];
+      const double L = log(feq[q] / (W[q] * rho));
+      kl += feq[q] * phi(x);
+      lin += fneq[q] * L;
+      sig += fneq[q] * log1p(x);
+    }
+    out[ORC_KL] = fabs(kl);
+    out[ORC_HR] = fabs(lin + kl);
+    out[ORC_SIGMA_H] = (lin + sig) / tau;
+    out[ORC_SIGMA_KL] = sig / tau;
+  }
+  {
+    double a[4];
+    out[ORC_ALPHA] = fabs(2.0 - orc_alpha_poly(ft, a));
+  }
+  if (nonpos) {
+    out[ORC_KN] = INFINITY;
+    out[ORC_HR] = INFINITY;
+    out[ORC_KL] = INFINITY;
+    out[ORC_SIGMA_H] = INFINITY;
+    out[ORC_SIGMA_KL] = INFINITY;
+    out[ORC_ALPHA] = INFINITY;
+  }
+  return nonpos;
+}
+
+/* Printed forms: Eq. Hneq-sensor, Eq. HKL-sensor, Eq. Dissip-H-sensor and
+ * Eq. Dissip-HKL-sensor, with Omega_i = -(f_i - f^eq_i)/tau. */
+void orc_cell_log_sensors_literal(const double ft[9], double tau, double out[4],
+                                  double scale[4]) {
+  double rho, ux, uy, feq[9];
+  cell_moments(ft, &rho, &ux, &uy);
+  orc_equilibrium(rho, ux, uy, feq);
+  double hf = 0.0, hfeq = 0.0, kl = 0.0, sh = 0.0, skl = 0.0;
+  double s_hr = 0.0, s_kl = 0.0, s_sh = 0.0, s_skl = 0.0;
+  for (int q = 0; q < 9; ++q) {
+    const double omega = -(ft[q] - feq[q]) / tau;
+    const double t1 = ft[q] * log(ft[q] / W[q]);
+    const double t2 = feq[q] * log(feq[q] / W[q]);
+    const double t3 = ft[q] * log(ft[q] / feq[q]);
+    const double t4 = omega * log(ft[q] / W[q]);
+    const double t5 = omega * log(ft[q] / feq[q]);
+    hf += t1;
+    hfeq += t2;
+    kl += t3;
+    sh += t4;
+    skl += t5;
+    /* rounding scale: |term| plus |prefactor| (the log's argument is rounded
+     * to one ulp, i.e. the log is off by ~eps absolute); for sigma_H also
+     * the rounding of Omega (~eps f / tau) times |ln(f/w)| */
+    s_hr += fabs(t1) + fabs(t2) + ft[q] + feq[q];
+    s_kl += fabs(t3) + ft[q];
+    s_sh += fabs(t4) + fabs(omega) + ft[q] / tau * fabs(log(ft[q] / W[q]));
+    s_skl += fabs(t5) + fabs(omega);
+  }
+  out[0] = fabs(hf - hfeq);
+  out[1] = fabs(kl);
+  out[2] = -sh;
+  out[3] = -skl;
+  scale[0] = s_hr;
+  scale[1] = s_kl;
+  scale[2] = s_sh;
+  scale[3] = s_skl;
+}
+
+void orc_sensor_fields(int nx, int ny, double tau, const double* f, int pull, double* out,
+                       uint8_t* nonpos) {
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      double c[9], s[ORC_NSENS];
+      for (int q = 0; q < 9; ++q) {
+        const int si = pull ? wrap(i - CX[q], nx) : i;
+        const int sj = pull ? wrap(j - CY[q], ny) : j;
+        c[q] = f[at(nx, ny, q, si, sj)];
+      }
+      const int np = orc_cell_sensors(c, tau, s);
+      for (int k = 0; k < ORC_NSENS; ++k) out[at(nx, ny, k, i, j)] = s[k];
+      if (nonpos) nonpos[(size_t)j * nx + i] = (uint8_t)np;
+    }
+}
+
+/* Regrid step (1) of the SAMR cycle: tag cells whose sensor exceeds its
+ * threshold (strict comparison); the AAR switch is a second criterion. */
+void orc_flags(int nx, int ny, const double* eps_r, double thr_r, const double* eps_s,
+               double thr_s, const uint8_t* nonpos, int tile, uint8_t* flags,
+               int32_t* tiles, int64_t counts[3]) {
+  const int ntx = (nx + tile - 1) / tile, nty = (ny + tile - 1) / tile;
+  for (int k = 0; k < 2 * ntx * nty; ++k) tiles[k] = 0;
+  counts[0] = counts[1] = counts[2] = 0;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const size_t c = (size_t)j * nx + i;
+      const int r = eps_r[c] > thr_r;
+      const int s = (thr_s >= 0.0) && (eps_s[c] > thr_s);
+      const int p = nonpos ? nonpos[c] != 0 : 0;
+      flags[c] = (uint8_t)(r | (s << 1) | (p << 7));
+      const int t = (j / tile) * ntx + (i / tile);
+      tiles[t] += r;
+      tiles[ntx * nty + t] += s;
+      counts[0] += r;
+      counts[1] += s;
+      counts[2] += p;
+    }
+}
+
+/* Neumaier-compensated running sum, so the lattice totals are accurate to a
+ * few ulps of the result whatever the lattice size (a naive running sum of
+ * 9 nx ny terms drifts by ~sqrt(n) ulps of the total). */
+static void kahan_add(double* s, double* c, double v) {
+  const double t = *s + v;
+  if (fabs(*s) >= fabs(v))
+    *c += (*s - t) + v;
+  else
+    *c += (v - t) + *s;
+  *s = t;
+}
+
+void orc_sums(int nx, int ny, const double* f, double sums[3]) {
+  double s[3] = {0.0, 0.0, 0.0}, c[3] = {0.0, 0.0, 0.0};
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i)
+      for (int q = 0; q < 9; ++q) {
+        const double v = f[at(nx, ny, q, i, j)];
+        kahan_add(&s[0], &c[0], v);
+        kahan_add(&s[1], &c[1], CX[q] * v);
+        kahan_add(&s[2], &c[2], CY[q] * v);
+      }
+  for (int k = 0; k < 3; ++k) sums[k] = s[k] + c[k];
+}
+
+void orc_mac_sensors(int nx, int ny, double tau, const double* rho, const double* ux,
+                     const double* uy, double* out) {
+  const size_t n = (size_t)nx * ny;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const size_t c = (size_t)j * nx + i;
+      const size_t ip = (size_t)j * nx + wrap(i + 1, nx), im = (size_t)j * nx + wrap(i - 1, nx);
+      const size_t jp = (size_t)wrap(j + 1, ny) * nx + i, jm = (size_t)wrap(j - 1, ny) * nx + i;
+      /* G[a][b] = d_a u_b */
+      const double G[2][2] = {{0.5 * (ux[ip] - ux[im]), 0.5 * (uy[ip] - uy[im])},
+                              {0.5 * (ux[jp] - ux[jm]), 0.5 * (uy[jp] - uy[jm])}};
+      const double div = G[0][0] + G[1][1];
+      const double mu = rho[c] * CS2 * tau;
+      double sym[2][2];
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) sym[a][b] = G[a][b] + G[b][a];
+      out[c] = mu * frob2(sym[0][0], sym[0][1], sym[1][0], sym[1][1]);
+      out[n + c] = sqrt(2.0) * fabs(div);
+      out[2 * n + c] = frob2(sym[0][0] - div, sym[0][1], sym[1][0], sym[1][1] - div);
+      out[3 * n + c] = 0.5 * frob2(sym[0][0], sym[0][1], sym[1][0], sym[1][1]);
+    }
+}
+
+int64_t orc_run(int nx, int ny, double tau, double* f, double* work, int nsteps,
+                int sensor_r, double thr_r, int sensor_s, double thr_s, int tile,
+                double* rec_field, uint8_t* flags, int32_t* tiles, int64_t counts[3],
+                double sums[3]) {
+  const size_t n = (size_t)nx * ny;
+  double* eps_s = (double*)malloc(sizeof(double) * n);
+  uint8_t* np = (uint8_t*)malloc(n);
+  for (int step = 0; step < nsteps; ++step) {
+    orc_stream(nx, ny, f, work);
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        double c[9], s[ORC_NSENS];
+        for (int q = 0; q < 9; ++q) c[q] = work[at(nx, ny, q, i, j)];
+        np[(size_t)j * nx + i] = (uint8_t)orc_cell_sensors(c, tau, s);
+        rec_field[(size_t)j * nx + i] = s[sensor_r];
+        eps_s[(size_t)j * nx + i] = s[sensor_s];
+      }
+    orc_flags(nx, ny, rec_field, thr_r, eps_s, thr_s, np, tile, flags, tiles, counts);
+    orc_sums(nx, ny, work, sums);
+    orc_collide(nx, ny, tau, work, f);
+  }
+  free(eps_s);
+  free(np);
+  return counts[2];
+}
