@@ -308,8 +308,17 @@ int orc_cell_sensors(const double ft[9], double tau, double out[ORC_NSENS]) {
     out[ORC_SIGMA_KL] = sig / tau;
   }
   {
+    /* |2 - alpha| of Eq. sensor-alpha-kin with alpha of Eq. alpha-polynomial-1;
+     * the constant 2 cancels exactly, so the correction terms are summed directly */
     double a[4];
-    out[ORC_ALPHA] = fabs(2.0 - orc_alpha_poly(ft, a));
+    orc_alpha_poly(ft, a);
+    double e = 0.0;
+    if (a[0] != 0.0) {
+      const double a1 = a[0], a2 = a[1], a3 = a[2], a4 = a[3];
+      e = 4.0 * a2 / a1 - 16.0 * a2 * a2 / (a1 * a1) + 8.0 * a3 / a1 -
+          80.0 * a2 * a3 / (a1 * a1) + 80.0 * a2 * a2 * a2 / (a1 * a1 * a1) + 16.0 * a4 / a1;
+    }
+    out[ORC_ALPHA] = fabs(e);
   }
   if (nonpos) {
     out[ORC_KN] = INFINITY;
