@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark of the fused D2Q9 stream + collide + sensor step (MLUPS and HBM roofline).
+
+Workload: 4096 x 4096 periodic D2Q9 lattice in FP32, tau = 0.6, seeded smooth density /
+velocity perturbations (max |drho| = 1e-2, max |u| = 0.1 c_s) on a density step
+rho_L / rho_R = 2 at x = 2048; every step is an output step: Knudsen sensor tagged
+against 1e-3 (refine flag), non-equilibrium sensor against 1e-4 (switch flag), the
+Kullback-Leibler sensor field stored, per-tile (16 x 16) tag counts and FP64
+conservation sums.  A step = one fused launch over the whole lattice.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 (launched by torchrun) runs one independent lattice per rank (replicas, weak
+scaling); rank 0 prints one JSON line.  --impl reference times the CPU oracle on the
+host cores on a bounded window of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX = NY = 4096
+TAU = 0.6
+THR_R, THR_S = 1e-3, 1e-4
+TILE = 16
+# algorithmic bytes per lattice update of the fused FP32 output step:
+# 9 population loads + 9 stores (4 B each) + the KL sensor value (4 B) + the flag byte
+BYTES_PER_LUP = 9 * 4 + 9 * 4 + 4 + 1
+METRIC = "MLUPS with sensors fused and % of HBM roofline, 1xGB300"
+WORKLOAD = ("D2Q9 FP32 4096x4096 periodic, tau=0.6, smooth perturbations (amp 1e-2, "
+            "Mach<=0.1) + density step 2:1 at x=2048; fused stream+collide+sensors "
+            "(Kn refine 1e-3, neq switch 1e-4, KL field) + flags + tile counts + sums "
+            "every step")
+KERNEL_SOURCES = ("paper_2603_13618_gb300/csrc/d2q9.cuh",
+                  "paper_2603_13618_gb300/csrc/step_kernel.cuh")
+PROFILE = os.path.join(ROOT, "profiles", "step_std_f32_4096.md")
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic():
+    """DRAM bytes per launch of the fused step from the committed ncu summary, or None
+    if the summary is missing or was taken on different kernel sources."""
+    try:
+        txt = open(PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]{16})", txt)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != kernel_hash():
+        return None
+    return float(t.group(1))
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during timing."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k] == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def workload_fields(nx=NX, ny=NY, x0=0, y0=0, wx=None, wy=None):
+    from paper_2603_13618_gb300 import inputs
+
+    return inputs.smooth_jump(NX, NY, seed=2603, kmax=8, x0=x0, y0=y0, wx=wx, wy=wy)
+
+
+def cpu_baseline(seconds: float = 10.0, window: int = 1024):
+    """The oracle as it stands (single thread) on a window of the workload."""
+    import oracle
+
+    rho, ux, uy = workload_fields(x0=NX // 2 - window // 2, y0=NY // 2 - window // 2,
+                                  wx=window, wy=window)
+    f = oracle.init_equilibrium(rho, ux, uy)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.run(f, TAU, 1, oracle.SENSOR_ID["kn"], THR_R, oracle.SENSOR_ID["neq"], THR_S, TILE)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": window * window * steps / el / 1e6, "unit": "MLUPS", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{steps} fused oracle step(s) (all 13 sensors, flags, tile counts, "
+                      f"sums) on the central {window}x{window} window of the workload, "
+                      f"{el:.1f} s, 1 thread"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    window = 128
+    rho, ux, uy = workload_fields(x0=NX // 2 - window // 2, y0=NY // 2 - window // 2,
+                                  wx=window, wy=window)
+    f = oracle.init_equilibrium(rho, ux, uy)
+    for _ in range(args.warmup):
+        oracle.run(f, TAU, 1, 5, THR_R, 6, THR_S, TILE)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run(f, TAU, 1, 5, THR_R, 6, THR_S, TILE)
+    el = time.perf_counter() - t0
+    value = window * window * args.steps / el / 1e6
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY,
+                   "sample": f"{window}x{window} central window per step"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: one fused oracle step on the central "
+                                   f"{window}x{window} window, 1 thread"},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2603_13618_gb300 import kss
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    rho, ux, uy = workload_fields()
+    lat = kss.Lattice(NX, NY, precision="fp32", tau=TAU, refine_sensor="kn",
+                      refine_threshold=THR_R, switch_sensor="neq", switch_threshold=THR_S,
+                      record=("kl",), output_every=1, tile=TILE, stream="torch")
+    lat.set_fields(rho, ux, uy)
+    stream = torch.cuda.current_stream()
+    lat.step(args.warmup)
+    barrier()
+
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    with ClockSampler(local) as clk:
+        barrier()
+        t_host = time.perf_counter()
+        for k in range(K):
+            starts[k].record(stream)
+            lat.step(1)
+            ends[k].record(stream)
+        barrier()
+        t_host = time.perf_counter() - t_host
+    clocks = clk.summary()
+    per_launch = [s.elapsed_time(e) for s, e in zip(starts, ends)]  # ms
+    total_ms = starts[0].elapsed_time(ends[-1])
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    cells = NX * NY
+    value = world * cells * K / (total_ms * 1e-3) / 1e6
+    kern_ms = sum(per_launch) / K
+    achieved = BYTES_PER_LUP * cells / (kern_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+    sums, counts, step = lat.read_stats()
+
+    # end to end through the C ABI with host buffers: each step copies its input fields
+    # from pinned host memory, runs one fused step and reads the flags, tile counts and
+    # stats back to pinned host memory
+    e2e = None
+    if rank == 0 or world > 1:
+        pin = [torch.from_numpy(a).pin_memory() for a in (rho, ux, uy)]
+        fl = torch.empty((NY, NX), dtype=torch.uint8).pin_memory()
+        tl = torch.empty((2, lat.nty, lat.ntx), dtype=torch.int32).pin_memory()
+        ke = max(3, min(20, K // 10))
+        for _ in range(2):
+            lat.set_fields(*pin)
+            lat.step(1)
+            lat.read_flags(out=(fl, tl))
+            lat.read_stats()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            lat.set_fields(*pin)
+            lat.step(1)
+            lat.read_flags(out=(fl, tl))
+            lat.read_stats()
+        barrier()
+        el = time.perf_counter() - t0
+        h2d = 3 * 8 * cells
+        d2h = cells + 4 * 2 * lat.nty * lat.ntx + 8 * 3 + 8 * 3 + 8 * 3
+        e2e = {"value": world * cells * ke / el / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "steps": ke, "calls_per_step": ["kss_set_fields(host)", "kss_step(1)",
+                                               "kss_read_flags(host)", "kss_read_stats"]}
+
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": total_ms / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "tau": TAU,
+                       "precision": "fp32", "tile": TILE, "output_every": 1,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2: 1.21 GB of populations per step "
+                             "vs 126 MB L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": profile_traffic(),
+                         "algorithmic_bytes_per_launch": BYTES_PER_LUP * cells,
+                         "kernel_ms": kern_ms,
+                         "kernel": "step_kernel<float, MODE_STD, pull, store>"},
+            "cpu_baseline": base,
+            "e2e": e2e,
+            "gpu_launches": K,
+            "clocks": clocks,
+            "host_s": t_host,
+            "check": {"sum_rho": sums[0], "refine": int(counts[0]), "switch": int(counts[1]),
+                      "nonpos": int(counts[2]), "step": step},
+        }
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", type=int, default=4096,
+                    help="lattice edge (profiling captures of a smaller case only)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    global NX, NY
+    NX = NY = args.size
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,172 @@
+/*
+ * kss.h -- C ABI of the GB300 (sm_103a) fused D2Q9 stream + collide + local kinetic
+ * sensor library ("kinetic sensor stepping").
+ *
+ * The library advances a periodic D2Q9 lattice-Boltzmann lattice with the BGK
+ * collision and, on output steps, evaluates in the same pass the local kinetic
+ * refinement sensors of arXiv 2603.13618 ("Local kinetic sensors for adaptive mesh
+ * and algorithm refinement", Table 1, single distribution) at every cell, tags the
+ * cells against sensor thresholds (regrid step 1 of the SAMR cycle, and the
+ * adaptive-algorithm-refinement switch of the conclusions), counts the tags per
+ * tile and forms the lattice's conservation sums.
+ *
+ * Conventions (all entry points):
+ *   - Lattice units dx = dt = 1; D2Q9 velocities
+ *       c0=(0,0) c1=(1,0) c2=(0,1) c3=(-1,0) c4=(0,-1)
+ *       c5=(1,1) c6=(-1,1) c7=(-1,-1) c8=(1,-1),  weights 4/9, 1/9 x4, 1/36 x4,
+ *     c_s^2 = 1/3; viscosity nu = c_s^2 (tau - 1/2).
+ *   - Fields are dense row-major arrays of nx*ny doubles, element (i, j) at j*nx + i
+ *     (x = i, y = j).  Populations are dense [9][ny][nx] doubles.  Every array at the
+ *     boundary is FP64 whatever the storage precision; conversion happens on the GPU.
+ *   - on_device = 0: the pointer is host memory (pageable or pinned) owned by the
+ *     caller; the call copies and synchronises before returning.
+ *     on_device = 1: the pointer is CUDA device memory of the current device, owned
+ *     by the caller, which must keep it valid until the lattice's stream has passed
+ *     the call (reads synchronise the stream before returning).
+ *   - Return value: KSS_OK (0) on success, a negative KSS_ERR_* code on error, or the
+ *     positive KSS_WARN_NONPOSITIVE from the calls that evaluate sensors when a cell
+ *     had a non-positive population (its flag bit 7 is set and the count reported).
+ *     A CUDA error is sticky: every later call on that lattice returns
+ *     KSS_ERR_CUDA; kss_last_error() gives the message.
+ *   - The library owns every device buffer of a lattice (two population buffers,
+ *     sensor/flag outputs, per-block scratch); kss_destroy frees them.
+ *   - A lattice is used from one host thread at a time.
+ */
+#ifndef KSS_H
+#define KSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KSS_OK 0
+#define KSS_ERR_ARG (-1)         /* invalid argument (size, pointer, id, threshold)   */
+#define KSS_ERR_OOM (-2)         /* device or host allocation failed                  */
+#define KSS_ERR_CUDA (-3)        /* a CUDA call failed (sticky)                       */
+#define KSS_ERR_TIMEOUT (-4)     /* a bounded device wait ran out                     */
+#define KSS_ERR_STATE (-5)       /* call not valid in the lattice's current state     */
+#define KSS_ERR_UNSUPPORTED (-6) /* precision or option not built into this library  */
+#define KSS_WARN_NONPOSITIVE 1   /* sensors evaluated; some cell had f_q <= 0 or f^eq_q <= 0 */
+
+/* Storage and arithmetic precision of a lattice. */
+typedef enum { KSS_FP64 = 0, KSS_FP32 = 1 } kss_precision;
+
+/* Sensor ids: Table 1 of the paper, f-distribution terms only (the model has no
+ * second distribution g).  mu = rho c_s^2 tau, lambda = 0, eta = mu (the D2Q9 BGK
+ * first-order stress P^neq = -rho c_s^2 tau (grad u + grad u^T)).  All sensors are
+ * evaluated on the post-streaming, pre-collision populations f of the step. */
+typedef enum {
+  KSS_S_TAU_NS = 0,   /* Eq. sensor-TauNS-kin:  |P^neq|_F, P^neq = sum c c f^neq        */
+  KSS_S_C = 1,        /* Eq. sensor-C-kin:      sqrt(2) |tr P^neq| / (2 mu)             */
+  KSS_S_S = 2,        /* Eq. sensor-S-kin:      |(tr P^neq / 2 I - P^neq) / mu|_F       */
+  KSS_S_E = 3,        /* Eq. sensor-E-kin:      |P^neq|_F / (2 mu)   (lambda = 0)       */
+  KSS_S_QH = 4,       /* Eq. sensor-qH-kin:     |u . P^neq|_2                           */
+  KSS_S_KN = 5,       /* Eq. sensor-Knudsen-kin_f: sum |f^neq / f^eq| (not averaged)    */
+  KSS_S_NEQ = 6,      /* Eq. sensor-neq-kin:    sum |f^neq|                             */
+  KSS_S_QE = 7,       /* Eq. Sensor-qe-kin:     sum |f* - f^eq|, identically 0 for BGK  */
+  KSS_S_HR = 8,       /* Eq. Hneq-sensor:       |H(f) - H(f^eq)|, H = sum f ln(f/w)     */
+  KSS_S_KL = 9,       /* Eq. HKL-sensor:        |sum f ln(f / f^eq)|                    */
+  KSS_S_SIGMA_H = 10, /* Eq. Dissip-H-sensor:   -sum Omega ln(f/w), Omega = -f^neq/tau  */
+  KSS_S_SIGMA_KL = 11,/* Eq. Dissip-HKL-sensor: -sum Omega ln(f/f^eq)                   */
+  KSS_S_ALPHA = 12,   /* Eqs. sensor-alpha-kin, alpha-polynomial-1/-2: |2 - alpha|      */
+  KSS_S_COUNT = 13
+} kss_sensor;
+
+/* Non-positive populations (positivity is not guaranteed by Grad-Hermite equilibria,
+ * section "Overview and further considerations"): in a cell with some f_q <= 0 or
+ * f^eq_q <= 0 the sensors KN, HR, KL, SIGMA_H, SIGMA_KL and ALPHA are +Inf, flag
+ * bit 7 is set and the cell is counted. */
+
+/* Flag byte of a cell. */
+#define KSS_FLAG_REFINE 0x01u   /* refine sensor > refine threshold (strict)         */
+#define KSS_FLAG_SWITCH 0x02u   /* switch sensor > switch threshold (strict)         */
+#define KSS_FLAG_NONPOS 0x80u   /* some population or equilibrium population <= 0    */
+
+typedef struct {
+  int32_t nx, ny;            /* lattice size, 1 <= nx, ny, nx*ny <= 2^31 - 1           */
+  int32_t precision;         /* kss_precision                                          */
+  double tau;                /* BGK relaxation time, > 0.5                             */
+  int32_t refine_sensor;     /* kss_sensor tagged against refine_threshold            */
+  double refine_threshold;   /* flag bit 0: eps > threshold                           */
+  int32_t switch_sensor;     /* kss_sensor tagged against switch_threshold            */
+  double switch_threshold;   /* flag bit 1: eps > threshold; < 0 disables the switch  */
+  uint32_t record_mask;      /* bit s set: sensor s's field is stored on output steps */
+  int32_t output_every;      /* steps n with n % output_every == 0 are output steps;  */
+                             /* 0 = no output steps (plain stream + collide)          */
+  int32_t tile;              /* tag-count tile edge: 8, 16, 32 or 64 cells             */
+  void* stream;              /* cudaStream_t to run on; NULL = the CUDA default stream */
+  int32_t own_stream;        /* 1: ignore `stream`, create a non-blocking stream owned */
+                             /*    by the lattice (destroyed with it)                  */
+} kss_config;
+
+typedef struct kss_lattice kss_lattice;  /* opaque */
+
+/* Fill *cfg with defaults for an nx x ny lattice: tau 0.8, refine on KSS_S_KN at 1e-3,
+ * switch on KSS_S_NEQ at 1e-4, record KSS_S_KL, output every step, tile 16, the CUDA
+ * default stream. */
+int kss_config_default(kss_config* cfg, int32_t nx, int32_t ny, int32_t precision);
+
+/* Create a lattice (device buffers allocated; populations zero until set). */
+int kss_create(const kss_config* cfg, kss_lattice** out);
+/* Free a lattice and its device buffers after its stream drains (NULL-safe). */
+void kss_destroy(kss_lattice* lat);
+
+/* Equilibrium initial condition (section "Evaluation of the local kinetic sensors":
+ * initial conditions are supplied as equilibrium populations): f_q := f^eq_q(rho, u)
+ * with the Grad-Hermite N = 2 equilibrium of section "Discrete kinetic model".
+ * rho, ux, uy: nx*ny doubles each.  Resets the step counter to 0. */
+int kss_set_fields(kss_lattice* lat, const double* rho, const double* ux, const double* uy,
+                   int on_device);
+
+/* Raw populations [9][ny][nx] (checkpoint / resume and tests).  Set resets the step
+ * counter to 0; get returns the stored post-collision state f^n. */
+int kss_set_populations(kss_lattice* lat, const double* f, int on_device);
+int kss_get_populations(kss_lattice* lat, double* f, int on_device);
+
+/* Advance nsteps >= 0 steps: pull streaming (periodic) + BGK collision
+ * f' = f - (f - f^eq)/tau (Eq. new_collision_fi with f* = f^eq), fused on output steps
+ * with the sensors, tagging, tile counts and sums.  Asynchronous on the lattice's
+ * stream; errors of the launches are reported here or by the next call. */
+int kss_step(kss_lattice* lat, int32_t nsteps);
+
+/* rho, ux, uy of the stored state (Eqs. eq_quadratur1-2), nx*ny doubles each. */
+int kss_read_moments(kss_lattice* lat, double* rho, double* ux, double* uy, int on_device);
+
+/* Sensor field (nx*ny doubles) of the pre-collision populations of the most recent
+ * step, or of the stored populations if no step was taken since the last set.  A
+ * field recorded on that step is returned as stored; any other is evaluated on
+ * demand from the population buffer the step read. */
+int kss_read_sensor(kss_lattice* lat, int32_t sensor, double* out, int on_device);
+
+/* Tags of the same state as kss_read_sensor: flags (nx*ny bytes, KSS_FLAG_*),
+ * tile_counts (int32 [2][nty][ntx], nty = ceil(ny/tile), ntx = ceil(nx/tile): refine
+ * then switch tags per tile; ragged edge tiles are partial) and counts[3] = {refine,
+ * switch, non-positive}.  Any output pointer may be NULL.  on_device applies to flags
+ * and tile_counts; counts is always host memory. */
+int kss_read_flags(kss_lattice* lat, uint8_t* flags, int32_t* tile_counts, int64_t counts[3],
+                   int on_device);
+
+/* Conservation sums {sum rho, sum rho ux, sum rho uy} (FP64, fixed-order reduction:
+ * bitwise reproducible for a given lattice and configuration) and counts[3] of the
+ * same state, and the step index it belongs to.  Host pointers; any may be NULL. */
+int kss_read_stats(kss_lattice* lat, double sums[3], int64_t counts[3], int64_t* step);
+
+/* Steps taken since the last set. */
+int kss_get_step(const kss_lattice* lat, int64_t* step);
+/* Wait for the lattice's stream. */
+int kss_sync(kss_lattice* lat);
+
+/* Static description of an error code, and the last error message of a lattice. */
+const char* kss_strerror(int code);
+const char* kss_last_error(const kss_lattice* lat);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int kss_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KSS_H */

@@ -1,0 +1,580 @@
+// kss_runtime.cu -- host runtime behind the C ABI of include/kss.h: owns each
+// lattice's device buffers and stream, sequences the fused-step launches, keeps
+// track of which outputs describe which step, and moves data across the boundary.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+
+#include "../../include/kss.h"
+#include "launch.h"
+
+namespace {
+
+using kss::MODE_FULL;
+using kss::MODE_PLAIN;
+using kss::MODE_STD;
+
+constexpr int kVersion = 100;  // 0.1.0
+
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct kss_lattice {
+  kss_config cfg{};
+  int device = 0;
+  size_t esz = 0;           // bytes per stored element
+  int pitch = 0;            // row pitch in elements (multiple of 128 bytes)
+  long long plane = 0;      // elements per plane
+  int ntx = 0, nty = 0, nblocks = 0;
+  void* f[2] = {nullptr, nullptr};
+  int cur = 0;              // f[cur] holds the stored state
+  void* rec = nullptr;      // recorded sensor planes
+  int rec_slot[KSS_S_COUNT];
+  void* evalplane = nullptr;
+  uint8_t* flags = nullptr;
+  int32_t* tiles = nullptr;
+  double* part_sum = nullptr;
+  uint32_t* part_cnt = nullptr;
+  unsigned char* small = nullptr;  // done counter + final sums + final counts
+  uint32_t* done = nullptr;
+  double* stat_sums = nullptr;
+  unsigned long long* stat_counts = nullptr;
+  double* staging = nullptr;
+  size_t staging_elems = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t step = 0;         // steps since the last set
+  int64_t out_step = -1;    // step whose flags / tiles / sums are stored
+  int64_t rec_step = -1;    // step whose recorded sensor planes are stored
+  int64_t eval_step = -1;   // step whose evalplane holds eval_sensor
+  int eval_sensor = -1;
+  int err = KSS_OK;
+  std::string msg;
+};
+
+namespace {
+
+int fail(kss_lattice* L, int code, const std::string& m) {
+  if (L) {
+    if (code == KSS_ERR_CUDA) L->err = code;  // sticky
+    L->msg = m;
+  }
+  return code;
+}
+
+#define KSS_CUDA(L, call)                                                             \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail((L), KSS_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+bool valid_sensor(int s) { return s >= 0 && s < KSS_S_COUNT; }
+
+int check_config(const kss_config* c) {
+  if (!c) return KSS_ERR_ARG;
+  if (c->nx < 1 || c->ny < 1) return KSS_ERR_ARG;
+  if ((long long)c->nx * c->ny > std::numeric_limits<int>::max()) return KSS_ERR_ARG;
+  if (c->precision != KSS_FP64 && c->precision != KSS_FP32) return KSS_ERR_UNSUPPORTED;
+  if (!(c->tau > 0.5) || !std::isfinite(c->tau)) return KSS_ERR_ARG;
+  if (!valid_sensor(c->refine_sensor) || !valid_sensor(c->switch_sensor)) return KSS_ERR_ARG;
+  if (std::isnan(c->refine_threshold) || std::isnan(c->switch_threshold)) return KSS_ERR_ARG;
+  if (c->record_mask >> KSS_S_COUNT) return KSS_ERR_ARG;
+  if (c->output_every < 0) return KSS_ERR_ARG;
+  if (c->tile != 8 && c->tile != 16 && c->tile != 32 && c->tile != 64) return KSS_ERR_ARG;
+  if (c->own_stream != 0 && c->own_stream != 1) return KSS_ERR_ARG;
+  return KSS_OK;
+}
+
+// Largest T value <= t, so that (T)eps > result  <=>  eps > t exactly.
+template <class T>
+T round_down(double t) {
+  T r = static_cast<T>(t);
+  if (static_cast<double>(r) > t) r = std::nextafter(r, -std::numeric_limits<T>::infinity());
+  return r;
+}
+
+uint32_t needed_mask(const kss_lattice* L, uint32_t extra) {
+  uint32_t m = extra | (1u << L->cfg.refine_sensor);
+  if (L->cfg.switch_threshold >= 0.0) m |= 1u << L->cfg.switch_sensor;
+  return m;
+}
+
+int mode_for(uint32_t mask) { return (mask & ~kss::kStdMask) ? MODE_FULL : MODE_STD; }
+
+template <class T>
+kss::StepParams<T> make_params(const kss_lattice* L, const void* src, void* dst) {
+  kss::StepParams<T> p{};
+  p.src = static_cast<const T*>(src);
+  p.dst = static_cast<T*>(dst);
+  p.rec = static_cast<T*>(L->rec);
+  p.flags = L->flags;
+  p.tiles = L->tiles;
+  p.part_sum = L->part_sum;
+  p.part_cnt = L->part_cnt;
+  p.done = L->done;
+  p.stat_sums = L->stat_sums;
+  p.stat_counts = L->stat_counts;
+  p.plane = L->plane;
+  p.pitch = L->pitch;
+  p.nx = L->cfg.nx;
+  p.ny = L->cfg.ny;
+  p.tile = L->cfg.tile;
+  p.ntx = L->ntx;
+  p.nty = L->nty;
+  p.omega = T(1.0 / L->cfg.tau);
+  p.tau = T(L->cfg.tau);
+  p.thr_r = round_down<T>(L->cfg.refine_threshold);
+  p.switch_on = L->cfg.switch_threshold >= 0.0;
+  p.thr_s = p.switch_on ? round_down<T>(L->cfg.switch_threshold) : T(0);
+  p.refine_s = L->cfg.refine_sensor;
+  p.switch_s = L->cfg.switch_sensor;
+  for (int s = 0; s < KSS_S_COUNT; ++s) p.rec_slot[s] = L->rec_slot[s];
+  return p;
+}
+
+template <class T>
+cudaError_t launch_one_step(kss_lattice* L, bool out) {
+  kss::StepParams<T> p = make_params<T>(L, L->f[L->cur], L->f[L->cur ^ 1]);
+  const int mode = out ? mode_for(needed_mask(L, L->cfg.record_mask)) : MODE_PLAIN;
+  return kss::launch_step<T>(p, mode, true, true, L->stream);
+}
+
+// Evaluate sensors / flags / tiles / sums of the state of the most recent step
+// (its pre-collision populations: the other buffer, streamed) or of the stored
+// state when no step was taken since the last set.  sensor >= 0 also writes
+// that sensor's field into evalplane.
+template <class T>
+cudaError_t launch_eval(kss_lattice* L, int sensor) {
+  const bool pull = L->step > 0;
+  const void* src = pull ? L->f[L->cur ^ 1] : L->f[L->cur];
+  kss::StepParams<T> p = make_params<T>(L, src, nullptr);
+  for (int s = 0; s < KSS_S_COUNT; ++s) p.rec_slot[s] = -1;
+  uint32_t extra = 0;
+  if (sensor >= 0) {
+    p.rec = static_cast<T*>(L->evalplane);
+    p.rec_slot[sensor] = 0;
+    extra = 1u << sensor;
+  }
+  return kss::launch_step<T>(p, mode_for(needed_mask(L, extra)), pull, false, L->stream);
+}
+
+int ensure_staging(kss_lattice* L, size_t elems) {
+  if (L->staging_elems >= elems) return KSS_OK;
+  if (L->staging) {
+    KSS_CUDA(L, cudaStreamSynchronize(L->stream));
+    cudaFree(L->staging);
+    L->staging = nullptr;
+    L->staging_elems = 0;
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, elems * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(L, KSS_ERR_OOM, "staging allocation failed");
+  }
+  L->staging = static_cast<double*>(p);
+  L->staging_elems = elems;
+  return KSS_OK;
+}
+
+int enter(kss_lattice* L) {
+  if (!L) return KSS_ERR_ARG;
+  if (L->err) return L->err;
+  return KSS_OK;
+}
+
+// Make flags / tiles / sums (and, if sensor >= 0, that sensor's field) describe
+// the current step.  Returns where the sensor field is (rec slot or evalplane).
+int ensure_outputs(kss_lattice* L, int sensor, const void** field) {
+  const bool fp32 = L->cfg.precision == KSS_FP32;
+  const bool have_out = L->out_step == L->step;
+  const void* where = nullptr;
+  if (sensor >= 0) {
+    if (L->rec_step == L->step && L->rec_slot[sensor] >= 0)
+      where = static_cast<const char*>(L->rec) + L->esz * L->plane * L->rec_slot[sensor];
+    else if (L->eval_step == L->step && L->eval_sensor == sensor)
+      where = L->evalplane;
+  }
+  if (have_out && (sensor < 0 || where)) {
+    if (field) *field = where;
+    return KSS_OK;
+  }
+  const int s = (sensor >= 0 && !where) ? sensor : -1;
+  KSS_CUDA(L, fp32 ? launch_eval<float>(L, s) : launch_eval<double>(L, s));
+  L->out_step = L->step;
+  if (s >= 0) {
+    L->eval_step = L->step;
+    L->eval_sensor = s;
+    where = L->evalplane;
+  }
+  if (field) *field = where;
+  return KSS_OK;
+}
+
+int nonpos_status(kss_lattice* L) {
+  unsigned long long c[3];
+  KSS_CUDA(L, cudaMemcpyAsync(c, L->stat_counts, sizeof(c), cudaMemcpyDeviceToHost, L->stream));
+  KSS_CUDA(L, cudaStreamSynchronize(L->stream));
+  return c[2] > 0 ? KSS_WARN_NONPOSITIVE : KSS_OK;
+}
+
+void release(kss_lattice* L) {
+  if (!L) return;
+  cudaStreamSynchronize(L->stream);
+  void* bufs[] = {L->f[0], L->f[1], L->rec, L->evalplane, L->flags, L->tiles, L->part_sum,
+                  L->part_cnt, L->small, L->staging};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
+  delete L;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kss_version(void) { return kVersion; }
+
+const char* kss_strerror(int code) {
+  switch (code) {
+    case KSS_OK: return "ok";
+    case KSS_ERR_ARG: return "invalid argument";
+    case KSS_ERR_OOM: return "out of memory";
+    case KSS_ERR_CUDA: return "CUDA error";
+    case KSS_ERR_TIMEOUT: return "device wait timed out";
+    case KSS_ERR_STATE: return "invalid state";
+    case KSS_ERR_UNSUPPORTED: return "unsupported option";
+    case KSS_WARN_NONPOSITIVE: return "non-positive populations present";
+    default: return "unknown error code";
+  }
+}
+
+const char* kss_last_error(const kss_lattice* L) { return L ? L->msg.c_str() : "null lattice"; }
+
+int kss_config_default(kss_config* c, int32_t nx, int32_t ny, int32_t precision) {
+  if (!c) return KSS_ERR_ARG;
+  std::memset(c, 0, sizeof(*c));
+  c->nx = nx;
+  c->ny = ny;
+  c->precision = precision;
+  c->tau = 0.8;
+  c->refine_sensor = KSS_S_KN;
+  c->refine_threshold = 1e-3;
+  c->switch_sensor = KSS_S_NEQ;
+  c->switch_threshold = 1e-4;
+  c->record_mask = 1u << KSS_S_KL;
+  c->output_every = 1;
+  c->tile = 16;
+  c->stream = nullptr;
+  c->own_stream = 0;
+  return KSS_OK;
+}
+
+int kss_create(const kss_config* cfg, kss_lattice** out) {
+  if (!out) return KSS_ERR_ARG;
+  *out = nullptr;
+  const int rc = check_config(cfg);
+  if (rc) return rc;
+  kss_lattice* L = new (std::nothrow) kss_lattice();
+  if (!L) return KSS_ERR_OOM;
+  L->cfg = *cfg;
+  if (cudaGetDevice(&L->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete L;
+    return KSS_ERR_CUDA;
+  }
+  const bool fp32 = cfg->precision == KSS_FP32;
+  L->esz = fp32 ? sizeof(float) : sizeof(double);
+  const int align = int(128 / L->esz);
+  L->pitch = (cfg->nx + align - 1) / align * align;
+  L->plane = (long long)L->pitch * cfg->ny;
+  L->ntx = (cfg->nx + cfg->tile - 1) / cfg->tile;
+  L->nty = (cfg->ny + cfg->tile - 1) / cfg->tile;
+  const dim3 g = fp32 ? kss::step_grid<float>(cfg->nx, cfg->ny, cfg->tile)
+                      : kss::step_grid<double>(cfg->nx, cfg->ny, cfg->tile);
+  L->nblocks = int(g.x * g.y);
+  int nrec = 0;
+  for (int s = 0; s < KSS_S_COUNT; ++s)
+    L->rec_slot[s] = ((cfg->record_mask >> s) & 1u) ? nrec++ : -1;
+
+  if (!cfg->own_stream) {
+    L->stream = static_cast<cudaStream_t>(cfg->stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete L;
+      return KSS_ERR_CUDA;
+    }
+    L->own_stream = true;
+  }
+  const size_t pop_bytes = 9 * size_t(L->plane) * L->esz;
+  const size_t plane_bytes = size_t(L->plane) * L->esz;
+  struct {
+    void** p;
+    size_t bytes;
+  } allocs[] = {
+      {&L->f[0], pop_bytes},
+      {&L->f[1], pop_bytes},
+      {&L->rec, plane_bytes * (nrec > 0 ? nrec : 1)},
+      {&L->evalplane, plane_bytes},
+      {reinterpret_cast<void**>(&L->flags), size_t(L->pitch) * cfg->ny},
+      {reinterpret_cast<void**>(&L->tiles), sizeof(int32_t) * 2 * size_t(L->ntx) * L->nty},
+      {reinterpret_cast<void**>(&L->part_sum), sizeof(double) * 3 * size_t(L->nblocks)},
+      {reinterpret_cast<void**>(&L->part_cnt), sizeof(uint32_t) * 4 * size_t(L->nblocks)},
+      {reinterpret_cast<void**>(&L->small), 256},
+  };
+  for (auto& a : allocs) {
+    if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
+      cudaGetLastError();
+      release(L);
+      return KSS_ERR_OOM;
+    }
+    if (cudaMemsetAsync(*a.p, 0, a.bytes, L->stream) != cudaSuccess) {
+      cudaGetLastError();
+      release(L);
+      return KSS_ERR_CUDA;
+    }
+  }
+  L->done = reinterpret_cast<uint32_t*>(L->small);
+  L->stat_sums = reinterpret_cast<double*>(L->small + 64);
+  L->stat_counts = reinterpret_cast<unsigned long long*>(L->small + 128);
+  if (cudaStreamSynchronize(L->stream) != cudaSuccess) {
+    cudaGetLastError();
+    release(L);
+    return KSS_ERR_CUDA;
+  }
+  *out = L;
+  return KSS_OK;
+}
+
+void kss_destroy(kss_lattice* L) {
+  if (!L) return;
+  DeviceGuard g(L->device);
+  release(L);
+}
+
+static void reset_after_set(kss_lattice* L) {
+  L->step = 0;
+  L->out_step = L->rec_step = L->eval_step = -1;
+  L->eval_sensor = -1;
+}
+
+int kss_set_fields(kss_lattice* L, const double* rho, const double* ux, const double* uy,
+                   int on_device) {
+  int rc = enter(L);
+  if (rc) return rc;
+  if (!rho || !ux || !uy) return fail(L, KSS_ERR_ARG, "null field pointer");
+  DeviceGuard g(L->device);
+  const size_t n = size_t(L->cfg.nx) * L->cfg.ny;
+  const double *r = rho, *u = ux, *v = uy;
+  if (!on_device) {
+    if ((rc = ensure_staging(L, 3 * n))) return rc;
+    KSS_CUDA(L, cudaMemcpyAsync(L->staging, rho, n * 8, cudaMemcpyHostToDevice, L->stream));
+    KSS_CUDA(L, cudaMemcpyAsync(L->staging + n, ux, n * 8, cudaMemcpyHostToDevice, L->stream));
+    KSS_CUDA(L, cudaMemcpyAsync(L->staging + 2 * n, uy, n * 8, cudaMemcpyHostToDevice, L->stream));
+    r = L->staging;
+    u = L->staging + n;
+    v = L->staging + 2 * n;
+  }
+  const int nx = L->cfg.nx, ny = L->cfg.ny;
+  if (L->cfg.precision == KSS_FP32)
+    KSS_CUDA(L, kss::launch_init_equilibrium<float>(r, u, v, static_cast<float*>(L->f[L->cur]),
+                                                    L->plane, L->pitch, nx, ny, L->stream));
+  else
+    KSS_CUDA(L, kss::launch_init_equilibrium<double>(r, u, v, static_cast<double*>(L->f[L->cur]),
+                                                     L->plane, L->pitch, nx, ny, L->stream));
+  if (!on_device) KSS_CUDA(L, cudaStreamSynchronize(L->stream));
+  reset_after_set(L);
+  return KSS_OK;
+}
+
+int kss_set_populations(kss_lattice* L, const double* f, int on_device) {
+  int rc = enter(L);
+  if (rc) return rc;
+  if (!f) return fail(L, KSS_ERR_ARG, "null population pointer");
+  DeviceGuard g(L->device);
+  const size_t n = 9 * size_t(L->cfg.nx) * L->cfg.ny;
+  const double* src = f;
+  if (!on_device) {
+    if ((rc = ensure_staging(L, n))) return rc;
+    KSS_CUDA(L, cudaMemcpyAsync(L->staging, f, n * 8, cudaMemcpyHostToDevice, L->stream));
+    src = L->staging;
+  }
+  const int nx = L->cfg.nx, ny = L->cfg.ny;
+  if (L->cfg.precision == KSS_FP32)
+    KSS_CUDA(L, kss::launch_dense_to_pitched<float>(src, L->plane, L->pitch, nx, ny, 9,
+                                                    static_cast<float*>(L->f[L->cur]), L->stream));
+  else
+    KSS_CUDA(L, kss::launch_dense_to_pitched<double>(src, L->plane, L->pitch, nx, ny, 9,
+                                                     static_cast<double*>(L->f[L->cur]), L->stream));
+  if (!on_device) KSS_CUDA(L, cudaStreamSynchronize(L->stream));
+  reset_after_set(L);
+  return KSS_OK;
+}
+
+int kss_get_populations(kss_lattice* L, double* f, int on_device) {
+  int rc = enter(L);
+  if (rc) return rc;
+  if (!f) return fail(L, KSS_ERR_ARG, "null population pointer");
+  DeviceGuard g(L->device);
+  const size_t n = 9 * size_t(L->cfg.nx) * L->cfg.ny;
+  double* dst = f;
+  if (!on_device) {
+    if ((rc = ensure_staging(L, n))) return rc;
+    dst = L->staging;
+  }
+  const int nx = L->cfg.nx, ny = L->cfg.ny;
+  if (L->cfg.precision == KSS_FP32)
+    KSS_CUDA(L, kss::launch_pitched_to_dense<float>(static_cast<const float*>(L->f[L->cur]),
+                                                    L->plane, L->pitch, nx, ny, 9, dst, L->stream));
+  else
+    KSS_CUDA(L, kss::launch_pitched_to_dense<double>(static_cast<const double*>(L->f[L->cur]),
+                                                     L->plane, L->pitch, nx, ny, 9, dst, L->stream));
+  if (!on_device)
+    KSS_CUDA(L, cudaMemcpyAsync(f, L->staging, n * 8, cudaMemcpyDeviceToHost, L->stream));
+  KSS_CUDA(L, cudaStreamSynchronize(L->stream));
+  return KSS_OK;
+}
+
+int kss_step(kss_lattice* L, int32_t nsteps) {
+  int rc = enter(L);
+  if (rc) return rc;
+  if (nsteps < 0) return fail(L, KSS_ERR_ARG, "negative step count");
+  DeviceGuard g(L->device);
+  const bool fp32 = L->cfg.precision == KSS_FP32;
+  for (int32_t s = 0; s < nsteps; ++s) {
+    const int64_t n = L->step + 1;
+    const bool out = L->cfg.output_every > 0 && (n % L->cfg.output_every) == 0;
+    KSS_CUDA(L, fp32 ? launch_one_step<float>(L, out) : launch_one_step<double>(L, out));
+    L->cur ^= 1;
+    L->step = n;
+    if (out) {
+      L->out_step = n;
+      L->rec_step = n;
+    }
+  }
+  return KSS_OK;
+}
+
+int kss_read_moments(kss_lattice* L, double* rho, double* ux, double* uy, int on_device) {
+  int rc = enter(L);
+  if (rc) return rc;
+  if (!rho || !ux || !uy) return fail(L, KSS_ERR_ARG, "null field pointer");
+  DeviceGuard g(L->device);
+  const size_t n = size_t(L->cfg.nx) * L->cfg.ny;
+  double *r = rho, *u = ux, *v = uy;
+  if (!on_device) {
+    if ((rc = ensure_staging(L, 3 * n))) return rc;
+    r = L->staging;
+    u = L->staging + n;
+    v = L->staging + 2 * n;
+  }
+  const int nx = L->cfg.nx, ny = L->cfg.ny;
+  if (L->cfg.precision == KSS_FP32)
+    KSS_CUDA(L, kss::launch_moments<float>(static_cast<const float*>(L->f[L->cur]), L->plane,
+                                           L->pitch, nx, ny, r, u, v, L->stream));
+  else
+    KSS_CUDA(L, kss::launch_moments<double>(static_cast<const double*>(L->f[L->cur]), L->plane,
+                                            L->pitch, nx, ny, r, u, v, L->stream));
+  if (!on_device) {
+    KSS_CUDA(L, cudaMemcpyAsync(rho, r, n * 8, cudaMemcpyDeviceToHost, L->stream));
+    KSS_CUDA(L, cudaMemcpyAsync(ux, u, n * 8, cudaMemcpyDeviceToHost, L->stream));
+    KSS_CUDA(L, cudaMemcpyAsync(uy, v, n * 8, cudaMemcpyDeviceToHost, L->stream));
+  }
+  KSS_CUDA(L, cudaStreamSynchronize(L->stream));
+  return KSS_OK;
+}
+
+int kss_read_sensor(kss_lattice* L, int32_t sensor, double* out, int on_device) {
+  int rc = enter(L);
+  if (rc) return rc;
+  if (!valid_sensor(sensor)) return fail(L, KSS_ERR_ARG, "invalid sensor id");
+  if (!out) return fail(L, KSS_ERR_ARG, "null output pointer");
+  DeviceGuard g(L->device);
+  const void* field = nullptr;
+  if ((rc = ensure_outputs(L, sensor, &field))) return rc;
+  const size_t n = size_t(L->cfg.nx) * L->cfg.ny;
+  double* dst = out;
+  if (!on_device) {
+    if ((rc = ensure_staging(L, n))) return rc;
+    dst = L->staging;
+  }
+  const int nx = L->cfg.nx, ny = L->cfg.ny;
+  if (L->cfg.precision == KSS_FP32)
+    KSS_CUDA(L, kss::launch_pitched_to_dense<float>(static_cast<const float*>(field), L->plane,
+                                                    L->pitch, nx, ny, 1, dst, L->stream));
+  else
+    KSS_CUDA(L, kss::launch_pitched_to_dense<double>(static_cast<const double*>(field), L->plane,
+                                                     L->pitch, nx, ny, 1, dst, L->stream));
+  if (!on_device)
+    KSS_CUDA(L, cudaMemcpyAsync(out, L->staging, n * 8, cudaMemcpyDeviceToHost, L->stream));
+  return nonpos_status(L);
+}
+
+int kss_read_flags(kss_lattice* L, uint8_t* flags, int32_t* tile_counts, int64_t counts[3],
+                   int on_device) {
+  int rc = enter(L);
+  if (rc) return rc;
+  DeviceGuard g(L->device);
+  if ((rc = ensure_outputs(L, -1, nullptr))) return rc;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (flags)
+    KSS_CUDA(L, cudaMemcpy2DAsync(flags, size_t(L->cfg.nx), L->flags, size_t(L->pitch),
+                                  size_t(L->cfg.nx), size_t(L->cfg.ny), kind, L->stream));
+  if (tile_counts)
+    KSS_CUDA(L, cudaMemcpyAsync(tile_counts, L->tiles,
+                                sizeof(int32_t) * 2 * size_t(L->ntx) * L->nty, kind, L->stream));
+  unsigned long long c[3];
+  KSS_CUDA(L, cudaMemcpyAsync(c, L->stat_counts, sizeof(c), cudaMemcpyDeviceToHost, L->stream));
+  KSS_CUDA(L, cudaStreamSynchronize(L->stream));
+  if (counts)
+    for (int k = 0; k < 3; ++k) counts[k] = int64_t(c[k]);
+  return c[2] > 0 ? KSS_WARN_NONPOSITIVE : KSS_OK;
+}
+
+int kss_read_stats(kss_lattice* L, double sums[3], int64_t counts[3], int64_t* step) {
+  int rc = enter(L);
+  if (rc) return rc;
+  DeviceGuard g(L->device);
+  if ((rc = ensure_outputs(L, -1, nullptr))) return rc;
+  double s[3];
+  unsigned long long c[3];
+  KSS_CUDA(L, cudaMemcpyAsync(s, L->stat_sums, sizeof(s), cudaMemcpyDeviceToHost, L->stream));
+  KSS_CUDA(L, cudaMemcpyAsync(c, L->stat_counts, sizeof(c), cudaMemcpyDeviceToHost, L->stream));
+  KSS_CUDA(L, cudaStreamSynchronize(L->stream));
+  if (sums)
+    for (int k = 0; k < 3; ++k) sums[k] = s[k];
+  if (counts)
+    for (int k = 0; k < 3; ++k) counts[k] = int64_t(c[k]);
+  if (step) *step = L->out_step;
+  return c[2] > 0 ? KSS_WARN_NONPOSITIVE : KSS_OK;
+}
+
+int kss_get_step(const kss_lattice* L, int64_t* step) {
+  if (!L || !step) return KSS_ERR_ARG;
+  *step = L->step;
+  return KSS_OK;
+}
+
+int kss_sync(kss_lattice* L) {
+  int rc = enter(L);
+  if (rc) return rc;
+  DeviceGuard g(L->device);
+  KSS_CUDA(L, cudaStreamSynchronize(L->stream));
+  return KSS_OK;
+}
+
+}  // extern "C"

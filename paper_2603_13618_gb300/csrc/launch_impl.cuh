@@ -1,0 +1,72 @@
+// launch_impl.cuh -- bodies of the launchers declared in launch.h; included once per
+// storage precision by launch_f32.cu / launch_f64.cu with KSS_T defined.
+#pragma once
+
+#include "launch.h"
+
+namespace kss {
+
+inline int helper_grid(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 152LL * 16) b = 152LL * 16;  // grid-stride beyond 16 CTAs per SM
+  return b < 1 ? 1 : int(b);
+}
+
+template <>
+cudaError_t launch_step<KSS_T>(const StepParams<KSS_T>& p, int mode, bool pull, bool store,
+                               cudaStream_t stream) {
+  const dim3 grid = step_grid<KSS_T>(p.nx, p.ny, p.tile);
+  const dim3 block(kThreads);
+  if (store && pull) {
+    switch (mode) {
+      case MODE_PLAIN: step_kernel<KSS_T, MODE_PLAIN, true, true><<<grid, block, 0, stream>>>(p); break;
+      case MODE_STD: step_kernel<KSS_T, MODE_STD, true, true><<<grid, block, 0, stream>>>(p); break;
+      case MODE_FULL: step_kernel<KSS_T, MODE_FULL, true, true><<<grid, block, 0, stream>>>(p); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else if (!store) {
+    if (mode == MODE_STD && pull) step_kernel<KSS_T, MODE_STD, true, false><<<grid, block, 0, stream>>>(p);
+    else if (mode == MODE_STD) step_kernel<KSS_T, MODE_STD, false, false><<<grid, block, 0, stream>>>(p);
+    else if (mode == MODE_FULL && pull) step_kernel<KSS_T, MODE_FULL, true, false><<<grid, block, 0, stream>>>(p);
+    else if (mode == MODE_FULL) step_kernel<KSS_T, MODE_FULL, false, false><<<grid, block, 0, stream>>>(p);
+    else return cudaErrorInvalidValue;
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_init_equilibrium<KSS_T>(const double* rho, const double* ux, const double* uy,
+                                           KSS_T* f, long long plane, int pitch, int nx, int ny,
+                                           cudaStream_t stream) {
+  init_equilibrium_kernel<KSS_T><<<helper_grid((long long)nx * ny), 256, 0, stream>>>(
+      rho, ux, uy, f, plane, pitch, nx, ny);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_moments<KSS_T>(const KSS_T* f, long long plane, int pitch, int nx, int ny,
+                                  double* rho, double* ux, double* uy, cudaStream_t stream) {
+  moments_kernel<KSS_T><<<helper_grid((long long)nx * ny), 256, 0, stream>>>(
+      f, plane, pitch, nx, ny, rho, ux, uy);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_pitched_to_dense<KSS_T>(const KSS_T* src, long long plane, int pitch, int nx,
+                                           int ny, int nplanes, double* dst, cudaStream_t stream) {
+  pitched_to_dense_kernel<KSS_T><<<helper_grid((long long)nx * ny * nplanes), 256, 0, stream>>>(
+      src, plane, pitch, nx, ny, nplanes, dst);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_dense_to_pitched<KSS_T>(const double* src, long long plane, int pitch, int nx,
+                                           int ny, int nplanes, KSS_T* dst, cudaStream_t stream) {
+  dense_to_pitched_kernel<KSS_T><<<helper_grid((long long)nx * ny * nplanes), 256, 0, stream>>>(
+      src, plane, pitch, nx, ny, nplanes, dst);
+  return cudaGetLastError();
+}
+
+}  // namespace kss

@@ -1,0 +1,252 @@
+"""Thin Python binding of the C ABI in ``include/kss.h`` (argument marshalling only).
+
+Every computation runs in the CUDA library ``_build/libkss.so``; this module only
+converts arguments: numpy arrays are host memory (``on_device=0``), torch CUDA
+tensors are device memory (``on_device=1``).  PyTorch supplies device memory and the
+stream.  There is no CPU fallback: if the library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libkss.so")
+
+KSS_OK = 0
+KSS_WARN_NONPOSITIVE = 1
+FP64, FP32 = 0, 1
+PRECISIONS = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}
+
+SENSORS = ("tau_ns", "c", "s", "e", "qh", "kn", "neq", "qe", "hr", "kl", "sigma_h",
+           "sigma_kl", "alpha")
+SENSOR_ID = {n: k for k, n in enumerate(SENSORS)}
+FLAG_REFINE, FLAG_SWITCH, FLAG_NONPOS = 0x01, 0x02, 0x80
+
+
+class KssError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"kss error {code}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("tau", ctypes.c_double),
+        ("refine_sensor", ctypes.c_int32), ("refine_threshold", ctypes.c_double),
+        ("switch_sensor", ctypes.c_int32), ("switch_threshold", ctypes.c_double),
+        ("record_mask", ctypes.c_uint32), ("output_every", ctypes.c_int32),
+        ("tile", ctypes.c_int32), ("stream", ctypes.c_void_p), ("own_stream", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+# Every entry point declared in include/kss.h, with its ctypes signature.
+_DP = ctypes.POINTER(ctypes.c_double)
+_SIGNATURES = {
+    "kss_version": (ctypes.c_int, []),
+    "kss_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "kss_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "kss_config_default": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_int32]),
+    "kss_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_void_p)]),
+    "kss_destroy": (None, [ctypes.c_void_p]),
+    "kss_set_fields": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int]),
+    "kss_set_populations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "kss_get_populations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "kss_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "kss_read_moments": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int]),
+    "kss_read_sensor": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_int]),
+    "kss_read_flags": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int]),
+    "kss_read_stats": (ctypes.c_int, [ctypes.c_void_p] * 4),
+    "kss_get_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "kss_sync": (ctypes.c_int, [ctypes.c_void_p]),
+}
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libkss.so; raise if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"CUDA library {path} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, dtype):
+    """(pointer, on_device) of a numpy array or torch tensor of the given dtype."""
+    if _is_torch(a):
+        import torch
+
+        want = {np.float64: torch.float64, np.uint8: torch.uint8, np.int32: torch.int32}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"tensor must be contiguous {want}")
+        return ctypes.c_void_p(a.data_ptr()), int(a.is_cuda)
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"array must be a C-contiguous numpy {np.dtype(dtype).name} array")
+    return ctypes.c_void_p(a.ctypes.data), 0
+
+
+def _sensor(s) -> int:
+    return SENSOR_ID[s] if isinstance(s, str) else int(s)
+
+
+def _torch_stream_handle():
+    import torch
+
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Lattice:
+    """A periodic D2Q9 lattice on the current CUDA device (see include/kss.h)."""
+
+    def __init__(self, nx: int, ny: int, precision="fp32", tau: float = 0.8,
+                 refine_sensor="kn", refine_threshold: float = 1e-3, switch_sensor="neq",
+                 switch_threshold: float = 1e-4, record=("kl",), output_every: int = 1,
+                 tile: int = 16, stream="torch"):
+        self._lib = load()
+        cfg = Config()
+        self._check(self._lib.kss_config_default(ctypes.byref(cfg), nx, ny,
+                                                  PRECISIONS[precision]))
+        cfg.tau = tau
+        cfg.refine_sensor = _sensor(refine_sensor)
+        cfg.refine_threshold = refine_threshold
+        cfg.switch_sensor = _sensor(switch_sensor)
+        cfg.switch_threshold = switch_threshold
+        cfg.record_mask = sum(1 << _sensor(s) for s in record)
+        cfg.output_every = output_every
+        cfg.tile = tile
+        # stream: "torch" = torch's current stream (handle 0 is the CUDA default
+        # stream), "own" = a stream created and owned by the lattice, or a raw handle
+        if stream == "own":
+            cfg.own_stream, cfg.stream = 1, None
+        else:
+            cfg.stream = _torch_stream_handle() if stream == "torch" else stream
+        self.cfg = cfg
+        self.nx, self.ny, self.tile = nx, ny, tile
+        self.precision = PRECISIONS[precision]
+        handle = ctypes.c_void_p()
+        self._h = None
+        self._check(self._lib.kss_create(ctypes.byref(cfg), ctypes.byref(handle)))
+        self._h = handle
+        self.last_status = KSS_OK
+
+    # -- plumbing --
+    def _check(self, rc: int) -> int:
+        if rc < 0:
+            detail = ""
+            if getattr(self, "_h", None):
+                detail = (self._lib.kss_last_error(self._h) or b"").decode()
+            raise KssError(rc, f"{self._lib.kss_strerror(rc).decode()} {detail}".strip())
+        self.last_status = rc
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.kss_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def ntx(self) -> int:
+        return -(-self.nx // self.tile)
+
+    @property
+    def nty(self) -> int:
+        return -(-self.ny // self.tile)
+
+    def _alloc(self, shape, dtype, device: bool):
+        if device:
+            import torch
+
+            tdt = {np.float64: torch.float64, np.uint8: torch.uint8, np.int32: torch.int32}[dtype]
+            return torch.empty(shape, dtype=tdt, device="cuda")
+        return np.empty(shape, dtype=dtype)
+
+    # -- API --
+    def set_fields(self, rho, ux, uy) -> None:
+        (pr, d0), (pu, d1), (pv, d2) = (_ptr(a, np.float64) for a in (rho, ux, uy))
+        if not d0 == d1 == d2:
+            raise TypeError("fields must all be host or all be device memory")
+        self._check(self._lib.kss_set_fields(self._h, pr, pu, pv, d0))
+
+    def set_populations(self, f) -> None:
+        p, d = _ptr(f, np.float64)
+        self._check(self._lib.kss_set_populations(self._h, p, d))
+
+    def get_populations(self, device: bool = False):
+        out = self._alloc((9, self.ny, self.nx), np.float64, device)
+        p, d = _ptr(out, np.float64)
+        self._check(self._lib.kss_get_populations(self._h, p, d))
+        return out
+
+    def step(self, n: int = 1) -> None:
+        self._check(self._lib.kss_step(self._h, int(n)))
+
+    def read_moments(self, device: bool = False):
+        outs = [self._alloc((self.ny, self.nx), np.float64, device) for _ in range(3)]
+        (p0, d), (p1, _), (p2, _) = (_ptr(a, np.float64) for a in outs)
+        self._check(self._lib.kss_read_moments(self._h, p0, p1, p2, d))
+        return tuple(outs)
+
+    def read_sensor(self, sensor, device: bool = False):
+        out = self._alloc((self.ny, self.nx), np.float64, device)
+        p, d = _ptr(out, np.float64)
+        self._check(self._lib.kss_read_sensor(self._h, _sensor(sensor), p, d))
+        return out
+
+    def read_flags(self, device: bool = False, out=None):
+        """(flags, tile_counts, counts); `out` = (flags, tiles) buffers to fill."""
+        if out is not None:
+            flags, tiles = out
+        else:
+            flags = self._alloc((self.ny, self.nx), np.uint8, device)
+            tiles = self._alloc((2, self.nty, self.ntx), np.int32, device)
+        counts = (ctypes.c_int64 * 3)()
+        pf, d = _ptr(flags, np.uint8)
+        pt, _ = _ptr(tiles, np.int32)
+        self._check(self._lib.kss_read_flags(self._h, pf, pt, counts, d))
+        return flags, tiles, np.array(list(counts), dtype=np.int64)
+
+    def read_stats(self):
+        sums = (ctypes.c_double * 3)()
+        counts = (ctypes.c_int64 * 3)()
+        step = ctypes.c_int64()
+        self._check(self._lib.kss_read_stats(self._h, sums, counts, ctypes.byref(step)))
+        return np.array(list(sums)), np.array(list(counts), dtype=np.int64), step.value
+
+    @property
+    def step_count(self) -> int:
+        s = ctypes.c_int64()
+        self._check(self._lib.kss_get_step(self._h, ctypes.byref(s)))
+        return s.value
+
+    def sync(self) -> None:
+        self._check(self._lib.kss_sync(self._h))

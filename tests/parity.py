@@ -1,0 +1,92 @@
+"""Tolerances and comparison helpers of the GPU-vs-oracle parity tests.
+
+Tolerance model (derived from the arithmetic; u = unit round-off of the storage type,
+2^-24 for FP32 and 2^-53 for FP64, n = steps taken):
+
+* populations / moments: the state drifts from the oracle's by independent rounding
+  of the collision each step, a few u relative per step, as a random walk:
+  |df| <= c u sqrt(n + 1) f.  FP64 uses c = 64; FP32 moments must meet the stated
+  1e-5 after 100 steps.
+* sensors: each f^neq_q = f_q - f^eq_q carries an absolute error of about 8 u f^eq_q
+  (rounding of f^eq) plus the state drift, so every sensor has an absolute error floor
+  proportional to the scale of its terms: atol_s = 64 u sqrt(n + 1) scale_s with
+      tau_ns, neq: rho;   C, S, E: rho / mu = 3 / tau;   qh: rho |u|;   Kn: 9;
+      KL: rho Kn;   HR: rho (Kn + |u|);   sigma_H: rho (Kn + |u|) / tau;
+      sigma_KL: rho Kn / tau;   alpha: 1;   qe: 0
+  on top of a relative tolerance (FP64 1e-10, FP32 1e-3).
+* flags: identical except at cells whose oracle sensor lies within 1e-4 of the
+  threshold (absolute band); tile counts and global counts are then compared as
+  exact integers after removing the band cells' contributions.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SENSORS = ("tau_ns", "c", "s", "e", "qh", "kn", "neq", "qe", "hr", "kl", "sigma_h",
+           "sigma_kl", "alpha")
+UNIT_ROUNDOFF = {"fp64": 2.0**-53, "fp32": 2.0**-24}
+RTOL = {"fp64": 1e-10, "fp32": 1e-3}
+FLAG_BAND = 1e-4
+
+
+def sensor_atol(name, prec, nsteps, rho, ux, uy, kn, tau):
+    u = UNIT_ROUNDOFF[prec]
+    speed = np.sqrt(ux * ux + uy * uy)
+    knf = np.where(np.isfinite(kn), kn, 0.0)
+    scale = {
+        "tau_ns": rho, "neq": rho, "c": 3.0 / tau + 0 * rho, "s": 3.0 / tau + 0 * rho,
+        "e": 3.0 / tau + 0 * rho, "qh": rho * speed, "kn": 9.0 + 0 * rho, "kl": rho * knf,
+        "hr": rho * (knf + speed), "sigma_h": rho * (knf + speed) / tau,
+        "sigma_kl": rho * knf / tau, "alpha": 1.0 + 0 * rho, "qe": 0 * rho,
+    }[name]
+    return 64.0 * u * math.sqrt(nsteps + 1) * scale
+
+
+def assert_sensor_close(name, got, want, prec, nsteps, rho, ux, uy, kn, tau):
+    both_inf = np.isinf(got) & np.isinf(want)
+    assert np.array_equal(np.isinf(got), np.isinf(want)), f"{name}: +Inf pattern differs"
+    g, w = np.where(both_inf, 0.0, got), np.where(both_inf, 0.0, want)
+    tol = RTOL[prec] * np.abs(w) + sensor_atol(name, prec, nsteps, rho, ux, uy, kn, tau)
+    err = np.abs(g - w)
+    bad = err > tol
+    assert not bad.any(), (f"{name} ({prec}): {int(bad.sum())} cells out of tolerance, "
+                           f"worst err {err.max():.3e} vs tol {tol[np.unravel_index(err.argmax(), err.shape)]:.3e}")
+    return float(np.max(err / np.maximum(np.abs(w), 1e-300), initial=0.0))
+
+
+def band_mask(eps_r, thr_r, eps_s, thr_s):
+    m = np.abs(eps_r - thr_r) <= FLAG_BAND
+    if thr_s >= 0:
+        m |= np.abs(eps_s - thr_s) <= FLAG_BAND
+    return m
+
+
+def assert_flags_match(flags, tiles, counts, ref_flags, ref_tiles, ref_counts, band, tile):
+    """Flags identical outside the threshold band; counts exact up to the band cells."""
+    diff = (flags != ref_flags) & ~band
+    assert not diff.any(), f"{int(diff.sum())} flags differ outside the threshold band"
+    nb = int(band.sum())
+    if nb == 0:
+        np.testing.assert_array_equal(tiles, ref_tiles)
+        np.testing.assert_array_equal(counts, ref_counts)
+        return 0
+    # every tile count differs from the oracle's by at most its band cells
+    ny, nx = flags.shape
+    nty, ntx = tiles.shape[1:]
+    bt = np.zeros((nty, ntx), dtype=np.int64)
+    jj, ii = np.nonzero(band)
+    np.add.at(bt, (jj // tile, ii // tile), 1)
+    assert np.all(np.abs(tiles[0] - ref_tiles[0]) <= bt)
+    assert np.all(np.abs(tiles[1] - ref_tiles[1]) <= bt)
+    # and equals the recount of the GPU's own flags exactly
+    ty = np.repeat((np.arange(ny) // tile)[:, None], nx, axis=1)
+    tx = np.repeat((np.arange(nx) // tile)[None, :], ny, axis=0)
+    rc = np.zeros((2, nty, ntx), dtype=np.int64)
+    np.add.at(rc[0], (ty, tx), (flags & 1).astype(np.int64))
+    np.add.at(rc[1], (ty, tx), ((flags >> 1) & 1).astype(np.int64))
+    np.testing.assert_array_equal(tiles, rc)
+    assert counts[0] == int(np.sum(flags & 1)) and counts[1] == int(np.sum((flags >> 1) & 1))
+    assert counts[2] == int(np.sum(flags >> 7))
+    return nb

@@ -1,0 +1,65 @@
+"""The C ABI library loads and exports every entry point that include/kss.h declares
+(no compute calls: these run without a GPU)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "kss.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(kss_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("kss_create", "kss_destroy", "kss_set_fields", "kss_step", "kss_read_moments",
+              "kss_read_sensor", "kss_read_flags", "kss_read_stats"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2603_13618_gb300 import kss
+
+    lib = kss.load()
+    for n in _declared():
+        assert hasattr(lib, n), n
+    so = kss.LIB_PATH
+    out = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True)
+    exported = set(re.findall(r"\bT (kss_\w+)", out.stdout))
+    assert set(_declared()) <= exported
+    assert set(kss._SIGNATURES) == set(_declared())
+
+
+def test_host_only_calls():
+    from paper_2603_13618_gb300 import kss
+
+    lib = kss.load()
+    assert lib.kss_version() >= 100
+    assert lib.kss_strerror(-1) == b"invalid argument"
+    cfg = kss.Config()
+    assert lib.kss_config_default(cfg, 64, 32, kss.FP32) == 0
+    assert (cfg.nx, cfg.ny, cfg.tile, cfg.output_every) == (64, 32, 16, 1)
+    assert abs(cfg.tau - 0.8) < 1e-15 and cfg.record_mask == 1 << kss.SENSOR_ID["kl"]
+
+
+@pytest.mark.parametrize("field,value", [("nx", 0), ("ny", -1), ("tau", 0.5), ("tile", 12),
+                                         ("precision", 7), ("refine_sensor", 13),
+                                         ("output_every", -2), ("record_mask", 1 << 13),
+                                         ("own_stream", 2)])
+def test_create_rejects_bad_config_before_touching_the_gpu(field, value):
+    import ctypes
+
+    from paper_2603_13618_gb300 import kss
+
+    lib = kss.load()
+    cfg = kss.Config()
+    lib.kss_config_default(cfg, 64, 32, kss.FP32)
+    setattr(cfg, field, value)
+    h = ctypes.c_void_p()
+    rc = lib.kss_create(cfg, ctypes.byref(h))
+    assert rc < 0 and not h.value

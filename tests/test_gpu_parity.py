@@ -1,0 +1,295 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle, element
+by element, on seeded synthetic inputs.  Tolerances: see tests/parity.py."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_13618_gb300 import inputs
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+ALL = tuple(range(13))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2603_13618_gb300 import kss
+
+    kss.load()
+    yield
+
+
+def _kss():
+    from paper_2603_13618_gb300 import kss
+
+    return kss
+
+
+def _oracle_run(rho, ux, uy, tau, nsteps):
+    """(state before the last step, final state) of the oracle."""
+    f = oracle.init_equilibrium(rho, ux, uy)
+    prev = f
+    for _ in range(nsteps):
+        prev = f
+        f = oracle.step(f, tau)
+    return prev, f
+
+
+def _check_step_outputs(lat, prec, prev, tau, nsteps, thr_r, thr_s, tile, sensors=ALL,
+                        refine="kn", switch="neq"):
+    """Sensors, flags, tiles, counts and sums of the last step vs the oracle."""
+    ref, nonpos = oracle.sensor_fields(prev, tau, pull=nsteps > 0)
+    ft = oracle.stream(prev) if nsteps > 0 else prev
+    r, u, v = oracle.moments(ft)
+    kn = ref[oracle.SENSOR_ID["kn"]]
+    for sid in sensors:
+        name = parity.SENSORS[sid]
+        got = lat.read_sensor(name)
+        parity.assert_sensor_close(name, got, ref[sid], prec, nsteps, r, u, v, kn, tau)
+    er, es = ref[oracle.SENSOR_ID[refine]], ref[oracle.SENSOR_ID[switch]]
+    rf, rt, rcnt = oracle.flags(er, thr_r, es, thr_s, nonpos, tile)
+    flags, tiles, counts = lat.read_flags()
+    band = parity.band_mask(er, thr_r, es, thr_s)
+    parity.assert_flags_match(flags, tiles, counts, rf, rt, rcnt, band, tile)
+    sums, c2, step = lat.read_stats()
+    np.testing.assert_array_equal(c2, counts)
+    assert step == nsteps
+    want = oracle.sums(ft)
+    scale = want[0]
+    tol = 64 * parity.UNIT_ROUNDOFF[prec] * math.sqrt(nsteps + 1) * scale
+    assert np.all(np.abs(sums - want) <= tol), (sums, want)
+
+
+@pytest.mark.parametrize("nx,ny,tile,tau", [(37, 21, 16, 0.7), (64, 64, 8, 0.55),
+                                            (130, 67, 32, 1.0), (1, 5, 8, 0.8),
+                                            (5, 1, 8, 0.8), (200, 9, 64, 0.6),
+                                            (3, 3, 16, 0.9)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_ragged_lattices(prec, nx, ny, tile, tau):
+    kss = _kss()
+    rho, ux, uy = inputs.smooth_jump(nx, ny, seed=nx * 1000 + ny, kmax=3)
+    nsteps = 7
+    prev, fin = _oracle_run(rho, ux, uy, tau, nsteps)
+    thr_r, thr_s = 2e-3, 3e-4
+    lat = kss.Lattice(nx, ny, precision=prec, tau=tau, refine_threshold=thr_r,
+                      switch_threshold=thr_s, record=("kl", "kn", "neq"), tile=tile)
+    lat.set_fields(rho, ux, uy)
+    lat.step(nsteps)
+    got = lat.get_populations()
+    u = parity.UNIT_ROUNDOFF[prec]
+    assert np.max(np.abs(got - fin) / fin) <= 64 * u * math.sqrt(nsteps + 1)
+    r, vx, vy = lat.read_moments()
+    rr, ru, rv = oracle.moments(fin)
+    assert np.max(np.abs(r - rr) / rr) <= 64 * u * math.sqrt(nsteps + 1)
+    _check_step_outputs(lat, prec, prev, tau, nsteps, thr_r, thr_s, tile)
+    lat.close()
+
+
+def test_cfg1_shear_wave_fp64_2000_steps():
+    """128^2 FP64 shear wave, tau = 0.8, 2000 steps, sensors and flags every 10 steps."""
+    kss = _kss()
+    nx = ny = 128
+    tau, thr = 0.8, 1e-3
+    rho, ux, uy = inputs.shear_wave(nx, ny, 0.01)
+    lat = kss.Lattice(nx, ny, precision="fp64", tau=tau, refine_sensor="kn",
+                      refine_threshold=thr, switch_sensor="neq", switch_threshold=1e-4,
+                      record=("kn", "kl"), output_every=10, tile=16)
+    lat.set_fields(rho, ux, uy)
+    f = oracle.init_equilibrium(rho, ux, uy)
+    done = 0
+    checkpoints = (10, 50, 500, 1000, 2000)
+    for t in checkpoints:
+        f_prev = oracle.step(f, tau, t - 1 - done) if t - 1 > done else f
+        f = oracle.step(f_prev, tau, 1)
+        lat.step(t - done)
+        done = t
+        got = lat.get_populations()
+        assert np.max(np.abs(got - f) / f) <= 1e-12
+        r, vx, vy = lat.read_moments()
+        rr, ru, rv = oracle.moments(f)
+        assert np.max(np.abs(r - rr) / rr) <= 1e-12
+        assert np.max(np.abs(vx - ru)) <= 1e-12 * np.max(np.abs(ru))
+        _check_step_outputs(lat, "fp64", f_prev, tau, t, thr, 1e-4, 16,
+                            sensors=(oracle.SENSOR_ID["kn"], oracle.SENSOR_ID["kl"],
+                                     oracle.SENSOR_ID["neq"]))
+    lat.close()
+
+
+@pytest.mark.parametrize("tau", [0.51, 0.6, 0.8, 1.0])
+def test_fp32_smooth_jump_100_steps(tau):
+    """FP32 moments within 1e-5 (relative) of the FP64 oracle after 100 steps, on the
+    density-jump workload at a size the oracle finishes in seconds."""
+    kss = _kss()
+    nx, ny, nsteps = 192, 160, 100
+    rho, ux, uy = inputs.smooth_jump(nx, ny, seed=2603, kmax=8)
+    prev, fin = _oracle_run(rho, ux, uy, tau, nsteps)
+    lat = kss.Lattice(nx, ny, precision="fp32", tau=tau, record=("kl",))
+    lat.set_fields(rho, ux, uy)
+    lat.step(nsteps)
+    r, vx, vy = lat.read_moments()
+    rr, ru, rv = oracle.moments(fin)
+    assert np.max(np.abs(r - rr) / rr) <= 1e-5
+    umax = np.max(np.hypot(ru, rv))
+    assert np.max(np.abs(r * vx - rr * ru)) <= 1e-5 * np.max(rr) * umax
+    assert np.max(np.abs(r * vy - rr * rv)) <= 1e-5 * np.max(rr) * umax
+    _check_step_outputs(lat, "fp32", prev, tau, nsteps, 1e-3, 1e-4, 16)
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sensors_on_the_same_state(prec):
+    """Sensor arithmetic alone: the oracle evaluates the GPU's own stored populations."""
+    kss = _kss()
+    nx, ny, tau = 96, 80, 0.65
+    rho, ux, uy = inputs.smooth_jump(nx, ny, seed=44, kmax=6)
+    lat = kss.Lattice(nx, ny, precision=prec, tau=tau, record=())
+    lat.set_fields(rho, ux, uy)
+    lat.step(20)
+    state = lat.get_populations()          # exact (FP32 values widen exactly)
+    lat.set_populations(state)             # no step since set: sensors of the stored state
+    ref, nonpos = oracle.sensor_fields(state, tau, pull=False)
+    r, u, v = oracle.moments(state)
+    for sid in ALL:
+        name = parity.SENSORS[sid]
+        parity.assert_sensor_close(name, lat.read_sensor(name), ref[sid], prec, 0, r, u, v,
+                                   ref[oracle.SENSOR_ID["kn"]], tau)
+    lat.close()
+
+
+def test_zero_at_equilibrium_and_rest_state():
+    kss = _kss()
+    rho, ux, uy = inputs.random_smooth(40, 24, seed=3)
+    for prec in ("fp64", "fp32"):
+        lat = kss.Lattice(40, 24, precision=prec, tau=0.9)
+        lat.set_fields(rho, ux, uy)
+        for name in ("kn", "kl", "neq", "tau_ns", "alpha"):
+            assert np.max(np.abs(lat.read_sensor(name))) <= (1e-13 if prec == "fp64" else 2e-5)
+        fl, tiles, counts = lat.read_flags()
+        assert not fl.any() and not tiles.any() and not counts.any()
+        lat.close()
+    # uniform rest state: a fixed point, bit for bit
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    f = np.ascontiguousarray(np.broadcast_to((1.25 * w)[:, None, None], (9, 8, 12)))
+    lat = kss.Lattice(12, 8, precision="fp64", tau=0.7)
+    lat.set_populations(f)
+    lat.step(5)
+    np.testing.assert_array_equal(lat.get_populations(), f)
+    lat.close()
+
+
+def test_nonpositive_convention():
+    kss = _kss()
+    nx, ny, tau = 24, 16, 0.8
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    f = np.ascontiguousarray(np.broadcast_to(w[:, None, None], (9, ny, nx))).copy()
+    f[5, 3, 4] = -1e-3
+    f[0, 3, 4] += 1e-3 + 1 / 36
+    for prec in ("fp64", "fp32"):
+        lat = kss.Lattice(nx, ny, precision=prec, tau=tau)
+        lat.set_populations(f)
+        kn = lat.read_sensor("kn")
+        assert lat.last_status == kss.KSS_WARN_NONPOSITIVE
+        assert kn[3, 4] == math.inf and np.isfinite(np.delete(kn.ravel(), 3 * nx + 4)).all()
+        for name in ("hr", "kl", "sigma_h", "sigma_kl", "alpha"):
+            assert lat.read_sensor(name)[3, 4] == math.inf
+        assert np.isfinite(lat.read_sensor("neq")).all()
+        fl, tiles, counts = lat.read_flags()
+        assert fl[3, 4] == kss.FLAG_NONPOS | kss.FLAG_REFINE | kss.FLAG_SWITCH
+        assert counts[2] == 1 and counts[0] == 1
+        lat.close()
+
+
+def test_conservation_and_reproducibility_fp64():
+    kss = _kss()
+    nx, ny, tau = 256, 200, 0.6
+    rho, ux, uy = inputs.smooth_jump(nx, ny, seed=9, kmax=8)
+    sums = []
+    for _ in range(2):
+        lat = kss.Lattice(nx, ny, precision="fp64", tau=tau, output_every=50)
+        lat.set_fields(rho, ux, uy)
+        s0 = lat.read_stats()[0]
+        lat.step(500)
+        s1, _, step = lat.read_stats()
+        assert step == 500
+        assert np.all(np.abs(s1 - s0) <= 4 * 2.0**-52 * 500 * s0[0])
+        sums.append(s1)
+        lat.close()
+    np.testing.assert_array_equal(sums[0], sums[1])  # fixed-order reductions
+
+
+def test_device_pointer_paths():
+    import torch
+
+    kss = _kss()
+    nx, ny, tau = 80, 48, 0.75
+    rho, ux, uy = inputs.smooth_jump(nx, ny, seed=12, kmax=4)
+    prev, fin = _oracle_run(rho, ux, uy, tau, 3)
+    lat = kss.Lattice(nx, ny, precision="fp64", tau=tau)
+    lat.set_fields(*(torch.from_numpy(a).cuda() for a in (rho, ux, uy)))
+    lat.step(3)
+    f_dev = lat.get_populations(device=True)
+    assert f_dev.is_cuda
+    np.testing.assert_allclose(f_dev.cpu().numpy(), fin, rtol=1e-13)
+    kl = lat.read_sensor("kl", device=True).cpu().numpy()
+    np.testing.assert_allclose(kl, lat.read_sensor("kl"), rtol=0, atol=0)
+    fl_d, t_d, c_d = lat.read_flags(device=True)
+    fl_h, t_h, c_h = lat.read_flags()
+    np.testing.assert_array_equal(fl_d.cpu().numpy(), fl_h)
+    np.testing.assert_array_equal(t_d.cpu().numpy(), t_h)
+    # populations round trip through device memory, then identical continuation
+    lat.set_populations(f_dev)
+    lat.step(2)
+    np.testing.assert_allclose(lat.get_populations(), oracle.step(fin, tau, 2), rtol=1e-13)
+    lat.close()
+
+
+def test_plain_steps_and_output_cadence():
+    """output_every = 0 runs plain stream + collide; reads then evaluate on demand."""
+    kss = _kss()
+    nx, ny, tau = 64, 40, 0.7
+    rho, ux, uy = inputs.smooth_jump(nx, ny, seed=21, kmax=4)
+    prev, fin = _oracle_run(rho, ux, uy, tau, 9)
+    for every in (0, 4):
+        lat = kss.Lattice(nx, ny, precision="fp64", tau=tau, output_every=every,
+                          record=("kl",))
+        lat.set_fields(rho, ux, uy)
+        lat.step(9)
+        np.testing.assert_allclose(lat.get_populations(), fin, rtol=1e-13)
+        _check_step_outputs(lat, "fp64", prev, tau, 9, 1e-3, 1e-4, 16)
+        lat.close()
+
+
+def test_switch_disabled_and_other_sensors_drive_flags():
+    kss = _kss()
+    nx, ny, tau = 72, 56, 0.6
+    rho, ux, uy = inputs.smooth_jump(nx, ny, seed=5, kmax=5)
+    prev, _ = _oracle_run(rho, ux, uy, tau, 6)
+    lat = kss.Lattice(nx, ny, precision="fp64", tau=tau, refine_sensor="alpha",
+                      refine_threshold=1e-4, switch_sensor="kl", switch_threshold=-1.0,
+                      record=("sigma_h", "tau_ns"))
+    lat.set_fields(rho, ux, uy)
+    lat.step(6)
+    _check_step_outputs(lat, "fp64", prev, tau, 6, 1e-4, -1.0, 16, refine="alpha",
+                        switch="kl")
+    fl, tiles, counts = lat.read_flags()
+    assert not (fl & 2).any() and counts[1] == 0
+    lat.close()
+
+
+def test_library_owned_stream():
+    kss = _kss()
+    nx, ny, tau = 50, 30, 0.8
+    rho, ux, uy = inputs.smooth_jump(nx, ny, seed=2, kmax=3)
+    prev, fin = _oracle_run(rho, ux, uy, tau, 4)
+    lat = kss.Lattice(nx, ny, precision="fp32", tau=tau, stream="own")
+    lat.set_fields(rho, ux, uy)
+    lat.step(4)
+    np.testing.assert_allclose(lat.get_populations(), fin, rtol=64 * 2.0**-24 * math.sqrt(5))
+    _check_step_outputs(lat, "fp32", prev, tau, 4, 1e-3, 1e-4, 16)
+    lat.close()
