@@ -63,3 +63,21 @@ def test_create_rejects_bad_config_before_touching_the_gpu(field, value):
     h = ctypes.c_void_p()
     rc = lib.kss_create(cfg, ctypes.byref(h))
     assert rc < 0 and not h.value
+
+
+def _prototypes():
+    src = open(os.path.join(ROOT, "include", "kss.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(kss_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src):
+        args = m.group(2).strip()
+        out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_arity_matches_header():
+    from paper_2603_13618_gb300 import kss
+
+    protos = _prototypes()
+    for name, (_, argtypes) in kss._SIGNATURES.items():
+        assert len(argtypes) == protos[name], (name, len(argtypes), protos[name])
