@@ -166,6 +166,48 @@ const char* kss_last_error(const kss_lattice* lat);
 /* Library version (major * 10000 + minor * 100 + patch). */
 int kss_version(void);
 
+/* ---- Allocation-free fused step (no counterpart in the paper) ----------------------
+ * For callers that cannot call cudaMalloc: code that owns all device memory itself
+ * (a pool or framework allocator whose buffers it hands in), or that must not allocate
+ * while it runs.  One FP32 fused step -- pull streaming, BGK collision, the Kn / KL /
+ * neq sensors, flags, tile counts and conservation sums, the same kernel as kss_step
+ * with the {Kn, KL, neq} sensor set -- on buffers the caller provides.  The kernel's
+ * scratch (per-CTA partial sums and counts, a CTA completion counter) lives in a fixed
+ * array with static storage in this library's device code, of about 640 KiB, which
+ * every GPU that loads the library holds until the process exits.  The call allocates
+ * nothing (no cudaMalloc, cudaFree or allocating library routine).
+ *
+ * Buffers (device memory of the current device, owned by the caller):
+ *   f_in, f_out   populations [9][ny][pitch] floats, 16-byte aligned, distinct; the
+ *                 step reads f_in and writes f_out; pitch >= nx, a multiple of 32
+ *   sensor_out    the record_sensor field [ny][pitch] floats (16-byte aligned), or NULL
+ *   flags         [ny][pitch] bytes (KSS_FLAG_*), 4-byte aligned
+ *   tile_counts   int32 [2][ceil(ny/tile)][ceil(nx/tile)] (refine, switch)
+ *   sums, counts  double[3] {sum rho, sum rho ux, sum rho uy} and uint64[3]
+ *                 {refine, switch, non-positive}
+ * refine_sensor, switch_sensor and record_sensor must be KSS_S_KN, KSS_S_KL or
+ * KSS_S_NEQ; switch_threshold < 0 disables the switch flag; tile is 8, 16, 32 or 64.
+ * Asynchronous on `stream` (NULL = the default stream).
+ *
+ * Limit: the launch has ceil(nx/128) * ceil(ny/tile) CTAs and the scratch holds
+ * KSS_NOALLOC_MAX_BLOCKS of them (4096 x 4096 with tile 16 uses 8192); larger problems
+ * are rejected with KSS_ERR_NOALLOC_CAPACITY before anything is launched (a larger tile
+ * uses fewer CTAs).
+ * The first call on each device looks up the device address of the scratch array
+ * (cudaGetSymbolAddress, with that device current); make that first call before any
+ * stream capture.  Every call shares the scratch array, which keeps the last call's
+ * contents (the call clears the counter it needs at zero): calls that overlap on the GPU,
+ * on any stream, race and give wrong sums and counts.
+ * Returns KSS_OK, KSS_ERR_ARG, KSS_ERR_NOALLOC_CAPACITY or KSS_ERR_CUDA. */
+#define KSS_NOALLOC_MAX_BLOCKS 16384
+#define KSS_ERR_NOALLOC_CAPACITY (-7)
+int kss_step_f32_noalloc(const float* f_in, float* f_out, int32_t nx, int32_t ny, int32_t pitch,
+                         double tau, int32_t refine_sensor, double refine_threshold,
+                         int32_t switch_sensor, double switch_threshold, int32_t tile,
+                         int32_t record_sensor, float* sensor_out, uint8_t* flags,
+                         int32_t* tile_counts, double* sums, unsigned long long* counts,
+                         void* stream);
+
 #ifdef __cplusplus
 }
 #endif

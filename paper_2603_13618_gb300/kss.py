@@ -66,6 +66,11 @@ _SIGNATURES = {
     "kss_read_stats": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "kss_get_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "kss_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "kss_step_f32_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                            ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                            ctypes.c_double, ctypes.c_int32, ctypes.c_int32]
+                             + [ctypes.c_void_p] * 6),
 }
 
 
