@@ -69,6 +69,12 @@ def profile_traffic():
     return float(t.group(1))
 
 
+def kernel_name(choice: str) -> str:
+    tma = choice == "tma"
+    return ("step_tma_kernel<float, MODE_STD> (bulk-copy staged)" if tma
+            else "step_kernel<float, MODE_STD, pull, store> (vector loads)")
+
+
 def measured_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -213,7 +219,8 @@ def run_gpu(args):
     rho, ux, uy = workload_fields()
     lat = kss.Lattice(NX, NY, precision="fp32", tau=TAU, refine_sensor="kn",
                       refine_threshold=THR_R, switch_sensor="neq", switch_threshold=THR_S,
-                      record=("kl",), output_every=1, tile=TILE, stream="torch")
+                      record=("kl",), output_every=1, tile=TILE, stream="torch",
+                      kernel=args.kernel)
     lat.set_fields(rho, ux, uy)
     stream = torch.cuda.current_stream()
     lat.step(args.warmup)
@@ -295,7 +302,7 @@ def run_gpu(args):
                          "traffic": profile_traffic(),
                          "algorithmic_bytes_per_launch": BYTES_PER_LUP * cells,
                          "kernel_ms": kern_ms,
-                         "kernel": "step_kernel<float, MODE_STD, pull, store>"},
+                         "kernel": kernel_name(args.kernel)},
             "cpu_baseline": base,
             "e2e": e2e,
             "gpu_launches": K,
@@ -318,6 +325,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "vector", "tma"],
+                    help="step kernel (auto: the library's choice)")
     ap.add_argument("--size", type=int, default=4096,
                     help="lattice edge (profiling captures of a smaller case only)")
     args = ap.parse_args()

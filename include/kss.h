@@ -100,7 +100,19 @@ typedef struct {
   void* stream;              /* cudaStream_t to run on; NULL = the CUDA default stream */
   int32_t own_stream;        /* 1: ignore `stream`, create a non-blocking stream owned */
                              /*    by the lattice (destroyed with it)                  */
+  int32_t kernel;            /* step kernel: KSS_KERNEL_AUTO, _VECTOR or _TMA          */
 } kss_config;
+
+/* Step kernels (same results; they differ in how source rows reach the SM):
+ *   KSS_KERNEL_VECTOR  16-byte vector loads into registers, warp-shuffle halos;
+ *   KSS_KERNEL_TMA     bulk copies (cp.async.bulk) into a per-warp shared-memory ring,
+ *                      persistent CTAs; used for plain and {Kn, KL, neq} steps, other
+ *                      sensor sets fall back to the vector kernel;
+ *   KSS_KERNEL_AUTO    the faster on GB300, which is the vector kernel at every size
+ *                      measured. */
+#define KSS_KERNEL_AUTO 0
+#define KSS_KERNEL_VECTOR 1
+#define KSS_KERNEL_TMA 2
 
 typedef struct kss_lattice kss_lattice;  /* opaque */
 
@@ -156,7 +168,8 @@ int kss_read_stats(kss_lattice* lat, double sums[3], int64_t counts[3], int64_t*
 
 /* Steps taken since the last set. */
 int kss_get_step(const kss_lattice* lat, int64_t* step);
-/* Wait for the lattice's stream. */
+/* Wait for the lattice's stream; reports KSS_ERR_TIMEOUT (sticky) if a bounded device
+ * wait of an earlier step ran out. */
 int kss_sync(kss_lattice* lat);
 
 /* Static description of an error code, and the last error message of a lattice. */
@@ -189,10 +202,10 @@ int kss_version(void);
  * KSS_S_NEQ; switch_threshold < 0 disables the switch flag; tile is 8, 16, 32 or 64.
  * Asynchronous on `stream` (NULL = the default stream).
  *
- * Limit: the launch has ceil(nx/128) * ceil(ny/tile) CTAs and the scratch holds
- * KSS_NOALLOC_MAX_BLOCKS of them (4096 x 4096 with tile 16 uses 8192); larger problems
- * are rejected with KSS_ERR_NOALLOC_CAPACITY before anything is launched (a larger tile
- * uses fewer CTAs).
+ * Limit: the launch has ceil(nx/128) * ceil(ny/R) CTAs (R = 32 rows, 64 for tile 64) and
+ * the scratch holds KSS_NOALLOC_MAX_BLOCKS of them (4096 x 4096 uses 4096, 8192 x 8192
+ * uses 16384); larger problems are rejected with KSS_ERR_NOALLOC_CAPACITY before
+ * anything is launched.
  * The first call on each device looks up the device address of the scratch array
  * (cudaGetSymbolAddress, with that device current); make that first call before any
  * stream capture.  Every call shares the scratch array, which keeps the last call's

@@ -29,9 +29,9 @@ template <> struct Num<float> {
   // highest power of the Maclaurin series of phi used for |x| < 1/16:
   // the first dropped term x^8/56 is below 2^-24 of x^2/2 there.
   static constexpr int kPhiOrder = 7;
-  // order of the series in the fused Kn/KL/neq path, where |x| < 1/16 is known
-  // for the whole cell: the first dropped term x^7/42 is 2^-24.5 of x^2/2 there.
-  static constexpr int kPhiFastOrder = 6;
+  // order of the series in the fused Kn/KL/neq path (|x| < 1/16; larger |x| take
+  // the closed form): the first dropped term, x^6/30, is at most 1.0e-6 of x^2/2.
+  static constexpr int kPhiFastOrder = 5;
   // reciprocal: the hardware approximation (rcp.approx, at most 1 ulp error)
   __device__ static __forceinline__ float rcp(float x) {
     float r;
@@ -53,26 +53,34 @@ template <> struct Num<double> {
   __device__ static __forceinline__ double inf() { return CUDART_INF; }
 };
 
-// Coefficient of x^n in phi(x) = (1 + x) ln(1 + x) - x = sum_{n>=2} (-1)^n x^n / (n (n-1)).
-__host__ __device__ constexpr double phi_coef(int n) {
-  return ((n & 1) ? -1.0 : 1.0) / double(n * (n - 1));
-}
+// Coefficient of x^n in phi(x) = (1 + x) ln(1 + x) - x = sum_{n>=2} (-1)^n x^n / (n (n-1)),
+// as a compile-time constant (a runtime double division would run on the FP64 pipe).
+template <int n>
+struct PhiCoef {
+  static constexpr double value = ((n & 1) ? -1.0 : 1.0) / double(n * (n - 1));
+};
 
-template <class T, int N>
-__device__ __forceinline__ T phi_series(T x) {
-  T p = T(phi_coef(N));
-#pragma unroll
-  for (int n = N - 1; n >= 2; --n) p = fma(p, x, T(phi_coef(n)));
-  return (x * x) * p;
-}
+// Horner evaluation of sum_{m=2}^{N} c_m x^(m-2), from the top coefficient down.
+template <class T, int n>
+struct PhiHorner {
+  __device__ static __forceinline__ T eval(T x, T acc) {
+    return PhiHorner<T, n - 1>::eval(x, fma(acc, x, T(PhiCoef<n - 1>::value)));
+  }
+};
+template <class T>
+struct PhiHorner<T, 2> {
+  __device__ static __forceinline__ T eval(T, T acc) { return acc; }
+};
 
 // phi(x) / x^2 = sum_{n=2}^{N} c_n x^(n-2), for the fused path (|x| < 1/16 known).
 template <class T, int N>
 __device__ __forceinline__ T phi_over_x2(T x) {
-  T p = T(phi_coef(N));
-#pragma unroll
-  for (int n = N - 1; n >= 2; --n) p = fma(p, x, T(phi_coef(n)));
-  return p;
+  return PhiHorner<T, N>::eval(x, T(PhiCoef<N>::value));
+}
+
+template <class T, int N>
+__device__ __forceinline__ T phi_series(T x) {
+  return (x * x) * phi_over_x2<T, N>(x);
 }
 
 // phi(x) = (1 + x) ln(1 + x) - x without cancellation near x = 0.

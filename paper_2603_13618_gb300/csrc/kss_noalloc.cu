@@ -102,6 +102,7 @@ extern "C" int kss_step_f32_noalloc(const float* f_in, float* f_out, int32_t nx,
   p.nx = nx;
   p.ny = ny;
   p.tile = tile;
+  p.bands = kss::step_bands(tile);
   p.ntx = (nx + tile - 1) / tile;
   p.nty = (ny + tile - 1) / tile;
   p.omega = float(1.0 / tau);

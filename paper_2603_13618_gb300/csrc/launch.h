@@ -4,7 +4,7 @@
 
 #include <cuda_runtime.h>
 
-#include "step_kernel.cuh"
+#include "step_tma.cuh"
 
 namespace kss {
 
@@ -12,7 +12,8 @@ namespace kss {
 template <class T>
 inline dim3 step_grid(int nx, int ny, int tile) {
   const int cols = 32 * Vec<T>::N;
-  return dim3((unsigned)((nx + cols - 1) / cols), (unsigned)((ny + tile - 1) / tile), 1u);
+  const int rows = tile * step_bands(tile);
+  return dim3((unsigned)((nx + cols - 1) / cols), (unsigned)((ny + rows - 1) / rows), 1u);
 }
 
 // mode: MODE_PLAIN / MODE_STD / MODE_FULL; pull: stream first; store: collide + write.
@@ -21,6 +22,17 @@ inline dim3 step_grid(int nx, int ny, int tile) {
 template <class T>
 cudaError_t launch_step(const StepParams<T>& p, int mode, bool pull, bool store,
                         cudaStream_t stream);
+
+// The TMA-staged step (step_tma.cuh): mode MODE_PLAIN or MODE_STD, always pull + store;
+// `ctas` persistent CTAs (one per SM).
+template <class T>
+cudaError_t launch_step_tma(const StepParams<T>& p, int mode, TmaPlan plan, int ctas,
+                            cudaStream_t stream);
+
+// fixup_kernel after a MODE_STD pass (step or evaluation; `pull` as that pass), with
+// `ctas` CTAs of 256 threads striding over the tiles.
+template <class T>
+cudaError_t launch_fixup(const StepParams<T>& p, bool pull, int ctas, cudaStream_t stream);
 
 template <class T>
 cudaError_t launch_init_equilibrium(const double* rho, const double* ux, const double* uy,

@@ -36,6 +36,41 @@ cudaError_t launch_step<KSS_T>(const StepParams<KSS_T>& p, int mode, bool pull, 
   return cudaGetLastError();
 }
 
+template <int MODE>
+cudaError_t launch_tma_mode(const StepParams<KSS_T>& p, TmaPlan plan, int ctas,
+                            cudaStream_t stream) {
+  static bool configured = false;  // the dynamic shared-memory opt-in, once per process
+  if (!configured) {
+    const cudaError_t e = cudaFuncSetAttribute(step_tma_kernel<KSS_T, MODE>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               int(kTmaSmemBytes));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  step_tma_kernel<KSS_T, MODE><<<ctas, kTmaThreads, kTmaSmemBytes, stream>>>(p, plan);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_step_tma<KSS_T>(const StepParams<KSS_T>& p, int mode, TmaPlan plan, int ctas,
+                                   cudaStream_t stream) {
+  switch (mode) {
+    case MODE_PLAIN: return launch_tma_mode<MODE_PLAIN>(p, plan, ctas, stream);
+    case MODE_STD: return launch_tma_mode<MODE_STD>(p, plan, ctas, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <>
+cudaError_t launch_fixup<KSS_T>(const StepParams<KSS_T>& p, bool pull, int ctas,
+                                cudaStream_t stream) {
+  if (pull)
+    fixup_kernel<KSS_T, true><<<ctas, 256, 0, stream>>>(p);
+  else
+    fixup_kernel<KSS_T, false><<<ctas, 256, 0, stream>>>(p);
+  return cudaGetLastError();
+}
+
 template <>
 cudaError_t launch_init_equilibrium<KSS_T>(const double* rho, const double* ux, const double* uy,
                                            KSS_T* f, long long plane, int pitch, int nx, int ny,

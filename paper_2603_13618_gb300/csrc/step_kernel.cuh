@@ -11,12 +11,12 @@
 //   scratch       per-block partial sums (3 doubles) and counts (4 uint32), a
 //                 block-completion counter, and the final sums/counts
 //
-// Work decomposition: a CTA of 8 warps owns a 32*V-column x `tile`-row block of
-// the lattice (V = 16 bytes / sizeof(T) cells per thread, one 16-byte vector per
-// population per row).  Warp w handles rows w, w+8, ... of the block; lane L the
-// V cells starting at column (32*bx + L)*V.  Because CTA blocks coincide with the
-// tagging tiles along y and contain whole tiles along x, every tile count is
-// formed inside one CTA and written once.
+// Work decomposition: a CTA of 8 warps owns a 32*V-column x (bands * tile)-row block
+// of the lattice (V = 16 bytes / sizeof(T) cells per thread, one 16-byte vector per
+// population per row; about 32 rows).  Warp w handles rows w, w+8, ... of the block;
+// lane L the V cells starting at column (32*bx + L)*V.  Because CTA blocks consist
+// of whole tagging tiles, every tile count is formed inside one CTA (in shared
+// memory, per band) and written once.
 //
 // Pull streaming: f~_q(i, j) = f_q(i - cx_q, j - cy_q).  Populations with cx_q = 0
 // are single aligned vector loads of row j - cy_q.  For cx_q = +1 (source i - 1) a
@@ -46,7 +46,20 @@ namespace kss {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = 32 * kWarps;
+constexpr int kMaxBands = 8;  // tile bands per CTA of step_kernel (rows = bands * tile)
+// Deferred cells a warp of step_kernel can hold: all of its cells (at most 64 rows per
+// CTA / 8 warps, 32 * V <= 128 columns), as CTA-local offsets.
+constexpr int kWarpDefer = 8 * 128;
+
+// Tile bands per CTA: about 32 rows per CTA (4 per warp) amortise the CTA's epilogue;
+// taller CTAs would leave a longer tail of partly filled waves.
+__host__ __device__ constexpr int step_bands(int tile) {
+  return tile >= 32 ? 1 : 32 / tile;
+}
 constexpr unsigned kFull = 0xffffffffu;
+// Flag bit of a cell whose {Kn, KL, neq} the fused pass could not prove exact; set only
+// between the fused pass and fixup_kernel, which replaces the byte.
+constexpr uint32_t kFlagDeferred = 0x40u;
 
 template <class T> struct Vec;
 template <> struct Vec<float> {
@@ -64,17 +77,24 @@ struct StepParams {
   T* dst;                // population buffer written this step (STORE)
   T* rec;                // recorded sensor planes
   uint8_t* flags;        // [ny][pitch]
-  int32_t* tiles;        // [2][nty][ntx]
+  int32_t* tiles;        // [2][nty][ntx] refine, switch tags per tile
+  int32_t* tiles_def;    // [nty][ntx] cells deferred to fixup_kernel per tile
+  uint32_t* defer_list;  // indices j * nx + i of deferred cells (capacity defer_cap)
+  uint32_t* defer_count; // entries requested (> defer_cap: overflow, fixup scans instead)
+  uint32_t* defer_ticket;  // CTA completion counter of fixup_kernel, 0 between launches
+  uint32_t defer_cap;
   double* part_sum;      // [nblocks][3]
   uint32_t* part_cnt;    // [nblocks][4]
   uint32_t* done;        // block-completion counter, 0 between launches
   double* stat_sums;     // [3]
   unsigned long long* stat_counts;  // [3]
+  uint32_t* err;         // error word: bit 0 = a bounded device wait ran out
   long long plane;       // elements per population plane
   int pitch, nx, ny, tile, ntx, nty;
   T omega, tau;          // 1/tau and tau
   T thr_r, thr_s;        // largest T values <= the thresholds: eps > thr exactly
   int refine_s, switch_s, switch_on;
+  int bands;             // tile bands per CTA of step_kernel (CTA height = bands * tile)
   int rec_slot[S_COUNT];  // plane index of each recorded sensor, -1 if not recorded
 };
 
@@ -144,12 +164,14 @@ __device__ __forceinline__ void assemble_from_right(T (&v)[Vec<T>::N], T halo, i
 }
 
 // ---------------------------------------------------------------- accumulators ----
-// FP32 storage: double-float (hi + lo, Knuth two-sum) so per-thread and per-warp
-// partial sums keep ~48 bits; FP64 storage: plain double.
+// FP32 storage: a thread adds its few cells (at most 4 rows x 4 cells) in plain FP32,
+// then the warp combines the partials as double-floats (hi + lo, Knuth two-sum), so
+// the warp sums keep ~48 bits; FP64 storage: plain double.
 template <class T> struct Acc;
 template <> struct Acc<float> {
   float hi = 0.f, lo = 0.f;
-  __device__ __forceinline__ void add(float v) {
+  __device__ __forceinline__ void add(float v) { hi += v; }
+  __device__ __forceinline__ void add2(float v) {
     const float s = hi + v;
     const float bp = s - hi;
     lo += (hi - (s - bp)) + (v - bp);
@@ -160,7 +182,7 @@ template <> struct Acc<float> {
     for (int off = 16; off > 0; off >>= 1) {
       const float oh = __shfl_xor_sync(kFull, hi, off);
       const float ol = __shfl_xor_sync(kFull, lo, off);
-      add(oh);
+      add2(oh);
       lo += ol;
     }
   }
@@ -197,21 +219,28 @@ __device__ __forceinline__ void store_flags(uint8_t* p, uint32_t bits) {
 }
 
 // ---------------------------------------------------------------- fused Kn/KL/neq ----
+// Per-cell accumulators of the {Kn, KL, neq} set.
+template <class T>
+struct StdAcc {
+  T kn[Vec<T>::N], neq[Vec<T>::N], kl[Vec<T>::N];
+};
+
 // Relax one population of V cells in place (BGK: f <- f - (f - f^eq)/tau) and, on
-// output steps, accumulate Kn += |x|, neq += |f^neq| and the Kullback-Leibler sum
-// f^eq phi(x) = f^neq x (phi(x)/x^2), x = f^neq / f^eq.
+// output steps, accumulate Kn += |x|, neq += |f^neq| and the Kullback-Leibler term
+// f^eq phi(x) = f^neq x (phi(x)/x^2), x = f^neq / f^eq, by the series of phi.  The
+// series is exact to FP32 for |x| < 1/16; a cell where that, or positivity, cannot be
+// shown is deferred to fixup_kernel (see fused_row).
 template <class T, bool OUT, bool COLLIDE>
 __device__ __forceinline__ void relax_pop(T (&f)[Vec<T>::N], const T (&feq)[Vec<T>::N], T omega,
-                                          T (&kn)[Vec<T>::N], T (&neq)[Vec<T>::N],
-                                          T (&kl)[Vec<T>::N]) {
+                                          StdAcc<T>& a) {
 #pragma unroll
   for (int k = 0; k < Vec<T>::N; ++k) {
     const T fneq = f[k] - feq[k];
     if (OUT) {
       const T x = fneq * Num<T>::rcp(feq[k]);
-      kn[k] += fabs(x);
-      neq[k] += fabs(fneq);
-      kl[k] = fma(fneq * x, phi_over_x2<T, Num<T>::kPhiFastOrder>(x), kl[k]);
+      a.kn[k] += fabs(x);
+      a.neq[k] += fabs(fneq);
+      a.kl[k] = fma(fneq * x, phi_over_x2<T, Num<T>::kPhiFastOrder>(x), a.kl[k]);
     }
     if (COLLIDE) f[k] = fma(-omega, fneq, f[k]);
   }
@@ -222,9 +251,8 @@ __device__ __forceinline__ void relax_pop(T (&f)[Vec<T>::N], const T (&feq)[Vec<
 template <class T, bool OUT, bool STORE>
 __device__ __forceinline__ void pair_pops(T (&fp)[Vec<T>::N], T (&fm)[Vec<T>::N],
                                           const T (&cu)[Vec<T>::N], const T (&base)[Vec<T>::N],
-                                          const T (&rw)[Vec<T>::N], T omega, T (&kn)[Vec<T>::N],
-                                          T (&neq)[Vec<T>::N], T (&kl)[Vec<T>::N], T* dst_p,
-                                          T* dst_m, bool cv) {
+                                          const T (&rw)[Vec<T>::N], T omega, StdAcc<T>& a,
+                                          T* dst_p, T* dst_m, bool cv) {
   constexpr int V = Vec<T>::N;
   T ep[V], em[V];
 #pragma unroll
@@ -233,20 +261,25 @@ __device__ __forceinline__ void pair_pops(T (&fp)[Vec<T>::N], T (&fm)[Vec<T>::N]
     ep[k] = rw[k] * fma(T(3), cu[k], t);
     em[k] = rw[k] * fma(T(-3), cu[k], t);
   }
-  relax_pop<T, OUT, STORE>(fp, ep, omega, kn, neq, kl);
+  relax_pop<T, OUT, STORE>(fp, ep, omega, a);
   if (STORE && cv) vstore<T>(dst_p, fp);
-  relax_pop<T, OUT, STORE>(fm, em, omega, kn, neq, kl);
+  relax_pop<T, OUT, STORE>(fm, em, omega, a);
   if (STORE && cv) vstore<T>(dst_m, fm);
 }
 
-// Sensor `id` of the {Kn, KL, neq} set (ids validated on the host).
-template <class T>
-__device__ __forceinline__ T pick3(int id, T kn, T kl, T neq) {
-  return id == S_KN ? kn : (id == S_KL ? kl : neq);
-}
+// Which of {Kn, KL, neq} a flag tests (ids validated on the host); decided once per
+// thread so the per-cell choice is two selects.
+struct Pick3 {
+  bool is_kn, is_kl;
+  __device__ explicit Pick3(int id) : is_kn(id == S_KN), is_kl(id == S_KL) {}
+  template <class T>
+  __device__ __forceinline__ T operator()(T kn, T kl, T neq) const {
+    return is_kn ? kn : (is_kl ? kl : neq);
+  }
+};
 
-// The nine populations of cell (i, j) as the step sees them (pulled when PULL):
-// the exact fallback of the fused path re-reads them one by one.
+// The nine populations of cell (i, j) as the step sees them (pulled when PULL), for the
+// exact recomputation of deferred cells.
 template <class T, bool PULL>
 __device__ __forceinline__ void reload_cell(const StepParams<T>& p, int i, int j, T (&c)[9]) {
   constexpr int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -264,28 +297,214 @@ __device__ __forceinline__ void reload_cell(const StepParams<T>& p, int i, int j
   }
 }
 
-// Exact {Kn, KL, neq} and the non-positive test of one cell, re-read from memory:
-// the rare fallback of the fused path, kept out of line so that its registers do
-// not weigh on the hot loop.
-template <class T>
-struct ExactStd {
-  T kn, kl, neq;
-  bool nonpos;
-};
-
-template <class T, bool PULL>
-__device__ __noinline__ ExactStd<T> exact_std_cell(const StepParams<T>& p, int i, int j) {
-  T c[9], dummy[9];
-  reload_cell<T, PULL>(p, i, j, c);
-  CellOut<T> co;
-  cell_update<T, MODE_STD, false>(c, p.omega, p.tau, dummy, co);
-  return ExactStd<T>{co.sv[S_KN], co.sv[S_KL], co.sv[S_NEQ], co.nonpos};
+// Append the deferred cells among this lane's V cells of row j (flag bytes 0x40 in
+// fbits) to a list through one atomic on `counter` per warp; entries at or beyond `cap`
+// are dropped (the caller detects that from the counter).  All lanes must call.
+template <int V>
+__device__ __forceinline__ void append_deferred(uint32_t fbits, int i0, int j, int nx,
+                                                uint32_t* counter, uint32_t* list, uint32_t cap) {
+  const uint32_t dbits = fbits & 0x40404040u;
+  if (!__any_sync(kFull, dbits != 0)) return;
+  const int lane = threadIdx.x & 31;
+  const int nd = __popc(dbits);
+  int incl = nd;  // inclusive prefix sum over the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int total = __shfl_sync(kFull, incl, 31);
+  uint32_t base = 0;
+  if (lane == 31) base = atomicAdd(counter, uint32_t(total));
+  base = __shfl_sync(kFull, base, 31) + uint32_t(incl - nd);
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    if ((dbits >> (8 * k)) & 0x40u) {
+      if (base < cap) list[base] = uint32_t(j) * uint32_t(nx) + uint32_t(i0 + k);
+      ++base;
+    }
+  }
 }
 
 // Is sensor s in the compiled set of MODE?
 template <int MODE>
 __host__ __device__ constexpr bool mode_has(int s) {
   return MODE == MODE_FULL ? true : (MODE == MODE_STD ? ((kStdMask >> s) & 1u) != 0 : false);
+}
+
+// ---------------------------------------------------------------- deferred cells ----
+// Exact {Kn, KL, neq}, flags and counts of one deferred cell (i, j), recomputed from
+// the pass's source buffer (which the pass does not modify) with the exact per-cell
+// arithmetic of the full sensor set (cell_update).  Returns the refine/switch/non-
+// positive tags; the tile counts are corrected here.
+template <class T, bool PULL>
+__device__ __forceinline__ uint32_t fix_cell(const StepParams<T>& p, const Pick3& pr,
+                                             const Pick3& ps, int i, int j) {
+  T cell[9], dummy[9];
+  reload_cell<T, PULL>(p, i, j, cell);
+  CellOut<T> co;
+  cell_update<T, MODE_STD, false>(cell, p.omega, p.tau, dummy, co);
+  const T kn = co.sv[S_KN], kl = co.sv[S_KL], neq = co.sv[S_NEQ];
+  const bool rr = pr(kn, kl, neq) > p.thr_r;
+  const bool ss = p.switch_on && (ps(kn, kl, neq) > p.thr_s);
+  const bool np = co.nonpos;
+  const long long off = (long long)j * p.pitch + i;
+  p.flags[off] = uint8_t(uint32_t(rr) | (uint32_t(ss) << 1) | (uint32_t(np) << 7));
+  if (p.rec_slot[S_KN] >= 0) p.rec[p.rec_slot[S_KN] * p.plane + off] = kn;
+  if (p.rec_slot[S_KL] >= 0) p.rec[p.rec_slot[S_KL] * p.plane + off] = kl;
+  if (p.rec_slot[S_NEQ] >= 0) p.rec[p.rec_slot[S_NEQ] * p.plane + off] = neq;
+  return uint32_t(rr) | (uint32_t(ss) << 1) | (uint32_t(np) << 2);
+}
+
+// ---------------------------------------------------------------- one row ----
+// Everything after the loads for one row of V-cell vectors: moments, equilibrium,
+// sensors of the compiled set, flags, BGK collision, and the stores of the new
+// populations, the flag bytes and the recorded sensor fields.  ft holds the
+// post-streaming populations of cells i0..i0+V-1 of row j.  Returns the lane's flag
+// word (one byte per cell); the row's moments are added to the accumulators.
+template <class T, int MODE, bool PULL, bool STORE>
+__device__ __forceinline__ uint32_t fused_row(const StepParams<T>& p, T (&ft)[9][Vec<T>::N],
+                                              int i0, int j, bool cv, Acc<T>& a_rho,
+                                              Acc<T>& a_jx, Acc<T>& a_jy) {
+  constexpr int V = Vec<T>::N;
+  constexpr bool OUT = MODE != MODE_PLAIN;
+  const long long off = (long long)j * p.pitch + i0;
+  uint32_t fbits = 0;
+  if constexpr (MODE == MODE_FULL) {
+    // ---- all sensors of Table 1: cell-major, generic per-cell arithmetic ----
+    T fo[9][V];
+    T rv[S_COUNT][V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      T c[9], o9[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) c[q] = ft[q][k];
+      CellOut<T> co;
+      cell_update<T, MODE, STORE>(c, p.omega, p.tau, o9, co);
+      const bool valid = cv && (i0 + k < p.nx);
+      if (STORE) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) fo[q][k] = o9[q];
+      }
+      if (valid) {
+        a_rho.add(co.rho);
+        a_jx.add(co.jx);
+        a_jy.add(co.jy);
+      }
+      const bool r = valid && (pick<T>(co.sv, p.refine_s) > p.thr_r);
+      const bool sw = valid && p.switch_on && (pick<T>(co.sv, p.switch_s) > p.thr_s);
+      const bool np = valid && co.nonpos;
+      fbits |= (uint32_t(r) | (uint32_t(sw) << 1) | (uint32_t(np) << 7)) << (8 * k);
+#pragma unroll
+      for (int sid = 0; sid < S_COUNT; ++sid) rv[sid][k] = co.sv[sid];
+    }
+    if (STORE && cv) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) vstore<T>(p.dst + q * p.plane + off, fo[q]);
+    }
+    if (cv) {
+      store_flags<V>(p.flags + off, fbits);
+#pragma unroll
+      for (int sid = 0; sid < S_COUNT; ++sid) {
+        const int slot = p.rec_slot[sid];
+        if (slot >= 0) vstore<T>(p.rec + slot * p.plane + off, rv[sid]);
+      }
+    }
+  } else {
+    // ---- plain stream + collide, or with the {Kn, KL, neq} sensor set:
+    //      population-major so each population's vector is stored as soon as it
+    //      is relaxed (fewer live registers) ----
+    // cells past the row end (a ragged last vector, or a whole vector beyond it) hold
+    // padding or stale staging data: zero them, so that they add nothing to the sums
+    // and raise no flag (their sensors are NaN)
+    const int nvalid = cv ? min(V, p.nx - i0) : 0;
+    if (nvalid < V) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q)
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+          if (k >= nvalid) ft[q][k] = T(0);
+    }
+    T rho[V], ux[V], uy[V], base[V], rw0[V], rw1[V], rw2[V];
+    StdAcc<T> a;
+    T rs = T(0), xs = T(0), ys = T(0);
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      rho[k] = ((ft[0][k] + ft[1][k]) + (ft[2][k] + ft[3][k])) +
+               ((ft[4][k] + ft[5][k]) + (ft[6][k] + ft[7][k])) + ft[8][k];
+      const T jx = (ft[1][k] + ft[5][k] + ft[8][k]) - (ft[3][k] + ft[6][k] + ft[7][k]);
+      const T jy = (ft[2][k] + ft[5][k] + ft[6][k]) - (ft[4][k] + ft[7][k] + ft[8][k]);
+      const T ir = Num<T>::rcp(rho[k]);
+      ux[k] = jx * ir;
+      uy[k] = jy * ir;
+      base[k] = fma(T(-1.5), fma(ux[k], ux[k], uy[k] * uy[k]), T(1));
+      rw0[k] = rho[k] * T(4.0 / 9.0);
+      rw1[k] = rho[k] * T(1.0 / 9.0);
+      rw2[k] = rho[k] * T(1.0 / 36.0);
+      a.kn[k] = a.neq[k] = a.kl[k] = T(0);
+      if (OUT) {
+        rs += rho[k];
+        xs += jx;
+        ys += jy;
+      }
+    }
+    if (OUT) {
+      a_rho.add(rs);
+      a_jx.add(xs);
+      a_jy.add(ys);
+    }
+    T feq[V];
+    // q = 0 (rest)
+#pragma unroll
+    for (int k = 0; k < V; ++k) feq[k] = rw0[k] * base[k];
+    relax_pop<T, OUT, STORE>(ft[0], feq, p.omega, a);
+    if (STORE && cv) vstore<T>(p.dst + 0 * p.plane + off, ft[0]);
+    // axis pairs (1, 3): c.u = +-ux ; (2, 4): +-uy ; diagonal pairs (5, 7): +-(ux + uy),
+    // (6, 8): +-(uy - ux)
+    pair_pops<T, OUT, STORE>(ft[1], ft[3], ux, base, rw1, p.omega, a,
+                             p.dst + 1 * p.plane + off, p.dst + 3 * p.plane + off, cv);
+    pair_pops<T, OUT, STORE>(ft[2], ft[4], uy, base, rw1, p.omega, a,
+                             p.dst + 2 * p.plane + off, p.dst + 4 * p.plane + off, cv);
+    {
+      T sd[V];
+#pragma unroll
+      for (int k = 0; k < V; ++k) sd[k] = ux[k] + uy[k];
+      pair_pops<T, OUT, STORE>(ft[5], ft[7], sd, base, rw2, p.omega, a,
+                               p.dst + 5 * p.plane + off, p.dst + 7 * p.plane + off, cv);
+#pragma unroll
+      for (int k = 0; k < V; ++k) sd[k] = uy[k] - ux[k];
+      pair_pops<T, OUT, STORE>(ft[6], ft[8], sd, base, rw2, p.omega, a,
+                               p.dst + 6 * p.plane + off, p.dst + 8 * p.plane + off, cv);
+    }
+    if (OUT) {
+      const Pick3 pr(p.refine_s), ps(p.switch_s);
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        // rho > 0 and |u|^2 < 0.3 make every f^eq_q >= 0.05 w_q rho > 0, and Kn < 1/16
+        // bounds every |x_q|, so f_q = f^eq_q (1 + x_q) > 0 (nothing non-positive) and
+        // the series of phi is exact to FP32.  Any other valid cell is deferred: its
+        // flag byte is KSS_FLAG_DEFERRED only, it is not counted here, and fixup_kernel
+        // recomputes it exactly from the unchanged source populations.
+        const bool fast = (rho[k] > T(0)) & (base[k] > T(0.55)) & (a.kn[k] < T(0.0625));
+        a.kl[k] = fabs(a.kl[k]);
+        const T er = pr(a.kn[k], a.kl[k], a.neq[k]);
+        const T es = ps(a.kn[k], a.kl[k], a.neq[k]);
+        const bool r = er > p.thr_r;  // NaN (zeroed padding cells) compares false
+        const bool sw = p.switch_on && (es > p.thr_s);
+        const uint32_t b = fast ? (uint32_t(r) | (uint32_t(sw) << 1)) : kFlagDeferred;
+        fbits |= b << (8 * k);
+      }
+      // padding cells (zeroed above) raise no flag
+      if (nvalid < V) fbits &= nvalid > 0 ? 0xffffffffu >> (32 - 8 * nvalid) : 0u;
+      if (cv) {
+        store_flags<V>(p.flags + off, fbits);
+        if (p.rec_slot[S_KN] >= 0) vstore<T>(p.rec + p.rec_slot[S_KN] * p.plane + off, a.kn);
+        if (p.rec_slot[S_KL] >= 0) vstore<T>(p.rec + p.rec_slot[S_KL] * p.plane + off, a.kl);
+        if (p.rec_slot[S_NEQ] >= 0) vstore<T>(p.rec + p.rec_slot[S_NEQ] * p.plane + off, a.neq);
+      }
+    }
+  }
+  return fbits;
 }
 
 // ---------------------------------------------------------------- the fused step ----
@@ -301,20 +520,25 @@ step_kernel(const StepParams<T> p) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i0 = (blockIdx.x * 32 + lane) * V;
   const bool cv = i0 < p.nx;
-  const int j0 = blockIdx.y * p.tile;
-  const int j1 = min(j0 + p.tile, p.ny);
+  const int j0 = blockIdx.y * p.tile * p.bands;
+  const int j1 = min(j0 + p.tile * p.bands, p.ny);
 
-  __shared__ int s_tiles[2][32];
+  __shared__ int s_tiles[2][kMaxBands][32];
+  __shared__ uint16_t s_dl[kWarps][kWarpDefer];  // each warp's deferred cells
+  __shared__ uint32_t s_wn[kWarps];              // and their number
+  __shared__ uint32_t s_cx[3];                   // their tags (refine, switch, nonpos)
   __shared__ double s_sum[kWarps][3];
   __shared__ uint32_t s_cnt[kWarps][3];
   __shared__ int s_last;
   if (OUT) {
-    if (threadIdx.x < 64) (&s_tiles[0][0])[threadIdx.x] = 0;
+    for (int t = threadIdx.x; t < 2 * kMaxBands * 32; t += kThreads) (&s_tiles[0][0][0])[t] = 0;
+    if (threadIdx.x < 3) s_cx[threadIdx.x] = 0;
     __syncthreads();
   }
 
   Acc<T> a_rho, a_jx, a_jy;
   uint32_t n_ref = 0, n_sw = 0, n_np = 0;
+  uint32_t wn = 0;  // deferred cells gathered by this warp (warp-uniform)
 
   for (int j = j0 + warp; j < j1; j += kWarps) {
     T ft[9][V];
@@ -358,137 +582,7 @@ step_kernel(const StepParams<T> p) {
       for (int q = 0; q < 9; ++q) vload<T>(base + q * p.plane + i0, cv, ft[q]);
     }
 
-    const long long off = (long long)j * p.pitch + i0;
-    uint32_t fbits = 0;
-    if constexpr (MODE == MODE_FULL) {
-      // ---- all sensors of Table 1: cell-major, generic per-cell arithmetic ----
-      T fo[9][V];
-      T rv[S_COUNT][V];
-#pragma unroll
-      for (int k = 0; k < V; ++k) {
-        T c[9], o9[9];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) c[q] = ft[q][k];
-        CellOut<T> co;
-        cell_update<T, MODE, STORE>(c, p.omega, p.tau, o9, co);
-        const bool valid = cv && (i0 + k < p.nx);
-        if (STORE) {
-#pragma unroll
-          for (int q = 0; q < 9; ++q) fo[q][k] = o9[q];
-        }
-        if (valid) {
-          a_rho.add(co.rho);
-          a_jx.add(co.jx);
-          a_jy.add(co.jy);
-        }
-        const bool r = valid && (pick<T>(co.sv, p.refine_s) > p.thr_r);
-        const bool sw = valid && p.switch_on && (pick<T>(co.sv, p.switch_s) > p.thr_s);
-        const bool np = valid && co.nonpos;
-        fbits |= (uint32_t(r) | (uint32_t(sw) << 1) | (uint32_t(np) << 7)) << (8 * k);
-#pragma unroll
-        for (int sid = 0; sid < S_COUNT; ++sid) rv[sid][k] = co.sv[sid];
-      }
-      if (STORE && cv) {
-#pragma unroll
-        for (int q = 0; q < 9; ++q) vstore<T>(p.dst + q * p.plane + off, fo[q]);
-      }
-      if (cv) {
-        store_flags<V>(p.flags + off, fbits);
-#pragma unroll
-        for (int sid = 0; sid < S_COUNT; ++sid) {
-          const int slot = p.rec_slot[sid];
-          if (slot >= 0) vstore<T>(p.rec + slot * p.plane + off, rv[sid]);
-        }
-      }
-    } else {
-      // ---- plain stream + collide, or with the {Kn, KL, neq} sensor set:
-      //      population-major so each population's vector is stored as soon as it
-      //      is relaxed (fewer live registers) ----
-      T rho[V], ux[V], uy[V], base[V], rw0[V], rw1[V], rw2[V];
-      T kn[V], neq[V], kl[V];
-      T rs = T(0), xs = T(0), ys = T(0);
-#pragma unroll
-      for (int k = 0; k < V; ++k) {
-        rho[k] = ((ft[0][k] + ft[1][k]) + (ft[2][k] + ft[3][k])) +
-                 ((ft[4][k] + ft[5][k]) + (ft[6][k] + ft[7][k])) + ft[8][k];
-        const T jx = (ft[1][k] + ft[5][k] + ft[8][k]) - (ft[3][k] + ft[6][k] + ft[7][k]);
-        const T jy = (ft[2][k] + ft[5][k] + ft[6][k]) - (ft[4][k] + ft[7][k] + ft[8][k]);
-        const T ir = Num<T>::rcp(rho[k]);
-        ux[k] = jx * ir;
-        uy[k] = jy * ir;
-        base[k] = fma(T(-1.5), fma(ux[k], ux[k], uy[k] * uy[k]), T(1));
-        rw0[k] = rho[k] * T(4.0 / 9.0);
-        rw1[k] = rho[k] * T(1.0 / 9.0);
-        rw2[k] = rho[k] * T(1.0 / 36.0);
-        kn[k] = neq[k] = kl[k] = T(0);
-        if (OUT) {
-          const bool vk = cv && (i0 + k < p.nx);
-          rs += vk ? rho[k] : T(0);
-          xs += vk ? jx : T(0);
-          ys += vk ? jy : T(0);
-        }
-      }
-      if (OUT) {
-        a_rho.add(rs);
-        a_jx.add(xs);
-        a_jy.add(ys);
-      }
-      T feq[V];
-      // q = 0 (rest)
-#pragma unroll
-      for (int k = 0; k < V; ++k) feq[k] = rw0[k] * base[k];
-      relax_pop<T, OUT, STORE>(ft[0], feq, p.omega, kn, neq, kl);
-      if (STORE && cv) vstore<T>(p.dst + 0 * p.plane + off, ft[0]);
-      // axis pairs (1, 3): c.u = +-ux ; (2, 4): +-uy ; diagonal pairs (5, 7): +-(ux + uy),
-      // (6, 8): +-(uy - ux)
-      pair_pops<T, OUT, STORE>(ft[1], ft[3], ux, base, rw1, p.omega, kn, neq, kl,
-                               p.dst + 1 * p.plane + off, p.dst + 3 * p.plane + off, cv);
-      pair_pops<T, OUT, STORE>(ft[2], ft[4], uy, base, rw1, p.omega, kn, neq, kl,
-                               p.dst + 2 * p.plane + off, p.dst + 4 * p.plane + off, cv);
-      {
-        T sd[V];
-#pragma unroll
-        for (int k = 0; k < V; ++k) sd[k] = ux[k] + uy[k];
-        pair_pops<T, OUT, STORE>(ft[5], ft[7], sd, base, rw2, p.omega, kn, neq, kl,
-                                 p.dst + 5 * p.plane + off, p.dst + 7 * p.plane + off, cv);
-#pragma unroll
-        for (int k = 0; k < V; ++k) sd[k] = uy[k] - ux[k];
-        pair_pops<T, OUT, STORE>(ft[6], ft[8], sd, base, rw2, p.omega, kn, neq, kl,
-                                 p.dst + 6 * p.plane + off, p.dst + 8 * p.plane + off, cv);
-      }
-      if (OUT) {
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-          const bool valid = cv && (i0 + k < p.nx);
-          bool np = false;
-          // rho > 0 and |u|^2 < 0.3 make every f^eq_q >= 0.05 w_q rho > 0, and
-          // Kn < 1/16 bounds every |x_q| so f_q = f^eq_q (1 + x_q) > 0 and the phi
-          // series is exact to FP32; any other cell is recomputed exactly
-          const bool fast = (rho[k] > T(0)) & (base[k] > T(0.55)) & (kn[k] < T(0.0625));
-          if (valid && !fast) {
-            const ExactStd<T> e = exact_std_cell<T, PULL>(p, i0 + k, j);
-            kn[k] = e.kn;
-            kl[k] = e.kl;
-            neq[k] = e.neq;
-            np = e.nonpos;
-          } else {
-            kl[k] = fabs(kl[k]);
-          }
-          const T er = pick3<T>(p.refine_s, kn[k], kl[k], neq[k]);
-          const T es = pick3<T>(p.switch_s, kn[k], kl[k], neq[k]);
-          const bool r = valid && (er > p.thr_r);
-          const bool sw = valid && p.switch_on && (es > p.thr_s);
-          np = valid && np;
-          fbits |= (uint32_t(r) | (uint32_t(sw) << 1) | (uint32_t(np) << 7)) << (8 * k);
-        }
-        if (cv) {
-          store_flags<V>(p.flags + off, fbits);
-          if (p.rec_slot[S_KN] >= 0) vstore<T>(p.rec + p.rec_slot[S_KN] * p.plane + off, kn);
-          if (p.rec_slot[S_KL] >= 0) vstore<T>(p.rec + p.rec_slot[S_KL] * p.plane + off, kl);
-          if (p.rec_slot[S_NEQ] >= 0) vstore<T>(p.rec + p.rec_slot[S_NEQ] * p.plane + off, neq);
-        }
-      }
-    }
+    const uint32_t fbits = fused_row<T, MODE, PULL, STORE>(p, ft, i0, j, cv, a_rho, a_jx, a_jy);
     if (OUT) {
       n_ref += __popc(fbits & 0x01010101u);
       n_sw += __popc(fbits & 0x02020202u);
@@ -503,8 +597,29 @@ step_kernel(const StepParams<T> p) {
         ts += __shfl_xor_sync(kFull, ts, o);
       }
       if ((lane & (lpt - 1)) == 0 && (tr | ts)) {
-        atomicAdd(&s_tiles[0][lane / lpt], tr);
-        atomicAdd(&s_tiles[1][lane / lpt], ts);
+        const int b = (j - j0) / p.tile;
+        atomicAdd(&s_tiles[0][b][lane / lpt], tr);
+        atomicAdd(&s_tiles[1][b][lane / lpt], ts);
+      }
+      if (MODE == MODE_STD) {
+        // gather this row's deferred cells in the warp's region (CTA-local offsets)
+        const uint32_t dbits = fbits & 0x40404040u;
+        if (__any_sync(kFull, dbits != 0)) {
+          const int nd = __popc(dbits);
+          int incl = nd;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+          }
+          uint32_t slot = wn + uint32_t(incl - nd);
+          const int rowoff = (j - j0) * 32 * V + lane * V;
+#pragma unroll
+          for (int k = 0; k < V; ++k) {
+            if ((dbits >> (8 * k)) & 0x40u) s_dl[warp][slot++] = uint16_t(rowoff + k);
+          }
+          wn += uint32_t(__shfl_sync(kFull, incl, 31));
+        }
       }
     }
   }
@@ -528,22 +643,58 @@ step_kernel(const StepParams<T> p) {
     s_cnt[warp][0] = n_ref;
     s_cnt[warp][1] = n_sw;
     s_cnt[warp][2] = n_np;
+    s_wn[warp] = wn;
   }
   __syncthreads();
   const int bid = blockIdx.y * gridDim.x + blockIdx.x;
   const int nblocks = gridDim.x * gridDim.y;
+  if (MODE == MODE_STD) {
+    // the CTA's deferred cells, all threads at once: exact recomputation from the
+    // unchanged source populations, then their tags join the CTA's counts
+    uint32_t total = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) total += s_wn[w];
+    if (total) {
+      const Pick3 pr(p.refine_s), ps(p.switch_s);
+      for (uint32_t e = threadIdx.x; e < total; e += kThreads) {
+        uint32_t w = 0, r = e;
+        while (r >= s_wn[w]) r -= s_wn[w++];
+        const int o = s_dl[w][r];
+        const int rl = o / (32 * V), cl = o - rl * (32 * V);
+        const int j = j0 + rl, i = blockIdx.x * 32 * V + cl;
+        const uint32_t tags = fix_cell<T, PULL>(p, pr, ps, i, j);
+        const int b = rl / p.tile, tl = cl / p.tile;
+        if (tags & 1u) {
+          atomicAdd(&s_cx[0], 1u);
+          atomicAdd(&s_tiles[0][b][tl], 1);
+        }
+        if (tags & 2u) {
+          atomicAdd(&s_cx[1], 1u);
+          atomicAdd(&s_tiles[1][b][tl], 1);
+        }
+        if (tags & 4u) atomicAdd(&s_cx[2], 1u);
+      }
+      __syncthreads();
+    }
+  }
   const int tpb = (32 * V) / p.tile;
-  if (threadIdx.x < tpb) {
-    const int tx = blockIdx.x * tpb + threadIdx.x;
-    if (tx < p.ntx) {
-      const long long t = (long long)blockIdx.y * p.ntx + tx;
-      p.tiles[t] = s_tiles[0][threadIdx.x];
-      p.tiles[(long long)p.ntx * p.nty + t] = s_tiles[1][threadIdx.x];
+  for (int t = threadIdx.x; t < tpb * p.bands; t += kThreads) {
+    const int b = t / tpb, tl = t - b * tpb;
+    const int tx = blockIdx.x * tpb + tl, ty = blockIdx.y * p.bands + b;
+    if (tx < p.ntx && ty < p.nty) {
+      const long long i = (long long)ty * p.ntx + tx;
+      p.tiles[i] = s_tiles[0][b][tl];
+      p.tiles[(long long)p.ntx * p.nty + i] = s_tiles[1][b][tl];
     }
   }
   if (threadIdx.x == 0) {
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     uint32_t c0 = 0, c1 = 0, c2 = 0;
+    if (MODE == MODE_STD) {
+      c0 = s_cx[0];
+      c1 = s_cx[1];
+      c2 = s_cx[2];
+    }
     for (int w = 0; w < kWarps; ++w) {
       s0 += s_sum[w][0];
       s1 += s_sum[w][1];
@@ -603,6 +754,90 @@ step_kernel(const StepParams<T> p) {
       p.stat_counts[m] = r_cnt[0][m];
     }
     *p.done = 0u;  // ready for the next launch (stream-ordered)
+  }
+}
+
+// ---------------------------------------------------------------- fixup ----
+// Add tags (bit 0 refine, bit 1 switch) of the active lanes' cells to their tiles, one
+// atomic per distinct tile per warp (list entries of a warp mostly share tiles).
+__device__ __forceinline__ void add_tile_tags(int32_t* tiles, long long ntiles, long long t,
+                                              uint32_t tags, unsigned active) {
+  const unsigned same = __match_any_sync(active, t);
+  const int r = __popc(__ballot_sync(active, tags & 1u) & same);
+  const int s = __popc(__ballot_sync(active, tags & 2u) & same);
+  if ((threadIdx.x & 31) == __ffs(same) - 1) {
+    if (r) atomicAdd(tiles + t, r);
+    if (s) atomicAdd(tiles + ntiles + t, s);
+  }
+}
+
+// The cells the fused pass deferred (flag byte KSS_FLAG_DEFERRED), from its compact
+// list: one thread per cell.  If the list overflowed, a grid-stride scan over groups of
+// 4 cells of a row finds them instead (skipping tiles with none).  Counts are corrected
+// with integer atomics, so they stay exact and reproducible; the last CTA resets the
+// list for the next pass.
+template <class T, bool PULL>
+__global__ void __launch_bounds__(256) fixup_kernel(const StepParams<T> p) {
+  const int lane = threadIdx.x & 31;
+  const Pick3 pr(p.refine_s), ps(p.switch_s);
+  unsigned long long cr = 0, cs = 0, cn = 0;
+  const uint32_t count = __ldcg(p.defer_count);
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nthreads = (long long)gridDim.x * blockDim.x;
+  if (count <= p.defer_cap) {
+    const long long ntiles = (long long)p.ntx * p.nty;
+    for (long long e0 = tid - lane; e0 < count; e0 += nthreads) {  // warp-uniform trips
+      const long long e = e0 + lane;
+      const bool has = e < count;
+      const unsigned active = __ballot_sync(kFull, has);
+      if (!has) continue;
+      const uint32_t cell = __ldcg(p.defer_list + e);
+      const int j = int(cell / uint32_t(p.nx)), i = int(cell - uint32_t(j) * uint32_t(p.nx));
+      const uint32_t tags = fix_cell<T, PULL>(p, pr, ps, i, j);
+      add_tile_tags(p.tiles, ntiles, (long long)(j / p.tile) * p.ntx + i / p.tile, tags, active);
+      cr += tags & 1u;
+      cs += (tags >> 1) & 1u;
+      cn += (tags >> 2) & 1u;
+    }
+  } else {
+    const int qpr = (p.nx + 3) / 4;  // groups per row (tile is a multiple of 4)
+    const long long ngroups = (long long)qpr * p.ny;
+    for (long long g = tid; g < ngroups; g += nthreads) {
+      const int j = int(g / qpr), i0 = int(g - (long long)j * qpr) * 4;
+      const long long t = (long long)(j / p.tile) * p.ntx + i0 / p.tile;
+      if (__ldcg(p.tiles_def + t) == 0) continue;
+      const uint32_t w = __ldcg(reinterpret_cast<const uint32_t*>(p.flags + (long long)j * p.pitch + i0));
+      if (!(w & 0x40404040u)) continue;
+      for (int k = 0; k < 4; ++k) {
+        if (i0 + k >= p.nx || !((w >> (8 * k)) & kFlagDeferred)) continue;
+        const uint32_t tags = fix_cell<T, PULL>(p, pr, ps, i0 + k, j);
+        if (tags & 1u) atomicAdd(p.tiles + t, 1);
+        if (tags & 2u) atomicAdd(p.tiles + (long long)p.ntx * p.nty + t, 1);
+        cr += tags & 1u;
+        cs += (tags >> 1) & 1u;
+        cn += (tags >> 2) & 1u;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    cr += __shfl_xor_sync(kFull, cr, o);
+    cs += __shfl_xor_sync(kFull, cs, o);
+    cn += __shfl_xor_sync(kFull, cn, o);
+  }
+  if (lane == 0) {
+    if (cr) atomicAdd(p.stat_counts + 0, cr);
+    if (cs) atomicAdd(p.stat_counts + 1, cs);
+    if (cn) atomicAdd(p.stat_counts + 2, cn);
+  }
+  // the last CTA to finish resets the list for the next pass (no CTA waits)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(p.defer_ticket, 1u) == gridDim.x - 1) {
+      *p.defer_count = 0u;
+      *p.defer_ticket = 0u;
+    }
   }
 }
 

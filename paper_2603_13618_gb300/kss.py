@@ -24,6 +24,7 @@ SENSORS = ("tau_ns", "c", "s", "e", "qh", "kn", "neq", "qe", "hr", "kl", "sigma_
            "sigma_kl", "alpha")
 SENSOR_ID = {n: k for k, n in enumerate(SENSORS)}
 FLAG_REFINE, FLAG_SWITCH, FLAG_NONPOS = 0x01, 0x02, 0x80
+KERNELS = {"auto": 0, "vector": 1, "tma": 2}
 
 
 class KssError(RuntimeError):
@@ -40,6 +41,7 @@ class Config(ctypes.Structure):
         ("switch_sensor", ctypes.c_int32), ("switch_threshold", ctypes.c_double),
         ("record_mask", ctypes.c_uint32), ("output_every", ctypes.c_int32),
         ("tile", ctypes.c_int32), ("stream", ctypes.c_void_p), ("own_stream", ctypes.c_int32),
+        ("kernel", ctypes.c_int32),
     ]
 
 
@@ -124,7 +126,7 @@ class Lattice:
     def __init__(self, nx: int, ny: int, precision="fp32", tau: float = 0.8,
                  refine_sensor="kn", refine_threshold: float = 1e-3, switch_sensor="neq",
                  switch_threshold: float = 1e-4, record=("kl",), output_every: int = 1,
-                 tile: int = 16, stream="torch"):
+                 tile: int = 16, stream="torch", kernel="auto"):
         self._lib = load()
         cfg = Config()
         self._check(self._lib.kss_config_default(ctypes.byref(cfg), nx, ny,
@@ -137,6 +139,7 @@ class Lattice:
         cfg.record_mask = sum(1 << _sensor(s) for s in record)
         cfg.output_every = output_every
         cfg.tile = tile
+        cfg.kernel = KERNELS[kernel]
         # stream: "torch" = torch's current stream (handle 0 is the CUDA default
         # stream), "own" = a stream created and owned by the lattice, or a raw handle
         if stream == "own":

@@ -71,14 +71,16 @@ def _check_step_outputs(lat, prec, prev, tau, nsteps, thr_r, thr_s, tile, sensor
                                             (5, 1, 8, 0.8), (200, 9, 64, 0.6),
                                             (3, 3, 16, 0.9)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_ragged_lattices(prec, nx, ny, tile, tau):
+@pytest.mark.parametrize("kernel", ["vector", "tma"])
+def test_ragged_lattices(kernel, prec, nx, ny, tile, tau):
     kss = _kss()
     rho, ux, uy = inputs.smooth_jump(nx, ny, seed=nx * 1000 + ny, kmax=3)
     nsteps = 7
     prev, fin = _oracle_run(rho, ux, uy, tau, nsteps)
     thr_r, thr_s = 2e-3, 3e-4
     lat = kss.Lattice(nx, ny, precision=prec, tau=tau, refine_threshold=thr_r,
-                      switch_threshold=thr_s, record=("kl", "kn", "neq"), tile=tile)
+                      switch_threshold=thr_s, record=("kl", "kn", "neq"), tile=tile,
+                      kernel=kernel)
     lat.set_fields(rho, ux, uy)
     lat.step(nsteps)
     got = lat.get_populations()
@@ -91,7 +93,8 @@ def test_ragged_lattices(prec, nx, ny, tile, tau):
     lat.close()
 
 
-def test_cfg1_shear_wave_fp64_2000_steps():
+@pytest.mark.parametrize("kernel", ["vector", "tma"])
+def test_cfg1_shear_wave_fp64_2000_steps(kernel):
     """128^2 FP64 shear wave, tau = 0.8, 2000 steps, sensors and flags every 10 steps."""
     kss = _kss()
     nx = ny = 128
@@ -99,7 +102,7 @@ def test_cfg1_shear_wave_fp64_2000_steps():
     rho, ux, uy = inputs.shear_wave(nx, ny, 0.01)
     lat = kss.Lattice(nx, ny, precision="fp64", tau=tau, refine_sensor="kn",
                       refine_threshold=thr, switch_sensor="neq", switch_threshold=1e-4,
-                      record=("kn", "kl"), output_every=10, tile=16)
+                      record=("kn", "kl"), output_every=10, tile=16, kernel=kernel)
     lat.set_fields(rho, ux, uy)
     f = oracle.init_equilibrium(rho, ux, uy)
     done = 0
@@ -121,15 +124,17 @@ def test_cfg1_shear_wave_fp64_2000_steps():
     lat.close()
 
 
-@pytest.mark.parametrize("tau", [0.51, 0.6, 0.8, 1.0])
-def test_fp32_smooth_jump_100_steps(tau):
+@pytest.mark.parametrize("tau,kernel", [(0.51, "vector"), (0.6, "vector"), (0.8, "vector"),
+                                        (1.0, "vector"), (0.51, "tma"), (0.6, "tma"),
+                                        (1.0, "tma")])
+def test_fp32_smooth_jump_100_steps(tau, kernel):
     """FP32 moments within 1e-5 (relative) of the FP64 oracle after 100 steps, on the
     density-jump workload at a size the oracle finishes in seconds."""
     kss = _kss()
     nx, ny, nsteps = 192, 160, 100
     rho, ux, uy = inputs.smooth_jump(nx, ny, seed=2603, kmax=8)
     prev, fin = _oracle_run(rho, ux, uy, tau, nsteps)
-    lat = kss.Lattice(nx, ny, precision="fp32", tau=tau, record=("kl",))
+    lat = kss.Lattice(nx, ny, precision="fp32", tau=tau, record=("kl",), kernel=kernel)
     lat.set_fields(rho, ux, uy)
     lat.step(nsteps)
     r, vx, vy = lat.read_moments()
@@ -292,4 +297,125 @@ def test_library_owned_stream():
     lat.step(4)
     np.testing.assert_allclose(lat.get_populations(), fin, rtol=64 * 2.0**-24 * math.sqrt(5))
     _check_step_outputs(lat, "fp32", prev, tau, 4, 1e-3, 1e-4, 16)
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_vector_and_tma_kernels_agree(prec):
+    """Both step kernels run the same per-cell arithmetic: same states, fields, flags."""
+    kss = _kss()
+    nx, ny, tau = 517, 263, 0.6
+    rho, ux, uy = inputs.smooth_jump(nx, ny, seed=8, kmax=8)
+    out = {}
+    for kernel in ("vector", "tma"):
+        lat = kss.Lattice(nx, ny, precision=prec, tau=tau, record=("kl", "kn"), kernel=kernel,
+                          output_every=3)
+        lat.set_fields(rho, ux, uy)
+        lat.step(30)
+        out[kernel] = (lat.get_populations(), lat.read_sensor("kl"), lat.read_sensor("kn"),
+                       *lat.read_flags(), lat.read_stats()[0], lat.read_moments())
+        lat.close()
+    a, b = out["vector"], out["tma"]
+    rt = 64 * parity.UNIT_ROUNDOFF[prec] * math.sqrt(31)
+    np.testing.assert_allclose(a[0], b[0], rtol=rt)
+    r, u, v = a[7]
+    for k, name in ((1, "kl"), (2, "kn")):
+        parity.assert_sensor_close(name, b[k], a[k], prec, 30, r, u, v, a[2], tau)
+    # the tag counts agree exactly wherever the flags do (both kernels' counts are
+    # recounts of their own flags, checked against the oracle elsewhere)
+    same = np.array_equal(a[3], b[3])
+    if same:
+        np.testing.assert_array_equal(a[4], b[4])
+        np.testing.assert_array_equal(a[5], b[5])
+    else:
+        assert np.mean(a[3] != b[3]) < 1e-3
+    # conservation sums: the states differ by round-off, bounded as in the oracle parity
+    np.testing.assert_allclose(a[6], b[6], rtol=0, atol=rt * a[6][0])
+
+
+def _cone_window(nx, ny, x0, y0, w, nsteps, tau):
+    """Oracle state of the w x w window at global (x0, y0) after nsteps and the window's
+    step-nsteps sensors, from the domain of dependence (margin nsteps + 1)."""
+    m = nsteps + 1
+    rho, ux, uy = inputs.smooth_jump(nx, ny, seed=2603, kmax=8, x0=x0 - m, y0=y0 - m,
+                                     wx=w + 2 * m, wy=w + 2 * m)
+    f = oracle.init_equilibrium(rho, ux, uy)
+    prev = f
+    for _ in range(nsteps):
+        prev = f
+        f = oracle.step(f, tau)
+    sens, nonpos = oracle.sensor_fields(prev, tau, pull=True)
+    sl = (slice(m, m + w), slice(m, m + w))
+    r, vx, vy = oracle.moments(f)
+    return {"rho": r[sl], "ux": vx[sl], "uy": vy[sl], "sens": sens[:, sl[0], sl[1]],
+            "nonpos": nonpos[sl]}
+
+
+def test_full_size_4096_fp32_bench_configuration():
+    """The benchmark's workload and launch configuration (4096^2 FP32, tau = 0.6, Kn
+    refine 1e-3, neq switch 1e-4, KL recorded, output every step, tile 16, automatic
+    kernel choice), 100 steps, checked on four 16 x 16 windows -- at the density step,
+    across both periodic seams, in the smooth interior -- against the oracle run on
+    each window's domain of dependence."""
+    kss = _kss()
+    nx = ny = 4096
+    tau, nsteps, w = 0.6, 100, 16
+    rho, ux, uy = inputs.smooth_jump(nx, ny, seed=2603, kmax=8)
+    lat = kss.Lattice(nx, ny, precision="fp32", tau=tau, refine_sensor="kn",
+                      refine_threshold=1e-3, switch_sensor="neq", switch_threshold=1e-4,
+                      record=("kl",), output_every=1, tile=16)
+    lat.set_fields(rho, ux, uy)
+    lat.step(nsteps)
+    r, vx, vy = lat.read_moments()
+    kl = lat.read_sensor("kl")
+    kn = lat.read_sensor("kn")
+    flags, tiles, counts = lat.read_flags()
+    lat.close()
+    for (x0, y0) in ((2040, 1000), (4088, 4088), (1000, 3000), (4090, 7)):
+        ref = _cone_window(nx, ny, x0, y0, w, nsteps, tau)
+        xs = (x0 + np.arange(w)) % nx
+        ys = (y0 + np.arange(w)) % ny
+        g = np.ix_(ys, xs)
+        assert np.max(np.abs(r[g] - ref["rho"]) / ref["rho"]) <= 1e-5
+        umax = 0.1 / math.sqrt(3.0)  # the lattice's velocity scale: max |u| = 0.1 c_s
+        assert np.max(np.abs(vx[g] - ref["ux"])) <= 1e-5 * umax
+        assert np.max(np.abs(vy[g] - ref["uy"])) <= 1e-5 * umax
+        rr, uu, vv = ref["rho"], ref["ux"], ref["uy"]
+        kn_ref = ref["sens"][oracle.SENSOR_ID["kn"]]
+        parity.assert_sensor_close("kl", kl[g], ref["sens"][oracle.SENSOR_ID["kl"]], "fp32",
+                                   nsteps, rr, uu, vv, kn_ref, tau)
+        parity.assert_sensor_close("kn", kn[g], kn_ref, "fp32", nsteps, rr, uu, vv, kn_ref, tau)
+        es = ref["sens"][oracle.SENSOR_ID["neq"]]
+        rf, _, _ = oracle.flags(kn_ref, 1e-3, es, 1e-4, ref["nonpos"], 16)
+        band = parity.band_mask(kn_ref, 1e-3, es, 1e-4)
+        assert not ((flags[g] != rf) & ~band).any()
+    # tile counts and totals are consistent with the flag field everywhere
+    fr = (flags & 1).astype(np.int64).reshape(256, 16, 256, 16).sum(axis=(1, 3))
+    fs = ((flags >> 1) & 1).astype(np.int64).reshape(256, 16, 256, 16).sum(axis=(1, 3))
+    np.testing.assert_array_equal(tiles[0], fr)
+    np.testing.assert_array_equal(tiles[1], fs)
+    assert counts[0] == fr.sum() and counts[1] == fs.sum() and counts[2] == np.sum(flags >> 7)
+
+
+@pytest.mark.parametrize("prec,kernel", [("fp32", "vector"), ("fp32", "tma"), ("fp64", "vector")])
+def test_deferred_cells_everywhere(prec, kernel):
+    """Every cell far from equilibrium (|x| >= 1/16): the fused pass defers all of them
+    to the exact fix-up pass, more than its list holds (1/8 of the lattice), so the
+    fix-up falls back to scanning; results must still match the oracle exactly."""
+    kss = _kss()
+    nx, ny, tau = 128, 128, 0.7
+    rng = np.random.default_rng(123)
+    rho, ux, uy = inputs.random_smooth(nx, ny, seed=4)
+    f = oracle.init_equilibrium(rho, ux, uy) * (1.0 + 0.3 * rng.uniform(-1, 1, (9, ny, nx)))
+    f[5, 10, 20] = -0.01  # and one non-positive cell
+    thr_r, thr_s = 0.5, 0.05
+    lat = kss.Lattice(nx, ny, precision=prec, tau=tau, refine_threshold=thr_r,
+                      switch_threshold=thr_s, record=("kl", "kn", "neq"), kernel=kernel)
+    lat.set_populations(np.ascontiguousarray(f))
+    lat.step(1)
+    _check_step_outputs(lat, prec, f, tau, 1, thr_r, thr_s, 16)
+    # and once more from the (still far from equilibrium) new state, list path again
+    prev = lat.get_populations()
+    lat.step(1)
+    _check_step_outputs(lat, prec, prev, tau, 2, thr_r, thr_s, 16)
     lat.close()

@@ -86,16 +86,16 @@ def test_noalloc_rejects_problems_beyond_its_scratch(torch_cuda):
     from paper_2603_13618_gb300 import kss
 
     lib = kss.load()
-    # 8192 x 8192 with tile 8: 64 x 1024 = 65536 CTAs > KSS_NOALLOC_MAX_BLOCKS (16384);
-    # rejected before any launch, so tiny stand-in buffers are never touched
+    # 16384 x 16384: 128 x 512 = 65536 CTAs > KSS_NOALLOC_MAX_BLOCKS (16384); rejected
+    # before any launch, so tiny stand-in buffers are never touched
     buf = torch.zeros(64, dtype=torch.float32, device="cuda")
     b8 = torch.zeros(64, dtype=torch.uint8, device="cuda")
     i32 = torch.zeros(64, dtype=torch.int32, device="cuda")
     d = torch.zeros(3, dtype=torch.float64, device="cuda")
     c = torch.zeros(3, dtype=torch.int64, device="cuda")
-    rc = lib.kss_step_f32_noalloc(_ptr(buf), _ptr(buf), 8192, 8192, 8192, 0.8, KN, 1e-3, NEQ,
-                                  1e-4, 8, KL, _ptr(buf), _ptr(b8), _ptr(i32), _ptr(d), _ptr(c),
-                                  None)
+    rc = lib.kss_step_f32_noalloc(_ptr(buf), _ptr(buf), 16384, 16384, 16384, 0.8, KN, 1e-3,
+                                  NEQ, 1e-4, 8, KL, _ptr(buf), _ptr(b8), _ptr(i32), _ptr(d),
+                                  _ptr(c), None)
     assert rc == -7
     # a non-{Kn, KL, neq} sensor is an argument error
     rc = lib.kss_step_f32_noalloc(_ptr(buf), _ptr(buf), 64, 8, 64, 0.8, 0, 1e-3, NEQ, 1e-4, 8,
