@@ -32,6 +32,8 @@
 // in block order.
 #pragma once
 
+#include <type_traits>
+
 #include "d2q9.cuh"
 
 namespace kss {
@@ -61,15 +63,30 @@ constexpr unsigned kFull = 0xffffffffu;
 // between the fused pass and fixup_kernel, which replaces the byte.
 constexpr uint32_t kFlagDeferred = 0x40u;
 
+// Cells per thread and the vector type of one population's load/store.  FP32 takes
+// 4 cells (16-byte vectors) by default; -DKSS_F32_VEC=2 selects 8-byte vectors (half the
+// per-thread state, more resident warps).
+#ifndef KSS_F32_VEC
+#define KSS_F32_VEC 4
+#endif
 template <class T> struct Vec;
 template <> struct Vec<float> {
-  static constexpr int N = 4;
-  using type = float4;
+  static constexpr int N = KSS_F32_VEC;
+  using type = typename std::conditional<KSS_F32_VEC == 4, float4, float2>::type;
 };
 template <> struct Vec<double> {
   static constexpr int N = 2;
   using type = double2;
 };
+
+template <class VT, class T, int N>
+__device__ __forceinline__ VT make_vec(const T (&v)[N]) {
+  if constexpr (N == 4) {
+    return VT{v[0], v[1], v[2], v[3]};
+  } else {
+    return VT{v[0], v[1]};
+  }
+}
 
 template <class T>
 struct StepParams {
@@ -202,11 +219,7 @@ template <> struct Acc<double> {
 template <class T>
 __device__ __forceinline__ void vstore(T* p, const T (&v)[Vec<T>::N]) {
   using VT = typename Vec<T>::type;
-  if constexpr (Vec<T>::N == 4) {
-    __stcs(reinterpret_cast<VT*>(p), make_float4(v[0], v[1], v[2], v[3]));
-  } else {
-    __stcs(reinterpret_cast<VT*>(p), make_double2(v[0], v[1]));
-  }
+  __stcs(reinterpret_cast<VT*>(p), make_vec<VT, T, Vec<T>::N>(v));
 }
 
 template <int V>
@@ -425,25 +438,25 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<T>& p, T (&ft)[9]
         for (int k = 0; k < V; ++k)
           if (k >= nvalid) ft[q][k] = T(0);
     }
-    T rho[V], ux[V], uy[V], base[V], rw0[V], rw1[V], rw2[V];
+    // per cell: rho/9 (the rest and diagonal weights are exact power-of-two multiples:
+    // 4/9 = 4 (1/9), 1/36 = (1/9)/4), u and 1 - 3/2 u^2; kept small for registers
+    T rw1[V], ux[V], uy[V], base[V];
     StdAcc<T> a;
     T rs = T(0), xs = T(0), ys = T(0);
 #pragma unroll
     for (int k = 0; k < V; ++k) {
-      rho[k] = ((ft[0][k] + ft[1][k]) + (ft[2][k] + ft[3][k])) +
-               ((ft[4][k] + ft[5][k]) + (ft[6][k] + ft[7][k])) + ft[8][k];
+      const T rho = ((ft[0][k] + ft[1][k]) + (ft[2][k] + ft[3][k])) +
+                    ((ft[4][k] + ft[5][k]) + (ft[6][k] + ft[7][k])) + ft[8][k];
       const T jx = (ft[1][k] + ft[5][k] + ft[8][k]) - (ft[3][k] + ft[6][k] + ft[7][k]);
       const T jy = (ft[2][k] + ft[5][k] + ft[6][k]) - (ft[4][k] + ft[7][k] + ft[8][k]);
-      const T ir = Num<T>::rcp(rho[k]);
+      const T ir = Num<T>::rcp(rho);
       ux[k] = jx * ir;
       uy[k] = jy * ir;
       base[k] = fma(T(-1.5), fma(ux[k], ux[k], uy[k] * uy[k]), T(1));
-      rw0[k] = rho[k] * T(4.0 / 9.0);
-      rw1[k] = rho[k] * T(1.0 / 9.0);
-      rw2[k] = rho[k] * T(1.0 / 36.0);
+      rw1[k] = rho * T(1.0 / 9.0);
       a.kn[k] = a.neq[k] = a.kl[k] = T(0);
       if (OUT) {
-        rs += rho[k];
+        rs += rho;
         xs += jx;
         ys += jy;
       }
@@ -456,7 +469,7 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<T>& p, T (&ft)[9]
     T feq[V];
     // q = 0 (rest)
 #pragma unroll
-    for (int k = 0; k < V; ++k) feq[k] = rw0[k] * base[k];
+    for (int k = 0; k < V; ++k) feq[k] = (T(4) * rw1[k]) * base[k];
     relax_pop<T, OUT, STORE>(ft[0], feq, p.omega, a);
     if (STORE && cv) vstore<T>(p.dst + 0 * p.plane + off, ft[0]);
     // axis pairs (1, 3): c.u = +-ux ; (2, 4): +-uy ; diagonal pairs (5, 7): +-(ux + uy),
@@ -469,6 +482,9 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<T>& p, T (&ft)[9]
       T sd[V];
 #pragma unroll
       for (int k = 0; k < V; ++k) sd[k] = ux[k] + uy[k];
+      T rw2[V];
+#pragma unroll
+      for (int k = 0; k < V; ++k) rw2[k] = T(0.25) * rw1[k];
       pair_pops<T, OUT, STORE>(ft[5], ft[7], sd, base, rw2, p.omega, a,
                                p.dst + 5 * p.plane + off, p.dst + 7 * p.plane + off, cv);
 #pragma unroll
@@ -485,7 +501,7 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<T>& p, T (&ft)[9]
         // the series of phi is exact to FP32.  Any other valid cell is deferred: its
         // flag byte is KSS_FLAG_DEFERRED only, it is not counted here, and fixup_kernel
         // recomputes it exactly from the unchanged source populations.
-        const bool fast = (rho[k] > T(0)) & (base[k] > T(0.55)) & (a.kn[k] < T(0.0625));
+        const bool fast = (rw1[k] > T(0)) & (base[k] > T(0.55)) & (a.kn[k] < T(0.0625));
         a.kl[k] = fabs(a.kl[k]);
         const T er = pr(a.kn[k], a.kl[k], a.neq[k]);
         const T es = ps(a.kn[k], a.kl[k], a.neq[k]);

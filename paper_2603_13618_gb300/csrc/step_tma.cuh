@@ -37,7 +37,7 @@ constexpr int kTmaGroups = 2;                          // independent row pipeli
 constexpr int kGroupWarps = kTmaWarps / kTmaGroups;    // warps sharing one row
 constexpr int kGroupThreads = 32 * kGroupWarps;
 constexpr int kTmaStages = 3;                          // ring depth per group
-constexpr int kSegBytes = kGroupWarps * 512 + 32;      // a row segment: 4096 B + 16 B halos
+constexpr int kSegBytes = kGroupWarps * 512 + 32;      // largest row segment: 4 KiB + 16 B halos
 constexpr int kStageBytes = 9 * kSegBytes;
 constexpr int kBarrierBytes = 128;
 constexpr size_t kTmaSmemBytes =
@@ -129,11 +129,12 @@ step_tma_kernel(const StepParams<T> p, const TmaPlan plan) {
   constexpr int V = Vec<T>::N;
   constexpr int H = 16 / int(sizeof(T));  // halo elements on each side of a segment
   constexpr int W = kGroupWarps * 32 * V;  // columns of a strip
-  constexpr int SEG = kSegBytes / int(sizeof(T));
+  constexpr int SEG = W + 2 * H;  // segment elements (stage slots are kSegBytes apart)
+  constexpr int SEGS = kSegBytes / int(sizeof(T));  // slot stride in elements
   constexpr bool OUT = MODE != MODE_PLAIN;
   constexpr int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
   constexpr int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-  static_assert(SEG == W + 2 * H, "segment layout");
+  static_assert(SEG <= SEGS, "segment layout");
   using VT = typename Vec<T>::type;
 
   extern __shared__ __align__(128) unsigned char smem[];
@@ -145,7 +146,7 @@ step_tma_kernel(const StepParams<T> p, const TmaPlan plan) {
   const int grp = warp / kGroupWarps, lw = warp % kGroupWarps;
   const bool leader = (threadIdx.x % kGroupThreads) == 0;  // issues the group's copies
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem) + grp * kTmaStages;
-  T* stages = reinterpret_cast<T*>(smem + kBarrierBytes) + size_t(grp) * kTmaStages * 9 * SEG;
+  T* stages = reinterpret_cast<T*>(smem + kBarrierBytes) + size_t(grp) * kTmaStages * 9 * SEGS;
 
   if (leader) {
 #pragma unroll
@@ -173,14 +174,14 @@ step_tma_kernel(const StepParams<T> p, const TmaPlan plan) {
     // leader: request row `row` into stage (n % stages)
     auto request = [&](int row, uint32_t n) {
       const int st = int(n % kTmaStages);
-      T* dst = stages + st * 9 * SEG + soff;
+      T* dst = stages + st * 9 * SEGS + soff;
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(bars + st, 9 * bytes);
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
         int sr = row - CY[q];
         sr = sr < 0 ? sr + p.ny : (sr >= p.ny ? sr - p.ny : sr);
-        bulk_copy_g2s(dst + q * SEG, p.src + q * p.plane + (long long)sr * p.pitch + L, bytes,
+        bulk_copy_g2s(dst + q * SEGS, p.src + q * p.plane + (long long)sr * p.pitch + L, bytes,
                       bars + st);
       }
     };
@@ -201,10 +202,10 @@ step_tma_kernel(const StepParams<T> p, const TmaPlan plan) {
       const bool got = mbar_wait_bounded(bars + st, (consumed / kTmaStages) & 1u);
       T ft[9][V];
       if (got) {
-        const T* sg = stages + st * 9 * SEG + H + col;
+        const T* sg = stages + st * 9 * SEGS + H + col;
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
-          const VT a = *reinterpret_cast<const VT*>(sg + q * SEG);
+          const VT a = *reinterpret_cast<const VT*>(sg + q * SEGS);
           T v[V];
           if constexpr (V == 4) {
             v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
@@ -219,13 +220,13 @@ step_tma_kernel(const StepParams<T> p, const TmaPlan plan) {
             sr = sr < 0 ? sr + p.ny : (sr >= p.ny ? sr - p.ny : sr);
             const T* grow = p.src + q * p.plane + (long long)sr * p.pitch;
             if (CX[q] == 1) {  // source column i - 1
-              T left = sg[q * SEG - 1];
+              T left = sg[q * SEGS - 1];
               if (i0 == 0) left = __ldg(grow + (p.nx - 1));
               ft[q][0] = left;
 #pragma unroll
               for (int k = 1; k < V; ++k) ft[q][k] = v[k - 1];
             } else {  // source column i + 1
-              T right = sg[q * SEG + V];
+              T right = sg[q * SEGS + V];
               if (cv && tail) right = __ldg(grow);
 #pragma unroll
               for (int k = 0; k < V - 1; ++k) ft[q][k] = v[k + 1];
