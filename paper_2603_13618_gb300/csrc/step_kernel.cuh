@@ -339,6 +339,91 @@ __device__ __forceinline__ void append_deferred(uint32_t fbits, int i0, int j, i
   }
 }
 
+// Partial sums above the warp level: FP32 storage keeps them as double-floats (hi + lo,
+// ~48 bits) so that no FP64 arithmetic (a slow pipe on GB300) sits in any CTA's
+// epilogue; FP64 storage uses double.  Stored in the double slots of part_sum.
+template <class T> struct Red;
+template <> struct Red<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(const Red& o) {
+    const float s = hi + o.hi;
+    const float bp = s - hi;
+    lo += ((hi - (s - bp)) + (o.hi - bp)) + o.lo;
+    hi = s;
+  }
+  __device__ __forceinline__ Red shfl_xor(int off) const {
+    return Red{__shfl_xor_sync(kFull, hi, off), __shfl_xor_sync(kFull, lo, off)};
+  }
+  __device__ __forceinline__ void store(double* p) const {
+    *reinterpret_cast<float2*>(p) = make_float2(hi, lo);
+  }
+  __device__ static __forceinline__ Red load(const double* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return Red{v.x, v.y};
+  }
+  __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+  __device__ static __forceinline__ Red of(const Acc<float>& a) { return Red{a.hi, a.lo}; }
+};
+template <> struct Red<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(const Red& o) { v += o.v; }
+  __device__ __forceinline__ Red shfl_xor(int off) const {
+    return Red{__shfl_xor_sync(kFull, v, off)};
+  }
+  __device__ __forceinline__ void store(double* p) const { *p = v; }
+  __device__ static __forceinline__ Red load(const double* p) { return Red{__ldcg(p)}; }
+  __device__ __forceinline__ double value() const { return v; }
+  __device__ static __forceinline__ Red of(const Acc<double>& a) { return Red{a.v}; }
+};
+
+// The last CTA's reduction of the per-CTA partials, in CTA order within each thread and
+// a fixed shuffle/shared-memory tree across threads (bitwise reproducible).
+template <class T, int NTHREADS>
+__device__ __forceinline__ void finalize_partials(const StepParams<T>& p, int nblocks) {
+  __shared__ Red<T> f_sum[NTHREADS / 32][3];
+  __shared__ unsigned long long f_cnt[NTHREADS / 32][3];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Red<T> t[3];
+  unsigned long long u[3] = {0, 0, 0};
+  for (int b = threadIdx.x; b < nblocks; b += NTHREADS) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      t[m].add(Red<T>::load(p.part_sum + 3 * b + m));
+      u[m] += __ldcg(p.part_cnt + 4 * b + m);
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      t[m].add(t[m].shfl_xor(off));
+      u[m] += __shfl_xor_sync(kFull, u[m], off);
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      f_sum[warp][m] = t[m];
+      f_cnt[warp][m] = u[m];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      Red<T> r = f_sum[0][m];
+      unsigned long long c = f_cnt[0][m];
+      for (int w = 1; w < NTHREADS / 32; ++w) {
+        r.add(f_sum[w][m]);
+        c += f_cnt[w][m];
+      }
+      p.stat_sums[m] = r.value();
+      p.stat_counts[m] = c;
+    }
+    *p.done = 0u;  // ready for the next launch (stream-ordered)
+  }
+}
+
 // Is sensor s in the compiled set of MODE?
 template <int MODE>
 __host__ __device__ constexpr bool mode_has(int s) {
@@ -543,7 +628,7 @@ step_kernel(const StepParams<T> p) {
   __shared__ uint16_t s_dl[kWarps][kWarpDefer];  // each warp's deferred cells
   __shared__ uint32_t s_wn[kWarps];              // and their number
   __shared__ uint32_t s_cx[3];                   // their tags (refine, switch, nonpos)
-  __shared__ double s_sum[kWarps][3];
+  __shared__ Red<T> s_sum[kWarps][3];
   __shared__ uint32_t s_cnt[kWarps][3];
   __shared__ int s_last;
   if (OUT) {
@@ -653,9 +738,9 @@ step_kernel(const StepParams<T> p) {
     n_np += __shfl_xor_sync(kFull, n_np, off);
   }
   if (lane == 0) {
-    s_sum[warp][0] = a_rho.value();
-    s_sum[warp][1] = a_jx.value();
-    s_sum[warp][2] = a_jy.value();
+    s_sum[warp][0] = Red<T>::of(a_rho);
+    s_sum[warp][1] = Red<T>::of(a_jx);
+    s_sum[warp][2] = Red<T>::of(a_jy);
     s_cnt[warp][0] = n_ref;
     s_cnt[warp][1] = n_sw;
     s_cnt[warp][2] = n_np;
@@ -704,7 +789,7 @@ step_kernel(const StepParams<T> p) {
     }
   }
   if (threadIdx.x == 0) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    Red<T> s0, s1, s2;
     uint32_t c0 = 0, c1 = 0, c2 = 0;
     if (MODE == MODE_STD) {
       c0 = s_cx[0];
@@ -712,16 +797,16 @@ step_kernel(const StepParams<T> p) {
       c2 = s_cx[2];
     }
     for (int w = 0; w < kWarps; ++w) {
-      s0 += s_sum[w][0];
-      s1 += s_sum[w][1];
-      s2 += s_sum[w][2];
+      s0.add(s_sum[w][0]);
+      s1.add(s_sum[w][1]);
+      s2.add(s_sum[w][2]);
       c0 += s_cnt[w][0];
       c1 += s_cnt[w][1];
       c2 += s_cnt[w][2];
     }
-    p.part_sum[3 * bid + 0] = s0;
-    p.part_sum[3 * bid + 1] = s1;
-    p.part_sum[3 * bid + 2] = s2;
+    s0.store(p.part_sum + 3 * bid + 0);
+    s1.store(p.part_sum + 3 * bid + 1);
+    s2.store(p.part_sum + 3 * bid + 2);
     p.part_cnt[4 * bid + 0] = c0;
     p.part_cnt[4 * bid + 1] = c1;
     p.part_cnt[4 * bid + 2] = c2;
@@ -732,45 +817,9 @@ step_kernel(const StepParams<T> p) {
   __syncthreads();
   if (!s_last) return;
 
-  // ---- last block: add the per-block partials in block order ----
+  // ---- last block: add the per-block partials ----
   __threadfence();
-  __shared__ double r_sum[kThreads][3];
-  __shared__ unsigned long long r_cnt[kThreads][3];
-  double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-  unsigned long long u0 = 0, u1 = 0, u2 = 0;
-  for (int b = threadIdx.x; b < nblocks; b += kThreads) {
-    t0 += __ldcg(p.part_sum + 3 * b + 0);
-    t1 += __ldcg(p.part_sum + 3 * b + 1);
-    t2 += __ldcg(p.part_sum + 3 * b + 2);
-    u0 += __ldcg(p.part_cnt + 4 * b + 0);
-    u1 += __ldcg(p.part_cnt + 4 * b + 1);
-    u2 += __ldcg(p.part_cnt + 4 * b + 2);
-  }
-  r_sum[threadIdx.x][0] = t0;
-  r_sum[threadIdx.x][1] = t1;
-  r_sum[threadIdx.x][2] = t2;
-  r_cnt[threadIdx.x][0] = u0;
-  r_cnt[threadIdx.x][1] = u1;
-  r_cnt[threadIdx.x][2] = u2;
-  __syncthreads();
-  for (int h = kThreads / 2; h > 0; h >>= 1) {
-    if (threadIdx.x < h) {
-#pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        r_sum[threadIdx.x][m] += r_sum[threadIdx.x + h][m];
-        r_cnt[threadIdx.x][m] += r_cnt[threadIdx.x + h][m];
-      }
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      p.stat_sums[m] = r_sum[0][m];
-      p.stat_counts[m] = r_cnt[0][m];
-    }
-    *p.done = 0u;  // ready for the next launch (stream-ordered)
-  }
+  finalize_partials<T, kThreads>(p, nblocks);
 }
 
 // ---------------------------------------------------------------- fixup ----

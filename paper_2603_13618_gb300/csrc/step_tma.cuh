@@ -138,7 +138,7 @@ step_tma_kernel(const StepParams<T> p, const TmaPlan plan) {
   using VT = typename Vec<T>::type;
 
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ double s_sum[kTmaWarps][3];
+  __shared__ Red<T> s_sum[kTmaWarps][3];
   __shared__ uint32_t s_cnt[kTmaWarps][3];
   __shared__ int s_last;
 
@@ -305,29 +305,29 @@ step_tma_kernel(const StepParams<T> p, const TmaPlan plan) {
     n_np += __shfl_xor_sync(kFull, n_np, off);
   }
   if (lane == 0) {
-    s_sum[warp][0] = a_rho.value();
-    s_sum[warp][1] = a_jx.value();
-    s_sum[warp][2] = a_jy.value();
+    s_sum[warp][0] = Red<T>::of(a_rho);
+    s_sum[warp][1] = Red<T>::of(a_jx);
+    s_sum[warp][2] = Red<T>::of(a_jy);
     s_cnt[warp][0] = n_ref;
     s_cnt[warp][1] = n_sw;
     s_cnt[warp][2] = n_np;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+    Red<T> t0, t1, t2;
     uint32_t c0 = 0, c1 = 0, c2 = 0;
     for (int w = 0; w < kTmaWarps; ++w) {
-      t0 += s_sum[w][0];
-      t1 += s_sum[w][1];
-      t2 += s_sum[w][2];
+      t0.add(s_sum[w][0]);
+      t1.add(s_sum[w][1]);
+      t2.add(s_sum[w][2]);
       c0 += s_cnt[w][0];
       c1 += s_cnt[w][1];
       c2 += s_cnt[w][2];
     }
     const int b = blockIdx.x;
-    p.part_sum[3 * b + 0] = t0;
-    p.part_sum[3 * b + 1] = t1;
-    p.part_sum[3 * b + 2] = t2;
+    t0.store(p.part_sum + 3 * b + 0);
+    t1.store(p.part_sum + 3 * b + 1);
+    t2.store(p.part_sum + 3 * b + 2);
     p.part_cnt[4 * b + 0] = c0;
     p.part_cnt[4 * b + 1] = c1;
     p.part_cnt[4 * b + 2] = c2;
@@ -335,24 +335,9 @@ step_tma_kernel(const StepParams<T> p, const TmaPlan plan) {
     s_last = atomicAdd(p.done, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (s_last && threadIdx.x == 0) {
-    __threadfence();
-    double t[3] = {0.0, 0.0, 0.0};
-    unsigned long long u[3] = {0, 0, 0};
-    for (int b = 0; b < int(gridDim.x); ++b) {
-#pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        t[m] += __ldcg(p.part_sum + 3 * b + m);
-        u[m] += __ldcg(p.part_cnt + 4 * b + m);
-      }
-    }
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      p.stat_sums[m] = t[m];
-      p.stat_counts[m] = u[m];
-    }
-    *p.done = 0u;
-  }
+  if (!s_last) return;
+  __threadfence();
+  finalize_partials<T, kTmaThreads>(p, gridDim.x);
 }
 
 }  // namespace kss
