@@ -53,10 +53,13 @@ constexpr int kMaxBands = 8;  // tile bands per CTA of step_kernel (rows = bands
 // CTA / 8 warps, 32 * V <= 128 columns), as CTA-local offsets.
 constexpr int kWarpDefer = 8 * 128;
 
-// Tile bands per CTA: about 32 rows per CTA (4 per warp) amortise the CTA's epilogue;
-// taller CTAs would leave a longer tail of partly filled waves.
+// Tile bands per CTA: about KSS_STEP_ROWS rows per CTA (32: 4 per warp) amortise the
+// CTA's epilogue; taller CTAs would leave a longer tail of partly filled waves.
+#ifndef KSS_STEP_ROWS
+#define KSS_STEP_ROWS 32
+#endif
 __host__ __device__ constexpr int step_bands(int tile) {
-  return tile >= 32 ? 1 : 32 / tile;
+  return tile >= KSS_STEP_ROWS ? 1 : KSS_STEP_ROWS / tile;
 }
 constexpr unsigned kFull = 0xffffffffu;
 // Flag bit of a cell whose {Kn, KL, neq} the fused pass could not prove exact; set only
