@@ -179,6 +179,62 @@ const char* kss_last_error(const kss_lattice* lat);
 /* Library version (major * 10000 + minor * 100 + patch). */
 int kss_version(void);
 
+/* ---- Batches: many independent lattices advanced by one launch per step -------------
+ * Under structured adaptive mesh refinement the discrete model is solved uniformly on
+ * every patch of every level (section "Static refinement"): many lattices of different
+ * sizes, most of them too small to fill the GPU one launch at a time.  A batch owns n lattices of any sizes and advances all
+ * of them with one launch of the fused step per time step: the lattices' CTA blocks form
+ * one work list.  Each member gives exactly the results it would give alone with the
+ * same CTA height (populations, sensors, flags, tile counts and counts bit for bit; the
+ * conservation sums too when its CTA height is its default one).
+ *
+ * Members are ordinary kss_lattice handles (set fields, read outputs, even step one
+ * alone); kss_destroy on a member does nothing, kss_batch_destroy frees them all.
+ * All members share one precision and one stream (those of cfgs[0]; the batch's own
+ * non-blocking stream if cfgs[0].own_stream).  Batched steps always use the vector
+ * kernel.  A batched step is an output step (each member's own sensor set, flags, tile
+ * counts and sums) for every member when it is one for any member by its own
+ * output_every; the populations do not depend on which steps are output steps. */
+typedef struct kss_batch kss_batch;  /* opaque */
+
+typedef struct {
+  int32_t rows;         /* CTA height in rows: 16, 32 or 64, a multiple of every member's */
+                        /* tile; 0 = 32 (the single-lattice default; 64 with a tile of 64) */
+  int32_t ctas_per_sm;  /* 0: one CTA per work item; k > 0: k CTAs per SM, each striding */
+                        /* over the work items (persistent)                              */
+  int32_t graph;        /* 1: kss_batch_step captures its launches once per (step count, */
+                        /* output pattern) as a CUDA graph and replays it               */
+  double ms_per_step;   /* kss_batch_autotune: measured time of one output step of the  */
+                        /* whole batch with this choice; ignored by kss_batch_set_tuning */
+} kss_batch_tuning;
+
+/* Create n >= 1 lattices from cfgs[0..n-1] (each validated as by kss_create).  Members
+ * start with zero populations, like kss_create. */
+int kss_batch_create(int32_t n, const kss_config* cfgs, kss_batch** out);
+/* Free the batch and all its members after the stream drains (NULL-safe). */
+void kss_batch_destroy(kss_batch* b);
+/* Member k (0 <= k < n), owned by the batch; NULL if k is out of range. */
+kss_lattice* kss_batch_member(kss_batch* b, int32_t k);
+/* Advance every member nsteps >= 0 steps, one launch per step (asynchronous on the
+ * batch's stream).  Returns a member's sticky error if one has any. */
+int kss_batch_step(kss_batch* b, int32_t nsteps);
+/* Current work decomposition, and a new one (validated; KSS_ERR_ARG if rows is not a
+ * multiple of every member's tile). */
+int kss_batch_get_tuning(const kss_batch* b, kss_batch_tuning* t);
+int kss_batch_set_tuning(kss_batch* b, const kss_batch_tuning* t);
+/* Choose rows and ctas_per_sm by timing `steps` output steps of every candidate on the
+ * members themselves, or take the choice from cache_path (a text file, one line per
+ * key "device name|SMs|precision|log2 cells|log2 lattices"; NULL = no file) when it
+ * holds one for this batch's key; a new measurement is appended to the file.  The timed
+ * launches read each member's stored state and write its other buffer, so every member
+ * must be at step 0 (just created or set): KSS_ERR_STATE otherwise.  The members' stored
+ * states are unchanged; their outputs are evaluated again on the next read.  The choice
+ * is applied (graph as before) and returned in *chosen (may be NULL). */
+int kss_batch_autotune(kss_batch* b, const char* cache_path, int32_t steps,
+                       kss_batch_tuning* chosen);
+/* Last error message of the batch's own calls. */
+const char* kss_batch_last_error(const kss_batch* b);
+
 /* ---- Allocation-free fused step (no counterpart in the paper) ----------------------
  * For callers that cannot call cudaMalloc: code that owns all device memory itself
  * (a pool or framework allocator whose buffers it hands in), or that must not allocate

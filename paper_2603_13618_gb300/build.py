@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libkss.so")
-SOURCES = ["launch_f32.cu", "launch_f64.cu", "kss_runtime.cu", "kss_noalloc.cu"]
+SOURCES = ["launch_f32.cu", "launch_f64.cu", "kss_runtime.cu", "kss_batch.cu", "kss_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

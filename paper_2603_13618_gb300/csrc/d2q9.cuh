@@ -41,6 +41,10 @@ template <> struct Num<float> {
   __device__ static __forceinline__ float log1p_(float x) { return log1pf(x); }
   __device__ static __forceinline__ float sqrt_(float x) { return sqrtf(x); }
   __device__ static __forceinline__ float inf() { return CUDART_INF_F; }
+  // rounded product / sum that the compiler never fuses into an FMA (see equilibrium)
+  __device__ static __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  __device__ static __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  __device__ static __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
 };
 
 template <> struct Num<double> {
@@ -51,6 +55,9 @@ template <> struct Num<double> {
   __device__ static __forceinline__ double log1p_(double x) { return log1p(x); }
   __device__ static __forceinline__ double sqrt_(double x) { return sqrt(x); }
   __device__ static __forceinline__ double inf() { return CUDART_INF; }
+  __device__ static __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  __device__ static __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  __device__ static __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
 };
 
 // Coefficient of x^n in phi(x) = (1 + x) ln(1 + x) - x = sum_{n>=2} (-1)^n x^n / (n (n-1)),
@@ -92,23 +99,31 @@ __device__ __forceinline__ T phi(T x) {
 
 // Grad-Hermite equilibrium to second order at R T_ref = c_s^2 = 1/3, expanded:
 // f^eq_q = w_q rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u).
+//
+// Every rounding of the collision is fixed: the velocity u = j / rho, the diagonal
+// projections u_x +- u_y and each f^eq_q are rounded products / sums (Num::mul, add,
+// sub) that the compiler cannot contract with the subtraction f - f^eq that follows,
+// and the other operations are explicit FMAs.  The kernels that step with or without
+// sensors (and the all-sensor per-cell path) therefore produce the same populations
+// bit for bit, and rho w_q is formed as rho (1/9) times 4, 1 or 1/4 (exact scalings).
 template <class T>
 __device__ __forceinline__ void equilibrium(T rho, T ux, T uy, T (&feq)[9]) {
   const T base = fma(T(-1.5), fma(ux, ux, uy * uy), T(1));
-  const T r0 = rho * T(4.0 / 9.0), r1 = rho * T(1.0 / 9.0), r2 = rho * T(1.0 / 36.0);
-  feq[0] = r0 * base;
+  const T r1 = rho * T(1.0 / 9.0);
+  const T r0 = T(4) * r1, r2 = T(0.25) * r1;
+  feq[0] = Num<T>::mul(r0, base);
   const T tx = fma(T(4.5) * ux, ux, base), ty = fma(T(4.5) * uy, uy, base);
-  feq[1] = r1 * fma(T(3), ux, tx);
-  feq[3] = r1 * fma(T(-3), ux, tx);
-  feq[2] = r1 * fma(T(3), uy, ty);
-  feq[4] = r1 * fma(T(-3), uy, ty);
-  const T s = ux + uy;  // c5 = (1,1): c.u = s ; c7 = -c5
-  const T d = uy - ux;  // c6 = (-1,1): c.u = d ; c8 = -c6
+  feq[1] = Num<T>::mul(r1, fma(T(3), ux, tx));
+  feq[3] = Num<T>::mul(r1, fma(T(-3), ux, tx));
+  feq[2] = Num<T>::mul(r1, fma(T(3), uy, ty));
+  feq[4] = Num<T>::mul(r1, fma(T(-3), uy, ty));
+  const T s = Num<T>::add(ux, uy);  // c5 = (1,1): c.u = s ; c7 = -c5
+  const T d = Num<T>::sub(uy, ux);  // c6 = (-1,1): c.u = d ; c8 = -c6
   const T ts = fma(T(4.5) * s, s, base), td = fma(T(4.5) * d, d, base);
-  feq[5] = r2 * fma(T(3), s, ts);
-  feq[7] = r2 * fma(T(-3), s, ts);
-  feq[6] = r2 * fma(T(3), d, td);
-  feq[8] = r2 * fma(T(-3), d, td);
+  feq[5] = Num<T>::mul(r2, fma(T(3), s, ts));
+  feq[7] = Num<T>::mul(r2, fma(T(-3), s, ts));
+  feq[6] = Num<T>::mul(r2, fma(T(3), d, td));
+  feq[8] = Num<T>::mul(r2, fma(T(-3), d, td));
 }
 
 // Per-cell results that the kernels reduce or store.
@@ -154,7 +169,7 @@ __device__ __forceinline__ void cell_update(const T (&ft)[9], T omega, T tau, T 
   const T jx = (ft[1] + ft[5] + ft[8]) - (ft[3] + ft[6] + ft[7]);
   const T jy = (ft[2] + ft[5] + ft[6]) - (ft[4] + ft[7] + ft[8]);
   const T inv_rho = Num<T>::rcp(rho);
-  const T ux = jx * inv_rho, uy = jy * inv_rho;
+  const T ux = Num<T>::mul(jx, inv_rho), uy = Num<T>::mul(jy, inv_rho);
   T feq[9];
   equilibrium<T>(rho, ux, uy, feq);
   o.rho = rho;
@@ -162,7 +177,7 @@ __device__ __forceinline__ void cell_update(const T (&ft)[9], T omega, T tau, T 
   o.jy = jy;
   if (COLLIDE) {
 #pragma unroll
-    for (int q = 0; q < 9; ++q) fo[q] = fma(omega, feq[q] - ft[q], ft[q]);
+    for (int q = 0; q < 9; ++q) fo[q] = fma(-omega, ft[q] - feq[q], ft[q]);
   }
   if (MODE == MODE_PLAIN) {
     o.nonpos = false;

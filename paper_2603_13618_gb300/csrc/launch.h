@@ -8,11 +8,12 @@
 
 namespace kss {
 
-// Grid of the fused step for an nx x ny lattice with tagging tile `tile`.
+// Grid of the fused step for an nx x ny lattice with tagging tile `tile` and
+// `bands` tile bands per CTA (0: the default, step_bands(tile)).
 template <class T>
-inline dim3 step_grid(int nx, int ny, int tile) {
+inline dim3 step_grid(int nx, int ny, int tile, int bands = 0) {
   const int cols = 32 * Vec<T>::N;
-  const int rows = tile * step_bands(tile);
+  const int rows = tile * (bands > 0 ? bands : step_bands(tile));
   return dim3((unsigned)((nx + cols - 1) / cols), (unsigned)((ny + rows - 1) / rows), 1u);
 }
 
@@ -22,6 +23,13 @@ inline dim3 step_grid(int nx, int ny, int tile) {
 template <class T>
 cudaError_t launch_step(const StepParams<T>& p, int mode, bool pull, bool store,
                         cudaStream_t stream);
+
+// One batched step (batch_step_kernel): `table` holds one StepParams per lattice
+// (grid_x, nblocks and bands set), `items` the nitems CTA blocks; `ctas` CTAs (<= nitems)
+// stride over the items.  mode MODE_PLAIN / MODE_STD / MODE_FULL; always pull + store.
+template <class T>
+cudaError_t launch_batch_step(const StepParams<T>* table, const BatchItem* items, int nitems,
+                              int ctas, int mode, cudaStream_t stream);
 
 // The TMA-staged step (step_tma.cuh): mode MODE_PLAIN or MODE_STD, always pull + store;
 // `ctas` persistent CTAs (one per SM).

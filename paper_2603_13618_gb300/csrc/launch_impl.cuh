@@ -6,10 +6,9 @@
 
 namespace kss {
 
-inline int helper_grid(long long n) {
-  long long b = (n + 255) / 256;
-  if (b > 152LL * 16) b = 152LL * 16;  // grid-stride beyond 16 CTAs per SM
-  return b < 1 ? 1 : int(b);
+// (column blocks of 256) x (rows, strided beyond 65535) for the auxiliary kernels.
+inline dim3 helper_grid(int nx, long long rows) {
+  return dim3((unsigned)((nx + 255) / 256), (unsigned)(rows < 65535 ? rows : 65535));
 }
 
 template <>
@@ -32,6 +31,20 @@ cudaError_t launch_step<KSS_T>(const StepParams<KSS_T>& p, int mode, bool pull, 
     else return cudaErrorInvalidValue;
   } else {
     return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_batch_step<KSS_T>(const StepParams<KSS_T>* table, const BatchItem* items,
+                                     int nitems, int ctas, int mode, cudaStream_t stream) {
+  if (nitems < 1 || ctas < 1) return cudaErrorInvalidValue;
+  const dim3 grid(unsigned(ctas < nitems ? ctas : nitems)), block(kThreads);
+  switch (mode) {
+    case MODE_PLAIN: batch_step_kernel<KSS_T, MODE_PLAIN><<<grid, block, 0, stream>>>(table, items, nitems); break;
+    case MODE_STD: batch_step_kernel<KSS_T, MODE_STD><<<grid, block, 0, stream>>>(table, items, nitems); break;
+    case MODE_FULL: batch_step_kernel<KSS_T, MODE_FULL><<<grid, block, 0, stream>>>(table, items, nitems); break;
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
@@ -75,7 +88,7 @@ template <>
 cudaError_t launch_init_equilibrium<KSS_T>(const double* rho, const double* ux, const double* uy,
                                            KSS_T* f, long long plane, int pitch, int nx, int ny,
                                            cudaStream_t stream) {
-  init_equilibrium_kernel<KSS_T><<<helper_grid((long long)nx * ny), 256, 0, stream>>>(
+  init_equilibrium_kernel<KSS_T><<<helper_grid(nx, ny), 256, 0, stream>>>(
       rho, ux, uy, f, plane, pitch, nx, ny);
   return cudaGetLastError();
 }
@@ -83,7 +96,7 @@ cudaError_t launch_init_equilibrium<KSS_T>(const double* rho, const double* ux, 
 template <>
 cudaError_t launch_moments<KSS_T>(const KSS_T* f, long long plane, int pitch, int nx, int ny,
                                   double* rho, double* ux, double* uy, cudaStream_t stream) {
-  moments_kernel<KSS_T><<<helper_grid((long long)nx * ny), 256, 0, stream>>>(
+  moments_kernel<KSS_T><<<helper_grid(nx, ny), 256, 0, stream>>>(
       f, plane, pitch, nx, ny, rho, ux, uy);
   return cudaGetLastError();
 }
@@ -91,7 +104,7 @@ cudaError_t launch_moments<KSS_T>(const KSS_T* f, long long plane, int pitch, in
 template <>
 cudaError_t launch_pitched_to_dense<KSS_T>(const KSS_T* src, long long plane, int pitch, int nx,
                                            int ny, int nplanes, double* dst, cudaStream_t stream) {
-  pitched_to_dense_kernel<KSS_T><<<helper_grid((long long)nx * ny * nplanes), 256, 0, stream>>>(
+  pitched_to_dense_kernel<KSS_T><<<helper_grid(nx, ny), 256, 0, stream>>>(
       src, plane, pitch, nx, ny, nplanes, dst);
   return cudaGetLastError();
 }
@@ -99,7 +112,7 @@ cudaError_t launch_pitched_to_dense<KSS_T>(const KSS_T* src, long long plane, in
 template <>
 cudaError_t launch_dense_to_pitched<KSS_T>(const double* src, long long plane, int pitch, int nx,
                                            int ny, int nplanes, KSS_T* dst, cudaStream_t stream) {
-  dense_to_pitched_kernel<KSS_T><<<helper_grid((long long)nx * ny * nplanes), 256, 0, stream>>>(
+  dense_to_pitched_kernel<KSS_T><<<helper_grid(nx, ny), 256, 0, stream>>>(
       src, plane, pitch, nx, ny, nplanes, dst);
   return cudaGetLastError();
 }

@@ -1,0 +1,153 @@
+// runtime.h -- internal declarations shared by the host runtime's translation units
+// (kss_runtime.cu: single lattices; kss_batch.cu: batches of lattices).  Not part of
+// the C ABI.
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+#include <limits>
+#include <string>
+
+#include "../../include/kss.h"
+#include "launch.h"
+
+namespace kss_rt {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace kss_rt
+
+struct kss_batch;
+
+struct kss_lattice {
+  kss_config cfg{};
+  int device = 0;
+  size_t esz = 0;           // bytes per stored element
+  int pitch = 0;            // row pitch in elements (multiple of 128 bytes)
+  long long plane = 0;      // elements per plane
+  int ntx = 0, nty = 0, nblocks = 0;
+  int nsm = 0;              // SMs of the device (persistent grid of the TMA kernel)
+  void* f[2] = {nullptr, nullptr};
+  int cur = 0;              // f[cur] holds the stored state
+  void* rec = nullptr;      // recorded sensor planes
+  int rec_slot[KSS_S_COUNT];
+  void* evalplane = nullptr;
+  uint8_t* flags = nullptr;
+  int32_t* tiles = nullptr;
+  double* part_sum = nullptr;
+  uint32_t* part_cnt = nullptr;
+  unsigned char* small = nullptr;  // done counter + final sums + final counts
+  uint32_t* done = nullptr;
+  double* stat_sums = nullptr;
+  unsigned long long* stat_counts = nullptr;
+  uint32_t* err_word = nullptr;    // device error word (bounded waits)
+  uint32_t* defer_list = nullptr;  // cells deferred by the fused pass to its fixup
+  uint32_t defer_cap = 0;
+  double* staging = nullptr;
+  size_t staging_elems = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t step = 0;         // steps since the last set
+  int64_t out_step = -1;    // step whose flags / tiles / sums are stored
+  int64_t rec_step = -1;    // step whose recorded sensor planes are stored
+  int64_t eval_step = -1;   // step whose evalplane holds eval_sensor
+  int eval_sensor = -1;
+  int err = KSS_OK;
+  std::string msg;
+  kss_batch* owner = nullptr;  // the batch that created this lattice, if any
+};
+
+namespace kss_rt {
+
+inline int fail(kss_lattice* L, int code, const std::string& m) {
+  if (L) {
+    if (code == KSS_ERR_CUDA) L->err = code;  // sticky
+    L->msg = m;
+  }
+  return code;
+}
+
+#define KSS_CUDA(L, call)                                                             \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail((L), KSS_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+// Largest T value <= t, so that (T)eps > result  <=>  eps > t exactly.
+template <class T>
+inline T round_down(double t) {
+  T r = static_cast<T>(t);
+  if (static_cast<double>(r) > t) r = std::nextafter(r, -std::numeric_limits<T>::infinity());
+  return r;
+}
+
+inline uint32_t needed_mask(const kss_lattice* L, uint32_t extra) {
+  uint32_t m = extra | (1u << L->cfg.refine_sensor);
+  if (L->cfg.switch_threshold >= 0.0) m |= 1u << L->cfg.switch_sensor;
+  return m;
+}
+
+inline int mode_for(uint32_t mask) { return (mask & ~kss::kStdMask) ? kss::MODE_FULL : kss::MODE_STD; }
+
+template <class T>
+kss::StepParams<T> make_params(const kss_lattice* L, const void* src, void* dst) {
+  kss::StepParams<T> p{};
+  p.src = static_cast<const T*>(src);
+  p.dst = static_cast<T*>(dst);
+  p.rec = static_cast<T*>(L->rec);
+  p.flags = L->flags;
+  p.tiles = L->tiles;
+  p.tiles_def = L->tiles + 2 * size_t(L->ntx) * L->nty;
+  p.defer_list = L->defer_list;
+  p.defer_count = reinterpret_cast<uint32_t*>(L->small + 208);
+  p.defer_ticket = reinterpret_cast<uint32_t*>(L->small + 212);
+  p.defer_cap = L->defer_cap;
+  p.part_sum = L->part_sum;
+  p.part_cnt = L->part_cnt;
+  p.done = L->done;
+  p.stat_sums = L->stat_sums;
+  p.stat_counts = L->stat_counts;
+  p.err = L->err_word;
+  p.plane = L->plane;
+  p.pitch = L->pitch;
+  p.nx = L->cfg.nx;
+  p.ny = L->cfg.ny;
+  p.tile = L->cfg.tile;
+  p.bands = kss::step_bands(L->cfg.tile);
+  p.ntx = L->ntx;
+  p.nty = L->nty;
+  p.omega = T(1.0 / L->cfg.tau);
+  p.tau = T(L->cfg.tau);
+  p.thr_r = round_down<T>(L->cfg.refine_threshold);
+  p.switch_on = L->cfg.switch_threshold >= 0.0;
+  p.thr_s = p.switch_on ? round_down<T>(L->cfg.switch_threshold) : T(0);
+  p.refine_s = L->cfg.refine_sensor;
+  p.switch_s = L->cfg.switch_sensor;
+  for (int s = 0; s < KSS_S_COUNT; ++s) p.rec_slot[s] = L->rec_slot[s];
+  return p;
+}
+
+// Sticky error of a lattice, if any (KSS_ERR_ARG for NULL).
+inline int enter(kss_lattice* L) {
+  if (!L) return KSS_ERR_ARG;
+  if (L->err) return L->err;
+  return KSS_OK;
+}
+
+// Free a lattice's device buffers and stream after its stream drains (kss_runtime.cu).
+void release(kss_lattice* L);
+
+// After a stream synchronisation: did a bounded device wait run out?  (sticky)
+int device_error(kss_lattice* L);
+
+}  // namespace kss_rt

@@ -115,6 +115,9 @@ struct StepParams {
   T thr_r, thr_s;        // largest T values <= the thresholds: eps > thr exactly
   int refine_s, switch_s, switch_on;
   int bands;             // tile bands per CTA of step_kernel (CTA height = bands * tile)
+  int grid_x, nblocks;   // step grid of the lattice: CTAs per block row, CTAs in all
+                         // (read by the batched step only; step_kernel uses its grid)
+  int mode;              // the lattice's sensor set on output steps (batched step only)
   int rec_slot[S_COUNT];  // plane index of each recorded sensor, -1 if not recorded
 };
 
@@ -274,8 +277,8 @@ __device__ __forceinline__ void pair_pops(T (&fp)[Vec<T>::N], T (&fm)[Vec<T>::N]
 #pragma unroll
   for (int k = 0; k < V; ++k) {
     const T t = fma(T(4.5) * cu[k], cu[k], base[k]);
-    ep[k] = rw[k] * fma(T(3), cu[k], t);
-    em[k] = rw[k] * fma(T(-3), cu[k], t);
+    ep[k] = Num<T>::mul(rw[k], fma(T(3), cu[k], t));
+    em[k] = Num<T>::mul(rw[k], fma(T(-3), cu[k], t));
   }
   relax_pop<T, OUT, STORE>(fp, ep, omega, a);
   if (STORE && cv) vstore<T>(dst_p, fp);
@@ -538,8 +541,8 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<T>& p, T (&ft)[9]
       const T jx = (ft[1][k] + ft[5][k] + ft[8][k]) - (ft[3][k] + ft[6][k] + ft[7][k]);
       const T jy = (ft[2][k] + ft[5][k] + ft[6][k]) - (ft[4][k] + ft[7][k] + ft[8][k]);
       const T ir = Num<T>::rcp(rho);
-      ux[k] = jx * ir;
-      uy[k] = jy * ir;
+      ux[k] = Num<T>::mul(jx, ir);
+      uy[k] = Num<T>::mul(jy, ir);
       base[k] = fma(T(-1.5), fma(ux[k], ux[k], uy[k] * uy[k]), T(1));
       rw1[k] = rho * T(1.0 / 9.0);
       a.kn[k] = a.neq[k] = a.kl[k] = T(0);
@@ -557,7 +560,7 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<T>& p, T (&ft)[9]
     T feq[V];
     // q = 0 (rest)
 #pragma unroll
-    for (int k = 0; k < V; ++k) feq[k] = (T(4) * rw1[k]) * base[k];
+    for (int k = 0; k < V; ++k) feq[k] = Num<T>::mul(T(4) * rw1[k], base[k]);
     relax_pop<T, OUT, STORE>(ft[0], feq, p.omega, a);
     if (STORE && cv) vstore<T>(p.dst + 0 * p.plane + off, ft[0]);
     // axis pairs (1, 3): c.u = +-ux ; (2, 4): +-uy ; diagonal pairs (5, 7): +-(ux + uy),
@@ -569,14 +572,14 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<T>& p, T (&ft)[9]
     {
       T sd[V];
 #pragma unroll
-      for (int k = 0; k < V; ++k) sd[k] = ux[k] + uy[k];
+      for (int k = 0; k < V; ++k) sd[k] = Num<T>::add(ux[k], uy[k]);
       T rw2[V];
 #pragma unroll
       for (int k = 0; k < V; ++k) rw2[k] = T(0.25) * rw1[k];
       pair_pops<T, OUT, STORE>(ft[5], ft[7], sd, base, rw2, p.omega, a,
                                p.dst + 5 * p.plane + off, p.dst + 7 * p.plane + off, cv);
 #pragma unroll
-      for (int k = 0; k < V; ++k) sd[k] = uy[k] - ux[k];
+      for (int k = 0; k < V; ++k) sd[k] = Num<T>::sub(uy[k], ux[k]);
       pair_pops<T, OUT, STORE>(ft[6], ft[8], sd, base, rw2, p.omega, a,
                                p.dst + 6 * p.plane + off, p.dst + 8 * p.plane + off, cv);
     }
@@ -616,15 +619,18 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<T>& p, T (&ft)[9]
 //        flags, tile counts, sums).
 // PULL:  stream before evaluating (false: evaluate the stored state as it is).
 // STORE: collide and write the new populations (false: evaluation only).
+// One CTA's block (bx, by) of a lattice whose step grid is gx CTAs wide and nblocks CTAs
+// in all.  Called by every thread of the CTA; the CTA's shared memory is free again when
+// it returns.
 template <class T, int MODE, bool PULL, bool STORE>
-__global__ void __launch_bounds__(kThreads, MODE == MODE_FULL ? 1 : KSS_STEP_MIN_BLOCKS)
-step_kernel(const StepParams<T> p) {
+__device__ __forceinline__ void step_cta(const StepParams<T>& p, const int bx, const int by,
+                                         const int gx, const int nblocks) {
   constexpr int V = Vec<T>::N;
   constexpr bool OUT = MODE != MODE_PLAIN;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i0 = (blockIdx.x * 32 + lane) * V;
+  const int i0 = (bx * 32 + lane) * V;
   const bool cv = i0 < p.nx;
-  const int j0 = blockIdx.y * p.tile * p.bands;
+  const int j0 = by * p.tile * p.bands;
   const int j1 = min(j0 + p.tile * p.bands, p.ny);
 
   __shared__ int s_tiles[2][kMaxBands][32];
@@ -750,8 +756,7 @@ step_kernel(const StepParams<T> p) {
     s_wn[warp] = wn;
   }
   __syncthreads();
-  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-  const int nblocks = gridDim.x * gridDim.y;
+  const int bid = by * gx + bx;
   if (MODE == MODE_STD) {
     // the CTA's deferred cells, all threads at once: exact recomputation from the
     // unchanged source populations, then their tags join the CTA's counts
@@ -765,7 +770,7 @@ step_kernel(const StepParams<T> p) {
         while (r >= s_wn[w]) r -= s_wn[w++];
         const int o = s_dl[w][r];
         const int rl = o / (32 * V), cl = o - rl * (32 * V);
-        const int j = j0 + rl, i = blockIdx.x * 32 * V + cl;
+        const int j = j0 + rl, i = bx * 32 * V + cl;
         const uint32_t tags = fix_cell<T, PULL>(p, pr, ps, i, j);
         const int b = rl / p.tile, tl = cl / p.tile;
         if (tags & 1u) {
@@ -784,7 +789,7 @@ step_kernel(const StepParams<T> p) {
   const int tpb = (32 * V) / p.tile;
   for (int t = threadIdx.x; t < tpb * p.bands; t += kThreads) {
     const int b = t / tpb, tl = t - b * tpb;
-    const int tx = blockIdx.x * tpb + tl, ty = blockIdx.y * p.bands + b;
+    const int tx = bx * tpb + tl, ty = by * p.bands + b;
     if (tx < p.ntx && ty < p.nty) {
       const long long i = (long long)ty * p.ntx + tx;
       p.tiles[i] = s_tiles[0][b][tl];
@@ -823,6 +828,50 @@ step_kernel(const StepParams<T> p) {
   // ---- last block: add the per-block partials ----
   __threadfence();
   finalize_partials<T, kThreads>(p, nblocks);
+}
+
+template <class T, int MODE, bool PULL, bool STORE>
+__global__ void __launch_bounds__(kThreads, MODE == MODE_FULL ? 1 : KSS_STEP_MIN_BLOCKS)
+step_kernel(const StepParams<T> p) {
+  step_cta<T, MODE, PULL, STORE>(p, blockIdx.x, blockIdx.y, gridDim.x, gridDim.x * gridDim.y);
+}
+
+// ---------------------------------------------------------------- batched step ----
+// One step of many independent lattices of any sizes in one launch.  The lattices'
+// step grids are laid end to end in a work list of CTA blocks; CTA b takes work items
+// b, b + gridDim.x, ... (one item each when the grid covers the list, persistent CTAs
+// otherwise).  Each item is exactly step_kernel's CTA for that block of that lattice,
+// with the lattice's parameters copied to shared memory, so every lattice's results
+// are those of its own step_kernel launch with the same CTA height.  Each lattice keeps
+// its own completion counter and partial sums: the CTA that finishes a lattice's last
+// block forms that lattice's sums.
+struct BatchItem {
+  uint32_t lat;     // lattice index into the parameter table
+  uint32_t bx, by;  // CTA block of that lattice's step grid
+  uint32_t pad;
+};
+
+// MODE: MODE_PLAIN (no outputs), MODE_STD (every lattice with {Kn, KL, neq}) or
+// MODE_FULL (each lattice with its own set: p.mode, MODE_STD or MODE_FULL).
+template <class T, int MODE>
+__global__ void __launch_bounds__(kThreads, MODE == MODE_FULL ? 1 : KSS_STEP_MIN_BLOCKS)
+batch_step_kernel(const StepParams<T>* __restrict__ table, const BatchItem* __restrict__ items,
+                  int nitems) {
+  static_assert(sizeof(StepParams<T>) % 8 == 0, "parameter copy in 8-byte words");
+  __shared__ __align__(16) unsigned long long s_raw[sizeof(StepParams<T>) / 8];
+  const StepParams<T>& sp = *reinterpret_cast<const StepParams<T>*>(s_raw);
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const BatchItem it = items[w];
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(table + it.lat);
+    for (int k = threadIdx.x; k < int(sizeof(StepParams<T>) / 8); k += kThreads) s_raw[k] = src[k];
+    __syncthreads();
+    if (MODE != MODE_FULL || sp.mode != MODE_FULL)
+      step_cta<T, MODE == MODE_FULL ? MODE_STD : MODE, true, true>(sp, int(it.bx), int(it.by),
+                                                                  sp.grid_x, sp.nblocks);
+    else
+      step_cta<T, MODE_FULL, true, true>(sp, int(it.bx), int(it.by), sp.grid_x, sp.nblocks);
+    __syncthreads();  // the CTA's shared memory is reused by the next item
+  }
 }
 
 // ---------------------------------------------------------------- fixup ----
@@ -911,19 +960,26 @@ __global__ void __launch_bounds__(256) fixup_kernel(const StepParams<T> p) {
 
 // ---------------------------------------------------------------- helpers ----
 // f := f^eq(rho, u), computed in double and rounded once to T.
+// The auxiliary kernels below run on a grid of (column blocks of 256) x (rows), rows
+// strided by gridDim.y: one row per CTA row, so no 64-bit division per element.
+
+// f := f^eq(rho, u) from dense FP64 fields, evaluated in the storage precision T (the
+// FP64 pipe is a small fraction of the FP32 one on this GPU, and an FP32 lattice keeps
+// only FP32 populations).
 template <class T>
 __global__ void init_equilibrium_kernel(const double* __restrict__ rho,
                                         const double* __restrict__ ux,
                                         const double* __restrict__ uy, T* __restrict__ f,
                                         long long plane, int pitch, int nx, int ny) {
-  const long long n = (long long)nx * ny;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
-       c += (long long)gridDim.x * blockDim.x) {
-    const int j = int(c / nx), i = int(c - (long long)j * nx);
-    double feq[9];
-    equilibrium<double>(rho[c], ux[c], uy[c], feq);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx) return;
+  for (int j = blockIdx.y; j < ny; j += gridDim.y) {
+    const long long c = (long long)j * nx + i;
+    T feq[9];
+    equilibrium<T>(T(rho[c]), T(ux[c]), T(uy[c]), feq);
+    T* o = f + (long long)j * pitch + i;
 #pragma unroll
-    for (int q = 0; q < 9; ++q) f[q * plane + (long long)j * pitch + i] = T(feq[q]);
+    for (int q = 0; q < 9; ++q) o[q * plane] = feq[q];
   }
 }
 
@@ -932,13 +988,14 @@ template <class T>
 __global__ void moments_kernel(const T* __restrict__ f, long long plane, int pitch, int nx,
                                int ny, double* __restrict__ rho, double* __restrict__ ux,
                                double* __restrict__ uy) {
-  const long long n = (long long)nx * ny;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
-       c += (long long)gridDim.x * blockDim.x) {
-    const int j = int(c / nx), i = int(c - (long long)j * nx);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx) return;
+  for (int j = blockIdx.y; j < ny; j += gridDim.y) {
+    const long long c = (long long)j * nx + i;
+    const T* in = f + (long long)j * pitch + i;
     double v[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) v[q] = double(f[q * plane + (long long)j * pitch + i]);
+    for (int q = 0; q < 9; ++q) v[q] = double(in[q * plane]);
     const double r = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
     const double jx = (v[1] + v[5] + v[8]) - (v[3] + v[6] + v[7]);
     const double jy = (v[2] + v[5] + v[6]) - (v[4] + v[7] + v[8]);
@@ -952,28 +1009,22 @@ __global__ void moments_kernel(const T* __restrict__ f, long long plane, int pit
 template <class T>
 __global__ void pitched_to_dense_kernel(const T* __restrict__ src, long long plane, int pitch,
                                         int nx, int ny, int nplanes, double* __restrict__ dst) {
-  const long long n = (long long)nx * ny, total = n * nplanes;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < total;
-       c += (long long)gridDim.x * blockDim.x) {
-    const int q = int(c / n);
-    const long long r = c - q * n;
-    const int j = int(r / nx), i = int(r - (long long)j * nx);
-    dst[c] = double(src[q * plane + (long long)j * pitch + i]);
-  }
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx) return;
+  for (int q = 0; q < nplanes; ++q)
+    for (int j = blockIdx.y; j < ny; j += gridDim.y)
+      dst[((long long)q * ny + j) * nx + i] = double(src[q * plane + (long long)j * pitch + i]);
 }
 
 template <class T>
 __global__ void dense_to_pitched_kernel(const double* __restrict__ src, long long plane,
                                         int pitch, int nx, int ny, int nplanes,
                                         T* __restrict__ dst) {
-  const long long n = (long long)nx * ny, total = n * nplanes;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < total;
-       c += (long long)gridDim.x * blockDim.x) {
-    const int q = int(c / n);
-    const long long r = c - q * n;
-    const int j = int(r / nx), i = int(r - (long long)j * nx);
-    dst[q * plane + (long long)j * pitch + i] = T(src[c]);
-  }
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx) return;
+  for (int q = 0; q < nplanes; ++q)
+    for (int j = blockIdx.y; j < ny; j += gridDim.y)
+      dst[q * plane + (long long)j * pitch + i] = T(src[((long long)q * ny + j) * nx + i]);
 }
 
 }  // namespace kss

@@ -9,6 +9,10 @@ Workloads (all in lattice units, c_s = 1/sqrt(3)):
 
 * ``shear_wave``: the decaying shear wave rho = 1, u_x = u0 sin(2 pi y / ny),
   u_y = 0 (128 x 128, u0 = 0.01 for the FP64 correctness case).
+* ``batch_specs``: the batched workload of many uneven lattices: for lattice k,
+  a square size drawn from {64, 128, 256, 512, 1024}, tau ~ U[0.51, 1.5] and a Mach
+  number ~ U[0.01, 0.15], all from one SplitMix64 stream; its fields are
+  ``random_smooth`` (kmax 8) scaled to that Mach number.
 * ``smooth_jump``: a density step rho_L / rho_R = 2 at x = nx/2 (and at the
   periodic seam x = 0) times (1 + drho), with drho, u_x, u_y random smooth fields:
   sums of Fourier modes with integer wavevectors (kx, ky) in [-kmax, kmax]^2
@@ -122,3 +126,27 @@ def random_smooth(nx: int, ny: int, seed: int, kmax: int = 4, drho_amp: float = 
     """Smooth random fields without the density step (rho = 1 + drho)."""
     return smooth_jump(nx, ny, seed=seed, kmax=kmax, drho_amp=drho_amp, mach=mach,
                        jump=1.0)
+
+
+def batch_specs(n: int = 64, seed: int = 13618, sizes=(64, 128, 256, 512, 1024),
+                tau_range=(0.51, 1.5), mach_range=(0.01, 0.15)):
+    """[(size, tau, mach, field_seed)] of n square periodic lattices, drawn from one
+    SplitMix64 stream started at `seed` (three outputs per lattice)."""
+    st = seed & _M64
+    out = []
+    for k in range(n):
+        st, z1 = splitmix64(st)
+        st, z2 = splitmix64(st)
+        st, z3 = splitmix64(st)
+        u2 = ((z2 >> 11) + 0.5) / float(1 << 53)
+        u3 = ((z3 >> 11) + 0.5) / float(1 << 53)
+        size = sizes[z1 % len(sizes)]
+        tau = tau_range[0] + (tau_range[1] - tau_range[0]) * u2
+        mach = mach_range[0] + (mach_range[1] - mach_range[0]) * u3
+        out.append((size, tau, mach, seed * 1000 + k))
+    return out
+
+
+def batch_fields(size: int, mach: float, field_seed: int):
+    """(rho, ux, uy) of one lattice of the batched workload."""
+    return random_smooth(size, size, seed=field_seed, kmax=8, mach=mach)

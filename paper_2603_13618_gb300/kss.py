@@ -45,6 +45,11 @@ class Config(ctypes.Structure):
     ]
 
 
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("graph", ctypes.c_int32), ("ms_per_step", ctypes.c_double)]
+
+
 _lib = None
 
 # Every entry point declared in include/kss.h, with its ctypes signature.
@@ -68,6 +73,16 @@ _SIGNATURES = {
     "kss_read_stats": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "kss_get_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "kss_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "kss_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(Config),
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "kss_batch_destroy": (None, [ctypes.c_void_p]),
+    "kss_batch_member": (ctypes.c_void_p, [ctypes.c_void_p, ctypes.c_int32]),
+    "kss_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "kss_batch_get_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(BatchTuning)]),
+    "kss_batch_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(BatchTuning)]),
+    "kss_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int32,
+                                          ctypes.POINTER(BatchTuning)]),
+    "kss_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "kss_step_f32_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                             ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
@@ -120,6 +135,34 @@ def _torch_stream_handle():
     return torch.cuda.current_stream().cuda_stream
 
 
+def make_config(nx: int, ny: int, precision="fp32", tau: float = 0.8, refine_sensor="kn",
+                refine_threshold: float = 1e-3, switch_sensor="neq",
+                switch_threshold: float = 1e-4, record=("kl",), output_every: int = 1,
+                tile: int = 16, stream="torch", kernel="auto") -> Config:
+    """A kss_config (see include/kss.h).  stream: "torch" = torch's current stream
+    (handle 0 is the CUDA default stream), "own" = a stream created and owned by the
+    lattice, or a raw cudaStream_t handle."""
+    lib = load()
+    cfg = Config()
+    rc = lib.kss_config_default(ctypes.byref(cfg), nx, ny, PRECISIONS[precision])
+    if rc < 0:
+        raise KssError(rc, lib.kss_strerror(rc).decode())
+    cfg.tau = tau
+    cfg.refine_sensor = _sensor(refine_sensor)
+    cfg.refine_threshold = refine_threshold
+    cfg.switch_sensor = _sensor(switch_sensor)
+    cfg.switch_threshold = switch_threshold
+    cfg.record_mask = sum(1 << _sensor(s) for s in record)
+    cfg.output_every = output_every
+    cfg.tile = tile
+    cfg.kernel = KERNELS[kernel]
+    if stream == "own":
+        cfg.own_stream, cfg.stream = 1, None
+    else:
+        cfg.stream = _torch_stream_handle() if stream == "torch" else stream
+    return cfg
+
+
 class Lattice:
     """A periodic D2Q9 lattice on the current CUDA device (see include/kss.h)."""
 
@@ -128,32 +171,31 @@ class Lattice:
                  switch_threshold: float = 1e-4, record=("kl",), output_every: int = 1,
                  tile: int = 16, stream="torch", kernel="auto"):
         self._lib = load()
-        cfg = Config()
-        self._check(self._lib.kss_config_default(ctypes.byref(cfg), nx, ny,
-                                                  PRECISIONS[precision]))
-        cfg.tau = tau
-        cfg.refine_sensor = _sensor(refine_sensor)
-        cfg.refine_threshold = refine_threshold
-        cfg.switch_sensor = _sensor(switch_sensor)
-        cfg.switch_threshold = switch_threshold
-        cfg.record_mask = sum(1 << _sensor(s) for s in record)
-        cfg.output_every = output_every
-        cfg.tile = tile
-        cfg.kernel = KERNELS[kernel]
-        # stream: "torch" = torch's current stream (handle 0 is the CUDA default
-        # stream), "own" = a stream created and owned by the lattice, or a raw handle
-        if stream == "own":
-            cfg.own_stream, cfg.stream = 1, None
-        else:
-            cfg.stream = _torch_stream_handle() if stream == "torch" else stream
-        self.cfg = cfg
-        self.nx, self.ny, self.tile = nx, ny, tile
-        self.precision = PRECISIONS[precision]
-        handle = ctypes.c_void_p()
         self._h = None
+        cfg = make_config(nx, ny, precision=precision, tau=tau, refine_sensor=refine_sensor,
+                          refine_threshold=refine_threshold, switch_sensor=switch_sensor,
+                          switch_threshold=switch_threshold, record=record,
+                          output_every=output_every, tile=tile, stream=stream, kernel=kernel)
+        handle = ctypes.c_void_p()
         self._check(self._lib.kss_create(ctypes.byref(cfg), ctypes.byref(handle)))
+        self._adopt(handle, cfg, owned=True)
+
+    def _adopt(self, handle, cfg, owned: bool):
+        self.cfg = cfg
+        self.nx, self.ny, self.tile = cfg.nx, cfg.ny, cfg.tile
+        self.precision = cfg.precision
         self._h = handle
+        self._owned = owned
         self.last_status = KSS_OK
+
+    @classmethod
+    def _member(cls, lib, handle, cfg, batch):
+        """A batch member's handle (owned by the batch, which it keeps alive)."""
+        self = cls.__new__(cls)
+        self._lib = lib
+        self._adopt(ctypes.c_void_p(handle), cfg, owned=False)
+        self._batch = batch
+        return self
 
     # -- plumbing --
     def _check(self, rc: int) -> int:
@@ -167,7 +209,8 @@ class Lattice:
 
     def close(self):
         if getattr(self, "_h", None):
-            self._lib.kss_destroy(self._h)
+            if self._owned:
+                self._lib.kss_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -258,3 +301,80 @@ class Lattice:
 
     def sync(self) -> None:
         self._check(self._lib.kss_sync(self._h))
+
+
+class Batch:
+    """n independent lattices advanced by one launch per step (see include/kss.h).
+
+    ``specs``: one dict of ``make_config`` keyword arguments per lattice (each with
+    ``nx`` and ``ny``); ``common``: keyword arguments shared by all of them.  The
+    stream is the first lattice's.  ``members`` are ``Lattice`` objects owned by the
+    batch (closing them does nothing; ``close()`` frees the batch and its members).
+    """
+
+    def __init__(self, specs, **common):
+        self._lib = load()
+        self._h = None
+        cfgs = [make_config(**{**common, **sp}) for sp in specs]
+        arr = (Config * len(cfgs))(*cfgs)
+        handle = ctypes.c_void_p()
+        rc = self._lib.kss_batch_create(len(cfgs), arr, ctypes.byref(handle))
+        if rc < 0:
+            raise KssError(rc, self._lib.kss_strerror(rc).decode())
+        self._h = handle
+        self.members = [Lattice._member(self._lib, self._lib.kss_batch_member(handle, k), c, self)
+                        for k, c in enumerate(cfgs)]
+
+    def _check(self, rc: int) -> int:
+        if rc < 0:
+            detail = ""
+            if self._h:
+                detail = (self._lib.kss_batch_last_error(self._h) or b"").decode()
+            raise KssError(rc, f"{self._lib.kss_strerror(rc).decode()} {detail}".strip())
+        return rc
+
+    def __len__(self):
+        return len(self.members)
+
+    def __getitem__(self, k) -> Lattice:
+        return self.members[k]
+
+    def step(self, n: int = 1) -> None:
+        self._check(self._lib.kss_batch_step(self._h, int(n)))
+
+    @property
+    def tuning(self) -> dict:
+        t = BatchTuning()
+        self._check(self._lib.kss_batch_get_tuning(self._h, ctypes.byref(t)))
+        return {"rows": t.rows, "ctas_per_sm": t.ctas_per_sm, "graph": t.graph,
+                "ms_per_step": t.ms_per_step}
+
+    def set_tuning(self, rows: int = 0, ctas_per_sm: int = 0, graph: int = 1) -> None:
+        t = BatchTuning(rows, ctas_per_sm, graph, 0.0)
+        self._check(self._lib.kss_batch_set_tuning(self._h, ctypes.byref(t)))
+
+    def autotune(self, cache_path: str | None = None, steps: int = 10) -> dict:
+        t = BatchTuning()
+        path = cache_path.encode() if cache_path else None
+        self._check(self._lib.kss_batch_autotune(self._h, path, int(steps), ctypes.byref(t)))
+        return {"rows": t.rows, "ctas_per_sm": t.ctas_per_sm, "graph": t.graph,
+                "ms_per_step": t.ms_per_step}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for m in self.members:
+                m._h = None
+            self._lib.kss_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
