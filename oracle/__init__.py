@@ -70,6 +70,7 @@ def lib():
             "orc_mac_sensors": (None, [ci, ci, cd, dp, dp, dp, dp]),
             "orc_run": (ctypes.c_int64, [ci, ci, cd, dp, dp, ci, ci, cd, ci, cd, ci,
                                           dp, u8p, i32p, i64p, dp]),
+            "orc_adjoint_kl": (ci, [ci, ci, cd, ci, ci, dp, dp, dp, dp, dp, dp, dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -215,3 +216,28 @@ def run(f, tau: float, nsteps: int, sensor_r: int, thr_r: float, sensor_s: int,
                   _p(tiles, ctypes.c_int32), _p(counts, ctypes.c_int64), _p(sm))
     return {"f": f, "eps_r": rec, "flags": fl, "tiles": tiles, "counts": counts,
             "sums": sm}
+
+
+def adjoint_kl(rho0, ux0, uy0, tau: float, nsteps: int, weight=None, store_every: int = 1):
+    """(J, dJ/drho0 [ny, nx], dJ/dtau) of J = sum W eps_KL at step nsteps (orc.h)."""
+    rho0, ux0, uy0 = _f64(rho0), _f64(ux0), _f64(uy0)
+    ny, nx = rho0.shape
+    w = None if weight is None else _f64(weight)
+    J, gt = ctypes.c_double(), ctypes.c_double()
+    g = np.empty((ny, nx))
+    rc = lib().orc_adjoint_kl(nx, ny, tau, nsteps, store_every, _p(rho0), _p(ux0), _p(uy0),
+                              None if w is None else _p(w), ctypes.byref(J), _p(g),
+                              ctypes.byref(gt))
+    if rc != 0:
+        raise MemoryError("orc_adjoint_kl failed")
+    return J.value, g, gt.value
+
+
+def objective_kl(rho0, ux0, uy0, tau: float, nsteps: int, weight=None) -> float:
+    """J = sum W eps_KL of step nsteps by plain forward steps and the sensor fields
+    (no adjoint code involved)."""
+    f = init_equilibrium(rho0, ux0, uy0)
+    f = step(f, tau, nsteps - 1)
+    kl = sensor_fields(f, tau, pull=True)[0][SENSOR_ID["kl"]]
+    w = 1.0 if weight is None else _f64(weight)
+    return float(np.sum(w * kl))

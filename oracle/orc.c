@@ -483,3 +483,161 @@ int64_t orc_run(int nx, int ny, double tau, double* f, double* work, int nsteps,
   free(np);
   return counts[2];
 }
+
+/* ---------------------------------------------------------------- adjoint ----
+ * Reverse-mode derivative of the sensor objective of orc_adjoint_kl (orc.h).
+ * Everything below differentiates the definitions used above as written: the
+ * Grad-Hermite equilibrium, the BGK collision, pull streaming, and the KL sensor
+ * in its printed form eps_KL = |sum_i f_i ln(f_i / f^eq_i)| (Eq. HKL-sensor). */
+
+/* Derivatives of the equilibrium with respect to the conserved moments rho and
+ * j = rho u.  With u = j / rho the GH expansion of orc_equilibrium reads
+ *   f^eq_i = w_i (rho + c_i.j / c_s^2 + ((c_i.j)^2 - c_s^2 |j|^2) / (2 c_s^4 rho)). */
+static void feq_moment_derivs(double rho, double jx, double jy, double drho[9],
+                              double djx[9], double djy[9]) {
+  const double j2 = jx * jx + jy * jy;
+  for (int q = 0; q < 9; ++q) {
+    const double cj = CX[q] * jx + CY[q] * jy;
+    drho[q] = W[q] * (1.0 - (cj * cj - CS2 * j2) / (2.0 * CS2 * CS2 * rho * rho));
+    djx[q] = W[q] * (CX[q] / CS2 + (cj * CX[q] - CS2 * jx) / (CS2 * CS2 * rho));
+    djy[q] = W[q] * (CY[q] / CS2 + (cj * CY[q] - CS2 * jy) / (CS2 * CS2 * rho));
+  }
+}
+
+/* d f^eq_q / d f_p: f^eq depends on f through rho = sum f and j = sum c f. */
+static double feq_dfp(const double drho[9], const double djx[9], const double djy[9], int q,
+                      int p) {
+  return drho[q] + CX[p] * djx[q] + CY[p] * djy[q];
+}
+
+/* Gradient g[9] of eps_KL(ft) = |K|, K = sum_q ft_q ln(ft_q / f^eq_q(ft)):
+ *   dK/dft_p = ln(ft_p / f^eq_p) + 1 - sum_q (ft_q / f^eq_q) d f^eq_q / d ft_p,
+ * times sign(K).  Cells with a non-positive population get NaN. */
+static void cell_kl_grad(const double ft[9], double g[9]) {
+  double rho = 0.0, jx = 0.0, jy = 0.0;
+  for (int q = 0; q < 9; ++q) {
+    rho += ft[q];
+    jx += CX[q] * ft[q];
+    jy += CY[q] * ft[q];
+  }
+  double feq[9], drho[9], djx[9], djy[9];
+  orc_equilibrium(rho, jx / rho, jy / rho, feq);
+  feq_moment_derivs(rho, jx, jy, drho, djx, djy);
+  int nonpos = 0;
+  double K = 0.0;
+  for (int q = 0; q < 9; ++q) {
+    if (ft[q] <= 0.0 || feq[q] <= 0.0) nonpos = 1;
+    K += feq[q] * phi(ft[q] / feq[q] - 1.0);  /* = sum ft ln(ft/feq), as in orc_cell_sensors */
+  }
+  const double sgn = K > 0.0 ? 1.0 : (K < 0.0 ? -1.0 : 0.0);
+  for (int p = 0; p < 9; ++p) {
+    if (nonpos) {
+      g[p] = NAN;
+      continue;
+    }
+    double s = 0.0;
+    for (int q = 0; q < 9; ++q) s += (ft[q] / feq[q]) * feq_dfp(drho, djx, djy, q, p);
+    g[p] = sgn * (log(ft[p] / feq[p]) + 1.0 - s);
+  }
+}
+
+/* Transpose of orc_stream: lf_q(i, j) = lt_q(i + cx_q, j + cy_q). */
+static void stream_transpose(int nx, int ny, const double* lt, double* lf) {
+  for (int q = 0; q < 9; ++q)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i)
+        lf[at(nx, ny, q, i, j)] = lt[at(nx, ny, q, wrap(i + CX[q], nx), wrap(j + CY[q], ny))];
+}
+
+int orc_adjoint_kl(int nx, int ny, double tau, int nsteps, int store_every, const double* rho0,
+                   const double* ux0, const double* uy0, const double* weight, double* J,
+                   double* grad_rho0, double* grad_tau) {
+  if (nsteps < 1 || store_every < 1) return -1;
+  const size_t n = (size_t)nx * ny, S = 9 * n;
+  /* f^0 .. f^{N-1}: every store_every-th state kept, the others recomputed per segment */
+  const int nck = (nsteps - 1) / store_every + 1;
+  double* ck = (double*)malloc(sizeof(double) * S * (size_t)nck);
+  double* seg = (double*)malloc(sizeof(double) * S * (size_t)store_every);
+  double* ft = (double*)malloc(sizeof(double) * S);
+  double* lt = (double*)malloc(sizeof(double) * S);
+  double* lf = (double*)malloc(sizeof(double) * S);
+  if (!ck || !seg || !ft || !lt || !lf) {
+    free(ck), free(seg), free(ft), free(lt), free(lf);
+    return -1;
+  }
+  orc_init_equilibrium(nx, ny, rho0, ux0, uy0, ck);
+  double* cur = ft; /* scratch while stepping forward */
+  memcpy(cur, ck, sizeof(double) * S);
+  for (int k = 1; k < nsteps; ++k) {
+    orc_step(nx, ny, tau, cur, lt);
+    memcpy(cur, lt, sizeof(double) * S);
+    if (k % store_every == 0) memcpy(ck + S * (size_t)(k / store_every), cur, sizeof(double) * S);
+  }
+  /* cur = f^{N-1}.  Objective on its streamed image, and its gradient lt = dJ/dft^{N-1}. */
+  double* fN = lf;
+  memcpy(fN, cur, sizeof(double) * S);
+  orc_stream(nx, ny, fN, ft);
+  double js = 0.0, jc = 0.0;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      double c[9], s[ORC_NSENS], g[9];
+      for (int q = 0; q < 9; ++q) c[q] = ft[at(nx, ny, q, i, j)];
+      orc_cell_sensors(c, tau, s);
+      cell_kl_grad(c, g);
+      const double w = weight ? weight[(size_t)j * nx + i] : 1.0;
+      kahan_add(&js, &jc, w * s[ORC_KL]);
+      for (int q = 0; q < 9; ++q) lt[at(nx, ny, q, i, j)] = w * g[q];
+    }
+  *J = js + jc;
+  /* Reverse sweep over f^{n+1} = collide(stream(f^n)), n = N-2 .. 0:
+   * lf = dJ/df^{n+1} = stream^T(lt), then lt = dJ/dft^n = (d collide / d ft)^T lf and
+   * dJ/dtau += sum lf . d collide/d tau = sum lf (ft - f^eq) / tau^2. */
+  double gs = 0.0, gc = 0.0;
+  for (int seg0 = ((nsteps - 2) / store_every) * store_every; nsteps >= 2 && seg0 >= 0;
+       seg0 -= store_every) {
+    /* states f^{seg0} .. f^{seg0 + store_every - 1} of this segment (those < N-1) */
+    const int last = seg0 + store_every - 1 < nsteps - 2 ? seg0 + store_every - 1 : nsteps - 2;
+    memcpy(seg, ck + S * (size_t)(seg0 / store_every), sizeof(double) * S);
+    for (int k = seg0 + 1; k <= last; ++k)
+      orc_step(nx, ny, tau, seg + S * (size_t)(k - 1 - seg0), seg + S * (size_t)(k - seg0));
+    for (int k = last; k >= seg0; --k) {
+      stream_transpose(nx, ny, lt, lf);
+      orc_stream(nx, ny, seg + S * (size_t)(k - seg0), ft);
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+          double c[9], l[9], feq[9], drho[9], djx[9], djy[9];
+          double rho = 0.0, jx = 0.0, jy = 0.0;
+          for (int q = 0; q < 9; ++q) {
+            c[q] = ft[at(nx, ny, q, i, j)];
+            l[q] = lf[at(nx, ny, q, i, j)];
+            rho += c[q];
+            jx += CX[q] * c[q];
+            jy += CY[q] * c[q];
+          }
+          orc_equilibrium(rho, jx / rho, jy / rho, feq);
+          feq_moment_derivs(rho, jx, jy, drho, djx, djy);
+          for (int q = 0; q < 9; ++q) kahan_add(&gs, &gc, l[q] * (c[q] - feq[q]) / (tau * tau));
+          for (int p = 0; p < 9; ++p) {
+            /* d fnext_q / d ft_p = delta_qp (1 - 1/tau) + (1/tau) d f^eq_q / d ft_p */
+            double s = 0.0;
+            for (int q = 0; q < 9; ++q) s += l[q] * feq_dfp(drho, djx, djy, q, p);
+            lt[at(nx, ny, p, i, j)] = (1.0 - 1.0 / tau) * l[p] + s / tau;
+          }
+        }
+    }
+  }
+  *grad_tau = gs + gc;
+  /* dJ/df^0 = stream^T(lt); f^0 = f^eq(rho0, u0) is rho0 times f^eq(1, u0) at fixed u0 */
+  stream_transpose(nx, ny, lt, lf);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const size_t c = (size_t)j * nx + i;
+      double e1[9];
+      orc_equilibrium(1.0, ux0[c], uy0[c], e1);
+      double s = 0.0;
+      for (int q = 0; q < 9; ++q) s += lf[at(nx, ny, q, i, j)] * e1[q];
+      grad_rho0[c] = s;
+    }
+  free(ck), free(seg), free(ft), free(lt), free(lf);
+  return 0;
+}

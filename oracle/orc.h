@@ -19,6 +19,8 @@
  * beyond its printed polynomial (section "Entropic estimate sensor", Eqs.
  * alpha-polynomial-1/-2): the polynomial does not reproduce the exact mirror
  * root of Eq. H-mirr-equal to first order, so nothing independent fixes it.
+ * The discrete adjoint (orc_adjoint_kl) is pinned by central finite differences of
+ * the objective evaluated with the forward functions alone (tests/test_oracle_adjoint.py).
  */
 #ifndef ORC_H
 #define ORC_H
@@ -123,6 +125,19 @@ int64_t orc_run(int nx, int ny, double tau, double* f, double* work, int nsteps,
                 int sensor_r, double thr_r, int sensor_s, double thr_s, int tile,
                 double* rec_field, uint8_t* flags, int32_t* tiles, int64_t counts[3],
                 double sums[3]);
+
+/* Discrete adjoint of the sensor objective
+ *   J = sum_x W(x) eps_KL(ft(x)),  ft = stream(f^{N-1}),
+ *   f^0 = f^eq(rho0, u0),  f^{n+1} = collide(stream(f^n); tau),
+ * i.e. the KL sensor (Eq. HKL-sensor) of step N (its pre-collision state, as for
+ * every sensor here) summed over the lattice with weights W (NULL: W = 1).
+ * Outputs J, grad_rho0[ny][nx] = dJ/drho0 (u0 fixed) and grad_tau = dJ/dtau, by a
+ * reverse sweep through the steps (every store_every-th state kept, the others
+ * recomputed from it).  Gradients are NaN where a population is non-positive.
+ * Returns 0, or -1 (nsteps < 1, store_every < 1 or no memory). */
+int orc_adjoint_kl(int nx, int ny, double tau, int nsteps, int store_every, const double* rho0,
+                   const double* ux0, const double* uy0, const double* weight, double* J,
+                   double* grad_rho0, double* grad_tau);
 
 #ifdef __cplusplus
 }
