@@ -10,6 +10,7 @@ conservation sums.  A step = one fused launch over the whole lattice.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
   python bench.py --workload batch64    # the batched workload (below)
+  python bench.py --workload adjoint512 # the adjoint workload (below)
 
 Batched workload (--workload batch64): 64 uneven periodic lattices (sizes 64^2 ..
 1024^2, tau ~ U[0.51, 1.5], Mach ~ U[0.01, 0.15], seed 13618, 15.8 M cells in all), the
@@ -252,6 +253,69 @@ def run_batch(args):
     return 0
 
 
+ADJ_METRIC = "adjoint MLUPS (forward with checkpoints + reverse sweep), 1xGB300"
+
+
+def run_adjoint(args):
+    """The adjoint workload: time(forward + backward) against time(200 plain steps)."""
+    import numpy as np
+    import torch
+
+    from paper_2603_13618_gb300 import inputs, kss
+
+    torch.cuda.set_device(0)
+    n, N, E, tau = 512, 200, 20, 0.6
+    r, u, v = inputs.random_smooth(n, n, seed=1361, kmax=8, drho_amp=1e-2, mach=0.1)
+    dr, du, dv = (torch.tensor(a, device="cuda") for a in (r, u, v))
+    stream = torch.cuda.current_stream()
+    adj = kss.Adjoint(n, n, N, precision="fp32", checkpoint_every=E)
+    lat = kss.Lattice(n, n, precision="fp32", tau=tau, output_every=0)
+
+    def timed(fn, reps):
+        for _ in range(max(1, args.warmup // 10)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def gradient():
+        adj.forward(dr, du, dv, tau)
+        return adj.backward(device=True)
+
+    def plain():
+        lat.set_fields(dr, du, dv)
+        lat.step(N)
+
+    reps = max(3, args.steps // 100)
+    with ClockSampler(0) as clk:
+        t_adj = timed(gradient, reps)
+        t_fwd = timed(plain, reps)
+    g, gt = gradient()
+    cells = n * n
+    line = {
+        "metric": ADJ_METRIC, "value": cells * N / (t_adj * 1e-3) / 1e6, "unit": "MLUPS",
+        "n_gpus": 1, "steps": reps, "warmup": max(1, args.warmup // 10),
+        "ms_per_step": t_adj / N, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "gradient of the summed KL sensor of step 200 in rho0 and "
+                               "tau, 512x512 FP32, checkpoint every 20, tau=0.6, seed 1361",
+                   "nx": n, "ny": n, "nsteps": N, "checkpoint_every": E},
+        "ms_gradient": t_adj, "ms_forward_plain": t_fwd, "adjoint_over_forward": t_adj / t_fwd,
+        "grad_tau": gt, "grad_rho0_norm": float(torch.linalg.vector_norm(g)),
+        "gpu_launches_per_gradient": 1 + (N - 1) + (N - 1 - (N - 2) // E - 1) + (N - 1) + 1 + 1,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    adj.close()
+    lat.close()
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -419,8 +483,10 @@ def main():
                     help="step kernel (auto: the library's choice)")
     ap.add_argument("--size", type=int, default=4096,
                     help="lattice edge (profiling captures of a smaller case only)")
-    ap.add_argument("--workload", default="single", choices=["single", "batch64"],
-                    help="single: the 4096^2 lattice (default); batch64: 64 uneven lattices")
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "batch64", "adjoint512"],
+                    help="single: the 4096^2 lattice (default); batch64: 64 uneven "
+                         "lattices; adjoint512: the gradient of the KL objective")
     ap.add_argument("--no-tune", action="store_true",
                     help="batch64: keep the default work decomposition")
     args = ap.parse_args()
@@ -432,6 +498,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch64":
         return run_batch(args)
+    if args.workload == "adjoint512":
+        return run_adjoint(args)
     return run_gpu(args)
 
 

@@ -235,6 +235,49 @@ int kss_batch_autotune(kss_batch* b, const char* cache_path, int32_t steps,
 /* Last error message of the batch's own calls. */
 const char* kss_batch_last_error(const kss_batch* b);
 
+/* ---- Adjoint: gradients of a sensor objective -----------------------------------------
+ * Gradient of the sensor-weighted objective
+ *   J = sum_x W(x) eps_KL(x)    (Eq. HKL-sensor, the KL sensor of step nsteps, i.e. of
+ *                                the pre-collision populations that step N acts on)
+ * of a periodic lattice started from equilibrium populations f^eq(rho0, u0) (section
+ * "Evaluation of the local kinetic sensors": equilibrium initial conditions), with
+ * respect to the initial density field rho0 (u0 held fixed) and the relaxation time
+ * tau, by the discrete adjoint of the stream + collide steps (reverse mode through the
+ * exact discrete map; see adjoint_kernel.cuh).  The forward pass keeps every
+ * checkpoint_every-th state; the backward pass recomputes each segment from its
+ * checkpoint and runs the adjoint steps through it, so memory is
+ * (nsteps / checkpoint_every + checkpoint_every + 4) population buffers.
+ * The sensor-tuning use of such gradients is the data-driven outlook of the
+ * conclusions ("Summary and conclusions"). */
+typedef struct kss_adjoint kss_adjoint;  /* opaque */
+
+typedef struct {
+  int32_t nx, ny;            /* lattice size (as kss_config)                         */
+  int32_t precision;         /* KSS_FP32 or KSS_FP64: storage and arithmetic         */
+  int32_t nsteps;            /* N >= 1: J is evaluated on the sensors of step N      */
+  int32_t checkpoint_every;  /* >= 1; states kept every this many steps              */
+  void* stream;              /* cudaStream_t, NULL = the default stream              */
+  int32_t own_stream;        /* 1: a stream created and owned by the object          */
+} kss_adjoint_config;
+
+int kss_adjoint_create(const kss_adjoint_config* cfg, kss_adjoint** out);
+void kss_adjoint_destroy(kss_adjoint* adj);  /* NULL-safe */
+
+/* Forward pass: rho0, ux0, uy0 (nx*ny doubles each) and the weights W (nx*ny doubles,
+ * NULL = all 1), host or device memory by on_device; tau > 0.5.  Writes J (host) and
+ * keeps the checkpoints for kss_adjoint_backward.  J is +Inf if some population or
+ * equilibrium population of step N is non-positive. */
+int kss_adjoint_forward(kss_adjoint* adj, const double* rho0, const double* ux0,
+                        const double* uy0, const double* weight, double tau, int on_device,
+                        double* J);
+
+/* Backward pass of the last forward pass (once per forward pass): grad_rho0 = dJ/drho0
+ * (nx*ny doubles, host or device by on_device; may be NULL) and *grad_tau = dJ/dtau
+ * (host; may be NULL).  KSS_ERR_STATE without a forward pass since the last backward. */
+int kss_adjoint_backward(kss_adjoint* adj, double* grad_rho0, double* grad_tau, int on_device);
+
+const char* kss_adjoint_last_error(const kss_adjoint* adj);
+
 /* ---- Allocation-free fused step (no counterpart in the paper) ----------------------
  * For callers that cannot call cudaMalloc: code that owns all device memory itself
  * (a pool or framework allocator whose buffers it hands in), or that must not allocate

@@ -1,0 +1,331 @@
+// adjoint_kernel.cuh -- discrete adjoint (reverse mode) of the fused step for the
+// sensor objective
+//   J = sum_x W(x) eps_KL(x)   (Eq. HKL-sensor on the pre-collision populations of
+//                               step N, weights W, default 1)
+// with respect to the initial density rho0 (initial populations f^eq(rho0, u0), u0
+// fixed) and to the relaxation time tau.
+//
+// Forward map: f^0 = f^eq(rho0, u0), f^{n+1} = C(S f^n) with S the pull streaming and
+// C the BGK collision, J = sum W KL(S f^{N-1}).  With ft^n = S f^n the reverse sweep is
+//   lt^{N-1} = W dKL/dft (ft^{N-1})                            adj_objective_kernel
+//   l^{n+1} = S^T lt^{n+1},   lt^n = (dC/dft (ft^n))^T l^{n+1},
+//   dJ/dtau += sum_x l^{n+1} . (ft^n - f^eq(ft^n)) / tau^2      adj_step_kernel
+//   dJ/drho0 = sum_q (S^T lt^0)_q f^eq_q(1, u0)                 adj_final_kernel
+// where S^T is the pull in the opposite direction, (S^T l)_q(x) = l_q(x + c_q).
+//
+// Per cell, with rho = sum f, j = sum c f = rho u, D_q = d f^eq_q / d rho and
+// E_q = d f^eq_q / d j of the N = 2 Grad-Hermite equilibrium:
+//   D_q = w_q (1 + 3/2 u.u - 9/2 (c_q.u)^2),   E_q = w_q ((3 + 9 c_q.u) c_q - 3 u),
+// so d f^eq_q / d f_p = D_q + c_p . E_q, and
+//   collision:  lt_p = (1 - omega) l_p + omega (A + c_p . B),
+//               A = sum_q l_q D_q,  B = sum_q l_q E_q;
+//   KL:         K = sum f ln(f / f^eq) = sum f^eq phi(x), x_q = (f_q - f^eq_q) / f^eq_q,
+//               dK/df_p = ln(1 + x_p) - (a + c_p . b),  a = sum x_q D_q,  b = sum x_q E_q,
+//               and eps_KL = |K| (gradient times sign K).
+// The last form is the derivative of sum f ln(f / f^eq) after the exact cancellations
+// sum_q D_q = 1 and sum_q E_q = 0, so no O(1) terms cancel in floating point.
+//
+// Layout and work decomposition as the fused step (pitched SoA planes), with 2 cells
+// per thread: a CTA of 8 warps covers 64 columns x kAdjRows rows.
+#pragma once
+
+#include "step_kernel.cuh"
+
+namespace kss {
+
+constexpr int kAdjV = 2;      // cells per thread
+constexpr int kAdjRows = 32;  // rows per CTA (4 per warp)
+
+template <class T>
+struct AdjParams {
+  const T* f;            // post-collision state f^n, pulled to ft^n
+  const T* lam_in;       // lt^{n+1} (adjoint of ft^{n+1}), pulled in reverse to l^{n+1}
+  T* lam_out;            // lt^n
+  const T* weight;       // W [ny][pitch], or nullptr for W = 1 (objective kernel)
+  const double* ux0;     // u0, dense [ny][nx] (final kernel)
+  const double* uy0;
+  double* grad;          // dJ/drho0, dense [ny][nx] (final kernel)
+  double* part;          // per-CTA partial sums [nblocks]
+  uint32_t* done;        // CTA completion counter, 0 between launches
+  double* acc;           // the launch's total is added to *acc (FP64)
+  long long plane;
+  int pitch, nx, ny;
+  T omega;
+};
+
+// Nine populations of V cells of row j pulled from src: forward (REV = false)
+// v_q(i, j) = src_q(i - cx_q, j - cy_q); reverse v_q(i, j) = src_q(i + cx_q, j + cy_q).
+template <class T, bool REV>
+__device__ __forceinline__ void adj_pull_row(const T* src, long long plane, int pitch, int nx,
+                                             int ny, int j, int i0, int lane, bool cv,
+                                             T (&v)[9][kAdjV]) {
+  constexpr int V = kAdjV;
+  const T* base = src + (long long)j * pitch;
+  const long long up = (long long)((j == 0 ? ny : j) - 1 - j) * pitch;    // row j-1
+  const long long dn = (long long)((j + 1 == ny ? 0 : j + 1) - j) * pitch;  // row j+1
+  const long long rp = REV ? dn : up;  // source row of the cy = +1 planes 2, 5, 6
+  const long long rm = REV ? up : dn;  // source row of the cy = -1 planes 4, 7, 8
+  const T* r[9] = {base,
+                   base + plane,
+                   base + 2 * plane + rp,
+                   base + 3 * plane,
+                   base + 4 * plane + rm,
+                   base + 5 * plane + rp,
+                   base + 6 * plane + rp,
+                   base + 7 * plane + rm,
+                   base + 8 * plane + rm};
+#pragma unroll
+  for (int q = 0; q < 9; ++q) vload<T, V>(r[q] + i0, cv, v[q]);
+  // cx = +1 planes (1, 5, 8) take column i - 1 forward, i + 1 in reverse; cx = -1
+  // planes (3, 6, 7) the opposite
+  if (!REV) {
+    const T h1 = load_left_halo<T>(r[1], i0, nx, lane, cv);
+    const T h5 = load_left_halo<T>(r[5], i0, nx, lane, cv);
+    const T h8 = load_left_halo<T>(r[8], i0, nx, lane, cv);
+    const T h3 = load_right_halo<T, V>(r[3], i0, nx, lane, cv);
+    const T h6 = load_right_halo<T, V>(r[6], i0, nx, lane, cv);
+    const T h7 = load_right_halo<T, V>(r[7], i0, nx, lane, cv);
+    assemble_from_left<T, V>(v[1], h1, lane);
+    assemble_from_left<T, V>(v[5], h5, lane);
+    assemble_from_left<T, V>(v[8], h8, lane);
+    assemble_from_right<T, V>(v[3], h3, i0, nx, lane);
+    assemble_from_right<T, V>(v[6], h6, i0, nx, lane);
+    assemble_from_right<T, V>(v[7], h7, i0, nx, lane);
+  } else {
+    const T h3 = load_left_halo<T>(r[3], i0, nx, lane, cv);
+    const T h6 = load_left_halo<T>(r[6], i0, nx, lane, cv);
+    const T h7 = load_left_halo<T>(r[7], i0, nx, lane, cv);
+    const T h1 = load_right_halo<T, V>(r[1], i0, nx, lane, cv);
+    const T h5 = load_right_halo<T, V>(r[5], i0, nx, lane, cv);
+    const T h8 = load_right_halo<T, V>(r[8], i0, nx, lane, cv);
+    assemble_from_left<T, V>(v[3], h3, lane);
+    assemble_from_left<T, V>(v[6], h6, lane);
+    assemble_from_left<T, V>(v[7], h7, lane);
+    assemble_from_right<T, V>(v[1], h1, i0, nx, lane);
+    assemble_from_right<T, V>(v[5], h5, i0, nx, lane);
+    assemble_from_right<T, V>(v[8], h8, i0, nx, lane);
+  }
+}
+
+// Moments and equilibrium of one cell, rounded exactly as the forward step rounds them.
+template <class T>
+__device__ __forceinline__ void adj_cell_eq(const T (&c)[9], T& ux, T& uy, T (&feq)[9]) {
+  const T rho = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7])) + c[8];
+  const T jx = (c[1] + c[5] + c[8]) - (c[3] + c[6] + c[7]);
+  const T jy = (c[2] + c[5] + c[6]) - (c[4] + c[7] + c[8]);
+  const T ir = Num<T>::rcp(rho);
+  ux = Num<T>::mul(jx, ir);
+  uy = Num<T>::mul(jy, ir);
+  equilibrium<T>(rho, ux, uy, feq);
+}
+
+// For weights y_q: A = sum y_q D_q and B = sum y_q E_q (see the header comment).
+template <class T>
+__device__ __forceinline__ void adj_moment_pullback(const T (&y)[9], T ux, T uy, T& A, T& Bx,
+                                                    T& By) {
+  constexpr int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  constexpr int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  const T w[9] = {T(4.0 / 9.0),  T(1.0 / 9.0),  T(1.0 / 9.0),  T(1.0 / 9.0), T(1.0 / 9.0),
+                  T(1.0 / 36.0), T(1.0 / 36.0), T(1.0 / 36.0), T(1.0 / 36.0)};
+  const T g = fma(T(1.5), fma(ux, ux, uy * uy), T(1));  // 1 + 3/2 u.u
+  T a = T(0), bx = T(0), by = T(0), sw = T(0);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    const T cu = T(cx[q]) * ux + T(cy[q]) * uy;
+    const T wy = w[q] * y[q];
+    a = fma(wy, fma(T(-4.5) * cu, cu, g), a);
+    const T s = wy * fma(T(9), cu, T(3));  // w y (3 + 9 c.u)
+    if (cx[q]) bx = fma(T(cx[q]), s, bx);
+    if (cy[q]) by = fma(T(cy[q]), s, by);
+    sw += wy;
+  }
+  A = a;
+  Bx = fma(T(-3) * ux, sw, bx);
+  By = fma(T(-3) * uy, sw, by);
+}
+
+// Per-CTA partial of one sum, then the last CTA adds the partials in CTA order and
+// adds the launch total to *p.acc.
+template <class T>
+__device__ __forceinline__ void adj_reduce(const AdjParams<T>& p, Acc<T>& s) {
+  __shared__ Red<T> s_red[kWarps];
+  __shared__ int s_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  s.warp_reduce();
+  if (lane == 0) s_red[warp] = Red<T>::of(s);
+  __syncthreads();
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  const int nblocks = gridDim.x * gridDim.y;
+  if (threadIdx.x == 0) {
+    Red<T> t;
+    for (int w = 0; w < kWarps; ++w) t.add(s_red[w]);
+    t.store(p.part + bid);
+    __threadfence();
+    s_last = atomicAdd(p.done, 1u) == uint32_t(nblocks - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  __shared__ Red<T> s_fin[kWarps];
+  Red<T> t;
+  for (int b = threadIdx.x; b < nblocks; b += kThreads) t.add(Red<T>::load(p.part + b));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) t.add(t.shfl_xor(off));
+  if (lane == 0) s_fin[warp] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Red<T> r = s_fin[0];
+    for (int w = 1; w < kWarps; ++w) r.add(s_fin[w]);
+    *p.acc += r.value();
+    *p.done = 0u;  // ready for the next launch (stream-ordered)
+  }
+}
+
+// Replace the cells past the row end (padding of a ragged vector) by a positive rest
+// state, so that they stay finite; they are neither summed nor read by real cells.
+template <class T>
+__device__ __forceinline__ void adj_pad(T (&v)[9][kAdjV], int nvalid, T value) {
+#pragma unroll
+  for (int q = 0; q < 9; ++q)
+#pragma unroll
+    for (int k = 0; k < kAdjV; ++k)
+      if (k >= nvalid) v[q][k] = value;
+}
+
+// lt^{N-1} = W dKL/dft at ft = S f^{N-1}; adds sum W KL to *acc.
+template <class T>
+__global__ void __launch_bounds__(kThreads) adj_objective_kernel(const AdjParams<T> p) {
+  constexpr int V = kAdjV;
+  constexpr int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  constexpr int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = (blockIdx.x * 32 + lane) * V;
+  const bool cv = i0 < p.nx;
+  const int nvalid = cv ? min(V, p.nx - i0) : 0;
+  const int j0 = blockIdx.y * kAdjRows, j1 = min(j0 + kAdjRows, p.ny);
+  Acc<T> sum;
+  for (int j = j0 + warp; j < j1; j += kWarps) {
+    T ft[9][V];
+    adj_pull_row<T, false>(p.f, p.plane, p.pitch, p.nx, p.ny, j, i0, lane, cv, ft);
+    adj_pad<T>(ft, nvalid, T(1));
+    T wv[V];
+    if (p.weight) {
+      vload<T, V>(p.weight + (long long)j * p.pitch + i0, cv, wv);
+    } else {
+#pragma unroll
+      for (int k = 0; k < V; ++k) wv[k] = T(1);
+    }
+    T g[9][V];
+    T rs = T(0);
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      T c[9], feq[9], x[9], ux, uy;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) c[q] = ft[q][k];
+      adj_cell_eq<T>(c, ux, uy, feq);
+      bool nonpos = false;
+      T K = T(0);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        nonpos |= (c[q] <= T(0)) | (feq[q] <= T(0));
+        x[q] = (c[q] - feq[q]) / feq[q];
+        K = fma(feq[q], phi<T>(x[q]), K);
+      }
+      T a, bx, by;
+      adj_moment_pullback<T>(x, ux, uy, a, bx, by);
+      const T sg = K > T(0) ? wv[k] : (K < T(0) ? -wv[k] : T(0));
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        const T cb = T(cx[q]) * bx + T(cy[q]) * by;
+        g[q][k] = nonpos ? T(CUDART_NAN) : sg * (Num<T>::log1p_(x[q]) - (a + cb));
+      }
+      if (k < nvalid) rs += wv[k] * (nonpos ? Num<T>::inf() : fabs(K));
+    }
+    sum.add(rs);
+    if (cv) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q)
+        vstore<T, V>(p.lam_out + q * p.plane + (long long)j * p.pitch + i0, g[q]);
+    }
+  }
+  adj_reduce<T>(p, sum);
+}
+
+// lt^n from l^{n+1} = S^T lt^{n+1} and ft^n = S f^n; adds sum l^{n+1} . f^neq to *acc
+// (dJ/dtau = that sum over all steps / tau^2).
+template <class T>
+__global__ void __launch_bounds__(kThreads) adj_step_kernel(const AdjParams<T> p) {
+  constexpr int V = kAdjV;
+  constexpr int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  constexpr int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = (blockIdx.x * 32 + lane) * V;
+  const bool cv = i0 < p.nx;
+  const int nvalid = cv ? min(V, p.nx - i0) : 0;
+  const int j0 = blockIdx.y * kAdjRows, j1 = min(j0 + kAdjRows, p.ny);
+  const T om = p.omega, om1 = T(1) - p.omega;
+  Acc<T> sum;
+  for (int j = j0 + warp; j < j1; j += kWarps) {
+    T ft[9][V], l[9][V];
+    adj_pull_row<T, false>(p.f, p.plane, p.pitch, p.nx, p.ny, j, i0, lane, cv, ft);
+    adj_pull_row<T, true>(p.lam_in, p.plane, p.pitch, p.nx, p.ny, j, i0, lane, cv, l);
+    adj_pad<T>(ft, nvalid, T(1));
+    adj_pad<T>(l, nvalid, T(0));
+    T rs = T(0);
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      T c[9], y[9], feq[9], ux, uy;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        c[q] = ft[q][k];
+        y[q] = l[q][k];
+      }
+      adj_cell_eq<T>(c, ux, uy, feq);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) rs = fma(y[q], c[q] - feq[q], rs);
+      T A, bx, by;
+      adj_moment_pullback<T>(y, ux, uy, A, bx, by);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        const T cb = T(cx[q]) * bx + T(cy[q]) * by;
+        l[q][k] = fma(om1, y[q], om * (A + cb));
+      }
+    }
+    sum.add(rs);
+    if (cv) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q)
+        vstore<T, V>(p.lam_out + q * p.plane + (long long)j * p.pitch + i0, l[q]);
+    }
+  }
+  adj_reduce<T>(p, sum);
+}
+
+// dJ/drho0(x) = sum_q (S^T lt^0)_q(x) f^eq_q(1, u0(x)) (f^0 = f^eq(rho0, u0) is linear in
+// rho0 at fixed u0), written as doubles to the dense grad array.
+template <class T>
+__global__ void __launch_bounds__(kThreads) adj_final_kernel(const AdjParams<T> p) {
+  constexpr int V = kAdjV;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = (blockIdx.x * 32 + lane) * V;
+  const bool cv = i0 < p.nx;
+  const int j0 = blockIdx.y * kAdjRows, j1 = min(j0 + kAdjRows, p.ny);
+  for (int j = j0 + warp; j < j1; j += kWarps) {
+    T l[9][V];
+    adj_pull_row<T, true>(p.lam_in, p.plane, p.pitch, p.nx, p.ny, j, i0, lane, cv, l);
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const int i = i0 + k;
+      if (!cv || i >= p.nx) continue;
+      const long long c = (long long)j * p.nx + i;
+      T e1[9];
+      equilibrium<T>(T(1), T(p.ux0[c]), T(p.uy0[c]), e1);
+      T s = T(0);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) s = fma(l[q][k], e1[q], s);
+      p.grad[c] = double(s);
+    }
+  }
+}
+
+}  // namespace kss

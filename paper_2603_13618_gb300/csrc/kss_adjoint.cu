@@ -1,0 +1,304 @@
+// kss_adjoint.cu -- host side of the adjoint entry points (include/kss.h): the forward
+// pass with checkpoints, the segment-wise recomputation and the reverse sweep of the
+// adjoint kernels (adjoint_kernel.cuh).
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "runtime.h"
+
+using namespace kss_rt;
+
+struct kss_adjoint {
+  kss_adjoint_config cfg{};
+  int device = 0;
+  bool fp32 = true;
+  size_t esz = 4;
+  int pitch = 0;
+  long long plane = 0;
+  size_t state_bytes = 0;  // one population buffer (9 planes)
+  int nck = 0;             // checkpoints kept: f^0, f^E, f^2E, ... (E = checkpoint_every)
+  unsigned char* ck = nullptr;   // nck states
+  unsigned char* seg = nullptr;  // checkpoint_every states: a recomputed segment
+  unsigned char* work[2] = {nullptr, nullptr};  // forward ping-pong
+  unsigned char* lam[2] = {nullptr, nullptr};   // adjoint ping-pong
+  void* wplane = nullptr;    // weights, one pitched plane of T
+  double* fields = nullptr;  // staging: rho0, ux0, uy0 (dense)
+  double* grad = nullptr;    // dense dJ/drho0
+  double* part = nullptr;    // per-CTA partials
+  unsigned char* small = nullptr;  // done counter @0, acc[2] @64
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  double tau = 0;
+  int lam_cur = 0;         // lam[lam_cur] holds lt^{N-1} after the forward pass
+  bool have_forward = false;
+  bool have_weight = false;
+  std::string msg;
+};
+
+namespace {
+
+int afail(kss_adjoint* A, int code, const std::string& m) {
+  if (A) A->msg = m;
+  return code;
+}
+
+#define KSS_ACUDA(A, call)                                                              \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return afail((A), KSS_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+void free_all(kss_adjoint* A) {
+  if (!A) return;
+  DeviceGuard g(A->device);
+  cudaStreamSynchronize(A->stream);
+  void* bufs[] = {A->ck,     A->seg,    A->work[0], A->work[1], A->lam[0], A->lam[1],
+                  A->wplane, A->fields, A->grad,    A->part,    A->small};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (A->own_stream && A->stream) cudaStreamDestroy(A->stream);
+  delete A;
+}
+
+unsigned char* state_at(kss_adjoint* A, unsigned char* base, long long k) {
+  return base + size_t(k) * A->state_bytes;
+}
+
+// One plain forward step (stream + collide, no outputs) from src to dst.
+template <class T>
+cudaError_t plain_step(const kss_adjoint* A, const void* src, void* dst) {
+  kss::StepParams<T> p{};
+  p.src = static_cast<const T*>(src);
+  p.dst = static_cast<T*>(dst);
+  p.plane = A->plane;
+  p.pitch = A->pitch;
+  p.nx = A->cfg.nx;
+  p.ny = A->cfg.ny;
+  p.tile = 16;
+  p.bands = kss::step_bands(16);
+  p.ntx = (A->cfg.nx + 15) / 16;
+  p.nty = (A->cfg.ny + 15) / 16;
+  p.omega = T(1.0 / A->tau);
+  p.tau = T(A->tau);
+  for (int s = 0; s < KSS_S_COUNT; ++s) p.rec_slot[s] = -1;
+  return kss::launch_step<T>(p, kss::MODE_PLAIN, true, true, A->stream);
+}
+
+template <class T>
+kss::AdjParams<T> adj_params(kss_adjoint* A) {
+  kss::AdjParams<T> p{};
+  p.part = A->part;
+  p.done = reinterpret_cast<uint32_t*>(A->small);
+  p.plane = A->plane;
+  p.pitch = A->pitch;
+  p.nx = A->cfg.nx;
+  p.ny = A->cfg.ny;
+  p.omega = T(1.0 / A->tau);
+  return p;
+}
+
+double* acc_at(kss_adjoint* A, int k) { return reinterpret_cast<double*>(A->small + 64) + k; }
+
+template <class T>
+int forward_impl(kss_adjoint* A, double* J) {
+  const int N = A->cfg.nsteps, E = A->cfg.checkpoint_every;
+  const size_t n = size_t(A->cfg.nx) * A->cfg.ny;
+  KSS_ACUDA(A, kss::launch_init_equilibrium<T>(A->fields, A->fields + n, A->fields + 2 * n,
+                                               reinterpret_cast<T*>(A->ck), A->plane, A->pitch,
+                                               A->cfg.nx, A->cfg.ny, A->stream));
+  // f^k for k = 1 .. N-1: checkpoints land in their slot, the others alternate in work[]
+  const void* cur = A->ck;
+  for (int k = 1; k < N; ++k) {
+    void* dst = (k % E == 0) ? state_at(A, A->ck, k / E) : A->work[k & 1];
+    KSS_ACUDA(A, plain_step<T>(A, cur, dst));
+    cur = dst;
+  }
+  KSS_ACUDA(A, cudaMemsetAsync(A->small + 64, 0, 2 * sizeof(double), A->stream));
+  kss::AdjParams<T> p = adj_params<T>(A);
+  p.f = static_cast<const T*>(cur);
+  p.lam_out = reinterpret_cast<T*>(A->lam[0]);
+  p.weight = A->have_weight ? static_cast<const T*>(A->wplane) : nullptr;
+  p.acc = acc_at(A, 0);
+  KSS_ACUDA(A, kss::launch_adj_objective<T>(p, A->stream));
+  KSS_ACUDA(A, cudaMemcpyAsync(J, acc_at(A, 0), sizeof(double), cudaMemcpyDeviceToHost, A->stream));
+  KSS_ACUDA(A, cudaStreamSynchronize(A->stream));
+  A->lam_cur = 0;
+  return KSS_OK;
+}
+
+template <class T>
+int backward_impl(kss_adjoint* A, double* grad_tau) {
+  const int N = A->cfg.nsteps, E = A->cfg.checkpoint_every;
+  int lc = A->lam_cur;
+  kss::AdjParams<T> p = adj_params<T>(A);
+  p.acc = acc_at(A, 1);
+  // segments [s0, last] of the states f^0 .. f^{N-2} that the reverse sweep needs,
+  // last segment first; slot 0 of a segment is its checkpoint
+  for (int s0 = N >= 2 ? ((N - 2) / E) * E : -1; s0 >= 0; s0 -= E) {
+    const int last = std::min(s0 + E - 1, N - 2);
+    auto state = [&](int k) -> const void* {
+      return k == s0 ? static_cast<const void*>(state_at(A, A->ck, s0 / E))
+                     : static_cast<const void*>(state_at(A, A->seg, k - s0));
+    };
+    for (int k = s0 + 1; k <= last; ++k)
+      KSS_ACUDA(A, plain_step<T>(A, state(k - 1), const_cast<void*>(state(k))));
+    for (int k = last; k >= s0; --k) {
+      p.f = static_cast<const T*>(state(k));
+      p.lam_in = reinterpret_cast<const T*>(A->lam[lc]);
+      p.lam_out = reinterpret_cast<T*>(A->lam[lc ^ 1]);
+      KSS_ACUDA(A, kss::launch_adj_step<T>(p, A->stream));
+      lc ^= 1;
+    }
+  }
+  const size_t n = size_t(A->cfg.nx) * A->cfg.ny;
+  p.lam_in = reinterpret_cast<const T*>(A->lam[lc]);
+  p.ux0 = A->fields + n;
+  p.uy0 = A->fields + 2 * n;
+  p.grad = A->grad;
+  KSS_ACUDA(A, kss::launch_adj_final<T>(p, A->stream));
+  double s = 0;
+  KSS_ACUDA(A, cudaMemcpyAsync(&s, acc_at(A, 1), sizeof(double), cudaMemcpyDeviceToHost, A->stream));
+  KSS_ACUDA(A, cudaStreamSynchronize(A->stream));
+  if (grad_tau) *grad_tau = s / (A->tau * A->tau);
+  return KSS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kss_adjoint_create(const kss_adjoint_config* cfg, kss_adjoint** out) {
+  if (!out) return KSS_ERR_ARG;
+  *out = nullptr;
+  if (!cfg || cfg->nx < 1 || cfg->ny < 1 || cfg->nsteps < 1 || cfg->checkpoint_every < 1)
+    return KSS_ERR_ARG;
+  if ((long long)cfg->nx * cfg->ny > 0x7fffffffLL) return KSS_ERR_ARG;
+  if (cfg->precision != KSS_FP32 && cfg->precision != KSS_FP64) return KSS_ERR_UNSUPPORTED;
+  if (cfg->own_stream != 0 && cfg->own_stream != 1) return KSS_ERR_ARG;
+  kss_adjoint* A = new (std::nothrow) kss_adjoint();
+  if (!A) return KSS_ERR_OOM;
+  A->cfg = *cfg;
+  A->cfg.checkpoint_every = std::min(cfg->checkpoint_every, cfg->nsteps);
+  if (cudaGetDevice(&A->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete A;
+    return KSS_ERR_CUDA;
+  }
+  A->fp32 = cfg->precision == KSS_FP32;
+  A->esz = A->fp32 ? 4 : 8;
+  const int align = int(128 / A->esz);
+  A->pitch = (cfg->nx + align - 1) / align * align;
+  A->plane = (long long)A->pitch * cfg->ny;
+  A->state_bytes = 9 * size_t(A->plane) * A->esz;
+  A->nck = (cfg->nsteps - 1) / A->cfg.checkpoint_every + 1;
+  if (cfg->own_stream) {
+    if (cudaStreamCreateWithFlags(&A->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete A;
+      return KSS_ERR_CUDA;
+    }
+    A->own_stream = true;
+  } else {
+    A->stream = static_cast<cudaStream_t>(cfg->stream);
+  }
+  const size_t n = size_t(cfg->nx) * cfg->ny;
+  const dim3 g = kss::adj_grid(cfg->nx, cfg->ny);
+  struct {
+    void** p;
+    size_t bytes;
+  } allocs[] = {
+      {reinterpret_cast<void**>(&A->ck), A->state_bytes * size_t(A->nck)},
+      {reinterpret_cast<void**>(&A->seg), A->state_bytes * size_t(A->cfg.checkpoint_every)},
+      {reinterpret_cast<void**>(&A->work[0]), A->state_bytes},
+      {reinterpret_cast<void**>(&A->work[1]), A->state_bytes},
+      {reinterpret_cast<void**>(&A->lam[0]), A->state_bytes},
+      {reinterpret_cast<void**>(&A->lam[1]), A->state_bytes},
+      {&A->wplane, size_t(A->plane) * A->esz},
+      {reinterpret_cast<void**>(&A->fields), 3 * n * sizeof(double)},
+      {reinterpret_cast<void**>(&A->grad), n * sizeof(double)},
+      {reinterpret_cast<void**>(&A->part), size_t(g.x) * g.y * sizeof(double)},
+      {reinterpret_cast<void**>(&A->small), 256},
+  };
+  for (auto& a : allocs) {
+    if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
+      cudaGetLastError();
+      free_all(A);
+      return KSS_ERR_OOM;
+    }
+  }
+  // zero everything once: the padding of every state stays finite
+  for (auto& a : allocs) {
+    if (cudaMemsetAsync(*a.p, 0, a.bytes, A->stream) != cudaSuccess) {
+      cudaGetLastError();
+      free_all(A);
+      return KSS_ERR_CUDA;
+    }
+  }
+  if (cudaStreamSynchronize(A->stream) != cudaSuccess) {
+    cudaGetLastError();
+    free_all(A);
+    return KSS_ERR_CUDA;
+  }
+  *out = A;
+  return KSS_OK;
+}
+
+void kss_adjoint_destroy(kss_adjoint* A) { free_all(A); }
+
+const char* kss_adjoint_last_error(const kss_adjoint* A) { return A ? A->msg.c_str() : "null adjoint"; }
+
+int kss_adjoint_forward(kss_adjoint* A, const double* rho0, const double* ux0, const double* uy0,
+                        const double* weight, double tau, int on_device, double* J) {
+  if (!A) return KSS_ERR_ARG;
+  if (!rho0 || !ux0 || !uy0 || !J) return afail(A, KSS_ERR_ARG, "null pointer");
+  if (!(tau > 0.5) || !std::isfinite(tau)) return afail(A, KSS_ERR_ARG, "tau must be > 0.5");
+  DeviceGuard g(A->device);
+  const size_t n = size_t(A->cfg.nx) * A->cfg.ny;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  KSS_ACUDA(A, cudaMemcpyAsync(A->fields, rho0, n * 8, kind, A->stream));
+  KSS_ACUDA(A, cudaMemcpyAsync(A->fields + n, ux0, n * 8, kind, A->stream));
+  KSS_ACUDA(A, cudaMemcpyAsync(A->fields + 2 * n, uy0, n * 8, kind, A->stream));
+  A->have_weight = weight != nullptr;
+  if (weight) {
+    // the weights go through the gradient staging buffer into one pitched plane
+    KSS_ACUDA(A, cudaMemcpyAsync(A->grad, weight, n * 8, kind, A->stream));
+    if (A->fp32)
+      KSS_ACUDA(A, kss::launch_dense_to_pitched<float>(A->grad, A->plane, A->pitch, A->cfg.nx,
+                                                       A->cfg.ny, 1, static_cast<float*>(A->wplane),
+                                                       A->stream));
+    else
+      KSS_ACUDA(A, kss::launch_dense_to_pitched<double>(A->grad, A->plane, A->pitch, A->cfg.nx,
+                                                        A->cfg.ny, 1, static_cast<double*>(A->wplane),
+                                                        A->stream));
+  }
+  A->tau = tau;
+  A->have_forward = false;
+  const int rc = A->fp32 ? forward_impl<float>(A, J) : forward_impl<double>(A, J);
+  if (rc) return rc;
+  A->have_forward = true;
+  return KSS_OK;
+}
+
+int kss_adjoint_backward(kss_adjoint* A, double* grad_rho0, double* grad_tau, int on_device) {
+  if (!A) return KSS_ERR_ARG;
+  if (!A->have_forward) return afail(A, KSS_ERR_STATE, "backward needs a forward pass");
+  DeviceGuard g(A->device);
+  // the sweep consumes the seed lt^{N-1}: one backward pass per forward pass
+  A->have_forward = false;
+  const int rc = A->fp32 ? backward_impl<float>(A, grad_tau) : backward_impl<double>(A, grad_tau);
+  if (rc) return rc;
+  if (grad_rho0) {
+    const size_t n = size_t(A->cfg.nx) * A->cfg.ny;
+    KSS_ACUDA(A, cudaMemcpyAsync(grad_rho0, A->grad, n * 8,
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                 A->stream));
+    KSS_ACUDA(A, cudaStreamSynchronize(A->stream));
+  }
+  return KSS_OK;
+}
+
+}  // extern "C"

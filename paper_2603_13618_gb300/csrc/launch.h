@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include "adjoint_kernel.cuh"
 #include "step_tma.cuh"
 
 namespace kss {
@@ -41,6 +42,18 @@ cudaError_t launch_step_tma(const StepParams<T>& p, int mode, TmaPlan plan, int 
 // `ctas` CTAs of 256 threads striding over the tiles.
 template <class T>
 cudaError_t launch_fixup(const StepParams<T>& p, bool pull, int ctas, cudaStream_t stream);
+
+// Adjoint kernels (adjoint_kernel.cuh) on the grid adj_grid(nx, ny).
+inline dim3 adj_grid(int nx, int ny) {
+  return dim3((unsigned)((nx + 32 * kAdjV - 1) / (32 * kAdjV)),
+              (unsigned)((ny + kAdjRows - 1) / kAdjRows), 1u);
+}
+template <class T>
+cudaError_t launch_adj_objective(const AdjParams<T>& p, cudaStream_t stream);
+template <class T>
+cudaError_t launch_adj_step(const AdjParams<T>& p, cudaStream_t stream);
+template <class T>
+cudaError_t launch_adj_final(const AdjParams<T>& p, cudaStream_t stream);
 
 template <class T>
 cudaError_t launch_init_equilibrium(const double* rho, const double* ux, const double* uy,

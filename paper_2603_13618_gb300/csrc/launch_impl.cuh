@@ -49,6 +49,24 @@ cudaError_t launch_batch_step<KSS_T>(const StepParams<KSS_T>* table, const Batch
   return cudaGetLastError();
 }
 
+template <>
+cudaError_t launch_adj_objective<KSS_T>(const AdjParams<KSS_T>& p, cudaStream_t stream) {
+  adj_objective_kernel<KSS_T><<<adj_grid(p.nx, p.ny), kThreads, 0, stream>>>(p);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_adj_step<KSS_T>(const AdjParams<KSS_T>& p, cudaStream_t stream) {
+  adj_step_kernel<KSS_T><<<adj_grid(p.nx, p.ny), kThreads, 0, stream>>>(p);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_adj_final<KSS_T>(const AdjParams<KSS_T>& p, cudaStream_t stream) {
+  adj_final_kernel<KSS_T><<<adj_grid(p.nx, p.ny), kThreads, 0, stream>>>(p);
+  return cudaGetLastError();
+}
+
 template <int MODE>
 cudaError_t launch_tma_mode(const StepParams<KSS_T>& p, TmaPlan plan, int ctas,
                             cudaStream_t stream) {

@@ -82,6 +82,12 @@ template <> struct Vec<double> {
   using type = double2;
 };
 
+// Vector type of V elements of T (one 8- or 16-byte load or store).
+template <class T, int V> struct VecT;
+template <> struct VecT<float, 4> { using type = float4; };
+template <> struct VecT<float, 2> { using type = float2; };
+template <> struct VecT<double, 2> { using type = double2; };
+
 template <class VT, class T, int N>
 __device__ __forceinline__ VT make_vec(const T (&v)[N]) {
   if constexpr (N == 4) {
@@ -122,19 +128,20 @@ struct StepParams {
 };
 
 // ---------------------------------------------------------------- loads ----
-template <class T>
-__device__ __forceinline__ void vload(const T* p, bool ok, T (&v)[Vec<T>::N]) {
-  using VT = typename Vec<T>::type;
+// V cells per thread (default: the fused step's Vec<T>::N).
+template <class T, int V = Vec<T>::N>
+__device__ __forceinline__ void vload(const T* p, bool ok, T (&v)[V]) {
+  using VT = typename VecT<T, V>::type;
   if (ok) {
     const VT a = __ldg(reinterpret_cast<const VT*>(p));
-    if constexpr (Vec<T>::N == 4) {
+    if constexpr (V == 4) {
       v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
     } else {
       v[0] = a.x; v[1] = a.y;
     }
   } else {
 #pragma unroll
-    for (int k = 0; k < Vec<T>::N; ++k) v[k] = T(0);
+    for (int k = 0; k < V; ++k) v[k] = T(0);
   }
 }
 
@@ -151,17 +158,16 @@ __device__ __forceinline__ T load_left_halo(const T* row, int i0, int nx, int la
 
 // Halo element of a cx = -1 population (source column i + 1): lane 31, and any lane
 // whose vector reaches the row end (then the element is column 0, periodic seam).
-template <class T>
+template <class T, int V = Vec<T>::N>
 __device__ __forceinline__ T load_right_halo(const T* row, int i0, int nx, int lane, bool cv) {
-  const bool tail = i0 + Vec<T>::N >= nx;
-  return (cv && (lane == 31 || tail)) ? __ldg(row + (tail ? 0 : i0 + Vec<T>::N)) : T(0);
+  const bool tail = i0 + V >= nx;
+  return (cv && (lane == 31 || tail)) ? __ldg(row + (tail ? 0 : i0 + V)) : T(0);
 }
 
 // Cells i0..i0+V-1 pulled from column i - 1: the left neighbour's last element by
 // shuffle, lane 0 from its halo load.
-template <class T>
-__device__ __forceinline__ void assemble_from_left(T (&v)[Vec<T>::N], T halo, int lane) {
-  constexpr int V = Vec<T>::N;
+template <class T, int V = Vec<T>::N>
+__device__ __forceinline__ void assemble_from_left(T (&v)[V], T halo, int lane) {
   const T left = __shfl_up_sync(kFull, v[V - 1], 1);
 #pragma unroll
   for (int k = V - 1; k > 0; --k) v[k] = v[k - 1];
@@ -170,10 +176,9 @@ __device__ __forceinline__ void assemble_from_left(T (&v)[Vec<T>::N], T halo, in
 
 // Cells i0..i0+V-1 pulled from column i + 1; cell nx-1 takes column 0 wherever it
 // sits in the vector.
-template <class T>
-__device__ __forceinline__ void assemble_from_right(T (&v)[Vec<T>::N], T halo, int i0, int nx,
+template <class T, int V = Vec<T>::N>
+__device__ __forceinline__ void assemble_from_right(T (&v)[V], T halo, int i0, int nx,
                                                     int lane) {
-  constexpr int V = Vec<T>::N;
   const T right = __shfl_down_sync(kFull, v[0], 1);
   const bool tail = i0 + V >= nx;
 #pragma unroll
@@ -222,10 +227,10 @@ template <> struct Acc<double> {
 };
 
 // ---------------------------------------------------------------- stores ----
-template <class T>
-__device__ __forceinline__ void vstore(T* p, const T (&v)[Vec<T>::N]) {
-  using VT = typename Vec<T>::type;
-  __stcs(reinterpret_cast<VT*>(p), make_vec<VT, T, Vec<T>::N>(v));
+template <class T, int V = Vec<T>::N>
+__device__ __forceinline__ void vstore(T* p, const T (&v)[V]) {
+  using VT = typename VecT<T, V>::type;
+  __stcs(reinterpret_cast<VT*>(p), make_vec<VT, T, V>(v));
 }
 
 template <int V>

@@ -50,6 +50,12 @@ class BatchTuning(ctypes.Structure):
                 ("graph", ctypes.c_int32), ("ms_per_step", ctypes.c_double)]
 
 
+class AdjointConfig(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("nsteps", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
+                ("stream", ctypes.c_void_p), ("own_stream", ctypes.c_int32)]
+
+
 _lib = None
 
 # Every entry point declared in include/kss.h, with its ctypes signature.
@@ -83,6 +89,13 @@ _SIGNATURES = {
     "kss_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int32,
                                           ctypes.POINTER(BatchTuning)]),
     "kss_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "kss_adjoint_create": (ctypes.c_int, [ctypes.POINTER(AdjointConfig),
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    "kss_adjoint_destroy": (None, [ctypes.c_void_p]),
+    "kss_adjoint_forward": (ctypes.c_int, [ctypes.c_void_p] * 5 + [ctypes.c_double, ctypes.c_int,
+                                                                    _DP]),
+    "kss_adjoint_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _DP, ctypes.c_int]),
+    "kss_adjoint_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "kss_step_f32_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                             ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
@@ -365,6 +378,76 @@ class Batch:
             for m in self.members:
                 m._h = None
             self._lib.kss_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Adjoint:
+    """Gradient of J = sum W eps_KL (step nsteps) in rho0 and tau (see include/kss.h)."""
+
+    def __init__(self, nx: int, ny: int, nsteps: int, precision="fp32",
+                 checkpoint_every: int = 20, stream="torch"):
+        self._lib = load()
+        self._h = None
+        cfg = AdjointConfig(nx, ny, PRECISIONS[precision], nsteps, checkpoint_every, None, 0)
+        if stream == "own":
+            cfg.own_stream = 1
+        else:
+            cfg.stream = _torch_stream_handle() if stream == "torch" else stream
+        handle = ctypes.c_void_p()
+        rc = self._lib.kss_adjoint_create(ctypes.byref(cfg), ctypes.byref(handle))
+        if rc < 0:
+            raise KssError(rc, self._lib.kss_strerror(rc).decode())
+        self._h = handle
+        self.nx, self.ny, self.nsteps = nx, ny, nsteps
+
+    def _check(self, rc: int) -> int:
+        if rc < 0:
+            detail = (self._lib.kss_adjoint_last_error(self._h) or b"").decode() if self._h else ""
+            raise KssError(rc, f"{self._lib.kss_strerror(rc).decode()} {detail}".strip())
+        return rc
+
+    def forward(self, rho0, ux0, uy0, tau: float, weight=None) -> float:
+        ptrs = [_ptr(a, np.float64) for a in (rho0, ux0, uy0)]
+        dev = {d for _, d in ptrs}
+        wp = None
+        if weight is not None:
+            wp, wd = _ptr(weight, np.float64)
+            dev.add(wd)
+        if len(dev) != 1:
+            raise TypeError("fields and weights must all be host or all be device memory")
+        J = ctypes.c_double()
+        self._check(self._lib.kss_adjoint_forward(self._h, ptrs[0][0], ptrs[1][0], ptrs[2][0],
+                                                  wp, float(tau), dev.pop(), ctypes.byref(J)))
+        return J.value
+
+    def backward(self, device: bool = False):
+        """(dJ/drho0 [ny, nx] float64, dJ/dtau) of the last forward pass."""
+        if device:
+            import torch
+
+            g = torch.empty((self.ny, self.nx), dtype=torch.float64, device="cuda")
+        else:
+            g = np.empty((self.ny, self.nx))
+        p, d = _ptr(g, np.float64)
+        gt = ctypes.c_double()
+        self._check(self._lib.kss_adjoint_backward(self._h, p, ctypes.byref(gt), d))
+        return g, gt.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.kss_adjoint_destroy(self._h)
             self._h = None
 
     def __del__(self):
