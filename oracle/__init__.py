@@ -71,6 +71,9 @@ def lib():
             "orc_run": (ctypes.c_int64, [ci, ci, cd, dp, dp, ci, ci, cd, ci, cd, ci,
                                           dp, u8p, i32p, i64p, dp]),
             "orc_adjoint_kl": (ci, [ci, ci, cd, ci, ci, dp, dp, dp, dp, dp, dp, dp]),
+            "orc_fp16_round": (cd, [cd]),
+            "orc_dev16_encode": (None, [ci, ci, cd, ci, ci, dp, dp]),
+            "orc_dev16_decode": (None, [ci, ci, cd, ci, ci, dp, dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -241,3 +244,23 @@ def objective_kl(rho0, ux0, uy0, tau: float, nsteps: int, weight=None) -> float:
     kl = sensor_fields(f, tau, pull=True)[0][SENSOR_ID["kl"]]
     w = 1.0 if weight is None else _f64(weight)
     return float(np.sum(w * kl))
+
+
+def fp16_round(x: float) -> float:
+    return lib().orc_fp16_round(float(x))
+
+
+def dev16_encode(f, rho0: float = 1.0, dev_exp: int = 12, unscaled: bool = False):
+    """FP16 deviation codes (binary16 values as float64) of populations f[9, ny, nx]."""
+    f = _f64(f)
+    h = np.empty_like(f)
+    lib().orc_dev16_encode(f.shape[2], f.shape[1], rho0, dev_exp, int(unscaled), _p(f), _p(h))
+    return h
+
+
+def dev16_decode(h, rho0: float = 1.0, dev_exp: int = 12, unscaled: bool = False):
+    """Populations f[9, ny, nx] (float64 holding binary32 values) of FP16 deviation codes."""
+    h = _f64(h)
+    f = np.empty_like(h)
+    lib().orc_dev16_decode(h.shape[2], h.shape[1], rho0, dev_exp, int(unscaled), _p(h), _p(f))
+    return f

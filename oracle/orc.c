@@ -641,3 +641,58 @@ int orc_adjoint_kl(int nx, int ny, double tau, int nsteps, int store_every, cons
   free(ck), free(seg), free(ft), free(lt), free(lf);
   return 0;
 }
+
+/* ------------------------------------------------------ FP16 deviation storage ----
+ * The storage form of populations as FP16 deviations from the rest equilibrium (the
+ * storage choice of the lattice library, not a formula of the paper):
+ *   h_q = RN16((f_q - b_q) s_q),  b_q = RN32(w_q rho0),  s_q = 2^(k_q + K),
+ *   k_q = 1, 3, 5 for w_q = 4/9, 1/9, 1/36 (s_q = 1 when unscaled),
+ *   decoded f_q = RN32(b_q + h_q / s_q).
+ * RN16 / RN32: round to the nearest binary16 / binary32 value, ties to even. */
+
+/* Nearest IEEE binary16 value of x (ties to even), as a double; +-Inf beyond the
+ * largest finite value 65504 (from 65520 up, the midpoint to 2^16). */
+double orc_fp16_round(double x) {
+  if (x == 0.0 || !isfinite(x)) return x;
+  const double a = fabs(x);
+  if (a >= 65520.0) return x > 0 ? INFINITY : -INFINITY;
+  int e2;
+  frexp(a, &e2);             /* a = m 2^e2, m in [0.5, 1): binade exponent e2 - 1 */
+  int e = e2 - 1;
+  if (e < -14) e = -14;      /* subnormal range: fixed spacing 2^-24 */
+  const double quantum = ldexp(1.0, e - 10);
+  const double r = rint(a / quantum) * quantum;  /* rint: nearest, ties to even */
+  return x > 0 ? r : -r;
+}
+
+static void dev16_params(double rho0, int dev_exp, int unscaled, double b[9], double s[9]) {
+  static const int K[9] = {1, 3, 3, 3, 3, 5, 5, 5, 5};
+  for (int q = 0; q < 9; ++q) {
+    b[q] = (double)(float)(W[q] * rho0);
+    s[q] = unscaled ? 1.0 : ldexp(1.0, K[q] + dev_exp);
+  }
+}
+
+void orc_dev16_encode(int nx, int ny, double rho0, int dev_exp, int unscaled, const double* f,
+                      double* h) {
+  double b[9], s[9];
+  dev16_params(rho0, dev_exp, unscaled, b, s);
+  for (int q = 0; q < 9; ++q)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const size_t k = at(nx, ny, q, i, j);
+        h[k] = orc_fp16_round((f[k] - b[q]) * s[q]);
+      }
+}
+
+void orc_dev16_decode(int nx, int ny, double rho0, int dev_exp, int unscaled, const double* h,
+                      double* f) {
+  double b[9], s[9];
+  dev16_params(rho0, dev_exp, unscaled, b, s);
+  for (int q = 0; q < 9; ++q)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const size_t k = at(nx, ny, q, i, j);
+        f[k] = (double)(float)(b[q] + h[k] / s[q]);
+      }
+}

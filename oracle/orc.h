@@ -139,6 +139,18 @@ int orc_adjoint_kl(int nx, int ny, double tau, int nsteps, int store_every, cons
                    const double* ux0, const double* uy0, const double* weight, double* J,
                    double* grad_rho0, double* grad_tau);
 
+/* FP16 deviation storage of populations (the library's KSS_FP16DEV form):
+ *   h_q = RN16((f_q - b_q) s_q),  b_q = RN32(w_q rho0),  s_q = 2^(k_q + K)
+ *   (k_q = 1, 3, 5 for w_q = 4/9, 1/9, 1/36; s_q = 1 if unscaled),
+ *   decoded f_q = RN32(b_q + h_q / s_q).
+ * orc_fp16_round: the nearest binary16 value (ties to even, +-Inf from 65520 up).
+ * Codes h are carried as doubles holding binary16 values; arrays are [9][ny][nx]. */
+double orc_fp16_round(double x);
+void orc_dev16_encode(int nx, int ny, double rho0, int dev_exp, int unscaled, const double* f,
+                      double* h);
+void orc_dev16_decode(int nx, int ny, double rho0, int dev_exp, int unscaled, const double* h,
+                      double* f);
+
 #ifdef __cplusplus
 }
 #endif
