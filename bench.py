@@ -11,6 +11,7 @@ conservation sums.  A step = one fused launch over the whole lattice.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
   python bench.py --workload batch64    # the batched workload (below)
   python bench.py --workload adjoint512 # the adjoint workload (below)
+  python bench.py --workload fp16dev8192 [--fp16-error]  # the precision workload (below)
 
 Batched workload (--workload batch64): 64 uneven periodic lattices (sizes 64^2 ..
 1024^2, tau ~ U[0.51, 1.5], Mach ~ U[0.01, 0.15], seed 13618, 15.8 M cells in all), the
@@ -316,6 +317,127 @@ def run_adjoint(args):
     return 0
 
 
+FP16_METRIC = "MLUPS with sensors fused, FP16 deviation storage, and % of HBM roofline, 1xGB300"
+
+
+def run_fp16(args):
+    """The precision workload: FP16 deviation storage against FP32 storage."""
+    import numpy as np
+    import torch
+
+    from paper_2603_13618_gb300 import inputs, kss
+
+    torch.cuda.set_device(0)
+    n = args.size or 8192
+    amp, tau, kexp = 1e-3, 0.6, 20
+    gen = dict(seed=8192, kmax=8, drho_amp=amp, mach=amp / inputs.CS, jump=1.0)
+    rho, ux, uy = inputs.smooth_jump(n, n, **gen)
+    stream = torch.cuda.current_stream()
+    K = args.steps
+    peak, peak_kind = measured_peak()
+    cells = n * n
+    runs = {}
+    with ClockSampler(0) as clk:
+        for name, prec, out in (("fp16dev", "fp16dev", 1), ("fp32", "fp32", 1),
+                                ("fp16dev_plain", "fp16dev", 0), ("fp32_plain", "fp32", 0)):
+            lat = kss.Lattice(n, n, precision=prec, tau=tau, refine_sensor="kn",
+                              refine_threshold=THR_R, switch_sensor="neq",
+                              switch_threshold=THR_S, record=("kl",), output_every=out,
+                              tile=TILE, dev_exp=kexp)
+            lat.set_fields(rho, ux, uy)
+            lat.step(args.warmup)
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K)]
+            for k in range(K):
+                ev[2 * k].record(stream)
+                lat.step(1)
+                ev[2 * k + 1].record(stream)
+            torch.cuda.synchronize()
+            total = ev[0].elapsed_time(ev[-1])
+            kern = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(K)) / K
+            bpl = (18 if prec == "fp16dev" else 36) * 2 + (5 if out else 0)
+            achieved = bpl * cells / (kern * 1e-3) / 1e9
+            runs[name] = {"value": cells * K / (total * 1e-3) / 1e6, "unit": "MLUPS",
+                          "ms_per_step": total / K, "kernel_ms": kern, "bytes_per_lup": bpl,
+                          "achieved_gbs": achieved, "frac": achieved / peak}
+            lat.close()
+    clocks = clk.summary()
+    err = None
+    if args.fp16_error:
+        err = fp16_error(n, tau, kexp, gen)
+    main = runs["fp16dev"]
+    line = {
+        "metric": FP16_METRIC, "value": main["value"], "unit": "MLUPS", "n_gpus": 1, "steps": K,
+        "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16 storage / f32 arithmetic",
+        "data": "synthetic",
+        "config": {"workload": f"D2Q9 {n}x{n} periodic, smooth perturbations amplitude 1e-3 "
+                               "(density and velocity), tau=0.6, FP16 deviation storage "
+                               "K=20, Kn refine 1e-3, neq switch 1e-4, KL field, flags, tile "
+                               "counts, sums every step", "nx": n, "ny": n,
+                   "l2": f"inputs larger than L2: {cells * 36 / 1e9:.2f} GB of populations "
+                         "per step"},
+        "roofline": {"bound": "hbm", "achieved": main["achieved_gbs"], "peak": peak,
+                     "unit": "GB/s", "frac": main["frac"], "peak_kind": peak_kind,
+                     "traffic": None, "algorithmic_bytes_per_launch": main["bytes_per_lup"] * cells,
+                     "kernel_ms": main["kernel_ms"],
+                     "kernel": "step_kernel<__half, MODE_STD, pull, store>"},
+        "variants": runs,
+        "speedup_vs_fp32": main["value"] / runs["fp32"]["value"],
+        "error_vs_fp64": err,
+        "gpu_launches": K,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def fp16_error(n, tau, kexp, gen, steps=500, window=256):
+    """Errors of FP16 deviation and FP32 storage after `steps` steps against the FP64
+    oracle on the central window (the oracle runs the window's domain of dependence)."""
+    import numpy as np
+
+    import oracle
+    from paper_2603_13618_gb300 import inputs, kss
+
+    x0 = n // 2 - window // 2
+    halo = steps
+    wr, wu, wv = inputs.smooth_jump(n, n, x0=x0 - halo, y0=x0 - halo, wx=window + 2 * halo,
+                                    wy=window + 2 * halo, **gen)
+    t0 = time.perf_counter()
+    f = oracle.step(oracle.init_equilibrium(wr, wu, wv), tau, steps - 1)
+    sens, nonpos = oracle.sensor_fields(f, tau, pull=True)
+    f = oracle.step(f, tau)
+    rr, ru, rv = oracle.moments(f)
+    t_orc = time.perf_counter() - t0
+    c = slice(halo, halo + window)
+    ref = {"rho": rr[c, c], "ux": ru[c, c], "uy": rv[c, c]}
+    for s in ("kn", "kl", "neq"):
+        ref[s] = sens[oracle.SENSOR_ID[s]][c, c]
+    rf, _, _ = oracle.flags(ref["kn"], THR_R, ref["neq"], THR_S, nonpos[c, c], TILE)
+    rho, ux, uy = inputs.smooth_jump(n, n, **gen)
+    out = {"steps": steps, "window": window, "oracle_s": t_orc}
+    win = (slice(x0, x0 + window), slice(x0, x0 + window))
+    for prec in ("fp16dev", "fp32"):
+        lat = kss.Lattice(n, n, precision=prec, tau=tau, record=("kn", "kl", "neq"),
+                          output_every=steps, dev_exp=kexp)
+        lat.set_fields(rho, ux, uy)
+        lat.step(steps)
+        got = dict(zip(("rho", "ux", "uy"), (a[win] for a in lat.read_moments())))
+        for s in ("kn", "kl", "neq"):
+            got[s] = lat.read_sensor(s)[win]
+        fl = lat.read_flags()[0][win]
+        lat.close()
+        e = {}
+        for key in got:
+            d = np.abs(got[key] - ref[key])
+            scale = np.max(np.abs(ref[key])) if key != "rho" else 1.0
+            e[key] = {"max_abs": float(np.max(d)), "max_rel_to_field_max": float(np.max(d) / scale)}
+        e["flags_mismatch"] = int(np.sum((fl & 3) != (rf & 3)))
+        out[prec] = e
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -481,10 +603,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", default="auto", choices=["auto", "vector", "tma"],
                     help="step kernel (auto: the library's choice)")
-    ap.add_argument("--size", type=int, default=4096,
-                    help="lattice edge (profiling captures of a smaller case only)")
+    ap.add_argument("--size", type=int, default=None,
+                    help="lattice edge (default 4096; 8192 for fp16dev8192; smaller sizes "
+                         "for profiling captures only)")
+    ap.add_argument("--fp16-error", action="store_true",
+                    help="fp16dev8192: also measure the error against the FP64 oracle")
     ap.add_argument("--workload", default="single",
-                    choices=["single", "batch64", "adjoint512"],
+                    choices=["single", "batch64", "adjoint512", "fp16dev8192"],
                     help="single: the 4096^2 lattice (default); batch64: 64 uneven "
                          "lattices; adjoint512: the gradient of the KL objective")
     ap.add_argument("--no-tune", action="store_true",
@@ -493,13 +618,15 @@ def main():
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     global NX, NY
-    NX = NY = args.size
+    NX = NY = args.size or 4096
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch64":
         return run_batch(args)
     if args.workload == "adjoint512":
         return run_adjoint(args)
+    if args.workload == "fp16dev8192":
+        return run_fp16(args)
     return run_gpu(args)
 
 

@@ -51,8 +51,17 @@ extern "C" {
 #define KSS_ERR_UNSUPPORTED (-6) /* precision or option not built into this library  */
 #define KSS_WARN_NONPOSITIVE 1   /* sensors evaluated; some cell had f_q <= 0 or f^eq_q <= 0 */
 
-/* Storage and arithmetic precision of a lattice. */
-typedef enum { KSS_FP64 = 0, KSS_FP32 = 1 } kss_precision;
+/* Storage and arithmetic precision of a lattice:
+ *   KSS_FP64, KSS_FP32  populations stored and collided in that precision;
+ *   KSS_FP16DEV         populations stored as FP16 deviations from the rest equilibrium
+ *                       of the reference density rho0 (kss_config.rho0):
+ *                         h_q = RN_fp16((f_q - b_q) s_q),  b_q = RN_fp32(w_q rho0),
+ *                         s_q = 2^(k_q + dev_exp), k_q = 1, 3, 5 for w_q = 4/9, 1/9, 1/36
+ *                       (s_q w_q = (8/9) 2^dev_exp for every q; dev_unscaled = 1 takes
+ *                       s_q = 1, the literal deviation), decoded as
+ *                       f_q = RN_fp32(b_q + h_q / s_q) and collided in FP32.  Sensor
+ *                       fields are FP32.  18 bytes per cell per buffer instead of 36. */
+typedef enum { KSS_FP64 = 0, KSS_FP32 = 1, KSS_FP16DEV = 2 } kss_precision;
 
 /* Sensor ids: Table 1 of the paper, f-distribution terms only (the model has no
  * second distribution g).  mu = rho c_s^2 tau, lambda = 0, eta = mu (the D2Q9 BGK
@@ -101,13 +110,16 @@ typedef struct {
   int32_t own_stream;        /* 1: ignore `stream`, create a non-blocking stream owned */
                              /*    by the lattice (destroyed with it)                  */
   int32_t kernel;            /* step kernel: KSS_KERNEL_AUTO, _VECTOR or _TMA          */
+  double rho0;               /* KSS_FP16DEV: reference density of the deviations, > 0  */
+  int32_t dev_exp;           /* KSS_FP16DEV: scale exponent K (-24 .. 40)              */
+  int32_t dev_unscaled;      /* KSS_FP16DEV: 1 = literal deviations (s_q = 1)          */
 } kss_config;
 
 /* Step kernels (same results; they differ in how source rows reach the SM):
  *   KSS_KERNEL_VECTOR  16-byte vector loads into registers, warp-shuffle halos;
  *   KSS_KERNEL_TMA     bulk copies (cp.async.bulk) into a per-warp shared-memory ring,
- *                      persistent CTAs; used for plain and {Kn, KL, neq} steps, other
- *                      sensor sets fall back to the vector kernel;
+ *                      persistent CTAs; used for plain and {Kn, KL, neq} steps of FP32 and
+ *                      FP64 lattices, other cases fall back to the vector kernel;
  *   KSS_KERNEL_AUTO    the faster on GB300, which is the vector kernel at every size
  *                      measured. */
 #define KSS_KERNEL_AUTO 0
@@ -118,7 +130,8 @@ typedef struct kss_lattice kss_lattice;  /* opaque */
 
 /* Fill *cfg with defaults for an nx x ny lattice: tau 0.8, refine on KSS_S_KN at 1e-3,
  * switch on KSS_S_NEQ at 1e-4, record KSS_S_KL, output every step, tile 16, the CUDA
- * default stream. */
+ * default stream, rho0 = 1, dev_exp = 12 (relative deviations up to about 15 stay in
+ * FP16 range), dev_unscaled = 0. */
 int kss_config_default(kss_config* cfg, int32_t nx, int32_t ny, int32_t precision);
 
 /* Create a lattice (device buffers allocated; populations zero until set). */

@@ -109,7 +109,8 @@ int forward_impl(kss_adjoint* A, double* J) {
   const size_t n = size_t(A->cfg.nx) * A->cfg.ny;
   KSS_ACUDA(A, kss::launch_init_equilibrium<T>(A->fields, A->fields + n, A->fields + 2 * n,
                                                reinterpret_cast<T*>(A->ck), A->plane, A->pitch,
-                                               A->cfg.nx, A->cfg.ny, A->stream));
+                                               A->cfg.nx, A->cfg.ny, kss::codec_t<T>{},
+                                               A->stream));
   // f^k for k = 1 .. N-1: checkpoints land in their slot, the others alternate in work[]
   const void* cur = A->ck;
   for (int k = 1; k < N; ++k) {

@@ -28,7 +28,7 @@ struct Graph {
 struct kss_batch {
   int n = 0;
   int device = 0;
-  bool fp32 = true;
+  int prec = KSS_FP32;  // every member's precision
   int nsm = 0;
   std::vector<kss_lattice*> mem;
   cudaStream_t stream = nullptr;  // every member's stream
@@ -70,7 +70,9 @@ int bfail(kss_batch* B, int code, const std::string& m) {
   } while (0)
 
 size_t param_bytes(const kss_batch* B) {
-  return B->fp32 ? sizeof(kss::StepParams<float>) : sizeof(kss::StepParams<double>);
+  return with_storage(B->prec, [](auto tag) {
+    return sizeof(kss::StepParams<typename decltype(tag)::type>);
+  });
 }
 
 int default_rows(const kss_batch* B) { return std::max(32, B->max_tile); }
@@ -84,8 +86,9 @@ bool valid_rows(const kss_batch* B, int rows) {
 
 dim3 member_grid(const kss_batch* B, const kss_lattice* L, int rows) {
   const int bands = rows / L->cfg.tile;
-  return B->fp32 ? kss::step_grid<float>(L->cfg.nx, L->cfg.ny, L->cfg.tile, bands)
-                 : kss::step_grid<double>(L->cfg.nx, L->cfg.ny, L->cfg.tile, bands);
+  return with_storage(B->prec, [&](auto tag) {
+    return kss::step_grid<typename decltype(tag)::type>(L->cfg.nx, L->cfg.ny, L->cfg.tile, bands);
+  });
 }
 
 void drop_graphs(kss_batch* B) {
@@ -139,16 +142,16 @@ int write_items(kss_batch* B) {
   return KSS_OK;
 }
 
-template <class T>
-void fill_params(const kss_batch* B, std::vector<kss::StepParams<T>>& t0,
-                 std::vector<kss::StepParams<T>>& t1) {
+template <class S>
+void fill_params(const kss_batch* B, std::vector<kss::StepParams<S>>& t0,
+                 std::vector<kss::StepParams<S>>& t1) {
   t0.resize(B->n);
   t1.resize(B->n);
   for (int k = 0; k < B->n; ++k) {
     const kss_lattice* L = B->mem[k];
     const int c = L->cur;
     for (int o = 0; o < 2; ++o) {
-      kss::StepParams<T> p = make_params<T>(L, L->f[c ^ o], L->f[c ^ o ^ 1]);
+      kss::StepParams<S> p = make_params<S>(L, L->f[c ^ o], L->f[c ^ o ^ 1]);
       p.bands = B->tun.rows / L->cfg.tile;
       p.grid_x = int(B->grids[k].x);
       p.nblocks = int(B->grids[k].x * B->grids[k].y);
@@ -164,17 +167,15 @@ void fill_params(const kss_batch* B, std::vector<kss::StepParams<T>>& t0,
 // state, table[1] the other buffer.
 int write_tables(kss_batch* B) {
   const size_t bytes = param_bytes(B) * B->n;
-  if (B->fp32) {
-    std::vector<kss::StepParams<float>> t0, t1;
-    fill_params<float>(B, t0, t1);
-    KSS_BCUDA(B, cudaMemcpy(B->table[0], t0.data(), bytes, cudaMemcpyHostToDevice));
-    KSS_BCUDA(B, cudaMemcpy(B->table[1], t1.data(), bytes, cudaMemcpyHostToDevice));
-  } else {
-    std::vector<kss::StepParams<double>> t0, t1;
-    fill_params<double>(B, t0, t1);
-    KSS_BCUDA(B, cudaMemcpy(B->table[0], t0.data(), bytes, cudaMemcpyHostToDevice));
-    KSS_BCUDA(B, cudaMemcpy(B->table[1], t1.data(), bytes, cudaMemcpyHostToDevice));
-  }
+  const cudaError_t e = with_storage(B->prec, [&](auto tag) {
+    using S = typename decltype(tag)::type;
+    std::vector<kss::StepParams<S>> t0, t1;
+    fill_params<S>(B, t0, t1);
+    cudaError_t r = cudaMemcpy(B->table[0], t0.data(), bytes, cudaMemcpyHostToDevice);
+    if (r == cudaSuccess) r = cudaMemcpy(B->table[1], t1.data(), bytes, cudaMemcpyHostToDevice);
+    return r;
+  });
+  KSS_BCUDA(B, e);
   for (int k = 0; k < B->n; ++k) B->base_cur[k] = B->mem[k]->cur;
   B->par = 0;
   B->tables_valid = true;
@@ -207,11 +208,11 @@ int launch_ctas(const kss_batch* B) {
 
 cudaError_t launch_one(kss_batch* B, int tbl, int mode, cudaStream_t s) {
   const int ctas = launch_ctas(B);
-  if (B->fp32)
-    return kss::launch_batch_step<float>(static_cast<const kss::StepParams<float>*>(B->table[tbl]),
-                                         B->items, B->nitems, ctas, mode, s);
-  return kss::launch_batch_step<double>(static_cast<const kss::StepParams<double>*>(B->table[tbl]),
-                                        B->items, B->nitems, ctas, mode, s);
+  return with_storage(B->prec, [&](auto tag) {
+    using S = typename decltype(tag)::type;
+    return kss::launch_batch_step<S>(static_cast<const kss::StepParams<S>*>(B->table[tbl]),
+                                     B->items, B->nitems, ctas, mode, s);
+  });
 }
 
 char mode_char(int mode) { return mode == kss::MODE_PLAIN ? 'P' : (mode == kss::MODE_STD ? 'S' : 'F'); }
@@ -287,7 +288,7 @@ std::string tune_key(const kss_batch* B) {
   for (const kss_lattice* L : B->mem) cells += (long long)L->cfg.nx * L->cfg.ny;
   const int lc = int(std::lround(std::log2(double(std::max(1LL, cells)))));
   const int ln = int(std::lround(std::log2(double(B->n))));
-  return name + "|" + std::to_string(B->nsm) + "|" + (B->fp32 ? "fp32" : "fp64") + "|" +
+  return name + "|" + std::to_string(B->nsm) + "|" + (B->prec == KSS_FP64 ? "fp64" : (B->prec == KSS_FP32 ? "fp32" : "fp16dev")) + "|" +
          std::to_string(lc) + "|" + std::to_string(ln);
 }
 
@@ -333,7 +334,7 @@ int kss_batch_create(int32_t n, const kss_config* cfgs, kss_batch** out) {
   kss_batch* B = new (std::nothrow) kss_batch();
   if (!B) return KSS_ERR_OOM;
   B->n = n;
-  B->fp32 = cfgs[0].precision == KSS_FP32;
+  B->prec = cfgs[0].precision;
   if (cudaGetDevice(&B->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&B->nsm, cudaDevAttrMultiProcessorCount, B->device) != cudaSuccess) {
     cudaGetLastError();

@@ -27,7 +27,13 @@ int check_config(const kss_config* c) {
   if (!c) return KSS_ERR_ARG;
   if (c->nx < 1 || c->ny < 1) return KSS_ERR_ARG;
   if ((long long)c->nx * c->ny > std::numeric_limits<int>::max()) return KSS_ERR_ARG;
-  if (c->precision != KSS_FP64 && c->precision != KSS_FP32) return KSS_ERR_UNSUPPORTED;
+  if (c->precision != KSS_FP64 && c->precision != KSS_FP32 && c->precision != KSS_FP16DEV)
+    return KSS_ERR_UNSUPPORTED;
+  if (c->precision == KSS_FP16DEV) {
+    if (!(c->rho0 > 0.0) || !std::isfinite(c->rho0)) return KSS_ERR_ARG;
+    if (c->dev_exp < -24 || c->dev_exp > 40) return KSS_ERR_ARG;
+    if (c->dev_unscaled != 0 && c->dev_unscaled != 1) return KSS_ERR_ARG;
+  }
   if (!(c->tau > 0.5) || !std::isfinite(c->tau)) return KSS_ERR_ARG;
   if (!valid_sensor(c->refine_sensor) || !valid_sensor(c->switch_sensor)) return KSS_ERR_ARG;
   if (std::isnan(c->refine_threshold) || std::isnan(c->switch_threshold)) return KSS_ERR_ARG;
@@ -49,16 +55,20 @@ bool use_tma(const kss_lattice* L, int mode) {
 // CTAs of the fixup pass (2 per SM, grid-striding over the deferred cells).
 int fixup_ctas(const kss_lattice* L) { return 2 * L->nsm; }
 
-template <class T>
+template <class S>
 cudaError_t launch_one_step(kss_lattice* L, bool out) {
-  kss::StepParams<T> p = make_params<T>(L, L->f[L->cur], L->f[L->cur ^ 1]);
+  kss::StepParams<S> p = make_params<S>(L, L->f[L->cur], L->f[L->cur ^ 1]);
   const int mode = out ? mode_for(needed_mask(L, L->cfg.record_mask)) : MODE_PLAIN;
-  // (the vector kernel recomputes its deferred cells itself, at the end of each CTA)
-  if (!use_tma(L, mode)) return kss::launch_step<T>(p, mode, true, true, L->stream);
+  // (the vector kernel recomputes its deferred cells itself, at the end of each CTA; FP16
+  // deviation storage has the vector kernel only)
+  if constexpr (std::is_same<S, __half>::value) {
+    return kss::launch_step<S>(p, mode, true, true, L->stream);
+  } else {
+    if (!use_tma(L, mode)) return kss::launch_step<S>(p, mode, true, true, L->stream);
   // persistent grid: one CTA (two warp groups) per SM; the groups on a strip split
   // its rows evenly, at least 4 rows per run
   kss::TmaPlan plan;
-  const int width = kss::kGroupWarps * 32 * kss::Vec<T>::N;
+  const int width = kss::kGroupWarps * 32 * kss::Vec<S>::N;
   plan.strips = (L->cfg.nx + width - 1) / width;
   const int groups = L->nsm * kss::kTmaGroups;
   const int by_groups = groups / plan.strips;
@@ -70,28 +80,29 @@ cudaError_t launch_one_step(kss_lattice* L, bool out) {
                                           L->stream);
     if (e != cudaSuccess) return e;
   }
-  const cudaError_t e = kss::launch_step_tma<T>(p, mode, plan, L->nsm, L->stream);
+  const cudaError_t e = kss::launch_step_tma<S>(p, mode, plan, L->nsm, L->stream);
   if (e != cudaSuccess || mode != MODE_STD) return e;
-  return kss::launch_fixup<T>(p, true, fixup_ctas(L), L->stream);
+  return kss::launch_fixup<S>(p, true, fixup_ctas(L), L->stream);
+  }
 }
 
 // Evaluate sensors / flags / tiles / sums of the state of the most recent step
 // (its pre-collision populations: the other buffer, streamed) or of the stored
 // state when no step was taken since the last set.  sensor >= 0 also writes
 // that sensor's field into evalplane.
-template <class T>
+template <class S>
 cudaError_t launch_eval(kss_lattice* L, int sensor) {
   const bool pull = L->step > 0;
   const void* src = pull ? L->f[L->cur ^ 1] : L->f[L->cur];
-  kss::StepParams<T> p = make_params<T>(L, src, nullptr);
+  kss::StepParams<S> p = make_params<S>(L, src, nullptr);
   for (int s = 0; s < KSS_S_COUNT; ++s) p.rec_slot[s] = -1;
   uint32_t extra = 0;
   if (sensor >= 0) {
-    p.rec = static_cast<T*>(L->evalplane);
+    p.rec = static_cast<kss::arith_t<S>*>(L->evalplane);
     p.rec_slot[sensor] = 0;
     extra = 1u << sensor;
   }
-  return kss::launch_step<T>(p, mode_for(needed_mask(L, extra)), pull, false, L->stream);
+  return kss::launch_step<S>(p, mode_for(needed_mask(L, extra)), pull, false, L->stream);
 }
 
 int ensure_staging(kss_lattice* L, size_t elems) {
@@ -115,12 +126,11 @@ int ensure_staging(kss_lattice* L, size_t elems) {
 // Make flags / tiles / sums (and, if sensor >= 0, that sensor's field) describe
 // the current step.  Returns where the sensor field is (rec slot or evalplane).
 int ensure_outputs(kss_lattice* L, int sensor, const void** field) {
-  const bool fp32 = L->cfg.precision == KSS_FP32;
   const bool have_out = L->out_step == L->step;
   const void* where = nullptr;
   if (sensor >= 0) {
     if (L->rec_step == L->step && L->rec_slot[sensor] >= 0)
-      where = static_cast<const char*>(L->rec) + L->esz * L->plane * L->rec_slot[sensor];
+      where = static_cast<const char*>(L->rec) + L->tsz * L->plane * L->rec_slot[sensor];
     else if (L->eval_step == L->step && L->eval_sensor == sensor)
       where = L->evalplane;
   }
@@ -129,7 +139,9 @@ int ensure_outputs(kss_lattice* L, int sensor, const void** field) {
     return KSS_OK;
   }
   const int s = (sensor >= 0 && !where) ? sensor : -1;
-  KSS_CUDA(L, fp32 ? launch_eval<float>(L, s) : launch_eval<double>(L, s));
+  KSS_CUDA(L, with_storage(L->cfg.precision, [&](auto tag) {
+             return launch_eval<typename decltype(tag)::type>(L, s);
+           }));
   L->out_step = L->step;
   if (s >= 0) {
     L->eval_step = L->step;
@@ -216,6 +228,9 @@ int kss_config_default(kss_config* c, int32_t nx, int32_t ny, int32_t precision)
   c->stream = nullptr;
   c->own_stream = 0;
   c->kernel = KSS_KERNEL_AUTO;
+  c->rho0 = 1.0;
+  c->dev_exp = 12;
+  c->dev_unscaled = 0;
   return KSS_OK;
 }
 
@@ -232,15 +247,28 @@ int kss_create(const kss_config* cfg, kss_lattice** out) {
     delete L;
     return KSS_ERR_CUDA;
   }
-  const bool fp32 = cfg->precision == KSS_FP32;
-  L->esz = fp32 ? sizeof(float) : sizeof(double);
+  L->esz = cfg->precision == KSS_FP64 ? 8 : (cfg->precision == KSS_FP32 ? 4 : 2);
+  L->tsz = cfg->precision == KSS_FP64 ? 8 : 4;
+  if (cfg->precision == KSS_FP16DEV) {
+    // b_q = RN_fp32(w_q rho0); s_q = 2^(k_q + K), k_q = 1, 3, 5 (w_q = 4/9, 1/9, 1/36)
+    static const double w[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                                1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+    static const int k[9] = {1, 3, 3, 3, 3, 5, 5, 5, 5};
+    for (int q = 0; q < 9; ++q) {
+      L->codec16.base[q] = static_cast<float>(w[q] * cfg->rho0);
+      const int e = cfg->dev_unscaled ? 0 : k[q] + cfg->dev_exp;
+      L->codec16.scale[q] = std::ldexp(1.0f, e);
+      L->codec16.inv[q] = std::ldexp(1.0f, -e);
+    }
+  }
   const int align = int(128 / L->esz);
   L->pitch = (cfg->nx + align - 1) / align * align;
   L->plane = (long long)L->pitch * cfg->ny;
   L->ntx = (cfg->nx + cfg->tile - 1) / cfg->tile;
   L->nty = (cfg->ny + cfg->tile - 1) / cfg->tile;
-  const dim3 g = fp32 ? kss::step_grid<float>(cfg->nx, cfg->ny, cfg->tile)
-                      : kss::step_grid<double>(cfg->nx, cfg->ny, cfg->tile);
+  const dim3 g = with_storage(cfg->precision, [&](auto tag) {
+    return kss::step_grid<typename decltype(tag)::type>(cfg->nx, cfg->ny, cfg->tile);
+  });
   L->nblocks = int(g.x * g.y);
   if (cudaDeviceGetAttribute(&L->nsm, cudaDevAttrMultiProcessorCount, L->device) != cudaSuccess ||
       L->nsm < 1) {
@@ -266,7 +294,7 @@ int kss_create(const kss_config* cfg, kss_lattice** out) {
     L->own_stream = true;
   }
   const size_t pop_bytes = 9 * size_t(L->plane) * L->esz;
-  const size_t plane_bytes = size_t(L->plane) * L->esz;
+  const size_t plane_bytes = size_t(L->plane) * L->tsz;  // sensor planes
   struct {
     void** p;
     size_t bytes;
@@ -337,12 +365,12 @@ int kss_set_fields(kss_lattice* L, const double* rho, const double* ux, const do
     v = L->staging + 2 * n;
   }
   const int nx = L->cfg.nx, ny = L->cfg.ny;
-  if (L->cfg.precision == KSS_FP32)
-    KSS_CUDA(L, kss::launch_init_equilibrium<float>(r, u, v, static_cast<float*>(L->f[L->cur]),
-                                                    L->plane, L->pitch, nx, ny, L->stream));
-  else
-    KSS_CUDA(L, kss::launch_init_equilibrium<double>(r, u, v, static_cast<double*>(L->f[L->cur]),
-                                                     L->plane, L->pitch, nx, ny, L->stream));
+  KSS_CUDA(L, with_storage(L->cfg.precision, [&](auto tag) {
+             using S = typename decltype(tag)::type;
+             return kss::launch_init_equilibrium<S>(r, u, v, static_cast<S*>(L->f[L->cur]),
+                                                    L->plane, L->pitch, nx, ny, codec_of<S>(L),
+                                                    L->stream);
+           }));
   if (!on_device) KSS_CUDA(L, cudaStreamSynchronize(L->stream));
   reset_after_set(L);
   return KSS_OK;
@@ -361,12 +389,12 @@ int kss_set_populations(kss_lattice* L, const double* f, int on_device) {
     src = L->staging;
   }
   const int nx = L->cfg.nx, ny = L->cfg.ny;
-  if (L->cfg.precision == KSS_FP32)
-    KSS_CUDA(L, kss::launch_dense_to_pitched<float>(src, L->plane, L->pitch, nx, ny, 9,
-                                                    static_cast<float*>(L->f[L->cur]), L->stream));
-  else
-    KSS_CUDA(L, kss::launch_dense_to_pitched<double>(src, L->plane, L->pitch, nx, ny, 9,
-                                                     static_cast<double*>(L->f[L->cur]), L->stream));
+  KSS_CUDA(L, with_storage(L->cfg.precision, [&](auto tag) {
+             using S = typename decltype(tag)::type;
+             return kss::launch_dense_to_pops<S>(src, L->plane, L->pitch, nx, ny,
+                                                 static_cast<S*>(L->f[L->cur]), codec_of<S>(L),
+                                                 L->stream);
+           }));
   if (!on_device) KSS_CUDA(L, cudaStreamSynchronize(L->stream));
   reset_after_set(L);
   return KSS_OK;
@@ -384,12 +412,11 @@ int kss_get_populations(kss_lattice* L, double* f, int on_device) {
     dst = L->staging;
   }
   const int nx = L->cfg.nx, ny = L->cfg.ny;
-  if (L->cfg.precision == KSS_FP32)
-    KSS_CUDA(L, kss::launch_pitched_to_dense<float>(static_cast<const float*>(L->f[L->cur]),
-                                                    L->plane, L->pitch, nx, ny, 9, dst, L->stream));
-  else
-    KSS_CUDA(L, kss::launch_pitched_to_dense<double>(static_cast<const double*>(L->f[L->cur]),
-                                                     L->plane, L->pitch, nx, ny, 9, dst, L->stream));
+  KSS_CUDA(L, with_storage(L->cfg.precision, [&](auto tag) {
+             using S = typename decltype(tag)::type;
+             return kss::launch_pops_to_dense<S>(static_cast<const S*>(L->f[L->cur]), L->plane,
+                                                 L->pitch, nx, ny, dst, codec_of<S>(L), L->stream);
+           }));
   if (!on_device)
     KSS_CUDA(L, cudaMemcpyAsync(f, L->staging, n * 8, cudaMemcpyDeviceToHost, L->stream));
   KSS_CUDA(L, cudaStreamSynchronize(L->stream));
@@ -401,11 +428,12 @@ int kss_step(kss_lattice* L, int32_t nsteps) {
   if (rc) return rc;
   if (nsteps < 0) return fail(L, KSS_ERR_ARG, "negative step count");
   DeviceGuard g(L->device);
-  const bool fp32 = L->cfg.precision == KSS_FP32;
   for (int32_t s = 0; s < nsteps; ++s) {
     const int64_t n = L->step + 1;
     const bool out = L->cfg.output_every > 0 && (n % L->cfg.output_every) == 0;
-    KSS_CUDA(L, fp32 ? launch_one_step<float>(L, out) : launch_one_step<double>(L, out));
+    KSS_CUDA(L, with_storage(L->cfg.precision, [&](auto tag) {
+               return launch_one_step<typename decltype(tag)::type>(L, out);
+             }));
     L->cur ^= 1;
     L->step = n;
     if (out) {
@@ -430,12 +458,11 @@ int kss_read_moments(kss_lattice* L, double* rho, double* ux, double* uy, int on
     v = L->staging + 2 * n;
   }
   const int nx = L->cfg.nx, ny = L->cfg.ny;
-  if (L->cfg.precision == KSS_FP32)
-    KSS_CUDA(L, kss::launch_moments<float>(static_cast<const float*>(L->f[L->cur]), L->plane,
-                                           L->pitch, nx, ny, r, u, v, L->stream));
-  else
-    KSS_CUDA(L, kss::launch_moments<double>(static_cast<const double*>(L->f[L->cur]), L->plane,
-                                            L->pitch, nx, ny, r, u, v, L->stream));
+  KSS_CUDA(L, with_storage(L->cfg.precision, [&](auto tag) {
+             using S = typename decltype(tag)::type;
+             return kss::launch_moments<S>(static_cast<const S*>(L->f[L->cur]), L->plane,
+                                           L->pitch, nx, ny, r, u, v, codec_of<S>(L), L->stream);
+           }));
   if (!on_device) {
     KSS_CUDA(L, cudaMemcpyAsync(rho, r, n * 8, cudaMemcpyDeviceToHost, L->stream));
     KSS_CUDA(L, cudaMemcpyAsync(ux, u, n * 8, cudaMemcpyDeviceToHost, L->stream));
@@ -460,7 +487,7 @@ int kss_read_sensor(kss_lattice* L, int32_t sensor, double* out, int on_device) 
     dst = L->staging;
   }
   const int nx = L->cfg.nx, ny = L->cfg.ny;
-  if (L->cfg.precision == KSS_FP32)
+  if (L->cfg.precision != KSS_FP64)  // FP32 and FP16-deviation lattices: FP32 sensor planes
     KSS_CUDA(L, kss::launch_pitched_to_dense<float>(static_cast<const float*>(field), L->plane,
                                                     L->pitch, nx, ny, 1, dst, L->stream));
   else

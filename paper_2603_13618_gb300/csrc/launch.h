@@ -1,5 +1,6 @@
 // launch.h -- host-side launchers of the kernels in step_kernel.cuh, one explicit
-// instantiation set per storage precision (launch_f32.cu, launch_f64.cu).
+// instantiation set per storage type (launch_f32.cu, launch_f64.cu, launch_f16.cu; the
+// TMA, fixup, adjoint and plain-plane launchers exist for float and double only).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -55,15 +56,26 @@ cudaError_t launch_adj_step(const AdjParams<T>& p, cudaStream_t stream);
 template <class T>
 cudaError_t launch_adj_final(const AdjParams<T>& p, cudaStream_t stream);
 
-template <class T>
+// Population conversions for any storage S (float, double, __half deviations); the
+// codec is that of the lattice (empty for float and double).
+template <class S>
 cudaError_t launch_init_equilibrium(const double* rho, const double* ux, const double* uy,
-                                    T* f, long long plane, int pitch, int nx, int ny,
-                                    cudaStream_t stream);
+                                    S* f, long long plane, int pitch, int nx, int ny,
+                                    const codec_t<S>& codec, cudaStream_t stream);
 
-template <class T>
-cudaError_t launch_moments(const T* f, long long plane, int pitch, int nx, int ny, double* rho,
-                           double* ux, double* uy, cudaStream_t stream);
+template <class S>
+cudaError_t launch_moments(const S* f, long long plane, int pitch, int nx, int ny, double* rho,
+                           double* ux, double* uy, const codec_t<S>& codec, cudaStream_t stream);
 
+template <class S>
+cudaError_t launch_pops_to_dense(const S* src, long long plane, int pitch, int nx, int ny,
+                                 double* dst, const codec_t<S>& codec, cudaStream_t stream);
+
+template <class S>
+cudaError_t launch_dense_to_pops(const double* src, long long plane, int pitch, int nx, int ny,
+                                 S* dst, const codec_t<S>& codec, cudaStream_t stream);
+
+// Plain pitched planes of an arithmetic type T (float, double): sensor fields, weights.
 template <class T>
 cudaError_t launch_pitched_to_dense(const T* src, long long plane, int pitch, int nx, int ny,
                                     int nplanes, double* dst, cudaStream_t stream);

@@ -49,6 +49,7 @@ cudaError_t launch_batch_step<KSS_T>(const StepParams<KSS_T>* table, const Batch
   return cudaGetLastError();
 }
 
+#ifndef KSS_STORAGE_HALF
 template <>
 cudaError_t launch_adj_objective<KSS_T>(const AdjParams<KSS_T>& p, cudaStream_t stream) {
   adj_objective_kernel<KSS_T><<<adj_grid(p.nx, p.ny), kThreads, 0, stream>>>(p);
@@ -102,23 +103,45 @@ cudaError_t launch_fixup<KSS_T>(const StepParams<KSS_T>& p, bool pull, int ctas,
   return cudaGetLastError();
 }
 
+#endif  // KSS_STORAGE_HALF
+
 template <>
 cudaError_t launch_init_equilibrium<KSS_T>(const double* rho, const double* ux, const double* uy,
                                            KSS_T* f, long long plane, int pitch, int nx, int ny,
-                                           cudaStream_t stream) {
+                                           const codec_t<KSS_T>& codec, cudaStream_t stream) {
   init_equilibrium_kernel<KSS_T><<<helper_grid(nx, ny), 256, 0, stream>>>(
-      rho, ux, uy, f, plane, pitch, nx, ny);
+      rho, ux, uy, f, plane, pitch, nx, ny, codec);
   return cudaGetLastError();
 }
 
 template <>
 cudaError_t launch_moments<KSS_T>(const KSS_T* f, long long plane, int pitch, int nx, int ny,
-                                  double* rho, double* ux, double* uy, cudaStream_t stream) {
+                                  double* rho, double* ux, double* uy,
+                                  const codec_t<KSS_T>& codec, cudaStream_t stream) {
   moments_kernel<KSS_T><<<helper_grid(nx, ny), 256, 0, stream>>>(
-      f, plane, pitch, nx, ny, rho, ux, uy);
+      f, plane, pitch, nx, ny, rho, ux, uy, codec);
   return cudaGetLastError();
 }
 
+template <>
+cudaError_t launch_pops_to_dense<KSS_T>(const KSS_T* src, long long plane, int pitch, int nx,
+                                        int ny, double* dst, const codec_t<KSS_T>& codec,
+                                        cudaStream_t stream) {
+  pops_to_dense_kernel<KSS_T><<<helper_grid(nx, ny), 256, 0, stream>>>(
+      src, plane, pitch, nx, ny, dst, codec);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_dense_to_pops<KSS_T>(const double* src, long long plane, int pitch, int nx,
+                                        int ny, KSS_T* dst, const codec_t<KSS_T>& codec,
+                                        cudaStream_t stream) {
+  dense_to_pops_kernel<KSS_T><<<helper_grid(nx, ny), 256, 0, stream>>>(
+      src, plane, pitch, nx, ny, dst, codec);
+  return cudaGetLastError();
+}
+
+#ifndef KSS_STORAGE_HALF
 template <>
 cudaError_t launch_pitched_to_dense<KSS_T>(const KSS_T* src, long long plane, int pitch, int nx,
                                            int ny, int nplanes, double* dst, cudaStream_t stream) {
@@ -134,5 +157,6 @@ cudaError_t launch_dense_to_pitched<KSS_T>(const double* src, long long plane, i
       src, plane, pitch, nx, ny, nplanes, dst);
   return cudaGetLastError();
 }
+#endif  // KSS_STORAGE_HALF
 
 }  // namespace kss

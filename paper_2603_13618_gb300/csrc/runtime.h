@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <limits>
 #include <string>
+#include <type_traits>
 
 #include "../../include/kss.h"
 #include "launch.h"
@@ -31,7 +32,9 @@ struct kss_batch;
 struct kss_lattice {
   kss_config cfg{};
   int device = 0;
-  size_t esz = 0;           // bytes per stored element
+  size_t esz = 0;           // bytes per stored population element
+  size_t tsz = 0;           // bytes per arithmetic element (sensor planes)
+  kss::codec_t<__half> codec16{};  // FP16 deviation codec (KSS_FP16DEV)
   int pitch = 0;            // row pitch in elements (multiple of 128 bytes)
   long long plane = 0;      // elements per plane
   int ntx = 0, nty = 0, nblocks = 0;
@@ -99,11 +102,23 @@ inline uint32_t needed_mask(const kss_lattice* L, uint32_t extra) {
 
 inline int mode_for(uint32_t mask) { return (mask & ~kss::kStdMask) ? kss::MODE_FULL : kss::MODE_STD; }
 
-template <class T>
-kss::StepParams<T> make_params(const kss_lattice* L, const void* src, void* dst) {
-  kss::StepParams<T> p{};
-  p.src = static_cast<const T*>(src);
-  p.dst = static_cast<T*>(dst);
+// Codec of a lattice's storage type S (empty unless S is the FP16 deviation storage).
+template <class S>
+inline kss::codec_t<S> codec_of(const kss_lattice* L) {
+  if constexpr (std::is_same<S, __half>::value) {
+    return L->codec16;
+  } else {
+    (void)L;
+    return kss::codec_t<S>{};
+  }
+}
+
+template <class S>
+kss::StepParams<S> make_params(const kss_lattice* L, const void* src, void* dst) {
+  using T = kss::arith_t<S>;
+  kss::StepParams<S> p{};
+  p.src = static_cast<const S*>(src);
+  p.dst = static_cast<S*>(dst);
   p.rec = static_cast<T*>(L->rec);
   p.flags = L->flags;
   p.tiles = L->tiles;
@@ -134,7 +149,21 @@ kss::StepParams<T> make_params(const kss_lattice* L, const void* src, void* dst)
   p.refine_s = L->cfg.refine_sensor;
   p.switch_s = L->cfg.switch_sensor;
   for (int s = 0; s < KSS_S_COUNT; ++s) p.rec_slot[s] = L->rec_slot[s];
+  p.codec = codec_of<S>(L);
   return p;
+}
+
+// Storage type of a precision, as a tag for generic lambdas: with_storage(prec, f) calls
+// f(Tag<S>{}) with S = float, double or __half.
+template <class S>
+struct Tag {
+  using type = S;
+};
+template <class F>
+inline auto with_storage(int precision, F&& f) {
+  if (precision == KSS_FP64) return f(Tag<double>{});
+  if (precision == KSS_FP16DEV) return f(Tag<__half>{});
+  return f(Tag<float>{});
 }
 
 // Sticky error of a lattice, if any (KSS_ERR_ARG for NULL).

@@ -32,6 +32,8 @@
 // in block order.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include <type_traits>
 
 #include "d2q9.cuh"
@@ -97,11 +99,65 @@ __device__ __forceinline__ VT make_vec(const T (&v)[N]) {
   }
 }
 
-template <class T>
+// ---------------------------------------------------------------- storage ----
+// Population storage S and the arithmetic type T = arith_t<S> of the step:
+//   float, double  the populations themselves (T = S);
+//   __half         FP16 deviations from the rest equilibrium of a reference density
+//                  rho0, h_q = RN_fp16((f_q - b_q) s_q) with b_q = RN_fp32(w_q rho0) and
+//                  s_q = 2^(k_q + K) (k_q = 1, 3, 5 for w_q = 4/9, 1/9, 1/36: s_q w_q =
+//                  (8/9) 2^K for every q), decoded as f_q = RN_fp32(b_q + h_q / s_q) and
+//                  collided in FP32 (T = float).  (s_q = 1 is the literal unscaled form.)
+template <class S> struct Store;
+template <> struct Store<float> {
+  using T = float;
+  struct Codec {};
+};
+template <> struct Store<double> {
+  using T = double;
+  struct Codec {};
+};
+template <> struct Store<__half> {
+  using T = float;
+  struct Codec {
+    float base[9];   // b_q
+    float scale[9];  // s_q
+    float inv[9];    // 1 / s_q (exact: a power of two)
+  };
+};
+template <class S>
+using arith_t = typename Store<S>::T;
+template <class S>
+using codec_t = typename Store<S>::Codec;
+template <> struct Vec<__half> {
+  static constexpr int N = KSS_F32_VEC;  // as FP32: the same cells per thread
+};
+template <> struct VecT<__half, 4> { using type = uint2; };
+template <> struct VecT<__half, 2> { using type = unsigned int; };
+
+template <class S>
+__device__ __forceinline__ arith_t<S> decode(S v, int q, const codec_t<S>& c) {
+  if constexpr (std::is_same<S, __half>::value) {
+    return fmaf(__half2float(v), c.inv[q], c.base[q]);
+  } else {
+    return v;
+  }
+}
+
+template <class S>
+__device__ __forceinline__ S encode(arith_t<S> f, int q, const codec_t<S>& c) {
+  if constexpr (std::is_same<S, __half>::value) {
+    return __float2half_rn((f - c.base[q]) * c.scale[q]);
+  } else {
+    return f;
+  }
+}
+
+template <class S>
 struct StepParams {
-  const T* src;          // population buffer read this step
-  T* dst;                // population buffer written this step (STORE)
-  T* rec;                // recorded sensor planes
+  using T = arith_t<S>;
+  const S* src;          // population buffer read this step
+  S* dst;                // population buffer written this step (STORE)
+  T* rec;                // recorded sensor planes (arithmetic type)
   uint8_t* flags;        // [ny][pitch]
   int32_t* tiles;        // [2][nty][ntx] refine, switch tags per tile
   int32_t* tiles_def;    // [nty][ntx] cells deferred to fixup_kernel per tile
@@ -125,6 +181,7 @@ struct StepParams {
                          // (read by the batched step only; step_kernel uses its grid)
   int mode;              // the lattice's sensor set on output steps (batched step only)
   int rec_slot[S_COUNT];  // plane index of each recorded sensor, -1 if not recorded
+  codec_t<S> codec;      // FP16 deviation codec (empty for float / double storage)
 };
 
 // ---------------------------------------------------------------- loads ----
@@ -233,6 +290,48 @@ __device__ __forceinline__ void vstore(T* p, const T (&v)[V]) {
   __stcs(reinterpret_cast<VT*>(p), make_vec<VT, T, V>(v));
 }
 
+// Populations of plane q: V cells loaded and decoded to the arithmetic type, or encoded
+// and stored (streaming stores).  FP16 deviations move as 8- (V = 4) or 4-byte vectors.
+template <class S, int V = Vec<S>::N>
+__device__ __forceinline__ void pop_vload(const S* p, bool ok, arith_t<S> (&v)[V], int q,
+                                          const codec_t<S>& c) {
+  if constexpr (std::is_same<S, __half>::value) {
+    if (!ok) {
+#pragma unroll
+      for (int k = 0; k < V; ++k) v[k] = 0.f;
+      return;
+    }
+    using VT = typename VecT<S, V>::type;
+    const VT raw = __ldg(reinterpret_cast<const VT*>(p));
+    const __half2* h = reinterpret_cast<const __half2*>(&raw);
+#pragma unroll
+    for (int k = 0; k < V / 2; ++k) {
+      const float2 a = __half22float2(h[k]);
+      v[2 * k] = fmaf(a.x, c.inv[q], c.base[q]);
+      v[2 * k + 1] = fmaf(a.y, c.inv[q], c.base[q]);
+    }
+  } else {
+    vload<S, V>(p, ok, v);
+  }
+}
+
+template <class S, int V = Vec<S>::N>
+__device__ __forceinline__ void pop_vstore(S* p, const arith_t<S> (&v)[V], int q,
+                                           const codec_t<S>& c) {
+  if constexpr (std::is_same<S, __half>::value) {
+    using VT = typename VecT<S, V>::type;
+    VT raw;
+    __half2* h = reinterpret_cast<__half2*>(&raw);
+#pragma unroll
+    for (int k = 0; k < V / 2; ++k)
+      h[k] = __floats2half2_rn((v[2 * k] - c.base[q]) * c.scale[q],
+                               (v[2 * k + 1] - c.base[q]) * c.scale[q]);
+    __stcs(reinterpret_cast<VT*>(p), raw);
+  } else {
+    vstore<S, V>(p, v);
+  }
+}
+
 template <int V>
 __device__ __forceinline__ void store_flags(uint8_t* p, uint32_t bits) {
   if constexpr (V == 4) {
@@ -272,12 +371,15 @@ __device__ __forceinline__ void relax_pop(T (&f)[Vec<T>::N], const T (&feq)[Vec<
 
 // The pair of opposite populations (+c, -c) with c.u = cu: f^eq = w rho (base + 9/2 cu^2
 // +- 3 cu); both relaxed and (STORE) written out.
-template <class T, bool OUT, bool STORE>
-__device__ __forceinline__ void pair_pops(T (&fp)[Vec<T>::N], T (&fm)[Vec<T>::N],
-                                          const T (&cu)[Vec<T>::N], const T (&base)[Vec<T>::N],
-                                          const T (&rw)[Vec<T>::N], T omega, StdAcc<T>& a,
-                                          T* dst_p, T* dst_m, bool cv) {
-  constexpr int V = Vec<T>::N;
+template <class S, bool OUT, bool STORE, int QP, int QM>
+__device__ __forceinline__ void pair_pops(arith_t<S> (&fp)[Vec<S>::N], arith_t<S> (&fm)[Vec<S>::N],
+                                          const arith_t<S> (&cu)[Vec<S>::N],
+                                          const arith_t<S> (&base)[Vec<S>::N],
+                                          const arith_t<S> (&rw)[Vec<S>::N], arith_t<S> omega,
+                                          StdAcc<arith_t<S>>& a, S* dst_p, S* dst_m,
+                                          const codec_t<S>& codec, bool cv) {
+  using T = arith_t<S>;
+  constexpr int V = Vec<S>::N;
   T ep[V], em[V];
 #pragma unroll
   for (int k = 0; k < V; ++k) {
@@ -286,9 +388,9 @@ __device__ __forceinline__ void pair_pops(T (&fp)[Vec<T>::N], T (&fm)[Vec<T>::N]
     em[k] = Num<T>::mul(rw[k], fma(T(-3), cu[k], t));
   }
   relax_pop<T, OUT, STORE>(fp, ep, omega, a);
-  if (STORE && cv) vstore<T>(dst_p, fp);
+  if (STORE && cv) pop_vstore<S>(dst_p, fp, QP, codec);
   relax_pop<T, OUT, STORE>(fm, em, omega, a);
-  if (STORE && cv) vstore<T>(dst_m, fm);
+  if (STORE && cv) pop_vstore<S>(dst_m, fm, QM, codec);
 }
 
 // Which of {Kn, KL, neq} a flag tests (ids validated on the host); decided once per
@@ -304,8 +406,9 @@ struct Pick3 {
 
 // The nine populations of cell (i, j) as the step sees them (pulled when PULL), for the
 // exact recomputation of deferred cells.
-template <class T, bool PULL>
-__device__ __forceinline__ void reload_cell(const StepParams<T>& p, int i, int j, T (&c)[9]) {
+template <class S, bool PULL>
+__device__ __forceinline__ void reload_cell(const StepParams<S>& p, int i, int j,
+                                            arith_t<S> (&c)[9]) {
   constexpr int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
   constexpr int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 #pragma unroll
@@ -317,7 +420,7 @@ __device__ __forceinline__ void reload_cell(const StepParams<T>& p, int i, int j
       si = si < 0 ? si + p.nx : (si >= p.nx ? si - p.nx : si);
       sj = sj < 0 ? sj + p.ny : (sj >= p.ny ? sj - p.ny : sj);
     }
-    c[q] = p.src[q * p.plane + (long long)sj * p.pitch + si];
+    c[q] = decode<S>(p.src[q * p.plane + (long long)sj * p.pitch + si], q, p.codec);
   }
 }
 
@@ -389,8 +492,9 @@ template <> struct Red<double> {
 
 // The last CTA's reduction of the per-CTA partials, in CTA order within each thread and
 // a fixed shuffle/shared-memory tree across threads (bitwise reproducible).
-template <class T, int NTHREADS>
-__device__ __forceinline__ void finalize_partials(const StepParams<T>& p, int nblocks) {
+template <class S, int NTHREADS>
+__device__ __forceinline__ void finalize_partials(const StepParams<S>& p, int nblocks) {
+  using T = arith_t<S>;
   __shared__ Red<T> f_sum[NTHREADS / 32][3];
   __shared__ unsigned long long f_cnt[NTHREADS / 32][3];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -446,11 +550,12 @@ __host__ __device__ constexpr bool mode_has(int s) {
 // the pass's source buffer (which the pass does not modify) with the exact per-cell
 // arithmetic of the full sensor set (cell_update).  Returns the refine/switch/non-
 // positive tags; the tile counts are corrected here.
-template <class T, bool PULL>
-__device__ __forceinline__ uint32_t fix_cell(const StepParams<T>& p, const Pick3& pr,
+template <class S, bool PULL>
+__device__ __forceinline__ uint32_t fix_cell(const StepParams<S>& p, const Pick3& pr,
                                              const Pick3& ps, int i, int j) {
+  using T = arith_t<S>;
   T cell[9], dummy[9];
-  reload_cell<T, PULL>(p, i, j, cell);
+  reload_cell<S, PULL>(p, i, j, cell);
   CellOut<T> co;
   cell_update<T, MODE_STD, false>(cell, p.omega, p.tau, dummy, co);
   const T kn = co.sv[S_KN], kl = co.sv[S_KL], neq = co.sv[S_NEQ];
@@ -471,11 +576,13 @@ __device__ __forceinline__ uint32_t fix_cell(const StepParams<T>& p, const Pick3
 // populations, the flag bytes and the recorded sensor fields.  ft holds the
 // post-streaming populations of cells i0..i0+V-1 of row j.  Returns the lane's flag
 // word (one byte per cell); the row's moments are added to the accumulators.
-template <class T, int MODE, bool PULL, bool STORE>
-__device__ __forceinline__ uint32_t fused_row(const StepParams<T>& p, T (&ft)[9][Vec<T>::N],
-                                              int i0, int j, bool cv, Acc<T>& a_rho,
-                                              Acc<T>& a_jx, Acc<T>& a_jy) {
-  constexpr int V = Vec<T>::N;
+template <class S, int MODE, bool PULL, bool STORE>
+__device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
+                                              arith_t<S> (&ft)[9][Vec<S>::N], int i0, int j,
+                                              bool cv, Acc<arith_t<S>>& a_rho,
+                                              Acc<arith_t<S>>& a_jx, Acc<arith_t<S>>& a_jy) {
+  using T = arith_t<S>;
+  constexpr int V = Vec<S>::N;
   constexpr bool OUT = MODE != MODE_PLAIN;
   const long long off = (long long)j * p.pitch + i0;
   uint32_t fbits = 0;
@@ -509,7 +616,7 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<T>& p, T (&ft)[9]
     }
     if (STORE && cv) {
 #pragma unroll
-      for (int q = 0; q < 9; ++q) vstore<T>(p.dst + q * p.plane + off, fo[q]);
+      for (int q = 0; q < 9; ++q) pop_vstore<S>(p.dst + q * p.plane + off, fo[q], q, p.codec);
     }
     if (cv) {
       store_flags<V>(p.flags + off, fbits);
@@ -567,13 +674,15 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<T>& p, T (&ft)[9]
 #pragma unroll
     for (int k = 0; k < V; ++k) feq[k] = Num<T>::mul(T(4) * rw1[k], base[k]);
     relax_pop<T, OUT, STORE>(ft[0], feq, p.omega, a);
-    if (STORE && cv) vstore<T>(p.dst + 0 * p.plane + off, ft[0]);
+    if (STORE && cv) pop_vstore<S>(p.dst + 0 * p.plane + off, ft[0], 0, p.codec);
     // axis pairs (1, 3): c.u = +-ux ; (2, 4): +-uy ; diagonal pairs (5, 7): +-(ux + uy),
     // (6, 8): +-(uy - ux)
-    pair_pops<T, OUT, STORE>(ft[1], ft[3], ux, base, rw1, p.omega, a,
-                             p.dst + 1 * p.plane + off, p.dst + 3 * p.plane + off, cv);
-    pair_pops<T, OUT, STORE>(ft[2], ft[4], uy, base, rw1, p.omega, a,
-                             p.dst + 2 * p.plane + off, p.dst + 4 * p.plane + off, cv);
+    pair_pops<S, OUT, STORE, 1, 3>(ft[1], ft[3], ux, base, rw1, p.omega, a,
+                                   p.dst + 1 * p.plane + off, p.dst + 3 * p.plane + off,
+                                   p.codec, cv);
+    pair_pops<S, OUT, STORE, 2, 4>(ft[2], ft[4], uy, base, rw1, p.omega, a,
+                                   p.dst + 2 * p.plane + off, p.dst + 4 * p.plane + off,
+                                   p.codec, cv);
     {
       T sd[V];
 #pragma unroll
@@ -581,12 +690,14 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<T>& p, T (&ft)[9]
       T rw2[V];
 #pragma unroll
       for (int k = 0; k < V; ++k) rw2[k] = T(0.25) * rw1[k];
-      pair_pops<T, OUT, STORE>(ft[5], ft[7], sd, base, rw2, p.omega, a,
-                               p.dst + 5 * p.plane + off, p.dst + 7 * p.plane + off, cv);
+      pair_pops<S, OUT, STORE, 5, 7>(ft[5], ft[7], sd, base, rw2, p.omega, a,
+                                     p.dst + 5 * p.plane + off, p.dst + 7 * p.plane + off,
+                                     p.codec, cv);
 #pragma unroll
       for (int k = 0; k < V; ++k) sd[k] = Num<T>::sub(uy[k], ux[k]);
-      pair_pops<T, OUT, STORE>(ft[6], ft[8], sd, base, rw2, p.omega, a,
-                               p.dst + 6 * p.plane + off, p.dst + 8 * p.plane + off, cv);
+      pair_pops<S, OUT, STORE, 6, 8>(ft[6], ft[8], sd, base, rw2, p.omega, a,
+                                     p.dst + 6 * p.plane + off, p.dst + 8 * p.plane + off,
+                                     p.codec, cv);
     }
     if (OUT) {
       const Pick3 pr(p.refine_s), ps(p.switch_s);
@@ -627,10 +738,11 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<T>& p, T (&ft)[9]
 // One CTA's block (bx, by) of a lattice whose step grid is gx CTAs wide and nblocks CTAs
 // in all.  Called by every thread of the CTA; the CTA's shared memory is free again when
 // it returns.
-template <class T, int MODE, bool PULL, bool STORE>
-__device__ __forceinline__ void step_cta(const StepParams<T>& p, const int bx, const int by,
+template <class S, int MODE, bool PULL, bool STORE>
+__device__ __forceinline__ void step_cta(const StepParams<S>& p, const int bx, const int by,
                                          const int gx, const int nblocks) {
-  constexpr int V = Vec<T>::N;
+  using T = arith_t<S>;
+  constexpr int V = Vec<S>::N;
   constexpr bool OUT = MODE != MODE_PLAIN;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i0 = (bx * 32 + lane) * V;
@@ -657,35 +769,35 @@ __device__ __forceinline__ void step_cta(const StepParams<T>& p, const int bx, c
 
   for (int j = j0 + warp; j < j1; j += kWarps) {
     T ft[9][V];
-    const T* base = p.src + (long long)j * p.pitch;
+    const S* base = p.src + (long long)j * p.pitch;
     if (PULL) {
       const long long up = (long long)((j == 0 ? p.ny : j) - 1 - j) * p.pitch;    // row j-1
       const long long dn = (long long)((j + 1 == p.ny ? 0 : j + 1) - j) * p.pitch;  // row j+1
       // source rows of q = 0..8 (pull: row j - cy_q)
-      const T* r0 = base;
-      const T* r1 = base + 1 * p.plane;
-      const T* r2 = base + 2 * p.plane + up;
-      const T* r3 = base + 3 * p.plane;
-      const T* r4 = base + 4 * p.plane + dn;
-      const T* r5 = base + 5 * p.plane + up;
-      const T* r6 = base + 6 * p.plane + up;
-      const T* r7 = base + 7 * p.plane + dn;
-      const T* r8 = base + 8 * p.plane + dn;
-      vload<T>(r0 + i0, cv, ft[0]);
-      vload<T>(r1 + i0, cv, ft[1]);
-      vload<T>(r2 + i0, cv, ft[2]);
-      vload<T>(r3 + i0, cv, ft[3]);
-      vload<T>(r4 + i0, cv, ft[4]);
-      vload<T>(r5 + i0, cv, ft[5]);
-      vload<T>(r6 + i0, cv, ft[6]);
-      vload<T>(r7 + i0, cv, ft[7]);
-      vload<T>(r8 + i0, cv, ft[8]);
-      const T h1 = load_left_halo<T>(r1, i0, p.nx, lane, cv);
-      const T h5 = load_left_halo<T>(r5, i0, p.nx, lane, cv);
-      const T h8 = load_left_halo<T>(r8, i0, p.nx, lane, cv);
-      const T h3 = load_right_halo<T>(r3, i0, p.nx, lane, cv);
-      const T h6 = load_right_halo<T>(r6, i0, p.nx, lane, cv);
-      const T h7 = load_right_halo<T>(r7, i0, p.nx, lane, cv);
+      const S* r0 = base;
+      const S* r1 = base + 1 * p.plane;
+      const S* r2 = base + 2 * p.plane + up;
+      const S* r3 = base + 3 * p.plane;
+      const S* r4 = base + 4 * p.plane + dn;
+      const S* r5 = base + 5 * p.plane + up;
+      const S* r6 = base + 6 * p.plane + up;
+      const S* r7 = base + 7 * p.plane + dn;
+      const S* r8 = base + 8 * p.plane + dn;
+      pop_vload<S>(r0 + i0, cv, ft[0], 0, p.codec);
+      pop_vload<S>(r1 + i0, cv, ft[1], 1, p.codec);
+      pop_vload<S>(r2 + i0, cv, ft[2], 2, p.codec);
+      pop_vload<S>(r3 + i0, cv, ft[3], 3, p.codec);
+      pop_vload<S>(r4 + i0, cv, ft[4], 4, p.codec);
+      pop_vload<S>(r5 + i0, cv, ft[5], 5, p.codec);
+      pop_vload<S>(r6 + i0, cv, ft[6], 6, p.codec);
+      pop_vload<S>(r7 + i0, cv, ft[7], 7, p.codec);
+      pop_vload<S>(r8 + i0, cv, ft[8], 8, p.codec);
+      const T h1 = decode<S>(load_left_halo<S>(r1, i0, p.nx, lane, cv), 1, p.codec);
+      const T h5 = decode<S>(load_left_halo<S>(r5, i0, p.nx, lane, cv), 5, p.codec);
+      const T h8 = decode<S>(load_left_halo<S>(r8, i0, p.nx, lane, cv), 8, p.codec);
+      const T h3 = decode<S>(load_right_halo<S>(r3, i0, p.nx, lane, cv), 3, p.codec);
+      const T h6 = decode<S>(load_right_halo<S>(r6, i0, p.nx, lane, cv), 6, p.codec);
+      const T h7 = decode<S>(load_right_halo<S>(r7, i0, p.nx, lane, cv), 7, p.codec);
       assemble_from_left<T>(ft[1], h1, lane);
       assemble_from_left<T>(ft[5], h5, lane);
       assemble_from_left<T>(ft[8], h8, lane);
@@ -694,10 +806,10 @@ __device__ __forceinline__ void step_cta(const StepParams<T>& p, const int bx, c
       assemble_from_right<T>(ft[7], h7, i0, p.nx, lane);
     } else {
 #pragma unroll
-      for (int q = 0; q < 9; ++q) vload<T>(base + q * p.plane + i0, cv, ft[q]);
+      for (int q = 0; q < 9; ++q) pop_vload<S>(base + q * p.plane + i0, cv, ft[q], q, p.codec);
     }
 
-    const uint32_t fbits = fused_row<T, MODE, PULL, STORE>(p, ft, i0, j, cv, a_rho, a_jx, a_jy);
+    const uint32_t fbits = fused_row<S, MODE, PULL, STORE>(p, ft, i0, j, cv, a_rho, a_jx, a_jy);
     if (OUT) {
       n_ref += __popc(fbits & 0x01010101u);
       n_sw += __popc(fbits & 0x02020202u);
@@ -776,7 +888,7 @@ __device__ __forceinline__ void step_cta(const StepParams<T>& p, const int bx, c
         const int o = s_dl[w][r];
         const int rl = o / (32 * V), cl = o - rl * (32 * V);
         const int j = j0 + rl, i = bx * 32 * V + cl;
-        const uint32_t tags = fix_cell<T, PULL>(p, pr, ps, i, j);
+        const uint32_t tags = fix_cell<S, PULL>(p, pr, ps, i, j);
         const int b = rl / p.tile, tl = cl / p.tile;
         if (tags & 1u) {
           atomicAdd(&s_cx[0], 1u);
@@ -832,13 +944,13 @@ __device__ __forceinline__ void step_cta(const StepParams<T>& p, const int bx, c
 
   // ---- last block: add the per-block partials ----
   __threadfence();
-  finalize_partials<T, kThreads>(p, nblocks);
+  finalize_partials<S, kThreads>(p, nblocks);
 }
 
-template <class T, int MODE, bool PULL, bool STORE>
+template <class S, int MODE, bool PULL, bool STORE>
 __global__ void __launch_bounds__(kThreads, MODE == MODE_FULL ? 1 : KSS_STEP_MIN_BLOCKS)
-step_kernel(const StepParams<T> p) {
-  step_cta<T, MODE, PULL, STORE>(p, blockIdx.x, blockIdx.y, gridDim.x, gridDim.x * gridDim.y);
+step_kernel(const StepParams<S> p) {
+  step_cta<S, MODE, PULL, STORE>(p, blockIdx.x, blockIdx.y, gridDim.x, gridDim.x * gridDim.y);
 }
 
 // ---------------------------------------------------------------- batched step ----
@@ -858,23 +970,23 @@ struct BatchItem {
 
 // MODE: MODE_PLAIN (no outputs), MODE_STD (every lattice with {Kn, KL, neq}) or
 // MODE_FULL (each lattice with its own set: p.mode, MODE_STD or MODE_FULL).
-template <class T, int MODE>
+template <class S, int MODE>
 __global__ void __launch_bounds__(kThreads, MODE == MODE_FULL ? 1 : KSS_STEP_MIN_BLOCKS)
-batch_step_kernel(const StepParams<T>* __restrict__ table, const BatchItem* __restrict__ items,
+batch_step_kernel(const StepParams<S>* __restrict__ table, const BatchItem* __restrict__ items,
                   int nitems) {
-  static_assert(sizeof(StepParams<T>) % 8 == 0, "parameter copy in 8-byte words");
-  __shared__ __align__(16) unsigned long long s_raw[sizeof(StepParams<T>) / 8];
-  const StepParams<T>& sp = *reinterpret_cast<const StepParams<T>*>(s_raw);
+  static_assert(sizeof(StepParams<S>) % 8 == 0, "parameter copy in 8-byte words");
+  __shared__ __align__(16) unsigned long long s_raw[sizeof(StepParams<S>) / 8];
+  const StepParams<S>& sp = *reinterpret_cast<const StepParams<S>*>(s_raw);
   for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
     const BatchItem it = items[w];
     const unsigned long long* src = reinterpret_cast<const unsigned long long*>(table + it.lat);
-    for (int k = threadIdx.x; k < int(sizeof(StepParams<T>) / 8); k += kThreads) s_raw[k] = src[k];
+    for (int k = threadIdx.x; k < int(sizeof(StepParams<S>) / 8); k += kThreads) s_raw[k] = src[k];
     __syncthreads();
     if (MODE != MODE_FULL || sp.mode != MODE_FULL)
-      step_cta<T, MODE == MODE_FULL ? MODE_STD : MODE, true, true>(sp, int(it.bx), int(it.by),
+      step_cta<S, MODE == MODE_FULL ? MODE_STD : MODE, true, true>(sp, int(it.bx), int(it.by),
                                                                   sp.grid_x, sp.nblocks);
     else
-      step_cta<T, MODE_FULL, true, true>(sp, int(it.bx), int(it.by), sp.grid_x, sp.nblocks);
+      step_cta<S, MODE_FULL, true, true>(sp, int(it.bx), int(it.by), sp.grid_x, sp.nblocks);
     __syncthreads();  // the CTA's shared memory is reused by the next item
   }
 }
@@ -898,8 +1010,8 @@ __device__ __forceinline__ void add_tile_tags(int32_t* tiles, long long ntiles, 
 // 4 cells of a row finds them instead (skipping tiles with none).  Counts are corrected
 // with integer atomics, so they stay exact and reproducible; the last CTA resets the
 // list for the next pass.
-template <class T, bool PULL>
-__global__ void __launch_bounds__(256) fixup_kernel(const StepParams<T> p) {
+template <class S, bool PULL>
+__global__ void __launch_bounds__(256) fixup_kernel(const StepParams<S> p) {
   const int lane = threadIdx.x & 31;
   const Pick3 pr(p.refine_s), ps(p.switch_s);
   unsigned long long cr = 0, cs = 0, cn = 0;
@@ -915,7 +1027,7 @@ __global__ void __launch_bounds__(256) fixup_kernel(const StepParams<T> p) {
       if (!has) continue;
       const uint32_t cell = __ldcg(p.defer_list + e);
       const int j = int(cell / uint32_t(p.nx)), i = int(cell - uint32_t(j) * uint32_t(p.nx));
-      const uint32_t tags = fix_cell<T, PULL>(p, pr, ps, i, j);
+      const uint32_t tags = fix_cell<S, PULL>(p, pr, ps, i, j);
       add_tile_tags(p.tiles, ntiles, (long long)(j / p.tile) * p.ntx + i / p.tile, tags, active);
       cr += tags & 1u;
       cs += (tags >> 1) & 1u;
@@ -932,7 +1044,7 @@ __global__ void __launch_bounds__(256) fixup_kernel(const StepParams<T> p) {
       if (!(w & 0x40404040u)) continue;
       for (int k = 0; k < 4; ++k) {
         if (i0 + k >= p.nx || !((w >> (8 * k)) & kFlagDeferred)) continue;
-        const uint32_t tags = fix_cell<T, PULL>(p, pr, ps, i0 + k, j);
+        const uint32_t tags = fix_cell<S, PULL>(p, pr, ps, i0 + k, j);
         if (tags & 1u) atomicAdd(p.tiles + t, 1);
         if (tags & 2u) atomicAdd(p.tiles + (long long)p.ntx * p.nty + t, 1);
         cr += tags & 1u;
@@ -968,39 +1080,41 @@ __global__ void __launch_bounds__(256) fixup_kernel(const StepParams<T> p) {
 // The auxiliary kernels below run on a grid of (column blocks of 256) x (rows), rows
 // strided by gridDim.y: one row per CTA row, so no 64-bit division per element.
 
-// f := f^eq(rho, u) from dense FP64 fields, evaluated in the storage precision T (the
-// FP64 pipe is a small fraction of the FP32 one on this GPU, and an FP32 lattice keeps
-// only FP32 populations).
-template <class T>
+// f := f^eq(rho, u) from dense FP64 fields, evaluated in the arithmetic type (the FP64
+// pipe is a small fraction of the FP32 one on this GPU, and an FP32 lattice keeps only
+// FP32 populations) and stored in S.
+template <class S>
 __global__ void init_equilibrium_kernel(const double* __restrict__ rho,
                                         const double* __restrict__ ux,
-                                        const double* __restrict__ uy, T* __restrict__ f,
-                                        long long plane, int pitch, int nx, int ny) {
+                                        const double* __restrict__ uy, S* __restrict__ f,
+                                        long long plane, int pitch, int nx, int ny,
+                                        const codec_t<S> codec) {
+  using T = arith_t<S>;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nx) return;
   for (int j = blockIdx.y; j < ny; j += gridDim.y) {
     const long long c = (long long)j * nx + i;
     T feq[9];
     equilibrium<T>(T(rho[c]), T(ux[c]), T(uy[c]), feq);
-    T* o = f + (long long)j * pitch + i;
+    S* o = f + (long long)j * pitch + i;
 #pragma unroll
-    for (int q = 0; q < 9; ++q) o[q * plane] = feq[q];
+    for (int q = 0; q < 9; ++q) o[q * plane] = encode<S>(feq[q], q, codec);
   }
 }
 
 // rho, ux, uy (double, dense) of a stored state.
-template <class T>
-__global__ void moments_kernel(const T* __restrict__ f, long long plane, int pitch, int nx,
+template <class S>
+__global__ void moments_kernel(const S* __restrict__ f, long long plane, int pitch, int nx,
                                int ny, double* __restrict__ rho, double* __restrict__ ux,
-                               double* __restrict__ uy) {
+                               double* __restrict__ uy, const codec_t<S> codec) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nx) return;
   for (int j = blockIdx.y; j < ny; j += gridDim.y) {
     const long long c = (long long)j * nx + i;
-    const T* in = f + (long long)j * pitch + i;
+    const S* in = f + (long long)j * pitch + i;
     double v[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) v[q] = double(in[q * plane]);
+    for (int q = 0; q < 9; ++q) v[q] = double(decode<S>(in[q * plane], q, codec));
     const double r = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
     const double jx = (v[1] + v[5] + v[8]) - (v[3] + v[6] + v[7]);
     const double jy = (v[2] + v[5] + v[6]) - (v[4] + v[7] + v[8]);
@@ -1010,7 +1124,35 @@ __global__ void moments_kernel(const T* __restrict__ f, long long plane, int pit
   }
 }
 
-// nplanes pitched T planes <-> dense double planes.
+// The nine population planes (decoded) <-> dense double planes [9][ny][nx].
+template <class S>
+__global__ void pops_to_dense_kernel(const S* __restrict__ src, long long plane, int pitch,
+                                     int nx, int ny, double* __restrict__ dst,
+                                     const codec_t<S> codec) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx) return;
+#pragma unroll
+  for (int q = 0; q < 9; ++q)
+    for (int j = blockIdx.y; j < ny; j += gridDim.y)
+      dst[((long long)q * ny + j) * nx + i] =
+          double(decode<S>(src[q * plane + (long long)j * pitch + i], q, codec));
+}
+
+template <class S>
+__global__ void dense_to_pops_kernel(const double* __restrict__ src, long long plane,
+                                     int pitch, int nx, int ny, S* __restrict__ dst,
+                                     const codec_t<S> codec) {
+  using T = arith_t<S>;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx) return;
+#pragma unroll
+  for (int q = 0; q < 9; ++q)
+    for (int j = blockIdx.y; j < ny; j += gridDim.y)
+      dst[q * plane + (long long)j * pitch + i] =
+          encode<S>(T(src[((long long)q * ny + j) * nx + i]), q, codec);
+}
+
+// nplanes pitched T planes <-> dense double planes (sensor fields, weights).
 template <class T>
 __global__ void pitched_to_dense_kernel(const T* __restrict__ src, long long plane, int pitch,
                                         int nx, int ny, int nplanes, double* __restrict__ dst) {

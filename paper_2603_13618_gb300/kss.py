@@ -17,8 +17,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libkss.so")
 
 KSS_OK = 0
 KSS_WARN_NONPOSITIVE = 1
-FP64, FP32 = 0, 1
-PRECISIONS = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}
+FP64, FP32, FP16DEV = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp16dev": FP16DEV, FP64: FP64, FP32: FP32,
+              FP16DEV: FP16DEV}
 
 SENSORS = ("tau_ns", "c", "s", "e", "qh", "kn", "neq", "qe", "hr", "kl", "sigma_h",
            "sigma_kl", "alpha")
@@ -41,7 +42,8 @@ class Config(ctypes.Structure):
         ("switch_sensor", ctypes.c_int32), ("switch_threshold", ctypes.c_double),
         ("record_mask", ctypes.c_uint32), ("output_every", ctypes.c_int32),
         ("tile", ctypes.c_int32), ("stream", ctypes.c_void_p), ("own_stream", ctypes.c_int32),
-        ("kernel", ctypes.c_int32),
+        ("kernel", ctypes.c_int32), ("rho0", ctypes.c_double), ("dev_exp", ctypes.c_int32),
+        ("dev_unscaled", ctypes.c_int32),
     ]
 
 
@@ -151,10 +153,12 @@ def _torch_stream_handle():
 def make_config(nx: int, ny: int, precision="fp32", tau: float = 0.8, refine_sensor="kn",
                 refine_threshold: float = 1e-3, switch_sensor="neq",
                 switch_threshold: float = 1e-4, record=("kl",), output_every: int = 1,
-                tile: int = 16, stream="torch", kernel="auto") -> Config:
+                tile: int = 16, stream="torch", kernel="auto", rho0: float = 1.0,
+                dev_exp: int = 12, dev_unscaled: bool = False) -> Config:
     """A kss_config (see include/kss.h).  stream: "torch" = torch's current stream
     (handle 0 is the CUDA default stream), "own" = a stream created and owned by the
-    lattice, or a raw cudaStream_t handle."""
+    lattice, or a raw cudaStream_t handle.  rho0, dev_exp, dev_unscaled: the FP16
+    deviation storage of precision "fp16dev"."""
     lib = load()
     cfg = Config()
     rc = lib.kss_config_default(ctypes.byref(cfg), nx, ny, PRECISIONS[precision])
@@ -169,6 +173,9 @@ def make_config(nx: int, ny: int, precision="fp32", tau: float = 0.8, refine_sen
     cfg.output_every = output_every
     cfg.tile = tile
     cfg.kernel = KERNELS[kernel]
+    cfg.rho0 = rho0
+    cfg.dev_exp = dev_exp
+    cfg.dev_unscaled = int(dev_unscaled)
     if stream == "own":
         cfg.own_stream, cfg.stream = 1, None
     else:
@@ -182,13 +189,15 @@ class Lattice:
     def __init__(self, nx: int, ny: int, precision="fp32", tau: float = 0.8,
                  refine_sensor="kn", refine_threshold: float = 1e-3, switch_sensor="neq",
                  switch_threshold: float = 1e-4, record=("kl",), output_every: int = 1,
-                 tile: int = 16, stream="torch", kernel="auto"):
+                 tile: int = 16, stream="torch", kernel="auto", rho0: float = 1.0,
+                 dev_exp: int = 12, dev_unscaled: bool = False):
         self._lib = load()
         self._h = None
         cfg = make_config(nx, ny, precision=precision, tau=tau, refine_sensor=refine_sensor,
                           refine_threshold=refine_threshold, switch_sensor=switch_sensor,
                           switch_threshold=switch_threshold, record=record,
-                          output_every=output_every, tile=tile, stream=stream, kernel=kernel)
+                          output_every=output_every, tile=tile, stream=stream, kernel=kernel,
+                          rho0=rho0, dev_exp=dev_exp, dev_unscaled=dev_unscaled)
         handle = ctypes.c_void_p()
         self._check(self._lib.kss_create(ctypes.byref(cfg), ctypes.byref(handle)))
         self._adopt(handle, cfg, owned=True)

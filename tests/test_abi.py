@@ -81,3 +81,48 @@ def test_binding_arity_matches_header():
     protos = _prototypes()
     for name, (_, argtypes) in kss._SIGNATURES.items():
         assert len(argtypes) == protos[name], (name, len(argtypes), protos[name])
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """ctypes mirrors of kss_config, kss_batch_tuning and kss_adjoint_config have the C
+    layout (sizes and field offsets from a C program compiled against include/kss.h)."""
+    import ctypes
+
+    from paper_2603_13618_gb300 import kss
+
+    structs = {"kss_config": kss.Config, "kss_batch_tuning": kss.BatchTuning,
+               "kss_adjoint_config": kss.AdjointConfig}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "kss.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    for line in filter(None, got):
+        cname, what, val = line.split()
+        cls = structs[cname]
+        want = ctypes.sizeof(cls) if what == "size" else getattr(cls, what).offset
+        assert int(val) == want, line
+
+
+@pytest.mark.parametrize("field,value", [("rho0", 0.0), ("rho0", float("nan")), ("dev_exp", 41),
+                                         ("dev_exp", -25), ("dev_unscaled", 2)])
+def test_create_rejects_bad_fp16_deviation_config(field, value):
+    import ctypes
+
+    from paper_2603_13618_gb300 import kss
+
+    lib = kss.load()
+    cfg = kss.Config()
+    lib.kss_config_default(cfg, 64, 32, kss.FP16DEV)
+    assert (cfg.rho0, cfg.dev_exp, cfg.dev_unscaled) == (1.0, 12, 0)
+    setattr(cfg, field, value)
+    h = ctypes.c_void_p()
+    rc = lib.kss_create(cfg, ctypes.byref(h))
+    assert rc == -1 and not h.value

@@ -149,15 +149,17 @@ def test_fp32_smooth_jump_100_steps(tau, kernel):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_sensors_on_the_same_state(prec):
-    """Sensor arithmetic alone: the oracle evaluates the GPU's own stored populations."""
+    """Sensor arithmetic alone: an oracle state, rounded to the storage precision by
+    numpy, is set on the lattice and evaluated by both sides without a step."""
     kss = _kss()
     nx, ny, tau = 96, 80, 0.65
     rho, ux, uy = inputs.smooth_jump(nx, ny, seed=44, kmax=6)
+    state = oracle.step(oracle.init_equilibrium(rho, ux, uy), tau, 20)
+    if prec == "fp32":
+        state = state.astype(np.float32).astype(np.float64)
     lat = kss.Lattice(nx, ny, precision=prec, tau=tau, record=())
-    lat.set_fields(rho, ux, uy)
-    lat.step(20)
-    state = lat.get_populations()          # exact (FP32 values widen exactly)
     lat.set_populations(state)             # no step since set: sensors of the stored state
+    np.testing.assert_array_equal(lat.get_populations(), state)
     ref, nonpos = oracle.sensor_fields(state, tau, pull=False)
     r, u, v = oracle.moments(state)
     for sid in ALL:
@@ -414,10 +416,14 @@ def test_deferred_cells_everywhere(prec, kernel):
     lat.set_populations(np.ascontiguousarray(f))
     lat.step(1)
     _check_step_outputs(lat, prec, f, tau, 1, thr_r, thr_s, 16)
-    # and once more from the (still far from equilibrium) new state, list path again
-    prev = lat.get_populations()
+    # and once more from the oracle's next (still far from equilibrium) state, stored in
+    # the lattice's precision: the list path again
+    f2 = oracle.step(f, tau)
+    if prec == "fp32":
+        f2 = f2.astype(np.float32).astype(np.float64)
+    lat.set_populations(f2)
     lat.step(1)
-    _check_step_outputs(lat, prec, prev, tau, 2, thr_r, thr_s, 16)
+    _check_step_outputs(lat, prec, f2, tau, 1, thr_r, thr_s, 16)
     lat.close()
 
 

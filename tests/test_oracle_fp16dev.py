@@ -23,7 +23,8 @@ def test_fp16_rounding_matches_numpy_float16():
     special = np.array([65504.0, 65519.999, 65520.0, -65520.0, 2.0 ** -25, 3 * 2.0 ** -26,
                         2.0 ** -14, 0.0])
     for x in np.concatenate([xs, mids, sub, -sub, special]):
-        want = float(np.float16(x))
+        with np.errstate(over="ignore"):
+            want = float(np.float16(x))
         got = oracle.fp16_round(x)
         assert got == want or (np.isinf(want) and got == want), (x, got, want)
 
