@@ -38,6 +38,7 @@ struct kss_lattice {
   int pitch = 0;            // row pitch in elements (multiple of 128 bytes)
   long long plane = 0;      // elements per plane
   int ntx = 0, nty = 0, nblocks = 0;
+  int bands = 0;            // tile bands per CTA of the vector step (CTA height bands * tile)
   int nsm = 0;              // SMs of the device (persistent grid of the TMA kernel)
   void* f[2] = {nullptr, nullptr};
   int cur = 0;              // f[cur] holds the stored state
@@ -138,7 +139,7 @@ kss::StepParams<S> make_params(const kss_lattice* L, const void* src, void* dst)
   p.nx = L->cfg.nx;
   p.ny = L->cfg.ny;
   p.tile = L->cfg.tile;
-  p.bands = kss::step_bands(L->cfg.tile);
+  p.bands = L->bands;
   p.ntx = L->ntx;
   p.nty = L->nty;
   p.omega = T(1.0 / L->cfg.tau);

@@ -37,6 +37,7 @@
 #include <type_traits>
 
 #include "d2q9.cuh"
+#include "f32x2.cuh"
 
 namespace kss {
 
@@ -353,9 +354,51 @@ struct StdAcc {
 // f^eq phi(x) = f^neq x (phi(x)/x^2), x = f^neq / f^eq, by the series of phi.  The
 // series is exact to FP32 for |x| < 1/16; a cell where that, or positivity, cannot be
 // shown is deferred to fixup_kernel (see fused_row).
+//
+// FP32 (KSS_PAIRED_F32, default on): cells are processed in pairs with the paired FP32
+// instructions; every operation and its rounding are those of the scalar form.
+#ifndef KSS_PAIRED_F32
+#define KSS_PAIRED_F32 1
+#endif
 template <class T, bool OUT, bool COLLIDE>
 __device__ __forceinline__ void relax_pop(T (&f)[Vec<T>::N], const T (&feq)[Vec<T>::N], T omega,
                                           StdAcc<T>& a) {
+#if KSS_PAIRED_F32
+  if constexpr (std::is_same<T, float>::value) {
+    constexpr int N = Num<float>::kPhiFastOrder;
+    const F2 nom = pack2(-omega, -omega);
+#pragma unroll
+    for (int k = 0; k < Vec<T>::N; k += 2) {
+      const F2 F = pack2(f[k], f[k + 1]);
+      const F2 fneq = sub2(F, pack2(feq[k], feq[k + 1]));
+      if (OUT) {
+        const F2 x = mul2(fneq, pack2(Num<float>::rcp(feq[k]), Num<float>::rcp(feq[k + 1])));
+        float x0, x1, n0, n1;
+        unpack2(x, x0, x1);
+        unpack2(fneq, n0, n1);
+        a.kn[k] += fabsf(x0);
+        a.kn[k + 1] += fabsf(x1);
+        a.neq[k] += fabsf(n0);
+        a.neq[k + 1] += fabsf(n1);
+        // phi(x)/x^2 by Horner from the top coefficient, as phi_over_x2
+        F2 acc = pack2(float(PhiCoef<N>::value), float(PhiCoef<N>::value));
+        constexpr float kC[8] = {0.f, 0.f, float(PhiCoef<2>::value), float(PhiCoef<3>::value),
+                                 float(PhiCoef<4>::value), float(PhiCoef<5>::value),
+                                 float(PhiCoef<6>::value), float(PhiCoef<7>::value)};
+        static_assert(N <= 7, "coefficient table");
+#pragma unroll
+        for (int n = N - 1; n >= 2; --n) acc = fma2(acc, x, pack2(kC[n], kC[n]));
+        const F2 kl = fma2(mul2(fneq, x), acc, pack2(a.kl[k], a.kl[k + 1]));
+        unpack2(kl, a.kl[k], a.kl[k + 1]);
+      }
+      if (COLLIDE) {
+        const F2 nf = fma2(nom, fneq, F);
+        unpack2(nf, f[k], f[k + 1]);
+      }
+    }
+    return;
+  }
+#endif
 #pragma unroll
   for (int k = 0; k < Vec<T>::N; ++k) {
     const T fneq = f[k] - feq[k];
@@ -735,12 +778,12 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
 //        flags, tile counts, sums).
 // PULL:  stream before evaluating (false: evaluate the stored state as it is).
 // STORE: collide and write the new populations (false: evaluation only).
-// One CTA's block (bx, by) of a lattice whose step grid is gx CTAs wide and nblocks CTAs
-// in all.  Called by every thread of the CTA; the CTA's shared memory is free again when
-// it returns.
+// Block (bx, by) of a lattice whose step grid is gx blocks wide: its rows, then (output
+// modes) its tile counts and its partial sums and counts in slot bid.  Called by every
+// thread of the CTA; the CTA's shared memory is free again when it returns.
 template <class S, int MODE, bool PULL, bool STORE>
-__device__ __forceinline__ void step_cta(const StepParams<S>& p, const int bx, const int by,
-                                         const int gx, const int nblocks) {
+__device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx, const int by,
+                                           const int gx) {
   using T = arith_t<S>;
   constexpr int V = Vec<S>::N;
   constexpr bool OUT = MODE != MODE_PLAIN;
@@ -756,7 +799,6 @@ __device__ __forceinline__ void step_cta(const StepParams<S>& p, const int bx, c
   __shared__ uint32_t s_cx[3];                   // their tags (refine, switch, nonpos)
   __shared__ Red<T> s_sum[kWarps][3];
   __shared__ uint32_t s_cnt[kWarps][3];
-  __shared__ int s_last;
   if (OUT) {
     for (int t = threadIdx.x; t < 2 * kMaxBands * 32; t += kThreads) (&s_tiles[0][0][0])[t] = 0;
     if (threadIdx.x < 3) s_cx[threadIdx.x] = 0;
@@ -935,22 +977,56 @@ __device__ __forceinline__ void step_cta(const StepParams<S>& p, const int bx, c
     p.part_cnt[4 * bid + 0] = c0;
     p.part_cnt[4 * bid + 1] = c1;
     p.part_cnt[4 * bid + 2] = c2;
+  }
+}
+
+// After a CTA's last block: one ticket from the completion counter per CTA (nunits CTAs
+// in all); the CTA that takes the last one adds the nblocks per-block partials in block
+// order.  Called by every thread of the CTA.
+template <class S>
+__device__ __forceinline__ void ticket_and_finalize(const StepParams<S>& p, int nunits,
+                                                    int nblocks) {
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {  // thread 0 wrote this CTA's partials
+
     __threadfence();
     const uint32_t ticket = atomicAdd(p.done, 1u);
-    s_last = (ticket == uint32_t(nblocks - 1));
+    s_last = (ticket == uint32_t(nunits - 1));
   }
   __syncthreads();
   if (!s_last) return;
-
-  // ---- last block: add the per-block partials ----
+  // ---- last CTA: add the per-block partials ----
   __threadfence();
   finalize_partials<S, kThreads>(p, nblocks);
+}
+
+// One CTA per block (bx, by) of a grid gx blocks wide, nblocks in all.
+template <class S, int MODE, bool PULL, bool STORE>
+__device__ __forceinline__ void step_cta(const StepParams<S>& p, const int bx, const int by,
+                                         const int gx, const int nblocks) {
+  step_block<S, MODE, PULL, STORE>(p, bx, by, gx);
+  if (MODE != MODE_PLAIN) ticket_and_finalize<S>(p, nblocks, nblocks);
 }
 
 template <class S, int MODE, bool PULL, bool STORE>
 __global__ void __launch_bounds__(kThreads, MODE == MODE_FULL ? 1 : KSS_STEP_MIN_BLOCKS)
 step_kernel(const StepParams<S> p) {
   step_cta<S, MODE, PULL, STORE>(p, blockIdx.x, blockIdx.y, gridDim.x, gridDim.x * gridDim.y);
+}
+
+// The same step with a persistent grid: CTA c takes blocks c, c + gridDim.x, ... of the
+// gx-wide step grid (nblocks in all) in a fixed assignment, so that no CTA is launched or
+// retired between blocks and the completion counter is taken once per CTA.  Each block's
+// partials keep their slot, so the sums are those of step_kernel bit for bit.
+template <class S, int MODE, bool PULL, bool STORE>
+__global__ void __launch_bounds__(kThreads, MODE == MODE_FULL ? 1 : KSS_STEP_MIN_BLOCKS)
+step_kernel_persistent(const StepParams<S> p, int gx, int nblocks) {
+  for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
+    const int by = b / gx;
+    step_block<S, MODE, PULL, STORE>(p, b - by * gx, by, gx);
+    if (MODE != MODE_PLAIN) __syncthreads();  // shared memory is reused by the next block
+  }
+  if (MODE != MODE_PLAIN) ticket_and_finalize<S>(p, gridDim.x, nblocks);
 }
 
 // ---------------------------------------------------------------- batched step ----
