@@ -248,6 +248,44 @@ int kss_batch_autotune(kss_batch* b, const char* cache_path, int32_t steps,
 /* Last error message of the batch's own calls. */
 const char* kss_batch_last_error(const kss_batch* b);
 
+/* ---- Regridding on the flags: tile tagging and clustering into patches -----------------
+ * Steps (1)-(2) of the regridding routine (section "Adaptive refinement and parallel
+ * processing"): cells tagged by the refine sensor, a buffer of `buffer` cells around them
+ * (the applications use 2, section "Application to adaptive mesh refinement"), and a
+ * clustering of the tagged region into rectangular patches with a grid-efficiency
+ * threshold (0.98 in the 2-D application).  Here the tagging tiles are the unit: a tile
+ * is marked when a refine-flagged cell lies within `buffer` cells of it (periodic), and
+ * the marked tiles are clustered by the signature method of Berger & Rigoutsos (the
+ * clustering the paper cites), breadth first:
+ *   1. signatures: marked tiles per column and per row of the box;
+ *   2. an empty box is dropped, any other shrunk to the bounding box of its marks;
+ *   3. accepted if marks >= efficiency * area, or if it is a single tile;
+ *   4. else cut at the interior hole (zero signature) nearest the centre (x before y,
+ *      lower index first on ties), the hole row / column in neither half;
+ *   5. else at the strongest sign change of the signature Laplacian
+ *      s[i-1] - 2 s[i] + s[i+1] (ties: nearest the centre, x before y, lower index);
+ *   6. else the longer side (x if equal) is halved.
+ * Boxes are reported level by level in list order (children lower half first): the
+ * result is a deterministic function of the flags.  Boxes do not wrap the periodic seam.
+ * Box coordinates are in tiles, half-open: cells [x0*tile, min(x1*tile, nx)). */
+typedef struct {
+  int32_t x0, y0, x1, y1;
+} kss_box;
+
+/* On the lattice's flags of its current step (evaluated first if that step had no
+ * outputs).  tile_mask: [nty][ntx] bytes or NULL; boxes: up to max_boxes boxes or NULL;
+ * *nboxes: the number of boxes (may exceed max_boxes: only max_boxes are written).
+ * on_device applies to tile_mask and boxes.  buffer in [0, 1024], efficiency in [0, 1];
+ * the tile grid is at most 8192 tiles per side (KSS_ERR_UNSUPPORTED beyond). */
+int kss_regrid(kss_lattice* lat, int32_t buffer, double efficiency, uint8_t* tile_mask,
+               kss_box* boxes, int32_t max_boxes, int32_t* nboxes, int on_device);
+
+/* The same on caller flags (dense [ny][nx] bytes, bit 0 = refine), host or device by
+ * on_device, on `stream` (NULL = the default stream); allocates its workspace per call. */
+int kss_regrid_flags(const uint8_t* flags, int32_t nx, int32_t ny, int32_t tile, int32_t buffer,
+                     double efficiency, uint8_t* tile_mask, kss_box* boxes, int32_t max_boxes,
+                     int32_t* nboxes, int on_device, void* stream);
+
 /* ---- Adjoint: gradients of a sensor objective -----------------------------------------
  * Gradient of the sensor-weighted objective
  *   J = sum_x W(x) eps_KL(x)    (Eq. HKL-sensor, the KL sensor of step nsteps, i.e. of

@@ -1,8 +1,8 @@
 """Build the CUDA library ``_build/libkss.so`` for sm_103a with nvcc.
 
-Seven translation units (the kernels for FP32, FP64 and FP16-deviation storage, and
-the host runtimes of single lattices, batches, the adjoint and the allocation-free
-entry point) compile in parallel and link into one shared library with the C ABI of ``include/kss.h``.
+Eight translation units (the kernels for FP32, FP64 and FP16-deviation storage, and
+the host runtimes of single lattices, batches, the adjoint, regridding and the
+allocation-free entry point) compile in parallel and link into one shared library with the C ABI of ``include/kss.h``.
 """
 from __future__ import annotations
 
@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libkss.so")
 SOURCES = ["launch_f32.cu", "launch_f64.cu", "launch_f16.cu", "kss_runtime.cu", "kss_batch.cu",
-           "kss_adjoint.cu", "kss_noalloc.cu"]
+           "kss_adjoint.cu", "kss_regrid.cu", "kss_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -52,6 +52,11 @@ class BatchTuning(ctypes.Structure):
                 ("graph", ctypes.c_int32), ("ms_per_step", ctypes.c_double)]
 
 
+class Box(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_int32), ("y0", ctypes.c_int32), ("x1", ctypes.c_int32),
+                ("y1", ctypes.c_int32)]
+
+
 class AdjointConfig(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("nsteps", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
@@ -91,6 +96,14 @@ _SIGNATURES = {
     "kss_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int32,
                                           ctypes.POINTER(BatchTuning)]),
     "kss_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "kss_regrid": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                  ctypes.POINTER(ctypes.c_int32), ctypes.c_int]),
+    "kss_regrid_flags": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_int32), ctypes.c_int,
+                                        ctypes.c_void_p]),
     "kss_adjoint_create": (ctypes.c_int, [ctypes.POINTER(AdjointConfig),
                                           ctypes.POINTER(ctypes.c_void_p)]),
     "kss_adjoint_destroy": (None, [ctypes.c_void_p]),
@@ -315,6 +328,17 @@ class Lattice:
         self._check(self._lib.kss_read_stats(self._h, sums, counts, ctypes.byref(step)))
         return np.array(list(sums)), np.array(list(counts), dtype=np.int64), step.value
 
+    def regrid(self, buffer: int = 2, efficiency: float = 0.98, max_boxes: int = 1 << 16):
+        """(boxes [(x0, y0, x1, y1)] in tile units, tile mask [nty, ntx] uint8) of the
+        current step's refine flags (see include/kss.h)."""
+        mask = np.empty((self.nty, self.ntx), dtype=np.uint8)
+        boxes = (Box * max_boxes)()
+        n = ctypes.c_int32()
+        self._check(self._lib.kss_regrid(self._h, int(buffer), float(efficiency),
+                                         ctypes.c_void_p(mask.ctypes.data), boxes,
+                                         int(max_boxes), ctypes.byref(n), 0))
+        return [(b.x0, b.y0, b.x1, b.y1) for b in boxes[:min(n.value, max_boxes)]], mask
+
     @property
     def step_count(self) -> int:
         s = ctypes.c_int64()
@@ -470,3 +494,22 @@ class Adjoint:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def regrid_flags(flags, tile: int = 16, buffer: int = 2, efficiency: float = 0.98,
+                 max_boxes: int = 1 << 16, stream="torch"):
+    """kss_regrid_flags on host flags [ny, nx] uint8: (boxes, tile mask)."""
+    lib = load()
+    f = np.ascontiguousarray(flags, dtype=np.uint8)
+    ny, nx = f.shape
+    ntx, nty = -(-nx // tile), -(-ny // tile)
+    mask = np.empty((nty, ntx), dtype=np.uint8)
+    boxes = (Box * max_boxes)()
+    n = ctypes.c_int32()
+    st = _torch_stream_handle() if stream == "torch" else stream
+    rc = lib.kss_regrid_flags(ctypes.c_void_p(f.ctypes.data), nx, ny, tile, int(buffer),
+                              float(efficiency), ctypes.c_void_p(mask.ctypes.data), boxes,
+                              int(max_boxes), ctypes.byref(n), 0, st)
+    if rc < 0:
+        raise KssError(rc, lib.kss_strerror(rc).decode())
+    return [(b.x0, b.y0, b.x1, b.y1) for b in boxes[:min(n.value, max_boxes)]], mask

@@ -91,7 +91,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     from paper_2603_13618_gb300 import kss
 
     structs = {"kss_config": kss.Config, "kss_batch_tuning": kss.BatchTuning,
-               "kss_adjoint_config": kss.AdjointConfig}
+               "kss_adjoint_config": kss.AdjointConfig, "kss_box": kss.Box}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "kss.h"', "int main(void) {"]
     for cname, cls in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
