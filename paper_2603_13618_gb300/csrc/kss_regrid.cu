@@ -2,7 +2,8 @@
 // within `buffer` cells of a refine-flagged cell are marked, and the marked tiles are
 // clustered into rectangular boxes by the signature method of Berger & Rigoutsos (the
 // clustering the paper's regridding routine cites, section "Adaptive refinement and
-// parallel processing"), breadth first, one CTA per box and level.
+// parallel processing"), breadth first: each level of boxes is clustered by CTAs striding
+// over its boxes, and the host checks the level sizes every few levels.
 //
 // Clustering rules (all integer except one efficiency comparison in FP64), for a box:
 //   1. signatures sx[i] = marked tiles of column i, sy[j] = of row j;
@@ -60,33 +61,78 @@ __global__ void tile_mask_kernel(const uint8_t* __restrict__ flags, long long pi
   mask[t] = any;
 }
 
+// Prefix sums of the mask: pc[j][i] = marked tiles of column i in rows < j ((nty + 1) x
+// ntx), pr[j][i] = of row j in columns < i (nty x (ntx + 1)).  One thread per column,
+// then one per row.
+__global__ void mask_prefix_kernel(const uint8_t* __restrict__ mask, int ntx, int nty,
+                                   int* __restrict__ pc, int* __restrict__ pr) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < ntx) {
+    int acc = 0;
+    for (int j = 0; j < nty; ++j) {
+      pc[(long long)j * ntx + t] = acc;
+      acc += mask[(long long)j * ntx + t];
+    }
+    pc[(long long)nty * ntx + t] = acc;
+  } else if (t < ntx + nty) {
+    const int j = t - ntx;
+    int acc = 0;
+    const uint8_t* row = mask + (long long)j * ntx;
+    int* out = pr + (long long)j * (ntx + 1);
+    for (int i = 0; i < ntx; ++i) {
+      out[i] = acc;
+      acc += row[i];
+    }
+    out[ntx] = acc;
+  }
+}
+
 __device__ __forceinline__ int tile_key(int i, int lo, int hi) { return abs(2 * i - (lo + hi - 1)); }
 __device__ __forceinline__ int cut_key(int i, int lo, int hi) { return abs(2 * i - (lo + hi)); }
 
-// One box per CTA.  acc[i]: the accepted (shrunk) box or x0 = -1; kids[2i], kids[2i+1]:
+// The boxes of one level, *count of them (written by the previous compaction), CTAs
+// striding over them.  acc[i]: box i accepted (shrunk) or x0 = -1; kids[2i], kids[2i+1]:
 // its two halves or x0 = -1.
-__global__ void __launch_bounds__(256) cluster_level_kernel(const uint8_t* __restrict__ mask,
+__device__ __forceinline__ void cluster_box(const int* __restrict__ pc,
+                                            const int* __restrict__ pr, int ntx, Box b, int bi,
+                                            double efficiency, Box* __restrict__ acc,
+                                            Box* __restrict__ kids, int* sig);
+
+__global__ void __launch_bounds__(256) cluster_level_kernel(const int* __restrict__ pc,
+                                                            const int* __restrict__ pr,
                                                             int ntx, const Box* __restrict__ in,
-                                                            double efficiency,
+                                                            const int* __restrict__ count,
+                                                            const double* __restrict__ eff,
                                                             Box* __restrict__ acc,
                                                             Box* __restrict__ kids) {
   extern __shared__ int sig[];  // sx[w] then sy[h]
-  const Box b = in[blockIdx.x];
+  const int n = *count;
+  const double efficiency = *eff;
+  for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
+    cluster_box(pc, pr, ntx, in[bi], bi, efficiency, acc, kids, sig);
+    __syncthreads();  // the signatures are reused by the next box
+  }
+}
+
+__device__ __forceinline__ void cluster_box(const int* __restrict__ pc,
+                                            const int* __restrict__ pr, int ntx, Box b, int bi,
+                                            double efficiency, Box* __restrict__ acc,
+                                            Box* __restrict__ kids, int* sig) {
   const int w = b.x1 - b.x0, h = b.y1 - b.y0;
   int* sx = sig;
   int* sy = sig + w;
-  for (int k = threadIdx.x; k < w + h; k += blockDim.x) sig[k] = 0;
-  __syncthreads();
-  const long long area = (long long)w * h;
-  for (long long e = threadIdx.x; e < area; e += blockDim.x) {
-    const int j = int(e / w), i = int(e - (long long)j * w);
-    if (mask[(long long)(b.y0 + j) * ntx + b.x0 + i]) {
-      atomicAdd(&sx[i], 1);
-      atomicAdd(&sy[j], 1);
+  // signatures from the prefix sums
+  for (int k = threadIdx.x; k < w + h; k += blockDim.x) {
+    if (k < w) {
+      const int i = b.x0 + k;
+      sx[k] = pc[(long long)b.y1 * ntx + i] - pc[(long long)b.y0 * ntx + i];
+    } else {
+      const long long r = (long long)(b.y0 + k - w) * (ntx + 1);
+      sy[k - w] = pr[r + b.x1] - pr[r + b.x0];
     }
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
+  if (threadIdx.x != 0) return;  // (the caller's barrier follows for every thread)
   const Box none{-1, -1, -1, -1};
   Box out_acc = none, k0 = none, k1 = none;
   long long total = 0;
@@ -162,27 +208,30 @@ __global__ void __launch_bounds__(256) cluster_level_kernel(const uint8_t* __res
       }
     }
   }
-  acc[blockIdx.x] = out_acc;
-  kids[2 * blockIdx.x] = k0;
-  kids[2 * blockIdx.x + 1] = k1;
+  acc[bi] = out_acc;
+  kids[2 * bi] = k0;
+  kids[2 * bi + 1] = k1;
 }
 
 // Appends the accepted boxes to the result (in order) and compacts the valid children
 // into the next level's list.  One CTA of 1024 threads; counts[0] = result size,
 // counts[1] = next level size.
 __global__ void __launch_bounds__(1024) compact_kernel(const Box* __restrict__ acc,
-                                                       const Box* __restrict__ kids, int n,
+                                                       const Box* __restrict__ kids,
                                                        Box* __restrict__ result,
                                                        int result_cap, Box* __restrict__ next,
                                                        int* __restrict__ counts) {
   __shared__ int s_warp[32];
   __shared__ int s_base[2];
+  __shared__ int s_n;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     s_base[0] = counts[0];
     s_base[1] = 0;
+    s_n = counts[1];  // boxes of the level just clustered
   }
   __syncthreads();
+  const int n = s_n;
   // two passes of the same block-wide ordered scan: accepted boxes, then children
   for (int pass = 0; pass < 2; ++pass) {
     const Box* src = pass == 0 ? acc : kids;
@@ -226,16 +275,20 @@ struct Workspace {
   Box* kids = nullptr;    // [2 cap]
   Box* result = nullptr;  // [cap]
   int* counts = nullptr;  // [2]
+  double* eff = nullptr;  // the efficiency threshold of the current call
   uint8_t* mask = nullptr;
+  int* pc = nullptr;      // column prefix sums [(nty + 1) ntx]
+  int* pr = nullptr;      // row prefix sums [nty (ntx + 1)]
   void release() {
-    void* b[] = {level[0], level[1], acc, kids, result, counts, mask};
+    void* b[] = {level[0], level[1], acc, kids, result, counts, eff, mask, pc, pr};
     for (void* p : b)
       if (p) cudaFree(p);
     *this = Workspace{};
   }
 };
 
-cudaError_t ws_alloc(Workspace& ws, int ntiles) {
+cudaError_t ws_alloc(Workspace& ws, int ntx, int nty) {
+  const int ntiles = ntx * nty;
   ws.cap = ntiles + 1;
   const size_t bb = sizeof(Box) * size_t(ws.cap);
   cudaError_t e = cudaSuccess;
@@ -245,7 +298,10 @@ cudaError_t ws_alloc(Workspace& ws, int ntiles) {
   if (e == cudaSuccess) e = cudaMalloc(&ws.kids, 2 * bb);
   if (e == cudaSuccess) e = cudaMalloc(&ws.result, bb);
   if (e == cudaSuccess) e = cudaMalloc(&ws.counts, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&ws.eff, sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&ws.mask, size_t(ntiles));
+  if (e == cudaSuccess) e = cudaMalloc(&ws.pc, sizeof(int) * size_t(nty + 1) * ntx);
+  if (e == cudaSuccess) e = cudaMalloc(&ws.pr, sizeof(int) * size_t(nty) * (ntx + 1));
   if (e != cudaSuccess) {
     cudaGetLastError();
     ws.release();
@@ -253,50 +309,111 @@ cudaError_t ws_alloc(Workspace& ws, int ntiles) {
   return e;
 }
 
+// Workspace of one tile grid, kept by a lattice between calls: the device arrays, a
+// stream to record on, and the recorded chunk of kChunk clustering levels.
+struct RegridWS {
+  Workspace ws;
+  int ntx = 0, nty = 0, ctas = 0;
+  size_t smem = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t chunk = nullptr;
+  void destroy() {
+    if (chunk) cudaGraphExecDestroy(chunk);
+    if (cap) cudaStreamDestroy(cap);
+    ws.release();
+    chunk = nullptr;
+    cap = nullptr;
+    ntx = nty = 0;
+  }
+};
+
+constexpr int kChunk = 8;  // clustering levels between host checks of the level size
+
+cudaError_t ws_setup(RegridWS& R, int ntx, int nty) {
+  if (R.ntx == ntx && R.nty == nty && R.chunk) return cudaSuccess;
+  R.destroy();
+  cudaError_t e = ws_alloc(R.ws, ntx, nty);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 1;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  R.ctas = std::max(1, std::min(ntx * nty, 2 * nsm));
+  R.smem = sizeof(int) * size_t(ntx + nty);
+  if (R.smem > 48 * 1024 &&
+      (e = cudaFuncSetAttribute(cluster_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(R.smem))) != cudaSuccess)
+    return e;
+  if ((e = cudaStreamCreateWithFlags(&R.cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  // one chunk: kChunk levels; the level lists alternate, so a chunk ends where it began
+  if ((e = cudaStreamBeginCapture(R.cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+  int cur = 0;
+  for (int k = 0; k < kChunk; ++k) {
+    cluster_level_kernel<<<R.ctas, 256, R.smem, R.cap>>>(R.ws.pc, R.ws.pr, ntx, R.ws.level[cur],
+                                                         R.ws.counts + 1, R.ws.eff, R.ws.acc,
+                                                         R.ws.kids);
+    compact_kernel<<<1, 1024, 0, R.cap>>>(R.ws.acc, R.ws.kids, R.ws.result, R.ws.cap,
+                                          R.ws.level[cur ^ 1], R.ws.counts);
+    cur ^= 1;
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t le = cudaGetLastError();
+  e = cudaStreamEndCapture(R.cap, &graph);
+  if (le != cudaSuccess || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return le != cudaSuccess ? le : e;
+  }
+  e = cudaGraphInstantiate(&R.chunk, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return e;
+  R.ntx = ntx;
+  R.nty = nty;
+  return cudaSuccess;
+}
+
 // The whole regrid on device flags; outputs to host or device pointers.
-int regrid_run(const uint8_t* d_flags, long long pitch, int nx, int ny, int tile, int buffer,
-               double efficiency, uint8_t* tile_mask, kss_box* boxes, int32_t max_boxes,
-               int32_t* nboxes, int on_device, cudaStream_t s, std::string* msg) {
+int regrid_run(RegridWS& R, const uint8_t* d_flags, long long pitch, int nx, int ny, int tile,
+               int buffer, double efficiency, uint8_t* tile_mask, kss_box* boxes,
+               int32_t max_boxes, int32_t* nboxes, int on_device, cudaStream_t s,
+               std::string* msg) {
   const int ntx = (nx + tile - 1) / tile, nty = (ny + tile - 1) / tile;
   if (ntx > kMaxSide || nty > kMaxSide) return KSS_ERR_UNSUPPORTED;
   const int ntiles = ntx * nty;
-  Workspace ws;
-  if (ws_alloc(ws, ntiles) != cudaSuccess) return KSS_ERR_OOM;
   auto fail_cuda = [&](cudaError_t e) {
     if (msg) *msg = std::string("regrid: ") + cudaGetErrorString(e);
     cudaGetLastError();
-    ws.release();
     return KSS_ERR_CUDA;
   };
-  cudaError_t e;
+  cudaError_t e = ws_setup(R, ntx, nty);
+  if (e != cudaSuccess) {
+    R.destroy();
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      return KSS_ERR_OOM;
+    }
+    return fail_cuda(e);
+  }
+  Workspace& ws = R.ws;
   tile_mask_kernel<<<(ntiles + 255) / 256, 256, 0, s>>>(d_flags, pitch, nx, ny, tile, buffer,
                                                          ntx, nty, ws.mask);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e);
-  const size_t smem = sizeof(int) * size_t(ntx + nty);
-  if (smem > 48 * 1024) {
-    if ((e = cudaFuncSetAttribute(cluster_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  int(smem))) != cudaSuccess)
-      return fail_cuda(e);
-  }
+  mask_prefix_kernel<<<(ntx + nty + 255) / 256, 256, 0, s>>>(ws.mask, ntx, nty, ws.pc, ws.pr);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e);
+  // first level: the whole tile grid; results so far 0; this call's efficiency (pageable
+  // sources: each copy completes before the call returns)
   const Box whole{0, 0, ntx, nty};
-  const int zero[2] = {0, 0};
+  const int init[2] = {0, 1};
   if ((e = cudaMemcpyAsync(ws.level[0], &whole, sizeof(Box), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(ws.counts, zero, sizeof(zero), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      (e = cudaMemcpyAsync(ws.counts, init, sizeof(init), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(ws.eff, &efficiency, sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return fail_cuda(e);
-  int n = 1, cur = 0, count[2] = {0, 0};
-  // every level splits some box, and a box of area A splits at most A - 1 times
-  for (int level = 0; n > 0 && level <= ntx + nty + 2; ++level) {
-    cluster_level_kernel<<<n, 256, smem, s>>>(ws.mask, ntx, ws.level[cur], efficiency, ws.acc,
-                                             ws.kids);
-    if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e);
-    compact_kernel<<<1, 1024, 0, s>>>(ws.acc, ws.kids, n, ws.result, ws.cap, ws.level[cur ^ 1],
-                                      ws.counts);
-    if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e);
+  int count[2] = {0, 1};
+  // every level splits some box, and a box splits at most w + h - 2 times on any path
+  for (int level = 0; count[1] > 0 && level <= ntx + nty + 2; level += kChunk) {
+    if ((e = cudaGraphLaunch(R.chunk, s)) != cudaSuccess) return fail_cuda(e);
     if ((e = cudaMemcpyAsync(count, ws.counts, sizeof(count), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
       return fail_cuda(e);
-    n = count[1];
-    cur ^= 1;
   }
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   const int total = count[0];
@@ -309,7 +426,6 @@ int regrid_run(const uint8_t* d_flags, long long pitch, int nx, int ny, int tile
     return fail_cuda(e);
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail_cuda(e);
   *nboxes = total;
-  ws.release();
   return KSS_OK;
 }
 
@@ -319,6 +435,16 @@ bool valid_args(int tile, int buffer, double efficiency, int32_t max_boxes, int3
 }
 
 }  // namespace
+
+namespace kss_rt {
+void regrid_release(kss_lattice* L) {
+  if (!L || !L->regrid) return;
+  RegridWS* R = static_cast<RegridWS*>(L->regrid);
+  R->destroy();
+  delete R;
+  L->regrid = nullptr;
+}
+}  // namespace kss_rt
 
 extern "C" {
 
@@ -331,8 +457,13 @@ int kss_regrid(kss_lattice* L, int32_t buffer, double efficiency, uint8_t* tile_
   DeviceGuard g(L->device);
   // the flags of the current step (evaluated if this step had no outputs)
   if ((rc = kss_read_flags(L, nullptr, nullptr, nullptr, 1)) < 0) return rc;
-  rc = regrid_run(L->flags, L->pitch, L->cfg.nx, L->cfg.ny, L->cfg.tile, buffer, efficiency,
-                  tile_mask, boxes, max_boxes, nboxes, on_device, L->stream, &L->msg);
+  if (!L->regrid) {
+    L->regrid = new (std::nothrow) RegridWS();
+    if (!L->regrid) return fail(L, KSS_ERR_OOM, "regrid workspace");
+  }
+  rc = regrid_run(*static_cast<RegridWS*>(L->regrid), L->flags, L->pitch, L->cfg.nx, L->cfg.ny,
+                  L->cfg.tile, buffer, efficiency, tile_mask, boxes, max_boxes, nboxes, on_device,
+                  L->stream, &L->msg);
   if (rc == KSS_ERR_CUDA) L->err = rc;  // sticky
   return rc;
 }
@@ -358,12 +489,12 @@ int kss_regrid_flags(const uint8_t* flags, int32_t nx, int32_t ny, int32_t tile,
     }
     d = staged;
   }
-  const int rc = regrid_run(d, nx, nx, ny, tile, buffer, efficiency, tile_mask, boxes, max_boxes,
+  RegridWS R;
+  const int rc = regrid_run(R, d, nx, nx, ny, tile, buffer, efficiency, tile_mask, boxes, max_boxes,
                             nboxes, on_device, s, nullptr);
-  if (staged) {
-    cudaStreamSynchronize(s);
-    cudaFree(staged);
-  }
+  cudaStreamSynchronize(s);
+  R.destroy();
+  if (staged) cudaFree(staged);
   return rc;
 }
 

@@ -181,6 +181,7 @@ int device_error(kss_lattice* L) {
 void release(kss_lattice* L) {
   if (!L) return;
   cudaStreamSynchronize(L->stream);
+  regrid_release(L);
   void* bufs[] = {L->f[0], L->f[1], L->rec, L->evalplane, L->flags, L->tiles, L->part_sum,
                   L->part_cnt, L->small, L->staging, L->defer_list};
   for (void* b : bufs)

@@ -68,6 +68,7 @@ struct kss_lattice {
   int err = KSS_OK;
   std::string msg;
   kss_batch* owner = nullptr;  // the batch that created this lattice, if any
+  void* regrid = nullptr;      // regridding workspace (kss_regrid.cu), made on first use
 };
 
 namespace kss_rt {
@@ -179,5 +180,8 @@ void release(kss_lattice* L);
 
 // After a stream synchronisation: did a bounded device wait run out?  (sticky)
 int device_error(kss_lattice* L);
+
+// Free a lattice's regridding workspace, if any (kss_regrid.cu).
+void regrid_release(kss_lattice* L);
 
 }  // namespace kss_rt
