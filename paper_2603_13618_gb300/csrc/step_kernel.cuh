@@ -749,8 +749,9 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
         // rho > 0 and |u|^2 < 0.3 make every f^eq_q >= 0.05 w_q rho > 0, and Kn < 1/16
         // bounds every |x_q|, so f_q = f^eq_q (1 + x_q) > 0 (nothing non-positive) and
         // the series of phi is exact to FP32.  Any other valid cell is deferred: its
-        // flag byte is KSS_FLAG_DEFERRED only, it is not counted here, and fixup_kernel
-        // recomputes it exactly from the unchanged source populations.
+        // flag byte is KSS_FLAG_DEFERRED only, it is not counted here, and it is
+        // recomputed exactly from the unchanged source populations (CTA epilogue or
+        // fixup_kernel).
         const bool fast = (rw1[k] > T(0)) & (base[k] > T(0.55)) & (a.kn[k] < T(0.0625));
         a.kl[k] = fabs(a.kl[k]);
         const T er = pr(a.kn[k], a.kl[k], a.neq[k]);

@@ -147,7 +147,7 @@ def test_batch_members_against_the_oracle():
         for name in ("kn", "kl", "neq", "tau_ns", "alpha"):
             sid = oracle.SENSOR_ID[name]
             parity.assert_sensor_close(name, b[k].read_sensor(name), ref[sid], "fp32", nsteps,
-                                       r, u, v, kn, sp["tau"])
+                                       r, u, v, kn, sp["tau"], ft=ft)
         er, es = ref[oracle.SENSOR_ID["kn"]], ref[oracle.SENSOR_ID["neq"]]
         rf, rt, rcnt = oracle.flags(er, 1e-3, es, 1e-4, nonpos, sp["tile"])
         flags, tiles, counts = b[k].read_flags()

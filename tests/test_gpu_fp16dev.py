@@ -68,7 +68,7 @@ def test_stored_state_round_trip_and_its_sensors(nx, ny, tile):
     for sid in ALL:
         name = parity.SENSORS[sid]
         parity.assert_sensor_close(name, lat.read_sensor(name), ref[sid], "fp32", 0, r, u, v,
-                                   ref[oracle.SENSOR_ID["kn"]], tau)
+                                   ref[oracle.SENSOR_ID["kn"]], tau, ft=X)
     lat.close()
 
 
@@ -96,7 +96,7 @@ def test_one_step_against_the_oracle_codec(nx, ny, tile, tau):
     for name in ("kn", "kl", "neq", "tau_ns", "alpha"):
         sid = oracle.SENSOR_ID[name]
         parity.assert_sensor_close(name, lat.read_sensor(name), ref[sid], "fp32", 0, r, u, v, kn,
-                                   tau)
+                                   tau, ft=ft)
     rf, rt, rcnt = oracle.flags(kn, 1e-3, ref[oracle.SENSOR_ID["neq"]], 1e-4, nonpos, tile)
     flags, tiles, counts = lat.read_flags()
     band = parity.band_mask(kn, 1e-3, ref[oracle.SENSOR_ID["neq"]], 1e-4)

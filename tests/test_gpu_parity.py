@@ -51,7 +51,7 @@ def _check_step_outputs(lat, prec, prev, tau, nsteps, thr_r, thr_s, tile, sensor
     for sid in sensors:
         name = parity.SENSORS[sid]
         got = lat.read_sensor(name)
-        parity.assert_sensor_close(name, got, ref[sid], prec, nsteps, r, u, v, kn, tau)
+        parity.assert_sensor_close(name, got, ref[sid], prec, nsteps, r, u, v, kn, tau, ft=ft)
     er, es = ref[oracle.SENSOR_ID[refine]], ref[oracle.SENSOR_ID[switch]]
     rf, rt, rcnt = oracle.flags(er, thr_r, es, thr_s, nonpos, tile)
     flags, tiles, counts = lat.read_flags()
@@ -165,7 +165,7 @@ def test_sensors_on_the_same_state(prec):
     for sid in ALL:
         name = parity.SENSORS[sid]
         parity.assert_sensor_close(name, lat.read_sensor(name), ref[sid], prec, 0, r, u, v,
-                                   ref[oracle.SENSOR_ID["kn"]], tau)
+                                   ref[oracle.SENSOR_ID["kn"]], tau, ft=state)
     lat.close()
 
 
@@ -399,17 +399,26 @@ def test_full_size_4096_fp32_bench_configuration():
     assert counts[0] == fr.sum() and counts[1] == fs.sum() and counts[2] == np.sum(flags >> 7)
 
 
+@pytest.mark.parametrize("state", ["far", "nonpositive"])
 @pytest.mark.parametrize("prec,kernel", [("fp32", "vector"), ("fp32", "tma"), ("fp64", "vector")])
-def test_deferred_cells_everywhere(prec, kernel):
-    """Every cell far from equilibrium (|x| >= 1/16): the fused pass defers all of them
-    to the exact fix-up pass, more than its list holds (1/8 of the lattice), so the
-    fix-up falls back to scanning; results must still match the oracle exactly."""
+def test_deferred_cells_everywhere(prec, kernel, state):
+    """far: every cell far from equilibrium (populations perturbed by up to 30 %, most
+    |x_q| >= 1/16), so its KL terms take the closed form in the fused pass.
+    nonpositive: the same, and in 30 % of the cells one population made negative (after
+    streaming, in as many cells), so those cells are deferred to the exact recomputation,
+    more than the fix-up list holds (1/8 of the lattice) on the TMA path, which then
+    scans.  Both must match the oracle."""
     kss = _kss()
     nx, ny, tau = 128, 128, 0.7
     rng = np.random.default_rng(123)
     rho, ux, uy = inputs.random_smooth(nx, ny, seed=4)
     f = oracle.init_equilibrium(rho, ux, uy) * (1.0 + 0.3 * rng.uniform(-1, 1, (9, ny, nx)))
     f[5, 10, 20] = -0.01  # and one non-positive cell
+    if state == "nonpositive":
+        hit = rng.random((ny, nx)) < 0.3
+        q = rng.integers(0, 9, (ny, nx))
+        jj, ii = np.nonzero(hit)
+        f[q[hit], jj, ii] *= -0.1
     thr_r, thr_s = 0.5, 0.05
     lat = kss.Lattice(nx, ny, precision=prec, tau=tau, refine_threshold=thr_r,
                       switch_threshold=thr_s, record=("kl", "kn", "neq"), kernel=kernel)
