@@ -6,7 +6,9 @@ velocity perturbations (max |drho| = 1e-2, max |u| = 0.1 c_s) on a density step
 rho_L / rho_R = 2 at x = 2048; every step is an output step: Knudsen sensor tagged
 against 1e-3 (refine flag), non-equilibrium sensor against 1e-4 (switch flag), the
 Kullback-Leibler sensor field stored, per-tile (16 x 16) tag counts and FP64
-conservation sums.  A step = one fused launch over the whole lattice.
+conservation sums.  The timed region is one kss_step(K) call: K such steps in one
+cooperative multi-step launch (each block of a step waits only for its neighbours'
+previous step); the same steps as one launch each are timed alongside.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
   python bench.py --workload batch64    # the batched workload (below)
@@ -65,14 +67,14 @@ def kernel_hash() -> str:
 
 
 def profile_traffic():
-    """DRAM bytes per launch of the fused step from the committed ncu summary, or None
-    if the summary is missing or was taken on different kernel sources."""
+    """DRAM bytes per step of the fused step from the committed ncu summary, or None if
+    the summary is missing or was taken on different kernel sources."""
     try:
         txt = open(PROFILE).read()
     except OSError:
         return None
     m = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]{16})", txt)
-    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    t = re.search(r"dram_bytes_per_step:\s*([0-9.eE+]+)", txt)
     if not m or not t or m.group(1) != kernel_hash():
         return None
     return float(t.group(1))
@@ -80,8 +82,9 @@ def profile_traffic():
 
 def kernel_name(choice: str) -> str:
     tma = choice == "tma"
-    return ("step_tma_kernel<float, MODE_STD> (bulk-copy staged)" if tma
-            else "step_kernel<float, MODE_STD, pull, store> (vector loads)")
+    return ("step_tma_kernel<float, MODE_STD> (bulk-copy staged), one launch per step" if tma
+            else "step_kernel_multi<float, MODE_STD> (vector loads; all steps in one "
+                 "cooperative launch, blocks waiting on their neighbours' previous step)")
 
 
 def measured_peak():
@@ -503,30 +506,46 @@ def run_gpu(args):
     barrier()
 
     K = args.steps
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    # the timed region: one kss_step(K) call -- K fused steps, each with its sensors,
+    # flags, tile counts and sums, in one cooperative multi-step launch (one launch per
+    # step for the TMA kernel)
+    multi = args.kernel != "tma"
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         barrier()
         t_host = time.perf_counter()
-        for k in range(K):
-            starts[k].record(stream)
-            lat.step(1)
-            ends[k].record(stream)
+        e0.record(stream)
+        lat.step(K)
+        e1.record(stream)
         barrier()
         t_host = time.perf_counter() - t_host
     clocks = clk.summary()
-    per_launch = [s.elapsed_time(e) for s, e in zip(starts, ends)]  # ms
-    total_ms = starts[0].elapsed_time(ends[-1])
+    total_ms = e0.elapsed_time(e1)
     if dist is not None:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     cells = NX * NY
     value = world * cells * K / (total_ms * 1e-3) / 1e6
-    kern_ms = sum(per_launch) / K
+    kern_ms = total_ms / K  # per step (the launch covers all K steps)
     achieved = BYTES_PER_LUP * cells / (kern_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
     sums, counts, step = lat.read_stats()
+
+    # the same steps as one launch per step, each timed on its own
+    k1 = min(K, 200)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(k1)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(k1)]
+    barrier()
+    for k in range(k1):
+        starts[k].record(stream)
+        lat.step(1)
+        ends[k].record(stream)
+    barrier()
+    per_launch = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    single = {"ms_per_step": starts[0].elapsed_time(ends[-1]) / k1,
+              "kernel_ms": sum(per_launch) / k1, "steps": k1}
+    single["frac"] = BYTES_PER_LUP * cells / (single["kernel_ms"] * 1e-3) / 1e9 / peak
 
     # end to end through the C ABI with host buffers: each step copies its input fields
     # from pinned host memory, runs one fused step and reads the flags, tile counts and
@@ -576,12 +595,14 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": profile_traffic(),
-                         "algorithmic_bytes_per_launch": BYTES_PER_LUP * cells,
-                         "kernel_ms": kern_ms,
+                         "algorithmic_bytes_per_step": BYTES_PER_LUP * cells,
+                         "steps_per_launch": K if multi else 1,
+                         "kernel_ms_per_step": kern_ms,
                          "kernel": kernel_name(args.kernel)},
+            "single_step_launches": single,
             "cpu_baseline": base,
             "e2e": e2e,
-            "gpu_launches": K,
+            "gpu_launches": 1 if multi else K,
             "clocks": clocks,
             "host_s": t_host,
             "check": {"sum_rho": sums[0], "refine": int(counts[0]), "switch": int(counts[1]),

@@ -33,6 +33,16 @@ template <class T>
 cudaError_t launch_batch_step(const StepParams<T>* table, const BatchItem* items, int nitems,
                               int ctas, int mode, cudaStream_t stream);
 
+// nsteps fused steps in one cooperative launch (step_kernel_multi): pa reads buffer A and
+// writes B, pb the reverse; mode MODE_STD (the {Kn, KL, neq} set every step);
+// ctas <= multi_resident_ctas.
+template <class T>
+cudaError_t launch_step_multi(const StepParams<T>& pa, const StepParams<T>& pb,
+                              const MultiState& m, int mode, int ctas, cudaStream_t stream);
+// CTAs of the multi-step kernel resident on the current device at once (0 on error).
+template <class T>
+int multi_resident_ctas(int mode);
+
 // The TMA-staged step (step_tma.cuh): mode MODE_PLAIN or MODE_STD, always pull + store;
 // `ctas` persistent CTAs (one per SM).
 template <class T>

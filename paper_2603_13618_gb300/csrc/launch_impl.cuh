@@ -13,10 +13,10 @@ inline dim3 helper_grid(int nx, long long rows) {
 
 // CTAs of `kernel` resident on the current device at once (its occupancy times the SM
 // count), looked up once per device.
-template <class K>
-int resident_ctas(K kernel) {
+template <auto kernel>
+int resident_ctas() {
   constexpr int kMaxDev = 64;
-  static int cache[kMaxDev] = {};
+  static int cache[kMaxDev] = {};  // one per kernel: `kernel` is a template argument
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 0;
   if (!cache[dev]) {
@@ -43,7 +43,7 @@ cudaError_t launch_step_mode(const StepParams<KSS_T>& p, dim3 grid, cudaStream_t
   const int nblocks = int(grid.x * grid.y);
   constexpr bool kHalfPlain = std::is_same<KSS_T, __half>::value && MODE == MODE_PLAIN;
   if (KSS_PERSISTENT || kHalfPlain) {
-    const int wave = resident_ctas(step_kernel_persistent<KSS_T, MODE, true, true>);
+    const int wave = resident_ctas<step_kernel_persistent<KSS_T, MODE, true, true>>();
     if (wave > 0 && nblocks > wave) {
       step_kernel_persistent<KSS_T, MODE, true, true><<<wave, kThreads, 0, stream>>>(
           p, int(grid.x), nblocks);
@@ -76,6 +76,23 @@ cudaError_t launch_step<KSS_T>(const StepParams<KSS_T>& p, int mode, bool pull, 
     return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+template <>
+int multi_resident_ctas<KSS_T>(int mode) {
+  return mode == MODE_STD ? resident_ctas<step_kernel_multi<KSS_T, MODE_STD>>() : 0;
+}
+
+template <>
+cudaError_t launch_step_multi<KSS_T>(const StepParams<KSS_T>& pa, const StepParams<KSS_T>& pb,
+                                     const MultiState& m, int mode, int ctas,
+                                     cudaStream_t stream) {
+  StepParams<KSS_T> a = pa, b = pb;
+  MultiState ms = m;
+  void* args[] = {&a, &b, &ms};
+  if (mode != MODE_STD) return cudaErrorInvalidValue;
+  const void* fn = reinterpret_cast<const void*>(step_kernel_multi<KSS_T, MODE_STD>);
+  return cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(kThreads), args, 0, stream);
 }
 
 template <>

@@ -69,6 +69,7 @@ struct kss_lattice {
   std::string msg;
   kss_batch* owner = nullptr;  // the batch that created this lattice, if any
   void* regrid = nullptr;      // regridding workspace (kss_regrid.cu), made on first use
+  void* multi = nullptr;       // multi-step kernel bookkeeping, made on first use
 };
 
 namespace kss_rt {

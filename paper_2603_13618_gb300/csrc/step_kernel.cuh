@@ -186,12 +186,25 @@ struct StepParams {
 };
 
 // ---------------------------------------------------------------- loads ----
+// Population loads: through the read-only data path (CG = false; the source buffer is
+// not written during the launch), or as ordinary cached loads (CG = true: the multi-step
+// kernel, whose source buffers other CTAs write during the launch; its loads follow an
+// acquire of the writers' release, which the read-only path would not honour).
+template <bool CG, class VT>
+__device__ __forceinline__ VT ld_pop(const VT* p) {
+  if constexpr (CG) {
+    return __ldca(p);
+  } else {
+    return __ldg(p);
+  }
+}
+
 // V cells per thread (default: the fused step's Vec<T>::N).
-template <class T, int V = Vec<T>::N>
+template <class T, int V = Vec<T>::N, bool CG = false>
 __device__ __forceinline__ void vload(const T* p, bool ok, T (&v)[V]) {
   using VT = typename VecT<T, V>::type;
   if (ok) {
-    const VT a = __ldg(reinterpret_cast<const VT*>(p));
+    const VT a = ld_pop<CG>(reinterpret_cast<const VT*>(p));
     if constexpr (V == 4) {
       v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
     } else {
@@ -209,17 +222,17 @@ __device__ __forceinline__ void vload(const T* p, bool ok, T (&v)[V]) {
 //
 // Halo element of a cx = +1 population (source column i - 1): lane 0 of each warp
 // needs the element left of its vector (column nx-1 at the periodic seam).
-template <class T>
+template <class T, bool CG = false>
 __device__ __forceinline__ T load_left_halo(const T* row, int i0, int nx, int lane, bool cv) {
-  return (lane == 0 && cv) ? __ldg(row + (i0 == 0 ? nx - 1 : i0 - 1)) : T(0);
+  return (lane == 0 && cv) ? ld_pop<CG>(row + (i0 == 0 ? nx - 1 : i0 - 1)) : T(0);
 }
 
 // Halo element of a cx = -1 population (source column i + 1): lane 31, and any lane
 // whose vector reaches the row end (then the element is column 0, periodic seam).
-template <class T, int V = Vec<T>::N>
+template <class T, int V = Vec<T>::N, bool CG = false>
 __device__ __forceinline__ T load_right_halo(const T* row, int i0, int nx, int lane, bool cv) {
   const bool tail = i0 + V >= nx;
-  return (cv && (lane == 31 || tail)) ? __ldg(row + (tail ? 0 : i0 + V)) : T(0);
+  return (cv && (lane == 31 || tail)) ? ld_pop<CG>(row + (tail ? 0 : i0 + V)) : T(0);
 }
 
 // Cells i0..i0+V-1 pulled from column i - 1: the left neighbour's last element by
@@ -293,7 +306,7 @@ __device__ __forceinline__ void vstore(T* p, const T (&v)[V]) {
 
 // Populations of plane q: V cells loaded and decoded to the arithmetic type, or encoded
 // and stored (streaming stores).  FP16 deviations move as 8- (V = 4) or 4-byte vectors.
-template <class S, int V = Vec<S>::N>
+template <class S, int V = Vec<S>::N, bool CG = false>
 __device__ __forceinline__ void pop_vload(const S* p, bool ok, arith_t<S> (&v)[V], int q,
                                           const codec_t<S>& c) {
   if constexpr (std::is_same<S, __half>::value) {
@@ -303,7 +316,7 @@ __device__ __forceinline__ void pop_vload(const S* p, bool ok, arith_t<S> (&v)[V
       return;
     }
     using VT = typename VecT<S, V>::type;
-    const VT raw = __ldg(reinterpret_cast<const VT*>(p));
+    const VT raw = ld_pop<CG>(reinterpret_cast<const VT*>(p));
     const __half2* h = reinterpret_cast<const __half2*>(&raw);
 #pragma unroll
     for (int k = 0; k < V / 2; ++k) {
@@ -312,7 +325,7 @@ __device__ __forceinline__ void pop_vload(const S* p, bool ok, arith_t<S> (&v)[V
       v[2 * k + 1] = fmaf(a.y, c.inv[q], c.base[q]);
     }
   } else {
-    vload<S, V>(p, ok, v);
+    vload<S, V, CG>(p, ok, v);
   }
 }
 
@@ -449,7 +462,7 @@ struct Pick3 {
 
 // The nine populations of cell (i, j) as the step sees them (pulled when PULL), for the
 // exact recomputation of deferred cells.
-template <class S, bool PULL>
+template <class S, bool PULL, bool CG = false>
 __device__ __forceinline__ void reload_cell(const StepParams<S>& p, int i, int j,
                                             arith_t<S> (&c)[9]) {
   constexpr int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -463,7 +476,7 @@ __device__ __forceinline__ void reload_cell(const StepParams<S>& p, int i, int j
       si = si < 0 ? si + p.nx : (si >= p.nx ? si - p.nx : si);
       sj = sj < 0 ? sj + p.ny : (sj >= p.ny ? sj - p.ny : sj);
     }
-    c[q] = decode<S>(p.src[q * p.plane + (long long)sj * p.pitch + si], q, p.codec);
+    c[q] = decode<S>(ld_pop<CG>(p.src + q * p.plane + (long long)sj * p.pitch + si), q, p.codec);
   }
 }
 
@@ -536,7 +549,9 @@ template <> struct Red<double> {
 // The last CTA's reduction of the per-CTA partials, in CTA order within each thread and
 // a fixed shuffle/shared-memory tree across threads (bitwise reproducible).
 template <class S, int NTHREADS>
-__device__ __forceinline__ void finalize_partials(const StepParams<S>& p, int nblocks) {
+__device__ __forceinline__ void finalize_sums(const double* part_sum, const uint32_t* part_cnt,
+                                              int nblocks, double* out_sums,
+                                              unsigned long long* out_counts) {
   using T = arith_t<S>;
   __shared__ Red<T> f_sum[NTHREADS / 32][3];
   __shared__ unsigned long long f_cnt[NTHREADS / 32][3];
@@ -546,8 +561,8 @@ __device__ __forceinline__ void finalize_partials(const StepParams<S>& p, int nb
   for (int b = threadIdx.x; b < nblocks; b += NTHREADS) {
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-      t[m].add(Red<T>::load(p.part_sum + 3 * b + m));
-      u[m] += __ldcg(p.part_cnt + 4 * b + m);
+      t[m].add(Red<T>::load(part_sum + 3 * b + m));
+      u[m] += __ldcg(part_cnt + 4 * b + m);
     }
   }
 #pragma unroll
@@ -575,11 +590,16 @@ __device__ __forceinline__ void finalize_partials(const StepParams<S>& p, int nb
         r.add(f_sum[w][m]);
         c += f_cnt[w][m];
       }
-      p.stat_sums[m] = r.value();
-      p.stat_counts[m] = c;
+      out_sums[m] = r.value();
+      out_counts[m] = c;
     }
-    *p.done = 0u;  // ready for the next launch (stream-ordered)
   }
+}
+
+template <class S, int NTHREADS>
+__device__ __forceinline__ void finalize_partials(const StepParams<S>& p, int nblocks) {
+  finalize_sums<S, NTHREADS>(p.part_sum, p.part_cnt, nblocks, p.stat_sums, p.stat_counts);
+  if (threadIdx.x == 0) *p.done = 0u;  // ready for the next launch (stream-ordered)
 }
 
 // Is sensor s in the compiled set of MODE?
@@ -593,12 +613,12 @@ __host__ __device__ constexpr bool mode_has(int s) {
 // the pass's source buffer (which the pass does not modify) with the exact per-cell
 // arithmetic of the full sensor set (cell_update).  Returns the refine/switch/non-
 // positive tags; the tile counts are corrected here.
-template <class S, bool PULL>
+template <class S, bool PULL, bool CG = false>
 __device__ __forceinline__ uint32_t fix_cell(const StepParams<S>& p, const Pick3& pr,
                                              const Pick3& ps, int i, int j) {
   using T = arith_t<S>;
   T cell[9], dummy[9];
-  reload_cell<S, PULL>(p, i, j, cell);
+  reload_cell<S, PULL, CG>(p, i, j, cell);
   CellOut<T> co;
   cell_update<T, MODE_STD, false>(cell, p.omega, p.tau, dummy, co);
   const T kn = co.sv[S_KN], kl = co.sv[S_KL], neq = co.sv[S_NEQ];
@@ -782,9 +802,9 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
 // Block (bx, by) of a lattice whose step grid is gx blocks wide: its rows, then (output
 // modes) its tile counts and its partial sums and counts in slot bid.  Called by every
 // thread of the CTA; the CTA's shared memory is free again when it returns.
-template <class S, int MODE, bool PULL, bool STORE>
+template <class S, int MODE, bool PULL, bool STORE, bool CG = false>
 __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx, const int by,
-                                           const int gx) {
+                                           const int gx, double* part_sum, uint32_t* part_cnt) {
   using T = arith_t<S>;
   constexpr int V = Vec<S>::N;
   constexpr bool OUT = MODE != MODE_PLAIN;
@@ -826,21 +846,21 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
       const S* r6 = base + 6 * p.plane + up;
       const S* r7 = base + 7 * p.plane + dn;
       const S* r8 = base + 8 * p.plane + dn;
-      pop_vload<S>(r0 + i0, cv, ft[0], 0, p.codec);
-      pop_vload<S>(r1 + i0, cv, ft[1], 1, p.codec);
-      pop_vload<S>(r2 + i0, cv, ft[2], 2, p.codec);
-      pop_vload<S>(r3 + i0, cv, ft[3], 3, p.codec);
-      pop_vload<S>(r4 + i0, cv, ft[4], 4, p.codec);
-      pop_vload<S>(r5 + i0, cv, ft[5], 5, p.codec);
-      pop_vload<S>(r6 + i0, cv, ft[6], 6, p.codec);
-      pop_vload<S>(r7 + i0, cv, ft[7], 7, p.codec);
-      pop_vload<S>(r8 + i0, cv, ft[8], 8, p.codec);
-      const T h1 = decode<S>(load_left_halo<S>(r1, i0, p.nx, lane, cv), 1, p.codec);
-      const T h5 = decode<S>(load_left_halo<S>(r5, i0, p.nx, lane, cv), 5, p.codec);
-      const T h8 = decode<S>(load_left_halo<S>(r8, i0, p.nx, lane, cv), 8, p.codec);
-      const T h3 = decode<S>(load_right_halo<S>(r3, i0, p.nx, lane, cv), 3, p.codec);
-      const T h6 = decode<S>(load_right_halo<S>(r6, i0, p.nx, lane, cv), 6, p.codec);
-      const T h7 = decode<S>(load_right_halo<S>(r7, i0, p.nx, lane, cv), 7, p.codec);
+      pop_vload<S, V, CG>(r0 + i0, cv, ft[0], 0, p.codec);
+      pop_vload<S, V, CG>(r1 + i0, cv, ft[1], 1, p.codec);
+      pop_vload<S, V, CG>(r2 + i0, cv, ft[2], 2, p.codec);
+      pop_vload<S, V, CG>(r3 + i0, cv, ft[3], 3, p.codec);
+      pop_vload<S, V, CG>(r4 + i0, cv, ft[4], 4, p.codec);
+      pop_vload<S, V, CG>(r5 + i0, cv, ft[5], 5, p.codec);
+      pop_vload<S, V, CG>(r6 + i0, cv, ft[6], 6, p.codec);
+      pop_vload<S, V, CG>(r7 + i0, cv, ft[7], 7, p.codec);
+      pop_vload<S, V, CG>(r8 + i0, cv, ft[8], 8, p.codec);
+      const T h1 = decode<S>(load_left_halo<S, CG>(r1, i0, p.nx, lane, cv), 1, p.codec);
+      const T h5 = decode<S>(load_left_halo<S, CG>(r5, i0, p.nx, lane, cv), 5, p.codec);
+      const T h8 = decode<S>(load_left_halo<S, CG>(r8, i0, p.nx, lane, cv), 8, p.codec);
+      const T h3 = decode<S>(load_right_halo<S, V, CG>(r3, i0, p.nx, lane, cv), 3, p.codec);
+      const T h6 = decode<S>(load_right_halo<S, V, CG>(r6, i0, p.nx, lane, cv), 6, p.codec);
+      const T h7 = decode<S>(load_right_halo<S, V, CG>(r7, i0, p.nx, lane, cv), 7, p.codec);
       assemble_from_left<T>(ft[1], h1, lane);
       assemble_from_left<T>(ft[5], h5, lane);
       assemble_from_left<T>(ft[8], h8, lane);
@@ -849,7 +869,7 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
       assemble_from_right<T>(ft[7], h7, i0, p.nx, lane);
     } else {
 #pragma unroll
-      for (int q = 0; q < 9; ++q) pop_vload<S>(base + q * p.plane + i0, cv, ft[q], q, p.codec);
+      for (int q = 0; q < 9; ++q) pop_vload<S, V, CG>(base + q * p.plane + i0, cv, ft[q], q, p.codec);
     }
 
     const uint32_t fbits = fused_row<S, MODE, PULL, STORE>(p, ft, i0, j, cv, a_rho, a_jx, a_jy);
@@ -931,7 +951,7 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
         const int o = s_dl[w][r];
         const int rl = o / (32 * V), cl = o - rl * (32 * V);
         const int j = j0 + rl, i = bx * 32 * V + cl;
-        const uint32_t tags = fix_cell<S, PULL>(p, pr, ps, i, j);
+        const uint32_t tags = fix_cell<S, PULL, CG>(p, pr, ps, i, j);
         const int b = rl / p.tile, tl = cl / p.tile;
         if (tags & 1u) {
           atomicAdd(&s_cx[0], 1u);
@@ -972,12 +992,12 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
       c1 += s_cnt[w][1];
       c2 += s_cnt[w][2];
     }
-    s0.store(p.part_sum + 3 * bid + 0);
-    s1.store(p.part_sum + 3 * bid + 1);
-    s2.store(p.part_sum + 3 * bid + 2);
-    p.part_cnt[4 * bid + 0] = c0;
-    p.part_cnt[4 * bid + 1] = c1;
-    p.part_cnt[4 * bid + 2] = c2;
+    s0.store(part_sum + 3 * bid + 0);
+    s1.store(part_sum + 3 * bid + 1);
+    s2.store(part_sum + 3 * bid + 2);
+    part_cnt[4 * bid + 0] = c0;
+    part_cnt[4 * bid + 1] = c1;
+    part_cnt[4 * bid + 2] = c2;
   }
 }
 
@@ -1005,7 +1025,7 @@ __device__ __forceinline__ void ticket_and_finalize(const StepParams<S>& p, int 
 template <class S, int MODE, bool PULL, bool STORE>
 __device__ __forceinline__ void step_cta(const StepParams<S>& p, const int bx, const int by,
                                          const int gx, const int nblocks) {
-  step_block<S, MODE, PULL, STORE>(p, bx, by, gx);
+  step_block<S, MODE, PULL, STORE>(p, bx, by, gx, p.part_sum, p.part_cnt);
   if (MODE != MODE_PLAIN) ticket_and_finalize<S>(p, nblocks, nblocks);
 }
 
@@ -1024,10 +1044,134 @@ __global__ void __launch_bounds__(kThreads, MODE == MODE_FULL ? 1 : KSS_STEP_MIN
 step_kernel_persistent(const StepParams<S> p, int gx, int nblocks) {
   for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
     const int by = b / gx;
-    step_block<S, MODE, PULL, STORE>(p, b - by * gx, by, gx);
+    step_block<S, MODE, PULL, STORE>(p, b - by * gx, by, gx, p.part_sum, p.part_cnt);
     if (MODE != MODE_PLAIN) __syncthreads();  // shared memory is reused by the next block
   }
   if (MODE != MODE_PLAIN) ticket_and_finalize<S>(p, gridDim.x, nblocks);
+}
+
+// ---------------------------------------------------------------- multi-step ----
+// nsteps steps in one cooperative launch (every CTA resident).  The (step, block) work
+// items are handed out in order from an atomic counter (as the hardware hands out the
+// blocks of a launch); block b of step s first waits until the blocks of its 3 x 3
+// neighbourhood (periodic) have completed step s - 1: they wrote the halo it reads and
+// have read the cells it overwrites.  So a step starts where the previous one has
+// finished, with no launch boundary between them, and every item it waits for was
+// handed out earlier (no cycle).  Each block's partial sums of step s go to ring slot
+// s % ring; the block that completes step s last adds them in block order (the step's
+// sums; the last step's are the lattice's), and a slot is reused only after its previous
+// step's sums were formed.  Every wait is bounded by a clock64 deadline, after which the
+// CTA sets bit 1 of the error word and returns (its neighbours then run out too).
+// Population loads are ordinary cached loads after an acquire (CG).
+struct MultiState {
+  uint32_t* done;      // [nblocks] steps each block has completed (0 at launch)
+  uint32_t* ticket;    // [ring] blocks of the slot's step completed (0 when free)
+  uint32_t* fin;       // [ring] 1 + the last step whose sums the slot formed (0 at launch)
+  uint32_t* work;      // next work item (0 at launch)
+  double* part_sum;    // [ring][nblocks][3]
+  uint32_t* part_cnt;  // [ring][nblocks][4]
+  double* ring_sums;   // [ring][3] each step's sums
+  unsigned long long* ring_counts;  // [ring][3]
+  uint32_t* err;       // bit 1: a wait ran out
+  long long deadline;  // clock64 cycles one wait may take
+  int ring, nsteps, gx, gy, nblocks;
+};
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0: wait until *p >= want, at most m.deadline cycles.
+__device__ __forceinline__ bool wait_at_least(const MultiState& m, const uint32_t* p,
+                                              uint32_t want) {
+  if (ld_acquire_u32(p) >= want) return true;
+  const long long t0 = clock64();
+  while (ld_acquire_u32(p) < want) {
+    if (clock64() - t0 > m.deadline) {
+      atomicOr(m.err, 2u);
+      return false;
+    }
+    __nanosleep(64);
+  }
+  return true;
+}
+
+// Work item (step s, block b); returns false if a wait ran out.  s_next receives the
+// CTA's next work item (taken early, so that the counter's latency is hidden).
+template <class S, int MODE>
+__device__ __forceinline__ bool multi_block(const StepParams<S>& p, const MultiState& m, int s,
+                                            int b, int* s_next) {
+  constexpr bool OUT = MODE != MODE_PLAIN;
+  __shared__ int s_go, s_fin;
+  const int slot = s % m.ring;
+  double* psum = m.part_sum + (long long)slot * m.nblocks * 3;
+  uint32_t* pcnt = m.part_cnt + (long long)slot * m.nblocks * 4;
+  const int by = b / m.gx, bx = b - by * m.gx;
+  if (threadIdx.x == 0) {
+    *s_next = int(atomicAdd(m.work, 1u));
+    bool ok = true;
+    if (s > 0) {
+      for (int dy = -1; dy <= 1 && ok; ++dy) {
+        const int yy = by + dy < 0 ? m.gy - 1 : (by + dy == m.gy ? 0 : by + dy);
+        for (int dx = -1; dx <= 1 && ok; ++dx) {
+          const int xx = bx + dx < 0 ? m.gx - 1 : (bx + dx == m.gx ? 0 : bx + dx);
+          ok = wait_at_least(m, m.done + yy * m.gx + xx, uint32_t(s));
+        }
+      }
+    }
+    // the slot's previous step (s - ring) must have its sums formed
+    if (OUT && ok && s >= m.ring) ok = wait_at_least(m, m.fin + slot, uint32_t(s - m.ring + 1));
+    s_go = ok;
+  }
+  __syncthreads();
+  if (!s_go) return false;
+  step_block<S, MODE, true, true, true>(p, bx, by, m.gx, psum, pcnt);
+  __syncthreads();  // every store of the block precedes thread 0's release
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release_u32(m.done + b, uint32_t(s + 1));
+    s_fin = OUT && atomicAdd(m.ticket + slot, 1u) == uint32_t(m.nblocks - 1);
+  }
+  __syncthreads();
+  if (OUT && s_fin) {
+    __threadfence();
+    const bool last = s == m.nsteps - 1;
+    finalize_sums<S, kThreads>(psum, pcnt, m.nblocks, last ? p.stat_sums : m.ring_sums + 3 * slot,
+                               last ? p.stat_counts : m.ring_counts + 3 * slot);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      m.ticket[slot] = 0u;
+      __threadfence();
+      st_release_u32(m.fin + slot, uint32_t(s + 1));
+    }
+  }
+  return true;
+}
+
+// pa: buffer A -> B (even steps); pb: B -> A (odd steps).
+template <class S, int MODE>
+__global__ void __launch_bounds__(kThreads, KSS_STEP_MIN_BLOCKS)
+step_kernel_multi(const StepParams<S> pa, const StepParams<S> pb, const MultiState m) {
+  __shared__ int s_next;
+  if (threadIdx.x == 0) s_next = int(atomicAdd(m.work, 1u));
+  __syncthreads();
+  int w = s_next;
+  const int total = m.nsteps * m.nblocks;
+  while (w < total) {
+    const int s = w / m.nblocks, b = w - s * m.nblocks;
+    __syncthreads();  // every thread has read s_next before thread 0 rewrites it
+    const bool ok = (s & 1) ? multi_block<S, MODE>(pb, m, s, b, &s_next)
+                            : multi_block<S, MODE>(pa, m, s, b, &s_next);
+    if (!ok) return;
+    __syncthreads();
+    w = s_next;
+  }
 }
 
 // ---------------------------------------------------------------- batched step ----

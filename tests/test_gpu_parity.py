@@ -455,3 +455,38 @@ def test_populations_do_not_depend_on_the_outputs(prec, kernel):
         lat.close()
     for st in states[1:]:
         np.testing.assert_array_equal(st, states[0])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "fp16dev"])
+@pytest.mark.parametrize("every", [1, 0])
+@pytest.mark.parametrize("nx,ny,nsteps", [(37, 21, 5), (1024, 640, 6), (2048, 2048, 7)])
+def test_multi_step_launch_equals_single_steps(prec, every, nx, ny, nsteps):
+    """kss_step(n) with every step an output step runs, on FP32 and FP64 storage, as one
+    cooperative multi-step launch whose blocks wait only on their neighbours; it must give
+    exactly the results of n single-step launches (populations, flags, tile counts,
+    counts, sums and the recorded field).  (FP16 deviations and plain steps take one
+    launch per step either way.)"""
+    kss = _kss()
+    rho, ux, uy = inputs.smooth_jump(nx, ny, seed=nx + nsteps, kmax=6)
+    lats = []
+    for _ in range(2):
+        lat = kss.Lattice(nx, ny, precision=prec, tau=0.62, output_every=every,
+                          record=("kl",), rho0=1.5)
+        lat.set_fields(rho, ux, uy)
+        lats.append(lat)
+    lats[0].step(nsteps)
+    for _ in range(nsteps):
+        lats[1].step(1)
+    a, b = lats
+    assert a.step_count == b.step_count == nsteps
+    np.testing.assert_array_equal(a.get_populations(), b.get_populations())
+    if every:
+        fa, ta, ca = a.read_flags()
+        fb, tb, cb = b.read_flags()
+        np.testing.assert_array_equal(fa, fb)
+        np.testing.assert_array_equal(ta, tb)
+        np.testing.assert_array_equal(ca, cb)
+        np.testing.assert_array_equal(a.read_stats()[0], b.read_stats()[0])
+        np.testing.assert_array_equal(a.read_sensor("kl"), b.read_sensor("kl"))
+    for lat in lats:
+        lat.close()
