@@ -61,6 +61,10 @@ def lib():
             "orc_step": (None, [ci, ci, cd, dp, dp]),
             "orc_moments": (None, [ci, ci, dp, dp, dp, dp]),
             "orc_cell_sensors": (ci, [dp, cd, dp]),
+            "orc_cell_sensors_model": (ci, [dp, cd, ci, dp]),
+            "orc_quasi_equilibrium": (None, [dp, dp]),
+            "orc_collide_aar": (None, [ci, ci, cd, cd, u8p, dp, dp]),
+            "orc_sensor_fields_model": (None, [ci, ci, cd, ci, dp, ci, dp, u8p]),
             "orc_cell_log_sensors_literal": (None, [dp, cd, dp, dp]),
             "orc_alpha_poly": (cd, [dp, dp]),
             "orc_alpha_exact": (cd, [dp]),
@@ -137,11 +141,38 @@ def moments(f):
     return rho, ux, uy
 
 
-def cell_sensors(ft, tau: float):
+def cell_sensors(ft, tau: float, two_relax: bool = False):
+    """All sensors of one cell's populations ft[9]; two_relax: the collision model is
+    the two-relaxation one (its quasi-equilibrium enters eps_qe), else BGK."""
     ft = _f64(ft)
     out = np.empty(NSENS)
-    nonpos = lib().orc_cell_sensors(_p(ft), tau, _p(out))
+    nonpos = lib().orc_cell_sensors_model(_p(ft), tau, int(two_relax), _p(out))
     return out, bool(nonpos)
+
+
+def quasi_equilibrium(ft) -> np.ndarray:
+    """f* of the two-relaxation model for one cell's populations ft[9] (orc.h)."""
+    ft = _f64(ft)
+    out = np.empty(9)
+    lib().orc_quasi_equilibrium(_p(ft), _p(out))
+    return out
+
+
+def collide_aar(ft, tau1: float, tau2: float, region) -> np.ndarray:
+    """Eq. new_collision_fi with the two-relaxation quasi-equilibrium where region != 0,
+    BGK elsewhere, of an already-streamed state ft[9, ny, nx]."""
+    ft = _f64(ft)
+    region = np.ascontiguousarray(region, dtype=np.uint8)
+    assert region.shape == ft.shape[1:]
+    out = np.empty_like(ft)
+    lib().orc_collide_aar(ft.shape[2], ft.shape[1], tau1, tau2, _p(region, ctypes.c_uint8),
+                          _p(ft), _p(out))
+    return out
+
+
+def step_aar(f, tau1: float, tau2: float, region) -> np.ndarray:
+    """One step (pull streaming, then collide_aar)."""
+    return collide_aar(stream(f), tau1, tau2, region)
 
 
 def cell_log_sensors_literal(ft, tau: float):
@@ -162,14 +193,15 @@ def alpha_exact(ft) -> float:
     return lib().orc_alpha_exact(_p(_f64(ft)))
 
 
-def sensor_fields(f, tau: float, pull: bool = True):
-    """All sensors of the state (streamed first when pull=True): ([13, ny, nx], nonpos)."""
+def sensor_fields(f, tau: float, pull: bool = True, two_relax: bool = False):
+    """All sensors of the state (streamed first when pull=True): ([13, ny, nx], nonpos).
+    two_relax: eps_qe of the two-relaxation model (else of BGK, identically 0)."""
     f = _f64(f)
     ny, nx = f.shape[1:]
     out = np.empty((NSENS, ny, nx))
     nonpos = np.empty((ny, nx), dtype=np.uint8)
-    lib().orc_sensor_fields(nx, ny, tau, _p(f), int(pull), _p(out),
-                            _p(nonpos, ctypes.c_uint8))
+    lib().orc_sensor_fields_model(nx, ny, tau, int(two_relax), _p(f), int(pull), _p(out),
+                                  _p(nonpos, ctypes.c_uint8))
     return out, nonpos
 
 
@@ -219,6 +251,37 @@ def run(f, tau: float, nsteps: int, sensor_r: int, thr_r: float, sensor_s: int,
                   _p(tiles, ctypes.c_int32), _p(counts, ctypes.c_int64), _p(sm))
     return {"f": f, "eps_r": rec, "flags": fl, "tiles": tiles, "counts": counts,
             "sums": sm}
+
+
+def run_aar(f, tau: float, tau2: float, nsteps: int, output_every: int = 1,
+            refine=("kn", 1e-3), switch=("neq", 1e-4), tile: int = 16, region=None):
+    """nsteps steps of adaptive algorithm refinement from the state f.
+
+    Step n: stream; on output steps (n % output_every == 0) all sensors of the
+    streamed state (eps_qe of the two-relaxation model), the flags and the sums;
+    collide with the two-relaxation model in the region in force (that of the most
+    recent output step before n: its switch flags; `region` (default: empty) before
+    the first one); after an output step the region is its switch flags.
+    Returns a dict: f, region, and of the last output step (None if there was none)
+    sensors, flags, tiles, counts, sums."""
+    f = _f64(f).copy()
+    ny, nx = f.shape[1:]
+    reg = (np.zeros((ny, nx), dtype=np.uint8) if region is None
+           else (np.asarray(region) != 0).astype(np.uint8))
+    rs, rt = SENSOR_ID.get(refine[0], refine[0]), refine[1]
+    ss, st = SENSOR_ID.get(switch[0], switch[0]), switch[1]
+    last = dict(sensors=None, flags=None, tiles=None, counts=None, sums=None)
+    for n in range(1, nsteps + 1):
+        ft = stream(f)
+        out = output_every > 0 and n % output_every == 0
+        if out:
+            sens, nonpos = sensor_fields(ft, tau, pull=False, two_relax=True)
+            fl, tl, cnt = flags(sens[rs], rt, sens[ss], st, nonpos, tile)
+            last = dict(sensors=sens, flags=fl, tiles=tl, counts=cnt, sums=sums(ft))
+        f = collide_aar(ft, tau, tau2, reg)
+        if out:
+            reg = ((last["flags"] & 0x02) != 0).astype(np.uint8)
+    return dict(f=f, region=reg, **last)
 
 
 def adjoint_kl(rho0, ux0, uy0, tau: float, nsteps: int, weight=None, store_every: int = 1):

@@ -108,6 +108,61 @@ void orc_step(int nx, int ny, double tau, const double* f, double* fnext) {
   free(ft);
 }
 
+/* ---------------------------------------------------------------- AAR ----
+ * Adaptive algorithm refinement (section "Conclusions"): where a sensor flags a cell,
+ * the single-relaxation BGK model gives way to a two-relaxation model, Eq.
+ * new_collision_fi with a quasi-equilibrium f* distinct from f^eq.
+ *
+ * Reading for the single-distribution D2Q9 lattice.  The quasi-equilibria of the
+ * paper are Grad-Hermite expansions built from the equilibrium moments plus the
+ * quasi-conserved fields (section "Kinetic model": pressure tensor or heat flux).
+ * Without an energy equation, the slow field kept here is the heat-flux-like one:
+ * the odd (third-order) non-equilibrium moments, which are exactly the odd part of
+ * f^neq under the velocity reversal i -> -i,
+ *   f*_i = f^eq_i + (f^neq_i - f^neq_{-i}) / 2,   f^neq = f - f^eq.
+ * tau1 (the lattice's tau) relaxes f toward f*, i.e. the even part of f^neq (the
+ * stress, so nu = c_s^2 (tau1 - 1/2)); tau2 relaxes f* toward f^eq, i.e. the odd
+ * part.  f* has the density and momentum of f, so both are conserved; tau2 = tau1
+ * is BGK. */
+static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6}; /* c_{OPP[i]} = -c_i */
+
+void orc_quasi_equilibrium(const double ft[9], double fstar[9]) {
+  double rho, ux, uy, feq[9];
+  cell_moments(ft, &rho, &ux, &uy);
+  orc_equilibrium(rho, ux, uy, feq);
+  for (int q = 0; q < 9; ++q) {
+    const double odd = 0.5 * ((ft[q] - feq[q]) - (ft[OPP[q]] - feq[OPP[q]]));
+    fstar[q] = feq[q] + odd;
+  }
+}
+
+/* Eq. new_collision_fi, added with dt = 1: in cells with region != 0
+ *   Omega_i = -(f_i - f*_i)/tau1 - (f*_i - f^eq_i)/tau2,
+ * elsewhere the BGK operator of orc_collide (computed by the same expression). */
+void orc_collide_aar(int nx, int ny, double tau1, double tau2, const uint8_t* region,
+                     const double* ft, double* fnext) {
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      double c[9], feq[9], rho, ux, uy;
+      for (int q = 0; q < 9; ++q) c[q] = ft[at(nx, ny, q, i, j)];
+      cell_moments(c, &rho, &ux, &uy);
+      orc_equilibrium(rho, ux, uy, feq);
+      if (region[(size_t)j * nx + i]) {
+        double fstar[9];
+        orc_quasi_equilibrium(c, fstar);
+        for (int q = 0; q < 9; ++q) {
+          const double omega = -(c[q] - fstar[q]) / tau1 - (fstar[q] - feq[q]) / tau2;
+          fnext[at(nx, ny, q, i, j)] = c[q] + omega;
+        }
+      } else {
+        for (int q = 0; q < 9; ++q) {
+          const double omega = -(c[q] - feq[q]) / tau1;
+          fnext[at(nx, ny, q, i, j)] = c[q] + omega;
+        }
+      }
+    }
+}
+
 void orc_moments(int nx, int ny, const double* f, double* rho, double* ux, double* uy) {
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
@@ -230,6 +285,11 @@ double orc_alpha_exact(const double ft[9]) {
  * positivity is not guaranteed by Grad-Hermite equilibria): if any ft_q <= 0
  * or f^eq_q <= 0, Kn and the five entropy-based sensors are +Inf.        */
 int orc_cell_sensors(const double ft[9], double tau, double out[ORC_NSENS]) {
+  return orc_cell_sensors_model(ft, tau, 0, out);
+}
+
+int orc_cell_sensors_model(const double ft[9], double tau, int two_relax,
+                           double out[ORC_NSENS]) {
   double rho, ux, uy, feq[9], fneq[9];
   cell_moments(ft, &rho, &ux, &uy);
   orc_equilibrium(rho, ux, uy, feq);
@@ -282,12 +342,18 @@ int orc_cell_sensors(const double ft[9], double tau, double out[ORC_NSENS]) {
     out[ORC_QH] = sqrt(qh[0] * qh[0] + qh[1] * qh[1]);
   }
   {
+    /* f*: the equilibrium itself for BGK, else the quasi-equilibrium of the
+     * two-relaxation model (orc_quasi_equilibrium) */
+    double fstar[9];
+    if (two_relax)
+      orc_quasi_equilibrium(ft, fstar);
+    else
+      for (int q = 0; q < 9; ++q) fstar[q] = feq[q];
     double kn = 0.0, neq = 0.0, qe = 0.0;
     for (int q = 0; q < 9; ++q) {
       kn += fabs(fneq[q] / feq[q]);
       neq += fabs(fneq[q]);
-      const double fstar = feq[q]; /* BGK: the quasi-equilibrium is the equilibrium */
-      qe += fabs(fstar - feq[q]);
+      qe += fabs(fstar[q] - feq[q]);
     }
     out[ORC_KN] = kn;
     out[ORC_NEQ] = neq;
@@ -372,6 +438,11 @@ void orc_cell_log_sensors_literal(const double ft[9], double tau, double out[4],
 
 void orc_sensor_fields(int nx, int ny, double tau, const double* f, int pull, double* out,
                        uint8_t* nonpos) {
+  orc_sensor_fields_model(nx, ny, tau, 0, f, pull, out, nonpos);
+}
+
+void orc_sensor_fields_model(int nx, int ny, double tau, int two_relax, const double* f,
+                             int pull, double* out, uint8_t* nonpos) {
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       double c[9], s[ORC_NSENS];
@@ -380,7 +451,7 @@ void orc_sensor_fields(int nx, int ny, double tau, const double* f, int pull, do
         const int sj = pull ? wrap(j - CY[q], ny) : j;
         c[q] = f[at(nx, ny, q, si, sj)];
       }
-      const int np = orc_cell_sensors(c, tau, s);
+      const int np = orc_cell_sensors_model(c, tau, two_relax, s);
       for (int k = 0; k < ORC_NSENS; ++k) out[at(nx, ny, k, i, j)] = s[k];
       if (nonpos) nonpos[(size_t)j * nx + i] = (uint8_t)np;
     }

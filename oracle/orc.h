@@ -67,6 +67,16 @@ void orc_collide(int nx, int ny, double tau, const double* ft, double* fnext);
 /* One full lattice step: stream then collide. */
 void orc_step(int nx, int ny, double tau, const double* f, double* fnext);
 
+/* Two-relaxation model of adaptive algorithm refinement (section "Conclusions"),
+ * single-distribution D2Q9 reading: the quasi-equilibrium keeps the odd part of the
+ * non-equilibrium populations, f*_i = f^eq_i + (f^neq_i - f^neq_{-i})/2, of the
+ * cell's populations ft[9] (orc_quasi_equilibrium); orc_collide_aar applies Eq.
+ * new_collision_fi with it (tau1, tau2) where region[ny][nx] != 0 and BGK (tau1)
+ * elsewhere, to an already-streamed state. */
+void orc_quasi_equilibrium(const double ft[9], double fstar[9]);
+void orc_collide_aar(int nx, int ny, double tau1, double tau2, const uint8_t* region,
+                     const double* ft, double* fnext);
+
 /* Moments (Eqs. eq_quadratur1-2) of a state: rho, ux, uy fields [ny][nx]. */
 void orc_moments(int nx, int ny, const double* f, double* rho, double* ux, double* uy);
 
@@ -74,6 +84,11 @@ void orc_moments(int nx, int ny, const double* f, double* rho, double* ux, doubl
  * state the collision acts on).  Returns 1 if any ft_q <= 0 or f^eq_q <= 0
  * (then the logarithmic sensors and the Knudsen sensor are +Inf), else 0.  */
 int orc_cell_sensors(const double ft[9], double tau, double out[ORC_NSENS]);
+/* The same for a given collision model: two_relax = 0 is BGK (f* = f^eq, so
+ * ORC_QE = 0), two_relax = 1 the two-relaxation model (ORC_QE = sum |f* - f^eq|
+ * with the quasi-equilibrium of orc_quasi_equilibrium). */
+int orc_cell_sensors_model(const double ft[9], double tau, int two_relax,
+                           double out[ORC_NSENS]);
 
 /* The four logarithmic sensors (HR, KL, SIGMA_H, SIGMA_KL) evaluated in their
  * literal printed form, for the consistency check of the cancellation-free
@@ -97,6 +112,8 @@ double orc_alpha_exact(const double ft[9]);
  * out is [ORC_NSENS][ny][nx]; nonpos is [ny][nx] (may be NULL). */
 void orc_sensor_fields(int nx, int ny, double tau, const double* f, int pull,
                        double* out, uint8_t* nonpos);
+void orc_sensor_fields_model(int nx, int ny, double tau, int two_relax, const double* f,
+                             int pull, double* out, uint8_t* nonpos);
 
 /* Tagging (regrid step 1): flag bit0 = refine (eps_r > thr_r), bit1 = switch
  * (thr_s >= 0 and eps_s > thr_s), bit7 = non-positive population.  Tile counts
