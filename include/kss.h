@@ -75,7 +75,8 @@ typedef enum {
   KSS_S_QH = 4,       /* Eq. sensor-qH-kin:     |u . P^neq|_2                           */
   KSS_S_KN = 5,       /* Eq. sensor-Knudsen-kin_f: sum |f^neq / f^eq| (not averaged)    */
   KSS_S_NEQ = 6,      /* Eq. sensor-neq-kin:    sum |f^neq|                             */
-  KSS_S_QE = 7,       /* Eq. Sensor-qe-kin:     sum |f* - f^eq|, identically 0 for BGK  */
+  KSS_S_QE = 7,       /* Eq. Sensor-qe-kin:     sum |f* - f^eq|: 0 for BGK (tau2 = 0);  */
+                      /*   with tau2 > 0 the two-relaxation quasi-equilibrium (below)   */
   KSS_S_HR = 8,       /* Eq. Hneq-sensor:       |H(f) - H(f^eq)|, H = sum f ln(f/w)     */
   KSS_S_KL = 9,       /* Eq. HKL-sensor:        |sum f ln(f / f^eq)|                    */
   KSS_S_SIGMA_H = 10, /* Eq. Dissip-H-sensor:   -sum Omega ln(f/w), Omega = -f^neq/tau  */
@@ -113,6 +114,9 @@ typedef struct {
   double rho0;               /* KSS_FP16DEV: reference density of the deviations, > 0  */
   int32_t dev_exp;           /* KSS_FP16DEV: scale exponent K (-24 .. 40)              */
   int32_t dev_unscaled;      /* KSS_FP16DEV: 1 = literal deviations (s_q = 1)          */
+  double tau2;               /* adaptive algorithm refinement: 0 = BGK everywhere; > 0.5 */
+                             /*   = the two-relaxation model (tau1 = tau, tau2) in the  */
+                             /*   cells of the switched region (see kss_set_aar_region) */
 } kss_config;
 
 /* Step kernels (same results; they differ in how source rows reach the SM):
@@ -131,7 +135,7 @@ typedef struct kss_lattice kss_lattice;  /* opaque */
 /* Fill *cfg with defaults for an nx x ny lattice: tau 0.8, refine on KSS_S_KN at 1e-3,
  * switch on KSS_S_NEQ at 1e-4, record KSS_S_KL, output every step, tile 16, the CUDA
  * default stream, rho0 = 1, dev_exp = 12 (relative deviations up to about 15 stay in
- * FP16 range), dev_unscaled = 0. */
+ * FP16 range), dev_unscaled = 0, tau2 = 0 (BGK everywhere). */
 int kss_config_default(kss_config* cfg, int32_t nx, int32_t ny, int32_t precision);
 
 /* Create a lattice (device buffers allocated; populations zero until set). */
@@ -178,6 +182,27 @@ int kss_read_flags(kss_lattice* lat, uint8_t* flags, int32_t* tile_counts, int64
  * bitwise reproducible for a given lattice and configuration) and counts[3] of the
  * same state, and the step index it belongs to.  Host pointers; any may be NULL. */
 int kss_read_stats(kss_lattice* lat, double sums[3], int64_t counts[3], int64_t* step);
+
+/* ---- Adaptive algorithm refinement (section "Conclusions": a sensor selects the cells
+ * where the single-relaxation BGK model gives way to a two-relaxation model) ----------
+ * With kss_config.tau2 > 0 the lattice keeps a switched region, one byte per cell.  The
+ * collision of step n is Eq. new_collision_fi with tau1 = tau and tau2 in the cells of
+ * the region and BGK elsewhere; its quasi-equilibrium keeps the odd part of the
+ * non-equilibrium populations,
+ *   f*_q = f^eq_q + (f^neq_q - f^neq_-q)/2   (-q: the opposite velocity),
+ * so tau1 relaxes the even part of f^neq (the stress: nu = c_s^2 (tau - 1/2)) and tau2
+ * the odd, third-order part; density and momentum are conserved.  KSS_S_QE is then
+ * sum |f* - f^eq| = sum over the four pairs of |f^neq_q - f^neq_-q|, in every cell (the
+ * quasi-equilibrium is a function of the state), and can serve as the switch sensor.
+ * The region in force at step n is the switch flags (KSS_FLAG_SWITCH) of the most
+ * recent output step before n; an output step replaces it with its own flags.  It is
+ * empty after kss_create, kss_set_fields and kss_set_populations, and
+ * kss_set_aar_region replaces it (nx*ny bytes, nonzero = two-relaxation; get returns
+ * 0 / 1).  KSS_ERR_STATE on a lattice with tau2 = 0.  AAR steps run on the vector
+ * kernel, one launch per step; batch members must have tau2 = 0 (else
+ * KSS_ERR_UNSUPPORTED from kss_batch_create). */
+int kss_set_aar_region(kss_lattice* lat, const uint8_t* region, int on_device);
+int kss_get_aar_region(kss_lattice* lat, uint8_t* region, int on_device);
 
 /* Steps taken since the last set. */
 int kss_get_step(const kss_lattice* lat, int64_t* step);

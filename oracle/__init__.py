@@ -262,8 +262,9 @@ def run_aar(f, tau: float, tau2: float, nsteps: int, output_every: int = 1,
     collide with the two-relaxation model in the region in force (that of the most
     recent output step before n: its switch flags; `region` (default: empty) before
     the first one); after an output step the region is its switch flags.
-    Returns a dict: f, region, and of the last output step (None if there was none)
-    sensors, flags, tiles, counts, sums."""
+    Returns a dict: f, region, switch_margin (the smallest |eps_s - thr_s| of any cell
+    at any output step: how far every switch decision was from the threshold), and of
+    the last output step (None if there was none) sensors, flags, tiles, counts, sums."""
     f = _f64(f).copy()
     ny, nx = f.shape[1:]
     reg = (np.zeros((ny, nx), dtype=np.uint8) if region is None
@@ -271,17 +272,19 @@ def run_aar(f, tau: float, tau2: float, nsteps: int, output_every: int = 1,
     rs, rt = SENSOR_ID.get(refine[0], refine[0]), refine[1]
     ss, st = SENSOR_ID.get(switch[0], switch[0]), switch[1]
     last = dict(sensors=None, flags=None, tiles=None, counts=None, sums=None)
+    margin = float("inf")
     for n in range(1, nsteps + 1):
         ft = stream(f)
         out = output_every > 0 and n % output_every == 0
         if out:
             sens, nonpos = sensor_fields(ft, tau, pull=False, two_relax=True)
             fl, tl, cnt = flags(sens[rs], rt, sens[ss], st, nonpos, tile)
+            margin = min(margin, float(np.min(np.abs(sens[ss] - st))))
             last = dict(sensors=sens, flags=fl, tiles=tl, counts=cnt, sums=sums(ft))
         f = collide_aar(ft, tau, tau2, reg)
         if out:
             reg = ((last["flags"] & 0x02) != 0).astype(np.uint8)
-    return dict(f=f, region=reg, **last)
+    return dict(f=f, region=reg, switch_margin=margin, **last)
 
 
 def adjoint_kl(rho0, ux0, uy0, tau: float, nsteps: int, weight=None, store_every: int = 1):

@@ -154,17 +154,40 @@ __device__ __forceinline__ T pick(const T (&sv)[S_COUNT], int id) {
   }
 }
 
+// Two-relaxation model of adaptive algorithm refinement (section "Conclusions"), in
+// cells of the switched region: Eq. new_collision_fi with the quasi-equilibrium
+// f*_q = f^eq_q + (f^neq_q - f^neq_-q)/2 (the odd part of f^neq kept), i.e.
+//   f'_q = f_q - A f^neq_q - B f^neq_-q,  A = (1/tau1 + 1/tau2)/2,  B = (1/tau1 - 1/tau2)/2,
+// and f'_0 = f_0 - f^neq_0 / tau1.  Outside the region A = 1/tau1 and B = 0, which gives
+// the BGK update bit for bit (a zero product added).
+template <class T>
+struct Trt {
+  T a = T(0), b = T(0);  // A and B of a switched cell
+  bool qe = false;       // the lattice's model is the two-relaxation one: eps_qe is
+                         // sum |f* - f^eq| (else f* = f^eq and eps_qe = 0)
+};
+
+// Index of the opposite velocity, c_{opp(q)} = -c_q: 0; 1 <-> 3, 2 <-> 4; 5 <-> 7, 6 <-> 8.
+__host__ __device__ constexpr int opp(int q) {
+  return q == 0 ? 0 : (q <= 4 ? ((q + 1) & 3) + 1 : ((q - 3) & 3) + 5);
+}
+static_assert(opp(1) == 3 && opp(2) == 4 && opp(3) == 1 && opp(4) == 2 && opp(5) == 7 &&
+                  opp(6) == 8 && opp(7) == 5 && opp(8) == 6 && opp(0) == 0,
+              "opposite velocities");
+
 // One cell: moments of the post-streaming populations ft, equilibrium, the sensors
-// of the compiled set, and (COLLIDE) the BGK update fo = ft - (ft - f^eq)/tau.
+// of the compiled set, and (COLLIDE) the BGK update fo = ft - (ft - f^eq)/tau, or
+// (AAR) the two-relaxation update in a switched cell (sw).
 //
 // Logarithmic sensors use x = f^neq/f^eq, phi(x) and sum_q f^neq_q = 0 (rho of ft
 // and of f^eq coincide), so no O(1) terms cancel:
 //   KL = |sum f^eq phi(x)|,  HR = |sum f^neq L + sum f^eq phi(x)|,
 //   sigma_H = (sum f^neq L + sum f^neq ln(1+x)) / tau,
 //   sigma_KL = sum f^neq ln(1+x) / tau,   L_q = ln(f^eq_q / (w_q rho)).
-template <class T, int MODE, bool COLLIDE>
+template <class T, int MODE, bool COLLIDE, bool AAR = false>
 __device__ __forceinline__ void cell_update(const T (&ft)[9], T omega, T tau, T (&fo)[9],
-                                            CellOut<T>& o) {
+                                            CellOut<T>& o, const Trt<T>& trt = Trt<T>{},
+                                            bool sw = false) {
   const T rho = ((ft[0] + ft[1]) + (ft[2] + ft[3])) + ((ft[4] + ft[5]) + (ft[6] + ft[7])) + ft[8];
   const T jx = (ft[1] + ft[5] + ft[8]) - (ft[3] + ft[6] + ft[7]);
   const T jy = (ft[2] + ft[5] + ft[6]) - (ft[4] + ft[7] + ft[8]);
@@ -176,8 +199,18 @@ __device__ __forceinline__ void cell_update(const T (&ft)[9], T omega, T tau, T 
   o.jx = jx;
   o.jy = jy;
   if (COLLIDE) {
+    if constexpr (AAR) {
+      const T A = sw ? trt.a : omega, B = sw ? trt.b : T(0);
+      T d[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) fo[q] = fma(-omega, ft[q] - feq[q], ft[q]);
+      for (int q = 0; q < 9; ++q) d[q] = ft[q] - feq[q];
+      fo[0] = fma(-omega, d[0], ft[0]);
+#pragma unroll
+      for (int q = 1; q < 9; ++q) fo[q] = fma(-B, d[opp(q)], fma(-A, d[q], ft[q]));
+    } else {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) fo[q] = fma(-omega, ft[q] - feq[q], ft[q]);
+    }
   }
   if (MODE == MODE_PLAIN) {
     o.nonpos = false;
@@ -219,7 +252,11 @@ __device__ __forceinline__ void cell_update(const T (&ft)[9], T omega, T tau, T 
     const T qx = fma(ux, pxx, uy * pxy), qy = fma(ux, pxy, uy * pyy);
     o.sv[S_QH] = Num<T>::sqrt_(fma(qx, qx, qy * qy));
   }
-  o.sv[S_QE] = T(0);  // BGK: the quasi-equilibrium is the equilibrium
+  // sum_q |f*_q - f^eq_q| = sum_q |f^neq_q - f^neq_-q| / 2 = sum over the 4 pairs of
+  // |f^neq_q - f^neq_-q|; 0 for BGK, whose quasi-equilibrium is the equilibrium
+  o.sv[S_QE] = trt.qe ? (fabs(fneq[1] - fneq[3]) + fabs(fneq[2] - fneq[4])) +
+                            (fabs(fneq[5] - fneq[7]) + fabs(fneq[6] - fneq[8]))
+                      : T(0);
 
   // ---- entropy-based sensors ----
   // L_q = ln(f^eq_q / (w_q rho)) = ln(1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u)

@@ -331,6 +331,10 @@ int kss_batch_create(int32_t n, const kss_config* cfgs, kss_batch** out) {
   if (n < 1 || !cfgs) return KSS_ERR_ARG;
   for (int k = 1; k < n; ++k)
     if (cfgs[k].precision != cfgs[0].precision) return KSS_ERR_ARG;
+  // batched steps run the BGK collision only (adaptive algorithm refinement is a
+  // single-lattice option)
+  for (int k = 0; k < n; ++k)
+    if (cfgs[k].tau2 != 0.0) return KSS_ERR_UNSUPPORTED;
   kss_batch* B = new (std::nothrow) kss_batch();
   if (!B) return KSS_ERR_OOM;
   B->n = n;

@@ -35,6 +35,7 @@ int check_config(const kss_config* c) {
     if (c->dev_unscaled != 0 && c->dev_unscaled != 1) return KSS_ERR_ARG;
   }
   if (!(c->tau > 0.5) || !std::isfinite(c->tau)) return KSS_ERR_ARG;
+  if (c->tau2 != 0.0 && (!(c->tau2 > 0.5) || !std::isfinite(c->tau2))) return KSS_ERR_ARG;
   if (!valid_sensor(c->refine_sensor) || !valid_sensor(c->switch_sensor)) return KSS_ERR_ARG;
   if (std::isnan(c->refine_threshold) || std::isnan(c->switch_threshold)) return KSS_ERR_ARG;
   if (c->record_mask >> KSS_S_COUNT) return KSS_ERR_ARG;
@@ -59,6 +60,7 @@ template <class S>
 cudaError_t launch_one_step(kss_lattice* L, bool out) {
   kss::StepParams<S> p = make_params<S>(L, L->f[L->cur], L->f[L->cur ^ 1]);
   const int mode = out ? mode_for(needed_mask(L, L->cfg.record_mask)) : MODE_PLAIN;
+  if (L->region) return kss::launch_step_aar<S>(p, mode, L->stream);
   // (the vector kernel recomputes its deferred cells itself, at the end of each CTA; FP16
   // deviation storage has the vector kernel only)
   if constexpr (std::is_same<S, __half>::value) {
@@ -165,6 +167,17 @@ cudaError_t launch_eval(kss_lattice* L, int sensor) {
   return kss::launch_step<S>(p, mode_for(needed_mask(L, extra)), pull, false, L->stream);
 }
 
+// Region bytes as the kernels write them: 1 for a switched cell, 0 otherwise.
+__global__ void region_to_01_kernel(uint8_t* r, int pitch, int nx, int ny) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int j = blockIdx.y; j < ny; j += gridDim.y) {
+    if (i < nx) {
+      uint8_t* c = r + (long long)j * pitch + i;
+      *c = *c != 0;
+    }
+  }
+}
+
 int ensure_staging(kss_lattice* L, size_t elems) {
   if (L->staging_elems >= elems) return KSS_OK;
   if (L->staging) {
@@ -243,6 +256,7 @@ void release(kss_lattice* L) {
   cudaStreamSynchronize(L->stream);
   regrid_release(L);
   if (L->multi) cudaFree(L->multi);
+  if (L->region) cudaFree(L->region);
   void* bufs[] = {L->f[0], L->f[1], L->rec, L->evalplane, L->flags, L->tiles, L->part_sum,
                   L->part_cnt, L->small, L->staging, L->defer_list};
   for (void* b : bufs)
@@ -293,6 +307,7 @@ int kss_config_default(kss_config* c, int32_t nx, int32_t ny, int32_t precision)
   c->rho0 = 1.0;
   c->dev_exp = 12;
   c->dev_unscaled = 0;
+  c->tau2 = 0.0;
   return KSS_OK;
 }
 
@@ -395,6 +410,20 @@ int kss_create(const kss_config* cfg, kss_lattice** out) {
       return KSS_ERR_CUDA;
     }
   }
+  if (cfg->tau2 > 0.0) {
+    const size_t bytes = size_t(L->pitch) * cfg->ny;
+    if (cudaMalloc(&L->region, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      L->region = nullptr;
+      release(L);
+      return KSS_ERR_OOM;
+    }
+    if (cudaMemsetAsync(L->region, 0, bytes, L->stream) != cudaSuccess) {
+      cudaGetLastError();
+      release(L);
+      return KSS_ERR_CUDA;
+    }
+  }
   L->done = reinterpret_cast<uint32_t*>(L->small);
   L->stat_sums = reinterpret_cast<double*>(L->small + 64);
   L->stat_counts = reinterpret_cast<unsigned long long*>(L->small + 128);
@@ -414,10 +443,14 @@ void kss_destroy(kss_lattice* L) {
   release(L);
 }
 
-static void reset_after_set(kss_lattice* L) {
+// A new state: step 0, no outputs yet, an empty two-relaxation region.
+static int reset_after_set(kss_lattice* L) {
   L->step = 0;
   L->out_step = L->rec_step = L->eval_step = -1;
   L->eval_sensor = -1;
+  if (L->region)
+    KSS_CUDA(L, cudaMemsetAsync(L->region, 0, size_t(L->pitch) * L->cfg.ny, L->stream));
+  return KSS_OK;
 }
 
 int kss_set_fields(kss_lattice* L, const double* rho, const double* ux, const double* uy,
@@ -445,8 +478,7 @@ int kss_set_fields(kss_lattice* L, const double* rho, const double* ux, const do
                                                     L->stream);
            }));
   if (!on_device) KSS_CUDA(L, cudaStreamSynchronize(L->stream));
-  reset_after_set(L);
-  return KSS_OK;
+  return reset_after_set(L);
 }
 
 int kss_set_populations(kss_lattice* L, const double* f, int on_device) {
@@ -469,8 +501,7 @@ int kss_set_populations(kss_lattice* L, const double* f, int on_device) {
                                                  L->stream);
            }));
   if (!on_device) KSS_CUDA(L, cudaStreamSynchronize(L->stream));
-  reset_after_set(L);
-  return KSS_OK;
+  return reset_after_set(L);
 }
 
 int kss_get_populations(kss_lattice* L, double* f, int on_device) {
@@ -507,7 +538,7 @@ int kss_step(kss_lattice* L, int32_t nsteps) {
   const int every = L->cfg.output_every;
   const int mode = every == 1 ? mode_for(needed_mask(L, L->cfg.record_mask)) : MODE_PLAIN;
   if (KSS_MULTISTEP && nsteps >= 2 && every == 1 && mode == MODE_STD &&
-      L->cfg.precision != KSS_FP16DEV && !use_tma(L, mode) &&
+      L->cfg.precision != KSS_FP16DEV && !use_tma(L, mode) && !L->region &&
       (long long)nsteps * L->nblocks < (1LL << 30)) {
     KSS_CUDA(L, with_storage(L->cfg.precision, [&](auto tag) {
                return launch_multi<typename decltype(tag)::type>(L, mode, nsteps);
@@ -626,6 +657,38 @@ int kss_read_stats(kss_lattice* L, double sums[3], int64_t counts[3], int64_t* s
     for (int k = 0; k < 3; ++k) counts[k] = int64_t(c[k]);
   if (step) *step = L->out_step;
   return c[2] > 0 ? KSS_WARN_NONPOSITIVE : KSS_OK;
+}
+
+int kss_set_aar_region(kss_lattice* L, const uint8_t* region, int on_device) {
+  int rc = enter(L);
+  if (rc) return rc;
+  if (!L->region) return fail(L, KSS_ERR_STATE, "the lattice has no two-relaxation model (tau2 = 0)");
+  if (!region) return fail(L, KSS_ERR_ARG, "null region pointer");
+  DeviceGuard g(L->device);
+  KSS_CUDA(L, cudaMemcpy2DAsync(L->region, size_t(L->pitch), region, size_t(L->cfg.nx),
+                                size_t(L->cfg.nx), size_t(L->cfg.ny),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                L->stream));
+  const int ny = L->cfg.ny;
+  region_to_01_kernel<<<dim3((L->cfg.nx + 255) / 256, ny < 65535 ? ny : 65535), 256, 0,
+                        L->stream>>>(L->region, L->pitch, L->cfg.nx, ny);
+  KSS_CUDA(L, cudaGetLastError());
+  if (!on_device) KSS_CUDA(L, cudaStreamSynchronize(L->stream));
+  return KSS_OK;
+}
+
+int kss_get_aar_region(kss_lattice* L, uint8_t* region, int on_device) {
+  int rc = enter(L);
+  if (rc) return rc;
+  if (!L->region) return fail(L, KSS_ERR_STATE, "the lattice has no two-relaxation model (tau2 = 0)");
+  if (!region) return fail(L, KSS_ERR_ARG, "null region pointer");
+  DeviceGuard g(L->device);
+  KSS_CUDA(L, cudaMemcpy2DAsync(region, size_t(L->cfg.nx), L->region, size_t(L->pitch),
+                                size_t(L->cfg.nx), size_t(L->cfg.ny),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                L->stream));
+  KSS_CUDA(L, cudaStreamSynchronize(L->stream));
+  return device_error(L);
 }
 
 int kss_get_step(const kss_lattice* L, int64_t* step) {

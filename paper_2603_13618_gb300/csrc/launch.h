@@ -26,6 +26,11 @@ template <class T>
 cudaError_t launch_step(const StepParams<T>& p, int mode, bool pull, bool store,
                         cudaStream_t stream);
 
+// One step with adaptive algorithm refinement: the two-relaxation collision in the
+// region p.region (output steps rewrite it); mode as launch_step, always pull + store.
+template <class T>
+cudaError_t launch_step_aar(const StepParams<T>& p, int mode, cudaStream_t stream);
+
 // One batched step (batch_step_kernel): `table` holds one StepParams per lattice
 // (grid_x, nblocks and bands set), `items` the nitems CTA blocks; `ctas` CTAs (<= nitems)
 // stride over the items.  mode MODE_PLAIN / MODE_STD / MODE_FULL; always pull + store.

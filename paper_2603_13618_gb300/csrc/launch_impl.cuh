@@ -79,6 +79,18 @@ cudaError_t launch_step<KSS_T>(const StepParams<KSS_T>& p, int mode, bool pull, 
 }
 
 template <>
+cudaError_t launch_step_aar<KSS_T>(const StepParams<KSS_T>& p, int mode, cudaStream_t stream) {
+  const dim3 grid = step_grid<KSS_T>(p.nx, p.ny, p.tile, p.bands);
+  switch (mode) {
+    case MODE_PLAIN: step_kernel<KSS_T, MODE_PLAIN, true, true, true><<<grid, kThreads, 0, stream>>>(p); break;
+    case MODE_STD: step_kernel<KSS_T, MODE_STD, true, true, true><<<grid, kThreads, 0, stream>>>(p); break;
+    case MODE_FULL: step_kernel<KSS_T, MODE_FULL, true, true, true><<<grid, kThreads, 0, stream>>>(p); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <>
 int multi_resident_ctas<KSS_T>(int mode) {
   return mode == MODE_STD ? resident_ctas<step_kernel_multi<KSS_T, MODE_STD>>() : 0;
 }

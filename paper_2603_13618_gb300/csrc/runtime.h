@@ -70,6 +70,7 @@ struct kss_lattice {
   kss_batch* owner = nullptr;  // the batch that created this lattice, if any
   void* regrid = nullptr;      // regridding workspace (kss_regrid.cu), made on first use
   void* multi = nullptr;       // multi-step kernel bookkeeping, made on first use
+  uint8_t* region = nullptr;   // two-relaxation region [ny][pitch] (cfg.tau2 > 0 only)
 };
 
 namespace kss_rt {
@@ -153,6 +154,13 @@ kss::StepParams<S> make_params(const kss_lattice* L, const void* src, void* dst)
   p.switch_s = L->cfg.switch_sensor;
   for (int s = 0; s < KSS_S_COUNT; ++s) p.rec_slot[s] = L->rec_slot[s];
   p.codec = codec_of<S>(L);
+  p.region = L->region;
+  if (L->cfg.tau2 > 0.0) {
+    const double w1 = 1.0 / L->cfg.tau, w2 = 1.0 / L->cfg.tau2;
+    p.trt.a = T(0.5 * (w1 + w2));
+    p.trt.b = T(0.5 * (w1 - w2));
+    p.trt.qe = true;
+  }
   return p;
 }
 

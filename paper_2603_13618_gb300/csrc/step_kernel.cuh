@@ -183,6 +183,10 @@ struct StepParams {
   int mode;              // the lattice's sensor set on output steps (batched step only)
   int rec_slot[S_COUNT];  // plane index of each recorded sensor, -1 if not recorded
   codec_t<S> codec;      // FP16 deviation codec (empty for float / double storage)
+  uint8_t* region;       // two-relaxation region [ny][pitch], a byte per cell (AAR steps):
+                         // read before the collision, rewritten with the switch flags
+                         // (0 / 1) on output steps
+  Trt<T> trt;            // two-relaxation coefficients, and the model of eps_qe
 };
 
 // ---------------------------------------------------------------- loads ----
@@ -355,6 +359,17 @@ __device__ __forceinline__ void store_flags(uint8_t* p, uint32_t bits) {
   }
 }
 
+// The region bytes of V cells (one per cell, in the low bytes).  An ordinary load: the
+// step rewrites them later in the same launch.
+template <int V>
+__device__ __forceinline__ uint32_t load_bytes(const uint8_t* p) {
+  if constexpr (V == 4) {
+    return *reinterpret_cast<const uint32_t*>(p);
+  } else {
+    return *reinterpret_cast<const uint16_t*>(p);
+  }
+}
+
 // ---------------------------------------------------------------- fused Kn/KL/neq ----
 // Per-cell accumulators of the {Kn, KL, neq} set.
 template <class T>
@@ -426,14 +441,17 @@ __device__ __forceinline__ void relax_pop(T (&f)[Vec<T>::N], const T (&feq)[Vec<
 }
 
 // The pair of opposite populations (+c, -c) with c.u = cu: f^eq = w rho (base + 9/2 cu^2
-// +- 3 cu); both relaxed and (STORE) written out.
-template <class S, bool OUT, bool STORE, int QP, int QM>
+// +- 3 cu); both relaxed and (STORE) written out.  AAR: the cells whose region byte (in
+// mbits, one per cell) is set take the two-relaxation update of cell_update, which
+// couples the pair; the others the BGK update, bit for bit.
+template <class S, bool OUT, bool STORE, int QP, int QM, bool AAR = false>
 __device__ __forceinline__ void pair_pops(arith_t<S> (&fp)[Vec<S>::N], arith_t<S> (&fm)[Vec<S>::N],
                                           const arith_t<S> (&cu)[Vec<S>::N],
                                           const arith_t<S> (&base)[Vec<S>::N],
                                           const arith_t<S> (&rw)[Vec<S>::N], arith_t<S> omega,
                                           StdAcc<arith_t<S>>& a, S* dst_p, S* dst_m,
-                                          const codec_t<S>& codec, bool cv) {
+                                          const codec_t<S>& codec, bool cv, uint32_t mbits = 0,
+                                          const Trt<arith_t<S>>& trt = Trt<arith_t<S>>{}) {
   using T = arith_t<S>;
   constexpr int V = Vec<S>::N;
   T ep[V], em[V];
@@ -442,6 +460,25 @@ __device__ __forceinline__ void pair_pops(arith_t<S> (&fp)[Vec<S>::N], arith_t<S
     const T t = fma(T(4.5) * cu[k], cu[k], base[k]);
     ep[k] = Num<T>::mul(rw[k], fma(T(3), cu[k], t));
     em[k] = Num<T>::mul(rw[k], fma(T(-3), cu[k], t));
+  }
+  if constexpr (AAR) {
+    relax_pop<T, OUT, false>(fp, ep, omega, a);  // the sensors only
+    relax_pop<T, OUT, false>(fm, em, omega, a);
+    if (STORE) {
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        const bool sw = ((mbits >> (8 * k)) & 0xffu) != 0u;
+        const T A = sw ? trt.a : omega, B = sw ? trt.b : T(0);
+        const T np = fp[k] - ep[k], nm = fm[k] - em[k];
+        fp[k] = fma(-B, nm, fma(-A, np, fp[k]));
+        fm[k] = fma(-B, np, fma(-A, nm, fm[k]));
+      }
+      if (cv) {
+        pop_vstore<S>(dst_p, fp, QP, codec);
+        pop_vstore<S>(dst_m, fm, QM, codec);
+      }
+    }
+    return;
   }
   relax_pop<T, OUT, STORE>(fp, ep, omega, a);
   if (STORE && cv) pop_vstore<S>(dst_p, fp, QP, codec);
@@ -639,7 +676,7 @@ __device__ __forceinline__ uint32_t fix_cell(const StepParams<S>& p, const Pick3
 // populations, the flag bytes and the recorded sensor fields.  ft holds the
 // post-streaming populations of cells i0..i0+V-1 of row j.  Returns the lane's flag
 // word (one byte per cell); the row's moments are added to the accumulators.
-template <class S, int MODE, bool PULL, bool STORE>
+template <class S, int MODE, bool PULL, bool STORE, bool AAR = false>
 __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
                                               arith_t<S> (&ft)[9][Vec<S>::N], int i0, int j,
                                               bool cv, Acc<arith_t<S>>& a_rho,
@@ -649,6 +686,12 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
   constexpr bool OUT = MODE != MODE_PLAIN;
   const long long off = (long long)j * p.pitch + i0;
   uint32_t fbits = 0;
+  // AAR: the region in force for this step's collision (the switch flags of the most
+  // recent output step before it); output steps replace it with their own
+  uint32_t mbits = 0;
+  if constexpr (AAR && STORE) {
+    if (cv) mbits = load_bytes<V>(p.region + off);
+  }
   if constexpr (MODE == MODE_FULL) {
     // ---- all sensors of Table 1: cell-major, generic per-cell arithmetic ----
     T fo[9][V];
@@ -659,7 +702,8 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
 #pragma unroll
       for (int q = 0; q < 9; ++q) c[q] = ft[q][k];
       CellOut<T> co;
-      cell_update<T, MODE, STORE>(c, p.omega, p.tau, o9, co);
+      cell_update<T, MODE, STORE, AAR>(c, p.omega, p.tau, o9, co, p.trt,
+                                       ((mbits >> (8 * k)) & 0xffu) != 0u);
       const bool valid = cv && (i0 + k < p.nx);
       if (STORE) {
 #pragma unroll
@@ -683,6 +727,7 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
     }
     if (cv) {
       store_flags<V>(p.flags + off, fbits);
+      if (AAR && STORE) store_flags<V>(p.region + off, (fbits >> 1) & 0x01010101u);
 #pragma unroll
       for (int sid = 0; sid < S_COUNT; ++sid) {
         const int slot = p.rec_slot[sid];
@@ -740,12 +785,12 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
     if (STORE && cv) pop_vstore<S>(p.dst + 0 * p.plane + off, ft[0], 0, p.codec);
     // axis pairs (1, 3): c.u = +-ux ; (2, 4): +-uy ; diagonal pairs (5, 7): +-(ux + uy),
     // (6, 8): +-(uy - ux)
-    pair_pops<S, OUT, STORE, 1, 3>(ft[1], ft[3], ux, base, rw1, p.omega, a,
-                                   p.dst + 1 * p.plane + off, p.dst + 3 * p.plane + off,
-                                   p.codec, cv);
-    pair_pops<S, OUT, STORE, 2, 4>(ft[2], ft[4], uy, base, rw1, p.omega, a,
-                                   p.dst + 2 * p.plane + off, p.dst + 4 * p.plane + off,
-                                   p.codec, cv);
+    pair_pops<S, OUT, STORE, 1, 3, AAR>(ft[1], ft[3], ux, base, rw1, p.omega, a,
+                                        p.dst + 1 * p.plane + off, p.dst + 3 * p.plane + off,
+                                        p.codec, cv, mbits, p.trt);
+    pair_pops<S, OUT, STORE, 2, 4, AAR>(ft[2], ft[4], uy, base, rw1, p.omega, a,
+                                        p.dst + 2 * p.plane + off, p.dst + 4 * p.plane + off,
+                                        p.codec, cv, mbits, p.trt);
     {
       T sd[V];
 #pragma unroll
@@ -753,14 +798,14 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
       T rw2[V];
 #pragma unroll
       for (int k = 0; k < V; ++k) rw2[k] = T(0.25) * rw1[k];
-      pair_pops<S, OUT, STORE, 5, 7>(ft[5], ft[7], sd, base, rw2, p.omega, a,
-                                     p.dst + 5 * p.plane + off, p.dst + 7 * p.plane + off,
-                                     p.codec, cv);
+      pair_pops<S, OUT, STORE, 5, 7, AAR>(ft[5], ft[7], sd, base, rw2, p.omega, a,
+                                          p.dst + 5 * p.plane + off, p.dst + 7 * p.plane + off,
+                                          p.codec, cv, mbits, p.trt);
 #pragma unroll
       for (int k = 0; k < V; ++k) sd[k] = Num<T>::sub(uy[k], ux[k]);
-      pair_pops<S, OUT, STORE, 6, 8>(ft[6], ft[8], sd, base, rw2, p.omega, a,
-                                     p.dst + 6 * p.plane + off, p.dst + 8 * p.plane + off,
-                                     p.codec, cv);
+      pair_pops<S, OUT, STORE, 6, 8, AAR>(ft[6], ft[8], sd, base, rw2, p.omega, a,
+                                          p.dst + 6 * p.plane + off, p.dst + 8 * p.plane + off,
+                                          p.codec, cv, mbits, p.trt);
     }
     if (OUT) {
       const Pick3 pr(p.refine_s), ps(p.switch_s);
@@ -785,6 +830,8 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
       if (nvalid < V) fbits &= nvalid > 0 ? 0xffffffffu >> (32 - 8 * nvalid) : 0u;
       if (cv) {
         store_flags<V>(p.flags + off, fbits);
+        // (a deferred cell's byte is 0x40: its region byte is set by the epilogue)
+        if (AAR && STORE) store_flags<V>(p.region + off, (fbits >> 1) & 0x01010101u);
         if (p.rec_slot[S_KN] >= 0) vstore<T>(p.rec + p.rec_slot[S_KN] * p.plane + off, a.kn);
         if (p.rec_slot[S_KL] >= 0) vstore<T>(p.rec + p.rec_slot[S_KL] * p.plane + off, a.kl);
         if (p.rec_slot[S_NEQ] >= 0) vstore<T>(p.rec + p.rec_slot[S_NEQ] * p.plane + off, a.neq);
@@ -802,7 +849,7 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
 // Block (bx, by) of a lattice whose step grid is gx blocks wide: its rows, then (output
 // modes) its tile counts and its partial sums and counts in slot bid.  Called by every
 // thread of the CTA; the CTA's shared memory is free again when it returns.
-template <class S, int MODE, bool PULL, bool STORE, bool CG = false>
+template <class S, int MODE, bool PULL, bool STORE, bool CG = false, bool AAR = false>
 __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx, const int by,
                                            const int gx, double* part_sum, uint32_t* part_cnt) {
   using T = arith_t<S>;
@@ -872,7 +919,8 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
       for (int q = 0; q < 9; ++q) pop_vload<S, V, CG>(base + q * p.plane + i0, cv, ft[q], q, p.codec);
     }
 
-    const uint32_t fbits = fused_row<S, MODE, PULL, STORE>(p, ft, i0, j, cv, a_rho, a_jx, a_jy);
+    const uint32_t fbits =
+        fused_row<S, MODE, PULL, STORE, AAR>(p, ft, i0, j, cv, a_rho, a_jx, a_jy);
     if (OUT) {
       n_ref += __popc(fbits & 0x01010101u);
       n_sw += __popc(fbits & 0x02020202u);
@@ -952,6 +1000,7 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
         const int rl = o / (32 * V), cl = o - rl * (32 * V);
         const int j = j0 + rl, i = bx * 32 * V + cl;
         const uint32_t tags = fix_cell<S, PULL, CG>(p, pr, ps, i, j);
+        if (AAR && STORE) p.region[(long long)j * p.pitch + i] = uint8_t((tags >> 1) & 1u);
         const int b = rl / p.tile, tl = cl / p.tile;
         if (tags & 1u) {
           atomicAdd(&s_cx[0], 1u);
@@ -1022,17 +1071,19 @@ __device__ __forceinline__ void ticket_and_finalize(const StepParams<S>& p, int 
 }
 
 // One CTA per block (bx, by) of a grid gx blocks wide, nblocks in all.
-template <class S, int MODE, bool PULL, bool STORE>
+template <class S, int MODE, bool PULL, bool STORE, bool AAR = false>
 __device__ __forceinline__ void step_cta(const StepParams<S>& p, const int bx, const int by,
                                          const int gx, const int nblocks) {
-  step_block<S, MODE, PULL, STORE>(p, bx, by, gx, p.part_sum, p.part_cnt);
+  step_block<S, MODE, PULL, STORE, false, AAR>(p, bx, by, gx, p.part_sum, p.part_cnt);
   if (MODE != MODE_PLAIN) ticket_and_finalize<S>(p, nblocks, nblocks);
 }
 
-template <class S, int MODE, bool PULL, bool STORE>
+// AAR: the step with the two-relaxation collision in the region p.region (pull + store).
+template <class S, int MODE, bool PULL, bool STORE, bool AAR = false>
 __global__ void __launch_bounds__(kThreads, MODE == MODE_FULL ? 1 : KSS_STEP_MIN_BLOCKS)
 step_kernel(const StepParams<S> p) {
-  step_cta<S, MODE, PULL, STORE>(p, blockIdx.x, blockIdx.y, gridDim.x, gridDim.x * gridDim.y);
+  step_cta<S, MODE, PULL, STORE, AAR>(p, blockIdx.x, blockIdx.y, gridDim.x,
+                                      gridDim.x * gridDim.y);
 }
 
 // The same step with a persistent grid: CTA c takes blocks c, c + gridDim.x, ... of the

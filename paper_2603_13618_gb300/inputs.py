@@ -13,6 +13,8 @@ Workloads (all in lattice units, c_s = 1/sqrt(3)):
   a square size drawn from {64, 128, 256, 512, 1024}, tau ~ U[0.51, 1.5] and a Mach
   number ~ U[0.01, 0.15], all from one SplitMix64 stream; its fields are
   ``random_smooth`` (kmax 8) scaled to that Mach number.
+* ``random_region``: a prescribed two-relaxation region (random cells, nonzero bytes)
+  for the adaptive-algorithm-refinement tests.
 * ``smooth_jump``: a density step rho_L / rho_R = 2 at x = nx/2 (and at the
   periodic seam x = 0) times (1 + drho), with drho, u_x, u_y random smooth fields:
   sums of Fourier modes with integer wavevectors (kx, ky) in [-kmax, kmax]^2
@@ -150,3 +152,12 @@ def batch_specs(n: int = 64, seed: int = 13618, sizes=(64, 128, 256, 512, 1024),
 def batch_fields(size: int, mach: float, field_seed: int):
     """(rho, ux, uy) of one lattice of the batched workload."""
     return random_smooth(size, size, seed=field_seed, kmax=8, mach=mach)
+
+
+def random_region(nx: int, ny: int, seed: int, frac: float = 0.4) -> np.ndarray:
+    """A prescribed adaptive-algorithm-refinement region, uint8 [ny, nx]: each cell
+    switched with probability frac (numpy PCG64 keyed on seed), switched cells holding
+    an arbitrary nonzero byte (any nonzero byte marks a switched cell)."""
+    rng = np.random.default_rng(seed)
+    on = rng.random((ny, nx)) < frac
+    return np.where(on, rng.integers(1, 256, size=(ny, nx)), 0).astype(np.uint8)

@@ -43,7 +43,7 @@ class Config(ctypes.Structure):
         ("record_mask", ctypes.c_uint32), ("output_every", ctypes.c_int32),
         ("tile", ctypes.c_int32), ("stream", ctypes.c_void_p), ("own_stream", ctypes.c_int32),
         ("kernel", ctypes.c_int32), ("rho0", ctypes.c_double), ("dev_exp", ctypes.c_int32),
-        ("dev_unscaled", ctypes.c_int32),
+        ("dev_unscaled", ctypes.c_int32), ("tau2", ctypes.c_double),
     ]
 
 
@@ -85,6 +85,8 @@ _SIGNATURES = {
     "kss_read_flags": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int]),
     "kss_read_stats": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "kss_get_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "kss_set_aar_region": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "kss_get_aar_region": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "kss_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "kss_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(Config),
                                         ctypes.POINTER(ctypes.c_void_p)]),
@@ -167,11 +169,12 @@ def make_config(nx: int, ny: int, precision="fp32", tau: float = 0.8, refine_sen
                 refine_threshold: float = 1e-3, switch_sensor="neq",
                 switch_threshold: float = 1e-4, record=("kl",), output_every: int = 1,
                 tile: int = 16, stream="torch", kernel="auto", rho0: float = 1.0,
-                dev_exp: int = 12, dev_unscaled: bool = False) -> Config:
+                dev_exp: int = 12, dev_unscaled: bool = False, tau2: float = 0.0) -> Config:
     """A kss_config (see include/kss.h).  stream: "torch" = torch's current stream
     (handle 0 is the CUDA default stream), "own" = a stream created and owned by the
     lattice, or a raw cudaStream_t handle.  rho0, dev_exp, dev_unscaled: the FP16
-    deviation storage of precision "fp16dev"."""
+    deviation storage of precision "fp16dev".  tau2 > 0: adaptive algorithm refinement,
+    the two-relaxation model (tau, tau2) in the switched region."""
     lib = load()
     cfg = Config()
     rc = lib.kss_config_default(ctypes.byref(cfg), nx, ny, PRECISIONS[precision])
@@ -189,6 +192,7 @@ def make_config(nx: int, ny: int, precision="fp32", tau: float = 0.8, refine_sen
     cfg.rho0 = rho0
     cfg.dev_exp = dev_exp
     cfg.dev_unscaled = int(dev_unscaled)
+    cfg.tau2 = tau2
     if stream == "own":
         cfg.own_stream, cfg.stream = 1, None
     else:
@@ -203,14 +207,14 @@ class Lattice:
                  refine_sensor="kn", refine_threshold: float = 1e-3, switch_sensor="neq",
                  switch_threshold: float = 1e-4, record=("kl",), output_every: int = 1,
                  tile: int = 16, stream="torch", kernel="auto", rho0: float = 1.0,
-                 dev_exp: int = 12, dev_unscaled: bool = False):
+                 dev_exp: int = 12, dev_unscaled: bool = False, tau2: float = 0.0):
         self._lib = load()
         self._h = None
         cfg = make_config(nx, ny, precision=precision, tau=tau, refine_sensor=refine_sensor,
                           refine_threshold=refine_threshold, switch_sensor=switch_sensor,
                           switch_threshold=switch_threshold, record=record,
                           output_every=output_every, tile=tile, stream=stream, kernel=kernel,
-                          rho0=rho0, dev_exp=dev_exp, dev_unscaled=dev_unscaled)
+                          rho0=rho0, dev_exp=dev_exp, dev_unscaled=dev_unscaled, tau2=tau2)
         handle = ctypes.c_void_p()
         self._check(self._lib.kss_create(ctypes.byref(cfg), ctypes.byref(handle)))
         self._adopt(handle, cfg, owned=True)
@@ -327,6 +331,18 @@ class Lattice:
         step = ctypes.c_int64()
         self._check(self._lib.kss_read_stats(self._h, sums, counts, ctypes.byref(step)))
         return np.array(list(sums)), np.array(list(counts), dtype=np.int64), step.value
+
+    def set_aar_region(self, region) -> None:
+        """Replace the two-relaxation region (uint8 [ny, nx], nonzero = switched)."""
+        p, d = _ptr(region, np.uint8)
+        self._check(self._lib.kss_set_aar_region(self._h, p, d))
+
+    def get_aar_region(self, device: bool = False):
+        """The two-relaxation region in force for the next step (uint8 [ny, nx], 0 / 1)."""
+        out = self._alloc((self.ny, self.nx), np.uint8, device)
+        p, d = _ptr(out, np.uint8)
+        self._check(self._lib.kss_get_aar_region(self._h, p, d))
+        return out
 
     def regrid(self, buffer: int = 2, efficiency: float = 0.98, max_boxes: int = 1 << 16):
         """(boxes [(x0, y0, x1, y1)] in tile units, tile mask [nty, ntx] uint8) of the

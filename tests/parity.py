@@ -12,7 +12,7 @@ Tolerance model (derived from the arithmetic; u = unit round-off of the storage 
   proportional to the scale of its terms: atol_s = 64 u sqrt(n + 1) scale_s with
       tau_ns, neq: rho;   C, S, E: rho / mu = 3 / tau;   qh: rho |u|;   Kn: 9;
       KL: rho Kn;   HR: rho (Kn + |u|);   sigma_H: rho (Kn + |u|) / tau;
-      sigma_KL: rho Kn / tau;   alpha: 1;   qe: 0
+      sigma_KL: rho Kn / tau;   alpha: 1;   qe: 0 (BGK), rho (two-relaxation model)
   on top of a relative tolerance (FP64 1e-10, FP32 1e-3).
 * alpha: when the pre-collision state ft is known, the floor is instead a first-order
   propagation of those input errors through the printed polynomial (alpha_error): its
@@ -80,7 +80,7 @@ def alpha_error(ft, prec, nsteps):
     return np.where(np.isfinite(err), err, 0.0)
 
 
-def sensor_atol(name, prec, nsteps, rho, ux, uy, kn, tau):
+def sensor_atol(name, prec, nsteps, rho, ux, uy, kn, tau, two_relax=False):
     u = UNIT_ROUNDOFF[prec]
     speed = np.sqrt(ux * ux + uy * uy)
     knf = np.where(np.isfinite(kn), kn, 0.0)
@@ -88,16 +88,18 @@ def sensor_atol(name, prec, nsteps, rho, ux, uy, kn, tau):
         "tau_ns": rho, "neq": rho, "c": 3.0 / tau + 0 * rho, "s": 3.0 / tau + 0 * rho,
         "e": 3.0 / tau + 0 * rho, "qh": rho * speed, "kn": 9.0 + 0 * rho, "kl": rho * knf,
         "hr": rho * (knf + speed), "sigma_h": rho * (knf + speed) / tau,
-        "sigma_kl": rho * knf / tau, "alpha": 1.0 + 0 * rho, "qe": 0 * rho,
+        "sigma_kl": rho * knf / tau, "alpha": 1.0 + 0 * rho,
+        "qe": rho if two_relax else 0 * rho,
     }[name]
     return 64.0 * u * math.sqrt(nsteps + 1) * scale
 
 
-def assert_sensor_close(name, got, want, prec, nsteps, rho, ux, uy, kn, tau, ft=None):
+def assert_sensor_close(name, got, want, prec, nsteps, rho, ux, uy, kn, tau, ft=None,
+                        two_relax=False):
     both_inf = np.isinf(got) & np.isinf(want)
     assert np.array_equal(np.isinf(got), np.isinf(want)), f"{name}: +Inf pattern differs"
     g, w = np.where(both_inf, 0.0, got), np.where(both_inf, 0.0, want)
-    atol = sensor_atol(name, prec, nsteps, rho, ux, uy, kn, tau)
+    atol = sensor_atol(name, prec, nsteps, rho, ux, uy, kn, tau, two_relax)
     if name == "alpha" and ft is not None:
         atol = np.maximum(atol, 4.0 * alpha_error(ft, prec, nsteps))
     tol = RTOL[prec] * np.abs(w) + atol

@@ -45,12 +45,14 @@ def test_host_only_calls():
     assert lib.kss_config_default(cfg, 64, 32, kss.FP32) == 0
     assert (cfg.nx, cfg.ny, cfg.tile, cfg.output_every) == (64, 32, 16, 1)
     assert abs(cfg.tau - 0.8) < 1e-15 and cfg.record_mask == 1 << kss.SENSOR_ID["kl"]
+    assert cfg.tau2 == 0.0
 
 
 @pytest.mark.parametrize("field,value", [("nx", 0), ("ny", -1), ("tau", 0.5), ("tile", 12),
                                          ("precision", 7), ("refine_sensor", 13),
                                          ("output_every", -2), ("record_mask", 1 << 13),
-                                         ("own_stream", 2)])
+                                         ("own_stream", 2), ("tau2", 0.5), ("tau2", -1.0),
+                                         ("tau2", float("inf"))])
 def test_create_rejects_bad_config_before_touching_the_gpu(field, value):
     import ctypes
 
