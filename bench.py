@@ -14,12 +14,19 @@ previous step); the same steps as one launch each are timed alongside.
   python bench.py --workload batch64    # the batched workload (below)
   python bench.py --workload adjoint512 # the adjoint workload (below)
   python bench.py --workload fp16dev8192 [--fp16-error]  # the precision workload (below)
+  python bench.py --workload aar4096    # adaptive algorithm refinement (below)
 
 Batched workload (--workload batch64): 64 uneven periodic lattices (sizes 64^2 ..
 1024^2, tau ~ U[0.51, 1.5], Mach ~ U[0.01, 0.15], seed 13618, 15.8 M cells in all), the
 same sensors, flags and sums every step, advanced by one launch per step for all of
 them (replayed as a CUDA graph), against the same 64 lattices stepped one launch per
 lattice per step.
+
+Adaptive-algorithm-refinement workload (--workload aar4096): the same 4096^2 lattice
+with the two-relaxation model in the switched region (tau2 = 1/2 + (3/16)/(tau - 1/2)):
+output steps with the {Kn, KL, neq} set and neq as the switch sensor (the region then
+follows the flags), with all of Table 1 and the quasi-equilibrium sensor as the switch,
+and plain steps in a fixed 40 % region, each against the same steps with BGK only.
 
 N > 1 (launched by torchrun) runs one independent lattice per rank (replicas, weak
 scaling); rank 0 prints one JSON line.  --impl reference times the CPU oracle on the
@@ -395,6 +402,90 @@ def run_fp16(args):
     return 0
 
 
+AAR_METRIC = ("MLUPS with adaptive algorithm refinement (two-relaxation collision in the "
+              "switched region) and sensors fused, 1xGB300")
+
+
+def run_aar(args):
+    """The adaptive-algorithm-refinement workload (one launch per step)."""
+    import numpy as np
+    import torch
+
+    from paper_2603_13618_gb300 import inputs, kss
+
+    torch.cuda.set_device(0)
+    n = args.size or 4096
+    cells = n * n
+    rho, ux, uy = workload_fields(n, n)
+    tau2 = 0.5 + (3.0 / 16.0) / (TAU - 0.5)
+    region = inputs.random_region(n, n, seed=4096)
+    stream = torch.cuda.current_stream()
+    K = args.steps
+    peak, peak_kind = measured_peak()
+    variants = (
+        # name, tau2, switch sensor, output_every, record, bytes per LUP
+        ("aar_std", tau2, "neq", 1, ("kl",), 72 + 5 + 2),
+        ("bgk_std", 0.0, "neq", 1, ("kl",), 72 + 5),
+        ("aar_qe_full", tau2, "qe", 1, ("kl",), 72 + 5 + 2),
+        ("aar_plain", tau2, "neq", 0, (), 72 + 1),
+        ("bgk_plain", 0.0, "neq", 0, (), 72),
+    )
+    runs = {}
+    with ClockSampler(0) as clk:
+        for name, t2, sw, out, rec, bpl in variants:
+            lat = kss.Lattice(n, n, precision="fp32", tau=TAU, tau2=t2, refine_sensor="kn",
+                              refine_threshold=THR_R, switch_sensor=sw,
+                              switch_threshold=THR_S, record=rec, output_every=out,
+                              tile=TILE)
+            lat.set_fields(rho, ux, uy)
+            if t2 and not out:
+                lat.set_aar_region(region)
+            lat.step(args.warmup)
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K)]
+            for k in range(K):
+                ev[2 * k].record(stream)
+                lat.step(1)
+                ev[2 * k + 1].record(stream)
+            torch.cuda.synchronize()
+            total = ev[0].elapsed_time(ev[-1])
+            kern = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(K)) / K
+            achieved = bpl * cells / (kern * 1e-3) / 1e9
+            r = {"value": cells * K / (total * 1e-3) / 1e6, "unit": "MLUPS",
+                 "ms_per_step": total / K, "kernel_ms": kern, "bytes_per_lup": bpl,
+                 "achieved_gbs": achieved, "frac": achieved / peak}
+            if t2:
+                r["switched_fraction"] = float(np.mean(lat.get_aar_region()))
+            runs[name] = r
+            lat.close()
+    main = runs["aar_std"]
+    line = {
+        "metric": AAR_METRIC, "value": main["value"], "unit": "MLUPS", "n_gpus": 1,
+        "steps": K, "warmup": args.warmup, "ms_per_step": main["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"D2Q9 FP32 {n}x{n} periodic as the headline workload, "
+                               f"two-relaxation model tau=0.6, tau2={tau2:.4g} in the cells "
+                               "switched by neq > 1e-4 at the previous step; Kn refine 1e-3, "
+                               "KL field, flags, tile counts, sums every step",
+                   "nx": n, "ny": n, "tau": TAU, "tau2": tau2,
+                   "l2": f"inputs larger than L2: {cells * 72 / 1e9:.2f} GB of populations "
+                         "per step"},
+        "roofline": {"bound": "hbm", "achieved": main["achieved_gbs"], "peak": peak,
+                     "unit": "GB/s", "frac": main["frac"], "peak_kind": peak_kind,
+                     "traffic": None,
+                     "algorithmic_bytes_per_launch": main["bytes_per_lup"] * cells,
+                     "kernel_ms": main["kernel_ms"],
+                     "kernel": "step_kernel<float, MODE_STD, pull, store, AAR>"},
+        "variants": runs,
+        "aar_cost_vs_bgk": main["kernel_ms"] / runs["bgk_std"]["kernel_ms"],
+        "gpu_launches": K,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def fp16_error(n, tau, kexp, gen, steps=500, window=256):
     """Errors of FP16 deviation and FP32 storage after `steps` steps against the FP64
     oracle on the central window (the oracle runs the window's domain of dependence)."""
@@ -630,7 +721,7 @@ def main():
     ap.add_argument("--fp16-error", action="store_true",
                     help="fp16dev8192: also measure the error against the FP64 oracle")
     ap.add_argument("--workload", default="single",
-                    choices=["single", "batch64", "adjoint512", "fp16dev8192"],
+                    choices=["single", "batch64", "adjoint512", "fp16dev8192", "aar4096"],
                     help="single: the 4096^2 lattice (default); batch64: 64 uneven "
                          "lattices; adjoint512: the gradient of the KL objective")
     ap.add_argument("--no-tune", action="store_true",
@@ -648,6 +739,8 @@ def main():
         return run_adjoint(args)
     if args.workload == "fp16dev8192":
         return run_fp16(args)
+    if args.workload == "aar4096":
+        return run_aar(args)
     return run_gpu(args)
 
 

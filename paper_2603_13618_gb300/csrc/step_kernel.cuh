@@ -388,6 +388,11 @@ struct StdAcc {
 #ifndef KSS_PAIRED_F32
 #define KSS_PAIRED_F32 1
 #endif
+// The two-relaxation update of AAR steps in paired FP32 instructions too (a build-time
+// tuning knob, -DKSS_AAR_PAIRED=0 for the scalar form; the results are the same).
+#ifndef KSS_AAR_PAIRED
+#define KSS_AAR_PAIRED 1
+#endif
 template <class T, bool OUT, bool COLLIDE>
 __device__ __forceinline__ void relax_pop(T (&f)[Vec<T>::N], const T (&feq)[Vec<T>::N], T omega,
                                           StdAcc<T>& a) {
@@ -465,13 +470,32 @@ __device__ __forceinline__ void pair_pops(arith_t<S> (&fp)[Vec<S>::N], arith_t<S
     relax_pop<T, OUT, false>(fp, ep, omega, a);  // the sensors only
     relax_pop<T, OUT, false>(fm, em, omega, a);
     if (STORE) {
+#if KSS_PAIRED_F32 && KSS_AAR_PAIRED
+      if constexpr (std::is_same<T, float>::value) {
+        // two cells per paired instruction, the roundings of the scalar form below
 #pragma unroll
-      for (int k = 0; k < V; ++k) {
-        const bool sw = ((mbits >> (8 * k)) & 0xffu) != 0u;
-        const T A = sw ? trt.a : omega, B = sw ? trt.b : T(0);
-        const T np = fp[k] - ep[k], nm = fm[k] - em[k];
-        fp[k] = fma(-B, nm, fma(-A, np, fp[k]));
-        fm[k] = fma(-B, np, fma(-A, nm, fm[k]));
+        for (int k = 0; k < V; k += 2) {
+          const bool s0 = ((mbits >> (8 * k)) & 0xffu) != 0u;
+          const bool s1 = ((mbits >> (8 * k + 8)) & 0xffu) != 0u;
+          const F2 nA = pack2(s0 ? -trt.a : -omega, s1 ? -trt.a : -omega);
+          const F2 nB = pack2(s0 ? -trt.b : -0.f, s1 ? -trt.b : -0.f);
+          const F2 P = pack2(fp[k], fp[k + 1]), M = pack2(fm[k], fm[k + 1]);
+          const F2 np = sub2(P, pack2(ep[k], ep[k + 1]));
+          const F2 nm = sub2(M, pack2(em[k], em[k + 1]));
+          unpack2(fma2(nB, nm, fma2(nA, np, P)), fp[k], fp[k + 1]);
+          unpack2(fma2(nB, np, fma2(nA, nm, M)), fm[k], fm[k + 1]);
+        }
+      } else
+#endif
+      {
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+          const bool sw = ((mbits >> (8 * k)) & 0xffu) != 0u;
+          const T A = sw ? trt.a : omega, B = sw ? trt.b : T(0);
+          const T np = fp[k] - ep[k], nm = fm[k] - em[k];
+          fp[k] = fma(-B, nm, fma(-A, np, fp[k]));
+          fm[k] = fma(-B, np, fma(-A, nm, fm[k]));
+        }
       }
       if (cv) {
         pop_vstore<S>(dst_p, fp, QP, codec);
@@ -680,18 +704,14 @@ template <class S, int MODE, bool PULL, bool STORE, bool AAR = false>
 __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
                                               arith_t<S> (&ft)[9][Vec<S>::N], int i0, int j,
                                               bool cv, Acc<arith_t<S>>& a_rho,
-                                              Acc<arith_t<S>>& a_jx, Acc<arith_t<S>>& a_jy) {
+                                              Acc<arith_t<S>>& a_jx, Acc<arith_t<S>>& a_jy,
+                                              uint32_t mbits = 0) {
+  // (AAR: mbits holds the row's region bytes, loaded by the caller with the populations)
   using T = arith_t<S>;
   constexpr int V = Vec<S>::N;
   constexpr bool OUT = MODE != MODE_PLAIN;
   const long long off = (long long)j * p.pitch + i0;
   uint32_t fbits = 0;
-  // AAR: the region in force for this step's collision (the switch flags of the most
-  // recent output step before it); output steps replace it with their own
-  uint32_t mbits = 0;
-  if constexpr (AAR && STORE) {
-    if (cv) mbits = load_bytes<V>(p.region + off);
-  }
   if constexpr (MODE == MODE_FULL) {
     // ---- all sensors of Table 1: cell-major, generic per-cell arithmetic ----
     T fo[9][V];
@@ -880,6 +900,13 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
   for (int j = j0 + warp; j < j1; j += kWarps) {
     T ft[9][V];
     const S* base = p.src + (long long)j * p.pitch;
+    // AAR: the region in force for this step's collision (the switch flags of the most
+    // recent output step before it), loaded ahead of the populations so that its latency
+    // overlaps theirs; output steps replace it with their own flags
+    uint32_t mbits = 0;
+    if constexpr (AAR && STORE) {
+      if (cv) mbits = load_bytes<V>(p.region + (long long)j * p.pitch + i0);
+    }
     if (PULL) {
       const long long up = (long long)((j == 0 ? p.ny : j) - 1 - j) * p.pitch;    // row j-1
       const long long dn = (long long)((j + 1 == p.ny ? 0 : j + 1) - j) * p.pitch;  // row j+1
@@ -920,7 +947,7 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
     }
 
     const uint32_t fbits =
-        fused_row<S, MODE, PULL, STORE, AAR>(p, ft, i0, j, cv, a_rho, a_jx, a_jy);
+        fused_row<S, MODE, PULL, STORE, AAR>(p, ft, i0, j, cv, a_rho, a_jx, a_jy, mbits);
     if (OUT) {
       n_ref += __popc(fbits & 0x01010101u);
       n_sw += __popc(fbits & 0x02020202u);
