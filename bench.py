@@ -73,11 +73,11 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profile_traffic():
-    """DRAM bytes per step of the fused step from the committed ncu summary, or None if
+def profile_traffic(path=PROFILE):
+    """DRAM bytes per step of the fused step from a committed ncu summary, or None if
     the summary is missing or was taken on different kernel sources."""
     try:
-        txt = open(PROFILE).read()
+        txt = open(path).read()
     except OSError:
         return None
     m = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]{16})", txt)
@@ -402,6 +402,7 @@ def run_fp16(args):
     return 0
 
 
+AAR_PROFILE = os.path.join(ROOT, "profiles", "step_aar_std_f32_4096.md")
 AAR_METRIC = ("MLUPS with adaptive algorithm refinement (two-relaxation collision in the "
               "switched region) and sensors fused, 1xGB300")
 
@@ -473,7 +474,7 @@ def run_aar(args):
                          "per step"},
         "roofline": {"bound": "hbm", "achieved": main["achieved_gbs"], "peak": peak,
                      "unit": "GB/s", "frac": main["frac"], "peak_kind": peak_kind,
-                     "traffic": None,
+                     "traffic": (profile_traffic(AAR_PROFILE) if n == 4096 else None),
                      "algorithmic_bytes_per_launch": main["bytes_per_lup"] * cells,
                      "kernel_ms": main["kernel_ms"],
                      "kernel": "step_kernel<float, MODE_STD, pull, store, AAR>"},
