@@ -19,7 +19,9 @@
  *     (x = i, y = j).  Populations are dense [9][ny][nx] doubles.  Every array at the
  *     boundary is FP64 whatever the storage precision; conversion happens on the GPU.
  *   - on_device = 0: the pointer is host memory (pageable or pinned) owned by the
- *     caller; the call copies and synchronises before returning.
+ *     caller; the call copies and synchronises before returning.  (kss_set_fields and
+ *     kss_set_populations read page-locked inputs directly over the host link, without
+ *     a staging copy.)
  *     on_device = 1: the pointer is CUDA device memory of the current device, owned
  *     by the caller, which must keep it valid until the lattice's stream has passed
  *     the call (reads synchronise the stream before returning).
