@@ -246,6 +246,11 @@ typedef struct {
                         /* output pattern) as a CUDA graph and replays it               */
   double ms_per_step;   /* kss_batch_autotune: measured time of one output step of the  */
                         /* whole batch with this choice; ignored by kss_batch_set_tuning */
+  int32_t multi_step;   /* 1 (default): a kss_batch_step(n >= 2) call whose steps are all */
+                        /* {Kn, KL, neq} output steps runs as ONE cooperative launch: each */
+                        /* block of a step waits (bounded, KSS_ERR_TIMEOUT) only for its  */
+                        /* lattice's neighbouring blocks of the previous step; same results */
+                        /* bit for bit; ctas_per_sm and graph then do not apply            */
 } kss_batch_tuning;
 
 /* Create n >= 1 lattices from cfgs[0..n-1] (each validated as by kss_create).  Members
@@ -255,8 +260,10 @@ int kss_batch_create(int32_t n, const kss_config* cfgs, kss_batch** out);
 void kss_batch_destroy(kss_batch* b);
 /* Member k (0 <= k < n), owned by the batch; NULL if k is out of range. */
 kss_lattice* kss_batch_member(kss_batch* b, int32_t k);
-/* Advance every member nsteps >= 0 steps, one launch per step (asynchronous on the
- * batch's stream).  Returns a member's sticky error if one has any. */
+/* Advance every member nsteps >= 0 steps: one launch per step, or all of them in one
+ * launch (kss_batch_tuning.multi_step); asynchronous on the batch's stream.  Returns a
+ * member's sticky error if one has any; a bounded wait of a multi-step launch that ran
+ * out shows as KSS_ERR_TIMEOUT on the members' next synchronising call. */
 int kss_batch_step(kss_batch* b, int32_t nsteps);
 /* Current work decomposition, and a new one (validated; KSS_ERR_ARG if rows is not a
  * multiple of every member's tile). */

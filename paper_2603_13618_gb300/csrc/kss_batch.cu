@@ -52,6 +52,12 @@ struct kss_batch {
   int par = 0;
   bool tables_valid = false;
   std::vector<Graph> graphs;
+  // multi-step launches: workspace sized for the smallest CTA height (a header of counters
+  // zeroed before every launch, then the rings of partial sums) and each member's
+  // MultiState at the current layout
+  void* multi = nullptr;
+  size_t multi_head = 0;          // header bytes at the current layout
+  kss::MultiState* mtab = nullptr;
   std::string msg;
 };
 
@@ -76,6 +82,69 @@ size_t param_bytes(const kss_batch* B) {
 }
 
 int default_rows(const kss_batch* B) { return std::max(32, B->max_tile); }
+
+constexpr int kMultiRing = 8;                   // partial-sum slots per member
+constexpr long long kMultiDeadline = 4000000000LL;  // clock64 cycles per wait, about 2 s
+
+// Bytes of the multi-step workspace for members with nb[k] blocks each: the header
+// (work counter; per member its blocks' step counters, ring tickets and slot counters),
+// then per member the ring of partial sums and counts and the ring of step sums.
+size_t multi_bytes(const std::vector<long long>& nb, size_t* head) {
+  long long h = 1, parts = 0;
+  for (long long b : nb) {
+    h += b + 2 * kMultiRing;
+    parts += b;
+  }
+  const size_t hb = (sizeof(uint32_t) * size_t(h) + 255) / 256 * 256;
+  if (head) *head = sizeof(uint32_t) * size_t(h);
+  return hb + size_t(kMultiRing) * size_t(parts) * (3 * sizeof(double) + 4 * sizeof(uint32_t)) +
+         nb.size() * size_t(kMultiRing) * 3 * (sizeof(double) + sizeof(unsigned long long));
+}
+
+// Each member's MultiState at the current layout (its blocks in the workspace).
+int write_multi_table(kss_batch* B) {
+  std::vector<long long> nb(B->n);
+  for (int k = 0; k < B->n; ++k) nb[k] = (long long)B->grids[k].x * B->grids[k].y;
+  const size_t total = multi_bytes(nb, &B->multi_head);
+  (void)total;
+  const int R = kMultiRing;
+  unsigned char* w = static_cast<unsigned char*>(B->multi);
+  uint32_t* hdr = reinterpret_cast<uint32_t*>(w);
+  unsigned char* q = w + (B->multi_head + 255) / 256 * 256;
+  long long parts = 0;
+  for (long long b : nb) parts += b;
+  double* psum = reinterpret_cast<double*>(q);
+  uint32_t* pcnt = reinterpret_cast<uint32_t*>(q + sizeof(double) * 3 * size_t(R) * size_t(parts));
+  double* rsum = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(pcnt) +
+                                           sizeof(uint32_t) * 4 * size_t(R) * size_t(parts));
+  unsigned long long* rcnt = reinterpret_cast<unsigned long long*>(rsum + 3 * size_t(R) * B->n);
+  std::vector<kss::MultiState> tab(B->n);
+  uint32_t* next = hdr + 1;
+  long long poff = 0;
+  for (int k = 0; k < B->n; ++k) {
+    kss::MultiState& m = tab[k];
+    m.work = hdr;
+    m.done = next;
+    m.ticket = next + nb[k];
+    m.fin = m.ticket + R;
+    next = m.fin + R;
+    m.part_sum = psum + 3 * size_t(R) * size_t(poff);
+    m.part_cnt = pcnt + 4 * size_t(R) * size_t(poff);
+    poff += nb[k];
+    m.ring_sums = rsum + 3 * size_t(R) * k;
+    m.ring_counts = rcnt + 3 * size_t(R) * k;
+    m.err = B->mem[k]->err_word;
+    m.deadline = kMultiDeadline;
+    m.ring = R;
+    m.nsteps = 0;  // set by the kernel from its argument
+    m.gx = int(B->grids[k].x);
+    m.gy = int(B->grids[k].y);
+    m.nblocks = int(nb[k]);
+  }
+  KSS_BCUDA(B, cudaMemcpy(B->mtab, tab.data(), sizeof(kss::MultiState) * B->n,
+                          cudaMemcpyHostToDevice));
+  return KSS_OK;
+}
 
 bool valid_rows(const kss_batch* B, int rows) {
   if (rows != 16 && rows != 32 && rows != 64) return false;
@@ -189,6 +258,7 @@ int relayout(kss_batch* B) {
   drop_graphs(B);
   int rc = write_items(B);
   if (rc) return rc;
+  if ((rc = write_multi_table(B))) return rc;
   return write_tables(B);
 }
 
@@ -204,6 +274,24 @@ int check_tables(kss_batch* B) {
 int launch_ctas(const kss_batch* B) {
   if (B->tun.ctas_per_sm <= 0) return B->nitems;
   return std::min<long long>(B->nitems, (long long)B->tun.ctas_per_sm * B->nsm);
+}
+
+// All nsteps {Kn, KL, neq} steps of the batch in one cooperative launch.
+cudaError_t launch_multi(kss_batch* B, int nsteps) {
+  cudaError_t e = cudaMemsetAsync(B->multi, 0, B->multi_head, B->stream);
+  if (e != cudaSuccess) return e;
+  return with_storage(B->prec, [&](auto tag) {
+    using S = typename decltype(tag)::type;
+    const int resident = kss::batch_multi_resident_ctas<S>(kss::MODE_STD);
+    if (resident < 1) return cudaErrorInvalidConfiguration;
+    const long long work = (long long)nsteps * B->nitems;
+    const int ctas = int(std::min<long long>(resident, work));
+    const auto* t = static_cast<const kss::StepParams<S>*>(B->table[B->par]);
+    const auto* u = static_cast<const kss::StepParams<S>*>(B->table[B->par ^ 1]);
+    return kss::launch_batch_multi<S>(t, u, B->mtab, B->items, B->nitems, nsteps,
+                                      static_cast<uint32_t*>(B->multi), kss::MODE_STD, ctas,
+                                      B->stream);
+  });
 }
 
 cudaError_t launch_one(kss_batch* B, int tbl, int mode, cudaStream_t s) {
@@ -269,7 +357,8 @@ void destroy_batch(kss_batch* B) {
     L->own_stream = false;  // the batch owns the shared stream
     release(L);
   }
-  void* bufs[] = {B->table[0], B->table[1], B->items, B->part_sum, B->part_cnt};
+  void* bufs[] = {B->table[0], B->table[1], B->items, B->part_sum, B->part_cnt, B->multi,
+                  B->mtab};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (B->cap) cudaStreamDestroy(B->cap);
@@ -379,12 +468,15 @@ int kss_batch_create(int32_t n, const kss_config* cfgs, kss_batch** out) {
   B->tun.ctas_per_sm = 0;
   B->tun.graph = 1;
   B->tun.ms_per_step = 0;
+  B->tun.multi_step = 1;
   B->base_cur.assign(n, 0);
   // partials for the smallest CTA height any tuning may choose
   long long parts = 0;
+  std::vector<long long> nb_max;
   for (const kss_lattice* L : B->mem) {
     const dim3 g = member_grid(B, L, B->rows_min);
     parts += (long long)g.x * g.y;
+    nb_max.push_back((long long)g.x * g.y);
   }
   const size_t pb = param_bytes(B) * size_t(n);
   struct {
@@ -395,6 +487,8 @@ int kss_batch_create(int32_t n, const kss_config* cfgs, kss_batch** out) {
       {&B->table[1], pb},
       {reinterpret_cast<void**>(&B->part_sum), sizeof(double) * 3 * size_t(parts)},
       {reinterpret_cast<void**>(&B->part_cnt), sizeof(uint32_t) * 4 * size_t(parts)},
+      {&B->multi, multi_bytes(nb_max, nullptr)},
+      {reinterpret_cast<void**>(&B->mtab), sizeof(kss::MultiState) * size_t(n)},
   };
   for (auto& a : allocs) {
     if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
@@ -433,11 +527,14 @@ int kss_batch_set_tuning(kss_batch* B, const kss_batch_tuning* t) {
   if (!valid_rows(B, rows)) return bfail(B, KSS_ERR_ARG, "rows must be 16, 32 or 64 and a multiple of every tile");
   if (t->ctas_per_sm < 0 || t->ctas_per_sm > 64) return bfail(B, KSS_ERR_ARG, "ctas_per_sm out of range");
   if (t->graph != 0 && t->graph != 1) return bfail(B, KSS_ERR_ARG, "graph must be 0 or 1");
+  if (t->multi_step != 0 && t->multi_step != 1)
+    return bfail(B, KSS_ERR_ARG, "multi_step must be 0 or 1");
   DeviceGuard g(B->device);
   const bool layout = rows != B->tun.rows || t->ctas_per_sm != B->tun.ctas_per_sm;
   B->tun.rows = rows;
   B->tun.ctas_per_sm = t->ctas_per_sm;
   B->tun.graph = t->graph;
+  B->tun.multi_step = t->multi_step;
   return layout ? relayout(B) : KSS_OK;
 }
 
@@ -462,7 +559,12 @@ int kss_batch_step(kss_batch* B, int32_t nsteps) {
       }
     }
   }
-  if (B->tun.graph && nsteps >= 2) {
+  const bool all_std = B->mode_out == kss::MODE_STD &&
+                       modes.find_first_not_of('S') == std::string::npos;
+  if (B->tun.multi_step && nsteps >= 2 && all_std &&
+      (long long)nsteps * B->nitems < (1LL << 30)) {
+    KSS_BCUDA(B, launch_multi(B, nsteps));
+  } else if (B->tun.graph && nsteps >= 2) {
     cudaGraphExec_t exec = nullptr;
     if ((rc = graph_for(B, nsteps, modes, &exec))) return rc;
     KSS_BCUDA(B, cudaGraphLaunch(exec, B->stream));
@@ -497,6 +599,7 @@ int kss_batch_autotune(kss_batch* B, const char* cache_path, int32_t steps,
   if (cache_path && cache_lookup(cache_path, key, &best) && valid_rows(B, best.rows) &&
       best.ctas_per_sm >= 0 && best.ctas_per_sm <= 64) {
     best.graph = B->tun.graph;
+    best.multi_step = B->tun.multi_step;
     const double ms = best.ms_per_step;
     if ((rc = kss_batch_set_tuning(B, &best))) return rc;
     B->tun.ms_per_step = ms;

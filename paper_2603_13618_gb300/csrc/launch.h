@@ -38,6 +38,17 @@ template <class T>
 cudaError_t launch_batch_step(const StepParams<T>* table, const BatchItem* items, int nitems,
                               int ctas, int mode, cudaStream_t stream);
 
+// nsteps batched steps in one cooperative launch (batch_kernel_multi): ta / tb are the
+// parameter tables of even / odd steps, mtab each lattice's MultiState, work the shared
+// work counter (0 at launch); mode MODE_STD; ctas <= batch_multi_resident_ctas.
+template <class T>
+cudaError_t launch_batch_multi(const StepParams<T>* ta, const StepParams<T>* tb,
+                               const MultiState* mtab, const BatchItem* items, int nitems,
+                               int nsteps, uint32_t* work, int mode, int ctas,
+                               cudaStream_t stream);
+template <class T>
+int batch_multi_resident_ctas(int mode);
+
 // nsteps fused steps in one cooperative launch (step_kernel_multi): pa reads buffer A and
 // writes B, pb the reverse; mode MODE_STD (the {Kn, KL, neq} set every step);
 // ctas <= multi_resident_ctas.

@@ -108,6 +108,28 @@ cudaError_t launch_step_multi<KSS_T>(const StepParams<KSS_T>& pa, const StepPara
 }
 
 template <>
+int batch_multi_resident_ctas<KSS_T>(int mode) {
+  return mode == MODE_STD ? resident_ctas<batch_kernel_multi<KSS_T, MODE_STD>>() : 0;
+}
+
+template <>
+cudaError_t launch_batch_multi<KSS_T>(const StepParams<KSS_T>* ta, const StepParams<KSS_T>* tb,
+                                      const MultiState* mtab, const BatchItem* items,
+                                      int nitems, int nsteps, uint32_t* work, int mode,
+                                      int ctas, cudaStream_t stream) {
+  if (mode != MODE_STD || nitems < 1 || nsteps < 1 || ctas < 1) return cudaErrorInvalidValue;
+  const StepParams<KSS_T>* a = ta;
+  const StepParams<KSS_T>* b = tb;
+  const MultiState* m = mtab;
+  const BatchItem* it = items;
+  int ni = nitems, ns = nsteps;
+  uint32_t* w = work;
+  void* args[] = {&a, &b, &m, &it, &ni, &ns, &w};
+  const void* fn = reinterpret_cast<const void*>(batch_kernel_multi<KSS_T, MODE_STD>);
+  return cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(kThreads), args, 0, stream);
+}
+
+template <>
 cudaError_t launch_batch_step<KSS_T>(const StepParams<KSS_T>* table, const BatchItem* items,
                                      int nitems, int ctas, int mode, cudaStream_t stream) {
   if (nitems < 1 || ctas < 1) return cudaErrorInvalidValue;

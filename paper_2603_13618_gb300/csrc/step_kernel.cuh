@@ -1290,6 +1290,48 @@ batch_step_kernel(const StepParams<S>* __restrict__ table, const BatchItem* __re
   }
 }
 
+// ---------------------------------------------------------------- batched multi-step ----
+// nsteps steps of a whole batch in one cooperative launch: work item w = s * nitems + i is
+// block items[i] of step s.  Each lattice has its own MultiState (its blocks' step
+// counters, ring of partial sums, ticket and slot counters); all share the work counter,
+// so items are handed out in (step, work-list) order and, as in step_kernel_multi, every
+// item waits only for items of its own lattice handed out before it.  mtab[k] is lattice
+// k's state; ta / tb its parameters for even / odd steps.
+template <class S, int MODE>
+__global__ void __launch_bounds__(kThreads, KSS_STEP_MIN_BLOCKS)
+batch_kernel_multi(const StepParams<S>* __restrict__ ta, const StepParams<S>* __restrict__ tb,
+                   const MultiState* __restrict__ mtab, const BatchItem* __restrict__ items,
+                   int nitems, int nsteps, uint32_t* work) {
+  static_assert(sizeof(StepParams<S>) % 8 == 0 && sizeof(MultiState) % 8 == 0,
+                "parameter copies in 8-byte words");
+  __shared__ __align__(16) unsigned long long s_p[sizeof(StepParams<S>) / 8];
+  __shared__ __align__(16) unsigned long long s_m[sizeof(MultiState) / 8];
+  __shared__ int s_next;
+  const StepParams<S>& sp = *reinterpret_cast<const StepParams<S>*>(s_p);
+  const MultiState& sm = *reinterpret_cast<const MultiState*>(s_m);
+  if (threadIdx.x == 0) s_next = int(atomicAdd(work, 1u));
+  __syncthreads();
+  int w = s_next;
+  const int total = nsteps * nitems;
+  while (w < total) {
+    const int s = w / nitems;
+    const BatchItem it = items[w - s * nitems];
+    __syncthreads();  // every thread has read s_next and is done with the shared copies
+    const unsigned long long* src =
+        reinterpret_cast<const unsigned long long*>(((s & 1) ? tb : ta) + it.lat);
+    for (int k = threadIdx.x; k < int(sizeof(StepParams<S>) / 8); k += kThreads) s_p[k] = src[k];
+    const unsigned long long* msrc = reinterpret_cast<const unsigned long long*>(mtab + it.lat);
+    for (int k = threadIdx.x; k < int(sizeof(MultiState) / 8); k += kThreads) s_m[k] = msrc[k];
+    __syncthreads();
+    // the table is shared by calls of any length: the launch's step count goes in here
+    // (other threads read it only after multi_block's barriers)
+    if (threadIdx.x == 0) reinterpret_cast<MultiState*>(s_m)->nsteps = nsteps;
+    if (!multi_block<S, MODE>(sp, sm, s, int(it.by) * sm.gx + int(it.bx), &s_next)) return;
+    __syncthreads();
+    w = s_next;
+  }
+}
+
 // ---------------------------------------------------------------- fixup ----
 // Add tags (bit 0 refine, bit 1 switch) of the active lanes' cells to their tiles, one
 // atomic per distinct tile per warp (list entries of a warp mostly share tiles).

@@ -49,7 +49,8 @@ class Config(ctypes.Structure):
 
 class BatchTuning(ctypes.Structure):
     _fields_ = [("rows", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("graph", ctypes.c_int32), ("ms_per_step", ctypes.c_double)]
+                ("graph", ctypes.c_int32), ("ms_per_step", ctypes.c_double),
+                ("multi_step", ctypes.c_int32)]
 
 
 class Box(ctypes.Structure):
@@ -409,10 +410,11 @@ class Batch:
         t = BatchTuning()
         self._check(self._lib.kss_batch_get_tuning(self._h, ctypes.byref(t)))
         return {"rows": t.rows, "ctas_per_sm": t.ctas_per_sm, "graph": t.graph,
-                "ms_per_step": t.ms_per_step}
+                "ms_per_step": t.ms_per_step, "multi_step": t.multi_step}
 
-    def set_tuning(self, rows: int = 0, ctas_per_sm: int = 0, graph: int = 1) -> None:
-        t = BatchTuning(rows, ctas_per_sm, graph, 0.0)
+    def set_tuning(self, rows: int = 0, ctas_per_sm: int = 0, graph: int = 1,
+                   multi_step: int = 1) -> None:
+        t = BatchTuning(rows, ctas_per_sm, graph, 0.0, multi_step)
         self._check(self._lib.kss_batch_set_tuning(self._h, ctypes.byref(t)))
 
     def autotune(self, cache_path: str | None = None, steps: int = 10) -> dict:
@@ -420,7 +422,7 @@ class Batch:
         path = cache_path.encode() if cache_path else None
         self._check(self._lib.kss_batch_autotune(self._h, path, int(steps), ctypes.byref(t)))
         return {"rows": t.rows, "ctas_per_sm": t.ctas_per_sm, "graph": t.graph,
-                "ms_per_step": t.ms_per_step}
+                "ms_per_step": t.ms_per_step, "multi_step": t.multi_step}
 
     def close(self):
         if getattr(self, "_h", None):

@@ -277,3 +277,52 @@ def test_seeded_64_lattice_workload():
             umax = np.max(np.hypot(ru, rv))
             assert np.max(np.abs(gr * gu - rr * ru)) <= 1e-5 * np.max(rr) * umax
     b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "fp16dev"])
+@pytest.mark.parametrize("rows", [16, 32, 64])
+def test_multi_step_batch_equals_per_step_launches(prec, rows):
+    """Every member an output step of the {Kn, KL, neq} set: kss_batch_step(n) runs all n
+    steps as one cooperative launch (multi_step = 1) and must give, member by member, the
+    results of one launch per step (multi_step = 0) bit for bit, and those of the member
+    stepped alone at its default CTA height."""
+    specs = [dict(sp, output_every=1, tile=min(sp["tile"], 16)) for sp in SPECS]
+    a = _batch(specs, prec)
+    b = _batch(specs, prec)
+    a.set_tuning(rows=rows, multi_step=1)
+    b.set_tuning(rows=rows, multi_step=0)
+    singles = _singles(specs, prec)
+    for n in (9, 1, 4):  # multi-step, single launch, multi-step again
+        a.step(n)
+        b.step(n)
+        for lat in singles:
+            lat.step(n)
+        for k in range(len(specs)):
+            _assert_same(a[k], b[k])
+            _assert_same(a[k], singles[k], sums_exact=(rows == 32),
+                         prec="fp64" if prec == "fp64" else "fp32", nsteps=14)
+    for lat in singles:
+        lat.close()
+    a.close()
+    b.close()
+
+
+def test_multi_step_batch_of_the_seeded_workload_shapes():
+    """The 64-lattice workload's member shapes (64^2 .. 1024^2) in one multi-step launch
+    against one launch per step, 12 steps."""
+    kss = _kss()
+    shapes = inputs.batch_specs(24)
+    specs = [dict(nx=size, ny=size, tau=tau) for size, tau, _, _ in shapes]
+    fields = [inputs.batch_fields(size, mach, seed) for size, _, mach, seed in shapes]
+    runs = []
+    for multi in (1, 0):
+        bt = kss.Batch(specs, precision="fp32", record=("kl",))
+        bt.set_tuning(multi_step=multi)
+        for k, f in enumerate(fields):
+            bt[k].set_fields(*f)
+        bt.step(12)
+        runs.append(bt)
+    for k in range(len(specs)):
+        _assert_same(runs[0][k], runs[1][k])
+    for bt in runs:
+        bt.close()
