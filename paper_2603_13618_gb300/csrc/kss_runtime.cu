@@ -148,15 +148,42 @@ cudaError_t launch_multi(kss_lattice* L, int mode, int nsteps) {
   return kss::launch_step_multi<S>(pa, pb, m, mode, ctas, L->stream);
 }
 
+// Scratch outputs of an evaluation that only a sensor field is wanted from: flags
+// [ny][pitch], tile counts [3][nty][ntx], then sums and counts.
+size_t eval_out_tiles(const kss_lattice* L) { return (size_t(L->pitch) * L->cfg.ny + 255) / 256 * 256; }
+size_t eval_out_small(const kss_lattice* L) {
+  return eval_out_tiles(L) + (sizeof(int32_t) * 3 * size_t(L->ntx) * L->nty + 255) / 256 * 256;
+}
+
+int ensure_eval_out(kss_lattice* L) {
+  if (L->eval_out) return KSS_OK;
+  if (cudaMalloc(&L->eval_out, eval_out_small(L) + 256) != cudaSuccess) {
+    cudaGetLastError();
+    L->eval_out = nullptr;
+    return fail(L, KSS_ERR_OOM, "evaluation scratch allocation failed");
+  }
+  return KSS_OK;
+}
+
 // Evaluate sensors / flags / tiles / sums of the state of the most recent step
 // (its pre-collision populations: the other buffer, streamed) or of the stored
 // state when no step was taken since the last set.  sensor >= 0 also writes
-// that sensor's field into evalplane.
+// that sensor's field into evalplane.  keep: the lattice's flags, tiles, sums and counts
+// already describe that state, so the pass writes its own into scratch (an all-sensor
+// pass sums in another order than the step did, and its KL series is another one).
 template <class S>
-cudaError_t launch_eval(kss_lattice* L, int sensor) {
+cudaError_t launch_eval(kss_lattice* L, int sensor, bool keep) {
   const bool pull = L->step > 0;
   const void* src = pull ? L->f[L->cur ^ 1] : L->f[L->cur];
   kss::StepParams<S> p = make_params<S>(L, src, nullptr);
+  if (keep) {
+    unsigned char* o = static_cast<unsigned char*>(L->eval_out);
+    p.flags = o;
+    p.tiles = reinterpret_cast<int32_t*>(o + eval_out_tiles(L));
+    p.tiles_def = p.tiles + 2 * size_t(L->ntx) * L->nty;
+    p.stat_sums = reinterpret_cast<double*>(o + eval_out_small(L));
+    p.stat_counts = reinterpret_cast<unsigned long long*>(o + eval_out_small(L) + 64);
+  }
   for (int s = 0; s < KSS_S_COUNT; ++s) p.rec_slot[s] = -1;
   uint32_t extra = 0;
   if (sensor >= 0) {
@@ -226,8 +253,10 @@ int ensure_outputs(kss_lattice* L, int sensor, const void** field) {
     return KSS_OK;
   }
   const int s = (sensor >= 0 && !where) ? sensor : -1;
+  int rc = KSS_OK;
+  if (have_out && (rc = ensure_eval_out(L))) return rc;
   KSS_CUDA(L, with_storage(L->cfg.precision, [&](auto tag) {
-             return launch_eval<typename decltype(tag)::type>(L, s);
+             return launch_eval<typename decltype(tag)::type>(L, s, have_out);
            }));
   L->out_step = L->step;
   if (s >= 0) {
@@ -271,6 +300,7 @@ void release(kss_lattice* L) {
   regrid_release(L);
   if (L->multi) cudaFree(L->multi);
   if (L->region) cudaFree(L->region);
+  if (L->eval_out) cudaFree(L->eval_out);
   void* bufs[] = {L->f[0], L->f[1], L->rec, L->evalplane, L->flags, L->tiles, L->part_sum,
                   L->part_cnt, L->small, L->staging, L->defer_list};
   for (void* b : bufs)

@@ -71,6 +71,8 @@ struct kss_lattice {
   void* regrid = nullptr;      // regridding workspace (kss_regrid.cu), made on first use
   void* multi = nullptr;       // multi-step kernel bookkeeping, made on first use
   uint8_t* region = nullptr;   // two-relaxation region [ny][pitch] (cfg.tau2 > 0 only)
+  void* eval_out = nullptr;    // flags, tiles, sums and counts of on-demand evaluations
+                               // while the step's own outputs are current, made on first use
 };
 
 namespace kss_rt {

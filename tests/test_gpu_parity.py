@@ -257,6 +257,28 @@ def test_device_pointer_paths():
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16dev"])
+def test_reading_other_sensors_keeps_the_step_outputs(prec):
+    """A sensor the step did not record is evaluated on demand (for alpha: the all-sensor
+    pass, which sums in another order and takes another KL series); the flags, tile
+    counts, counts and sums of the step must stay exactly those the step produced."""
+    kss = _kss()
+    nx, ny = 150, 70
+    rho, ux, uy = inputs.smooth_jump(nx, ny, seed=17, kmax=6)
+    lat = kss.Lattice(nx, ny, precision=prec, tau=0.62, record=("kl",))
+    lat.set_fields(rho, ux, uy)
+    lat.step(5)
+    before = (lat.read_flags(), lat.read_stats())
+    for name in ("alpha", "sigma_h", "kn", "qe"):
+        lat.read_sensor(name)
+    after = (lat.read_flags(), lat.read_stats())
+    for x, y in zip(before[0], after[0]):
+        np.testing.assert_array_equal(x, y)
+    for x, y in zip(before[1], after[1]):
+        np.testing.assert_array_equal(x, y)
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16dev"])
 def test_pinned_host_inputs(prec):
     """Page-locked host inputs are read by the initialisation kernels directly; pageable
     ones (or a mix) go through the staging copy.  Both give the same state bit for bit."""
