@@ -222,6 +222,12 @@ def run_batch(args):
     clocks = clk.summary()
     value = cells * K / (total_ms * 1e-3) / 1e6
     multi = bool(b.tuning["multi_step"])
+    # the multi-step launch at each CTA height (the tuner times per-step launches)
+    multi_rows = {}
+    for rows in (16, 32, 64):
+        b.set_tuning(rows=rows, ctas_per_sm=0, graph=1, multi_step=1)
+        b.step(args.warmup)
+        multi_rows[rows] = timed(lambda: b.step(K)) / K
     # the same steps as one launch per step: a captured graph, then direct launches
     b.set_tuning(rows=tuning["rows"], ctas_per_sm=tuning["ctas_per_sm"], graph=1,
                  multi_step=0)
@@ -261,6 +267,7 @@ def run_batch(args):
                      "kernel": ("batch_kernel_multi<float, MODE_STD> (all steps in one "
                                 "cooperative launch)" if multi
                                 else "batch_step_kernel<float, MODE_STD>")},
+        "multi_step_ms_by_rows": multi_rows,
         "graph_of_per_step_launches": {"value": cells * K / (graph_ms * 1e-3) / 1e6,
                                        "unit": "MLUPS", "ms_per_step": graph_ms / K},
         "direct_launches": {"value": cells * K / (direct_ms * 1e-3) / 1e6, "unit": "MLUPS",

@@ -366,7 +366,8 @@ void destroy_batch(kss_batch* B) {
   delete B;
 }
 
-// ---- autotuner cache: "key<TAB>rows<TAB>ctas_per_sm<TAB>ms" lines ----
+// ---- autotuner cache: "key<TAB>rows<TAB>ctas_per_sm<TAB>ms<TAB>multi_step" lines (a
+// line without the last field is a per-step choice) ----
 std::string tune_key(const kss_batch* B) {
   cudaDeviceProp prop{};
   std::string name = "unknown";
@@ -390,12 +391,14 @@ bool cache_lookup(const char* path, const std::string& key, kss_batch_tuning* t)
     char* tab = std::strchr(line, '\t');
     if (!tab) continue;
     if (std::string(line, tab - line) != key) continue;
-    int rows = 0, cps = 0;
+    int rows = 0, cps = 0, multi = 0;
     double ms = 0;
-    if (std::sscanf(tab + 1, "%d\t%d\t%lf", &rows, &cps, &ms) == 3) {
+    const int got = std::sscanf(tab + 1, "%d\t%d\t%lf\t%d", &rows, &cps, &ms, &multi);
+    if (got >= 3) {
       t->rows = rows;
       t->ctas_per_sm = cps;
       t->ms_per_step = ms;
+      t->multi_step = got == 4 ? (multi != 0) : 0;
       found = true;  // the last entry for a key wins
     }
   }
@@ -406,7 +409,8 @@ bool cache_lookup(const char* path, const std::string& key, kss_batch_tuning* t)
 void cache_append(const char* path, const std::string& key, const kss_batch_tuning& t) {
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s\t%d\t%d\t%.9g\n", key.c_str(), t.rows, t.ctas_per_sm, t.ms_per_step);
+  std::fprintf(f, "%s\t%d\t%d\t%.9g\t%d\n", key.c_str(), t.rows, t.ctas_per_sm, t.ms_per_step,
+               t.multi_step);
   std::fclose(f);
 }
 
@@ -596,10 +600,14 @@ int kss_batch_autotune(kss_batch* B, const char* cache_path, int32_t steps,
   const std::string key = tune_key(B);
   kss_batch_tuning best = B->tun;
   int rc = KSS_OK;
+  // multi-step launches are timed too when the members' steps qualify for them (every
+  // member an output step of the {Kn, KL, neq} set every step) and they are enabled
+  bool multi_ok = B->tun.multi_step && B->mode_out == kss::MODE_STD;
+  for (const kss_lattice* L : B->mem) multi_ok = multi_ok && L->cfg.output_every == 1;
   if (cache_path && cache_lookup(cache_path, key, &best) && valid_rows(B, best.rows) &&
       best.ctas_per_sm >= 0 && best.ctas_per_sm <= 64) {
     best.graph = B->tun.graph;
-    best.multi_step = B->tun.multi_step;
+    if (!multi_ok) best.multi_step = B->tun.multi_step;
     const double ms = best.ms_per_step;
     if ((rc = kss_batch_set_tuning(B, &best))) return rc;
     B->tun.ms_per_step = ms;
@@ -623,6 +631,7 @@ int kss_batch_autotune(kss_batch* B, const char* cache_path, int32_t steps,
       kss_batch_tuning t = B->tun;
       t.rows = rows;
       t.ctas_per_sm = cps;
+      if (multi_ok) t.multi_step = 0;  // these are per-step launches
       if ((rc = kss_batch_set_tuning(B, &t))) break;
       // every launch reads the stored states (table[par]) and writes the other buffers
       cudaError_t e = cudaSuccess;
@@ -644,6 +653,61 @@ int kss_batch_autotune(kss_batch* B, const char* cache_path, int32_t steps,
       }
     }
     if (rc) break;
+  }
+  if (!rc && multi_ok) {
+    // a multi-step launch advances the states: keep every member's stored state aside
+    size_t total = 0;
+    for (const kss_lattice* L : B->mem) total += 9 * size_t(L->plane) * L->esz;
+    unsigned char* snap = nullptr;
+    if (cudaMalloc(&snap, total) != cudaSuccess) {
+      cudaGetLastError();
+      rc = bfail(B, KSS_ERR_OOM, "autotune: state snapshot allocation failed");
+    }
+    size_t o = 0;
+    for (kss_lattice* L : B->mem) {
+      if (rc) break;
+      const size_t bytes = 9 * size_t(L->plane) * L->esz;
+      if (cudaMemcpyAsync(snap + o, L->f[L->cur], bytes, cudaMemcpyDeviceToDevice, B->stream) !=
+          cudaSuccess)
+        rc = bfail(B, KSS_ERR_CUDA, "autotune: state snapshot copy failed");
+      o += bytes;
+    }
+    for (int rows : rows_c) {
+      if (rc || !valid_rows(B, rows)) continue;
+      kss_batch_tuning t = B->tun;
+      t.rows = rows;
+      t.ctas_per_sm = 0;
+      t.multi_step = 1;
+      if ((rc = kss_batch_set_tuning(B, &t))) break;
+      cudaError_t e = launch_multi(B, 2);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, B->stream);
+      if (e == cudaSuccess) e = launch_multi(B, std::max(2, int(steps)));
+      if (e == cudaSuccess) e = cudaEventRecord(e1, B->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        rc = bfail(B, KSS_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+        break;
+      }
+      const double per = double(ms) / std::max(2, int(steps));
+      if (best.ms_per_step < 0 || per < best.ms_per_step) {
+        best = t;
+        best.ms_per_step = per;
+      }
+    }
+    if (snap) {
+      o = 0;
+      for (kss_lattice* L : B->mem) {
+        const size_t bytes = 9 * size_t(L->plane) * L->esz;
+        if (cudaMemcpyAsync(L->f[L->cur], snap + o, bytes, cudaMemcpyDeviceToDevice,
+                            B->stream) != cudaSuccess && !rc)
+          rc = bfail(B, KSS_ERR_CUDA, "autotune: state restore failed");
+        o += bytes;
+      }
+      cudaStreamSynchronize(B->stream);
+      cudaFree(snap);
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -220,7 +220,7 @@ def test_autotune_keeps_states_and_uses_its_cache(tmp_path):
     assert t["rows"] in (16, 32, 64) and t["ctas_per_sm"] in (0, 2, 3, 4)
     assert t["ms_per_step"] > 0
     lines = open(cache).read().splitlines()
-    assert len(lines) == 1 and lines[0].count("\t") == 3
+    assert len(lines) == 1 and lines[0].count("\t") == 4
     # the stored states are unchanged and the step-0 outputs are evaluated again
     for k in range(len(specs)):
         _assert_same(b[k], singles[k])
@@ -237,7 +237,8 @@ def test_autotune_keeps_states_and_uses_its_cache(tmp_path):
     # a second batch of the same shape takes the cached choice without timing
     b2 = _batch(specs, "fp32")
     t2 = b2.autotune(cache, steps=3)
-    assert (t2["rows"], t2["ctas_per_sm"]) == (t["rows"], t["ctas_per_sm"])
+    assert (t2["rows"], t2["ctas_per_sm"], t2["multi_step"]) == (t["rows"], t["ctas_per_sm"],
+                                                                 t["multi_step"])
     assert t2["ms_per_step"] == pytest.approx(t["ms_per_step"], rel=1e-6)
     assert len(open(cache).read().splitlines()) == 1
     b2.close()
@@ -326,3 +327,23 @@ def test_multi_step_batch_of_the_seeded_workload_shapes():
         _assert_same(runs[0][k], runs[1][k])
     for bt in runs:
         bt.close()
+
+
+def test_autotune_times_multi_step_launches_and_restores_the_states(tmp_path):
+    """Every member an output step every step: the tuner also times multi-step launches
+    (which advance the states) at each CTA height and restores the stored states."""
+    specs = [dict(sp, output_every=1, tile=min(sp["tile"], 16)) for sp in SPECS]
+    b = _batch(specs, "fp32")
+    singles = _singles(specs, "fp32")
+    t = b.autotune(str(tmp_path / "tune.txt"), steps=4)
+    assert t["multi_step"] in (0, 1) and t["ms_per_step"] > 0
+    for k in range(len(specs)):
+        np.testing.assert_array_equal(b[k].get_populations(), singles[k].get_populations())
+    b.step(6)
+    for lat in singles:
+        lat.step(6)
+    for k in range(len(specs)):
+        _assert_same(b[k], singles[k], sums_exact=(t["rows"] == 32), nsteps=6)
+    for lat in singles:
+        lat.close()
+    b.close()
