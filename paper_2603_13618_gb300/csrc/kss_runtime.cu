@@ -393,9 +393,10 @@ int kss_create(const kss_config* cfg, kss_lattice** out) {
     delete L;
     return KSS_ERR_CUDA;
   }
-  // CTA height: 32 rows; 64 rows when even 64-row CTAs make at least 8 waves of the 3
-  // resident CTAs per SM (the per-CTA epilogue then costs more than the longer tail:
-  // fused 8192^2 FP32 0.876 vs 0.914 ms, while 4096^2 gains nothing)
+  // CTA height: 32 rows; 64 rows when even 64-row CTAs make at least 4 waves of the 3
+  // resident CTAs per SM (the per-CTA epilogue and, in multi-step launches, the per-block
+  // dependency waits then cost more than the longer tail: fused 4096^2 FP32 multi-step
+  // 0.2282 vs 0.2306 ms per step, single launches 0.2415 vs 0.2437 ms)
   auto grid_for = [&](int bands) {
     return with_storage(cfg->precision, [&](auto tag) {
       return kss::step_grid<typename decltype(tag)::type>(cfg->nx, cfg->ny, cfg->tile, bands);
@@ -404,7 +405,7 @@ int kss_create(const kss_config* cfg, kss_lattice** out) {
   L->bands = kss::step_bands(cfg->tile);
   if (cfg->tile <= 64 && 64 % cfg->tile == 0 && 64 / cfg->tile <= kss::kMaxBands) {
     const dim3 g64 = grid_for(64 / cfg->tile);
-    if ((long long)g64.x * g64.y >= 8LL * 3 * L->nsm) L->bands = 64 / cfg->tile;
+    if ((long long)g64.x * g64.y >= 4LL * 3 * L->nsm) L->bands = 64 / cfg->tile;
   }
   const dim3 g = grid_for(L->bands);
   L->nblocks = int(g.x * g.y);
