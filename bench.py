@@ -25,8 +25,9 @@ lattice per step.
 Adaptive-algorithm-refinement workload (--workload aar4096): the same 4096^2 lattice
 with the two-relaxation model in the switched region (tau2 = 1/2 + (3/16)/(tau - 1/2)):
 output steps with the {Kn, KL, neq} set and neq as the switch sensor (the region then
-follows the flags), with all of Table 1 and the quasi-equilibrium sensor as the switch,
-and plain steps in a fixed 40 % region, each against the same steps with BGK only.
+follows the flags), the same with the quasi-equilibrium sensor as the switch, all of
+Table 1 with that switch, and plain steps in a fixed 40 % region, each against the same
+steps with BGK only.
 
 N > 1 (launched by torchrun) runs one independent lattice per rank (replicas, weak
 scaling); rank 0 prints one JSON line.  --impl reference times the CPU oracle on the
@@ -447,7 +448,8 @@ def run_aar(args):
         # name, tau2, switch sensor, output_every, record, bytes per LUP
         ("aar_std", tau2, "neq", 1, ("kl",), 72 + 5 + 2),
         ("bgk_std", 0.0, "neq", 1, ("kl",), 72 + 5),
-        ("aar_qe_full", tau2, "qe", 1, ("kl",), 72 + 5 + 2),
+        ("aar_qe", tau2, "qe", 1, ("kl",), 72 + 5 + 2),
+        ("aar_all_sensors", tau2, "qe", 1, ("kl", "alpha"), 72 + 5 + 2),
         ("aar_plain", tau2, "neq", 0, (), 72 + 1),
         ("bgk_plain", 0.0, "neq", 0, (), 72),
     )

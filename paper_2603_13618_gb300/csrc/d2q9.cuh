@@ -233,6 +233,13 @@ __device__ __forceinline__ void cell_update(const T (&ft)[9], T omega, T tau, T 
   o.sv[S_KN] = nonpos ? kInf : kn;
   o.sv[S_NEQ] = neq;
   o.sv[S_KL] = nonpos ? kInf : fabs(kl);
+  // sum_q |f*_q - f^eq_q| = sum_q |f^neq_q - f^neq_-q| / 2 = sum over the 4 pairs of
+  // |f^neq_q - f^neq_-q| (in the fused pair order); 0 for BGK, whose quasi-equilibrium is
+  // the equilibrium
+  o.sv[S_QE] = trt.qe ? ((fabs(fneq[1] - fneq[3]) + fabs(fneq[2] - fneq[4])) +
+                         fabs(fneq[5] - fneq[7])) +
+                            fabs(fneq[6] - fneq[8])
+                      : T(0);
   if (MODE != MODE_FULL) return;
 
   // ---- class 1: the non-equilibrium pressure tensor P^neq = sum c c f^neq ----
@@ -252,11 +259,6 @@ __device__ __forceinline__ void cell_update(const T (&ft)[9], T omega, T tau, T 
     const T qx = fma(ux, pxx, uy * pxy), qy = fma(ux, pxy, uy * pyy);
     o.sv[S_QH] = Num<T>::sqrt_(fma(qx, qx, qy * qy));
   }
-  // sum_q |f*_q - f^eq_q| = sum_q |f^neq_q - f^neq_-q| / 2 = sum over the 4 pairs of
-  // |f^neq_q - f^neq_-q|; 0 for BGK, whose quasi-equilibrium is the equilibrium
-  o.sv[S_QE] = trt.qe ? (fabs(fneq[1] - fneq[3]) + fabs(fneq[2] - fneq[4])) +
-                            (fabs(fneq[5] - fneq[7]) + fabs(fneq[6] - fneq[8]))
-                      : T(0);
 
   // ---- entropy-based sensors ----
   // L_q = ln(f^eq_q / (w_q rho)) = ln(1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u)

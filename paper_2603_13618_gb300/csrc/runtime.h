@@ -39,6 +39,7 @@ struct kss_lattice {
   long long plane = 0;      // elements per plane
   int ntx = 0, nty = 0, nblocks = 0;
   int bands = 0;            // tile bands per CTA of the vector step (CTA height bands * tile)
+  int bands_plain = 0;      // the same for steps without outputs
   int nsm = 0;              // SMs of the device (persistent grid of the TMA kernel)
   void* f[2] = {nullptr, nullptr};
   int cur = 0;              // f[cur] holds the stored state
@@ -106,7 +107,13 @@ inline uint32_t needed_mask(const kss_lattice* L, uint32_t extra) {
   return m;
 }
 
-inline int mode_for(uint32_t mask) { return (mask & ~kss::kStdMask) ? kss::MODE_FULL : kss::MODE_STD; }
+// The kernel of an output step computing the sensors in mask: {Kn, KL, neq} (and qe on the
+// steps of a lattice with adaptive algorithm refinement, qe_std) in the fused pair loop,
+// anything else in the all-sensor kernel.
+inline int mode_for(uint32_t mask, bool qe_std = false) {
+  const uint32_t fused = kss::kStdMask | (qe_std ? 1u << KSS_S_QE : 0u);
+  return (mask & ~fused) ? kss::MODE_FULL : kss::MODE_STD;
+}
 
 // Codec of a lattice's storage type S (empty unless S is the FP16 deviation storage).
 template <class S>

@@ -375,6 +375,7 @@ __device__ __forceinline__ uint32_t load_bytes(const uint8_t* p) {
 template <class T>
 struct StdAcc {
   T kn[Vec<T>::N], neq[Vec<T>::N], kl[Vec<T>::N];
+  T qe[Vec<T>::N];  // AAR steps only: the quasi-equilibrium sensor
 };
 
 // Relax one population of V cells in place (BGK: f <- f - (f - f^eq)/tau) and, on
@@ -482,6 +483,12 @@ __device__ __forceinline__ void pair_pops(arith_t<S> (&fp)[Vec<S>::N], arith_t<S
           const F2 P = pack2(fp[k], fp[k + 1]), M = pack2(fm[k], fm[k + 1]);
           const F2 np = sub2(P, pack2(ep[k], ep[k + 1]));
           const F2 nm = sub2(M, pack2(em[k], em[k + 1]));
+          if (OUT) {
+            float d0, d1;
+            unpack2(sub2(np, nm), d0, d1);
+            a.qe[k] += fabsf(d0);
+            a.qe[k + 1] += fabsf(d1);
+          }
           unpack2(fma2(nB, nm, fma2(nA, np, P)), fp[k], fp[k + 1]);
           unpack2(fma2(nB, np, fma2(nA, nm, M)), fm[k], fm[k + 1]);
         }
@@ -493,6 +500,7 @@ __device__ __forceinline__ void pair_pops(arith_t<S> (&fp)[Vec<S>::N], arith_t<S
           const bool sw = ((mbits >> (8 * k)) & 0xffu) != 0u;
           const T A = sw ? trt.a : omega, B = sw ? trt.b : T(0);
           const T np = fp[k] - ep[k], nm = fm[k] - em[k];
+          if (OUT) a.qe[k] += fabs(np - nm);
           fp[k] = fma(-B, nm, fma(-A, np, fp[k]));
           fm[k] = fma(-B, np, fma(-A, nm, fm[k]));
         }
@@ -510,14 +518,18 @@ __device__ __forceinline__ void pair_pops(arith_t<S> (&fp)[Vec<S>::N], arith_t<S
   if (STORE && cv) pop_vstore<S>(dst_m, fm, QM, codec);
 }
 
-// Which of {Kn, KL, neq} a flag tests (ids validated on the host); decided once per
-// thread so the per-cell choice is two selects.
+// Which of {Kn, KL, neq} (and, on AAR steps, qe) a flag tests (ids validated on the
+// host); decided once per thread so the per-cell choice is a few selects.
 struct Pick3 {
-  bool is_kn, is_kl;
-  __device__ explicit Pick3(int id) : is_kn(id == S_KN), is_kl(id == S_KL) {}
+  bool is_kn, is_kl, is_qe;
+  __device__ explicit Pick3(int id) : is_kn(id == S_KN), is_kl(id == S_KL), is_qe(id == S_QE) {}
   template <class T>
   __device__ __forceinline__ T operator()(T kn, T kl, T neq) const {
     return is_kn ? kn : (is_kl ? kl : neq);
+  }
+  template <class T>
+  __device__ __forceinline__ T operator()(T kn, T kl, T neq, T qe) const {
+    return is_kn ? kn : (is_kl ? kl : (is_qe ? qe : neq));
   }
 };
 
@@ -681,16 +693,17 @@ __device__ __forceinline__ uint32_t fix_cell(const StepParams<S>& p, const Pick3
   T cell[9], dummy[9];
   reload_cell<S, PULL, CG>(p, i, j, cell);
   CellOut<T> co;
-  cell_update<T, MODE_STD, false>(cell, p.omega, p.tau, dummy, co);
-  const T kn = co.sv[S_KN], kl = co.sv[S_KL], neq = co.sv[S_NEQ];
-  const bool rr = pr(kn, kl, neq) > p.thr_r;
-  const bool ss = p.switch_on && (ps(kn, kl, neq) > p.thr_s);
+  cell_update<T, MODE_STD, false>(cell, p.omega, p.tau, dummy, co, p.trt);
+  const T kn = co.sv[S_KN], kl = co.sv[S_KL], neq = co.sv[S_NEQ], qe = co.sv[S_QE];
+  const bool rr = pr(kn, kl, neq, qe) > p.thr_r;
+  const bool ss = p.switch_on && (ps(kn, kl, neq, qe) > p.thr_s);
   const bool np = co.nonpos;
   const long long off = (long long)j * p.pitch + i;
   p.flags[off] = uint8_t(uint32_t(rr) | (uint32_t(ss) << 1) | (uint32_t(np) << 7));
   if (p.rec_slot[S_KN] >= 0) p.rec[p.rec_slot[S_KN] * p.plane + off] = kn;
   if (p.rec_slot[S_KL] >= 0) p.rec[p.rec_slot[S_KL] * p.plane + off] = kl;
   if (p.rec_slot[S_NEQ] >= 0) p.rec[p.rec_slot[S_NEQ] * p.plane + off] = neq;
+  if (p.trt.qe && p.rec_slot[S_QE] >= 0) p.rec[p.rec_slot[S_QE] * p.plane + off] = qe;
   return uint32_t(rr) | (uint32_t(ss) << 1) | (uint32_t(np) << 2);
 }
 
@@ -786,6 +799,7 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
       base[k] = fma(T(-1.5), fma(ux[k], ux[k], uy[k] * uy[k]), T(1));
       rw1[k] = rho * T(1.0 / 9.0);
       a.kn[k] = a.neq[k] = a.kl[k] = T(0);
+      if (AAR) a.qe[k] = T(0);
       if (OUT) {
         rs += rho;
         xs += jx;
@@ -839,8 +853,8 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
         // fixup_kernel).
         const bool fast = (rw1[k] > T(0)) & (base[k] > T(0.55)) & (a.kn[k] < T(0.0625));
         a.kl[k] = fabs(a.kl[k]);
-        const T er = pr(a.kn[k], a.kl[k], a.neq[k]);
-        const T es = ps(a.kn[k], a.kl[k], a.neq[k]);
+        const T er = AAR ? pr(a.kn[k], a.kl[k], a.neq[k], a.qe[k]) : pr(a.kn[k], a.kl[k], a.neq[k]);
+        const T es = AAR ? ps(a.kn[k], a.kl[k], a.neq[k], a.qe[k]) : ps(a.kn[k], a.kl[k], a.neq[k]);
         const bool r = er > p.thr_r;  // NaN (zeroed padding cells) compares false
         const bool sw = p.switch_on && (es > p.thr_s);
         const uint32_t b = fast ? (uint32_t(r) | (uint32_t(sw) << 1)) : kFlagDeferred;
@@ -855,6 +869,7 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
         if (p.rec_slot[S_KN] >= 0) vstore<T>(p.rec + p.rec_slot[S_KN] * p.plane + off, a.kn);
         if (p.rec_slot[S_KL] >= 0) vstore<T>(p.rec + p.rec_slot[S_KL] * p.plane + off, a.kl);
         if (p.rec_slot[S_NEQ] >= 0) vstore<T>(p.rec + p.rec_slot[S_NEQ] * p.plane + off, a.neq);
+        if (AAR && p.rec_slot[S_QE] >= 0) vstore<T>(p.rec + p.rec_slot[S_QE] * p.plane + off, a.qe);
       }
     }
   }

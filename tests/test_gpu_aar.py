@@ -65,22 +65,23 @@ def _check_outputs(lat, prec, X, tau, thr_r, thr_s, tile, switch, names, nsteps=
 
 @pytest.mark.parametrize("nx,ny,tile", [(37, 21, 16), (130, 67, 8), (5, 1, 8), (1, 5, 8),
                                         (200, 9, 32)])
-@pytest.mark.parametrize("outputs", ["plain", "std", "full"])
+@pytest.mark.parametrize("outputs", ["plain", "std", "std_qe", "full"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_one_step_in_a_prescribed_region(prec, outputs, nx, ny, tile):
-    """kss_set_aar_region, then one step of each kernel variant (no outputs, the
-    {Kn, KL, neq} set with neq as the switch sensor, all of Table 1 with qe as the switch
-    sensor) against oracle.collide_aar; the output step's switch flags become the
-    region."""
+    """kss_set_aar_region, then one step of each kernel variant (no outputs; the
+    {Kn, KL, neq} set with neq as the switch sensor; the same set plus qe, computed in the
+    fused pair loop, as the switch; all of Table 1 with qe as the switch) against
+    oracle.collide_aar; the output step's switch flags become the region."""
     kss = _kss()
     tau, tau2 = 0.7, 1.35
     X = _state(nx, ny, seed=7 * nx + ny, tau=tau)
     reg = inputs.random_region(nx, ny, seed=nx + 3 * ny)
     ref0, _ = oracle.sensor_fields(X, tau, pull=True, two_relax=True)
-    switch = "qe" if outputs == "full" else "neq"
+    switch = "neq" if outputs == "std" else "qe"
     thr_r, thr_s = 1e-3, _split(ref0[oracle.SENSOR_ID[switch]])
     kw = {"plain": dict(output_every=0, record=()),
           "std": dict(output_every=1, record=("kn", "kl", "neq")),
+          "std_qe": dict(output_every=1, record=("kn", "qe")),
           "full": dict(output_every=1, record=ALL)}[outputs]
     lat = kss.Lattice(nx, ny, precision=prec, tau=tau, tau2=tau2, tile=tile,
                       refine_threshold=thr_r, switch_sensor=switch, switch_threshold=thr_s,
@@ -102,7 +103,7 @@ def test_one_step_in_a_prescribed_region(prec, outputs, nx, ny, tile):
     if outputs == "plain":
         np.testing.assert_array_equal(lat.get_aar_region(), (reg != 0).astype(np.uint8))
     else:
-        names = ("kn", "kl", "neq") if outputs == "std" else ALL
+        names = {"std": ("kn", "kl", "neq"), "std_qe": ("kn", "qe", "kl")}.get(outputs, ALL)
         flags = _check_outputs(lat, prec, X, tau, thr_r, thr_s, tile, switch, names)
         np.testing.assert_array_equal(lat.get_aar_region(), (flags >> 1) & 1)
     lat.close()
@@ -221,8 +222,9 @@ def test_empty_region_is_bgk_bit_for_bit(prec, every):
     np.testing.assert_array_equal(states[0], states[1])
 
 
+@pytest.mark.parametrize("switch", ["neq", "qe"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_deferred_cells_write_the_region(prec):
+def test_deferred_cells_write_the_region(prec, switch):
     """Far from equilibrium (populations perturbed by up to 30 %) the {Kn, KL, neq} step
     defers most cells to its exact recomputation, which decides their switch flags after
     the rows were stored: the region must still be the step's switch flags."""
@@ -233,9 +235,10 @@ def test_deferred_cells_write_the_region(prec):
     f = oracle.init_equilibrium(rho, ux, uy) * (1.0 + 0.3 * rng.uniform(-1, 1, (9, ny, nx)))
     reg = inputs.random_region(nx, ny, seed=321)
     ref, _ = oracle.sensor_fields(f, tau, pull=True, two_relax=True)
-    thr_r, thr_s = 0.5, _split(ref[oracle.SENSOR_ID["neq"]])
+    thr_r, thr_s = 0.5, _split(ref[oracle.SENSOR_ID[switch]])
     lat = kss.Lattice(nx, ny, precision=prec, tau=tau, tau2=tau2, refine_threshold=thr_r,
-                      switch_threshold=thr_s, record=("kl", "kn", "neq"))
+                      switch_sensor=switch, switch_threshold=thr_s,
+                      record=("kl", "kn", "neq", "qe"))
     lat.set_populations(np.ascontiguousarray(f))
     lat.set_aar_region(reg)
     lat.step(1)
@@ -243,7 +246,8 @@ def test_deferred_cells_write_the_region(prec):
     u = parity.UNIT_ROUNDOFF[prec]
     got = lat.get_populations()
     assert np.max(np.abs(got - want) / np.abs(want)) <= 64 * u * math.sqrt(2)
-    flags = _check_outputs(lat, prec, f, tau, thr_r, thr_s, 16, "neq", ("kn", "kl", "neq"))
+    flags = _check_outputs(lat, prec, f, tau, thr_r, thr_s, 16, switch,
+                           ("kn", "kl", "neq", "qe"))
     region = lat.get_aar_region()
     np.testing.assert_array_equal(region, (flags >> 1) & 1)
     assert 0 < region.sum() < nx * ny
