@@ -26,7 +26,8 @@
 // sum_q D_q = 1 and sum_q E_q = 0, so no O(1) terms cancel in floating point.
 //
 // Layout and work decomposition as the fused step (pitched SoA planes), with 2 cells
-// per thread: a CTA of 8 warps covers 64 columns x kAdjRows rows.
+// per thread: a CTA of 8 warps covers 64 columns x p.rows rows (8, 16 or 32: small lattices
+// take short CTAs so that the grid fills the GPU).
 #pragma once
 
 #include "step_kernel.cuh"
@@ -34,7 +35,7 @@
 namespace kss {
 
 constexpr int kAdjV = 2;      // cells per thread
-constexpr int kAdjRows = 32;  // rows per CTA (4 per warp)
+constexpr int kAdjRows = 32;  // largest rows per CTA (4 per warp)
 
 template <class T>
 struct AdjParams {
@@ -50,6 +51,7 @@ struct AdjParams {
   double* acc;           // the launch's total is added to *acc (FP64)
   long long plane;
   int pitch, nx, ny;
+  int rows;              // rows per CTA (grid adj_grid(nx, ny, rows))
   T omega;
 };
 
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(kThreads) adj_objective_kernel(const AdjParams
   const int i0 = (blockIdx.x * 32 + lane) * V;
   const bool cv = i0 < p.nx;
   const int nvalid = cv ? min(V, p.nx - i0) : 0;
-  const int j0 = blockIdx.y * kAdjRows, j1 = min(j0 + kAdjRows, p.ny);
+  const int j0 = blockIdx.y * p.rows, j1 = min(j0 + p.rows, p.ny);
   Acc<T> sum;
   for (int j = j0 + warp; j < j1; j += kWarps) {
     T ft[9][V];
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(kThreads) adj_step_kernel(const AdjParams<T> p
   const int i0 = (blockIdx.x * 32 + lane) * V;
   const bool cv = i0 < p.nx;
   const int nvalid = cv ? min(V, p.nx - i0) : 0;
-  const int j0 = blockIdx.y * kAdjRows, j1 = min(j0 + kAdjRows, p.ny);
+  const int j0 = blockIdx.y * p.rows, j1 = min(j0 + p.rows, p.ny);
   const T om = p.omega, om1 = T(1) - p.omega;
   Acc<T> sum;
   for (int j = j0 + warp; j < j1; j += kWarps) {
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(kThreads) adj_final_kernel(const AdjParams<T> 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i0 = (blockIdx.x * 32 + lane) * V;
   const bool cv = i0 < p.nx;
-  const int j0 = blockIdx.y * kAdjRows, j1 = min(j0 + kAdjRows, p.ny);
+  const int j0 = blockIdx.y * p.rows, j1 = min(j0 + p.rows, p.ny);
   for (int j = j0 + warp; j < j1; j += kWarps) {
     T l[9][V];
     adj_pull_row<T, true>(p.lam_in, p.plane, p.pitch, p.nx, p.ny, j, i0, lane, cv, l);

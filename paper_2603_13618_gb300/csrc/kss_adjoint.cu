@@ -20,6 +20,8 @@ struct kss_adjoint {
   long long plane = 0;
   size_t state_bytes = 0;  // one population buffer (9 planes)
   int nck = 0;             // checkpoints kept: f^0, f^E, f^2E, ... (E = checkpoint_every)
+  int adj_rows = 32;       // rows per CTA of the adjoint kernels (fill_rows)
+  int step_rows = 32;      // rows per CTA of the forward steps (fill_rows)
   unsigned char* ck = nullptr;   // nck states
   unsigned char* seg = nullptr;  // checkpoint_every states: a recomputed segment
   unsigned char* work[2] = {nullptr, nullptr};  // forward ping-pong
@@ -78,10 +80,10 @@ cudaError_t plain_step(const kss_adjoint* A, const void* src, void* dst) {
   p.pitch = A->pitch;
   p.nx = A->cfg.nx;
   p.ny = A->cfg.ny;
-  p.tile = 16;
-  p.bands = kss::step_bands(16);
-  p.ntx = (A->cfg.nx + 15) / 16;
-  p.nty = (A->cfg.ny + 15) / 16;
+  p.tile = 8;  // no outputs: the tile only shapes the grid, step_rows rows per CTA
+  p.bands = A->step_rows / 8;
+  p.ntx = (A->cfg.nx + 7) / 8;
+  p.nty = (A->cfg.ny + 7) / 8;
   p.omega = T(1.0 / A->tau);
   p.tau = T(A->tau);
   for (int s = 0; s < KSS_S_COUNT; ++s) p.rec_slot[s] = -1;
@@ -97,6 +99,7 @@ kss::AdjParams<T> adj_params(kss_adjoint* A) {
   p.pitch = A->pitch;
   p.nx = A->cfg.nx;
   p.ny = A->cfg.ny;
+  p.rows = A->adj_rows;
   p.omega = T(1.0 / A->tau);
   return p;
 }
@@ -207,7 +210,14 @@ int kss_adjoint_create(const kss_adjoint_config* cfg, kss_adjoint** out) {
     A->stream = static_cast<cudaStream_t>(cfg->stream);
   }
   const size_t n = size_t(cfg->nx) * cfg->ny;
-  const dim3 g = kss::adj_grid(cfg->nx, cfg->ny);
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, A->device) != cudaSuccess) {
+    cudaGetLastError();
+    nsm = 1;
+  }
+  A->adj_rows = kss::fill_rows(cfg->nx, cfg->ny, 32 * kss::kAdjV, nsm);
+  A->step_rows = kss::fill_rows(cfg->nx, cfg->ny, 32 * (A->fp32 ? kss::Vec<float>::N : kss::Vec<double>::N), nsm);
+  const dim3 g = kss::adj_grid(cfg->nx, cfg->ny, A->adj_rows);
   struct {
     void** p;
     size_t bytes;

@@ -61,7 +61,10 @@ cudaError_t launch_one_step(kss_lattice* L, bool out) {
   kss::StepParams<S> p = make_params<S>(L, L->f[L->cur], L->f[L->cur ^ 1]);
   const int mode = out ? mode_for(needed_mask(L, L->cfg.record_mask), L->region != nullptr)
                        : MODE_PLAIN;
-  if (mode == MODE_PLAIN) p.bands = L->bands_plain;
+  if (mode == MODE_PLAIN) {  // the tile only shapes the grid of a step without outputs
+    p.tile = 8;
+    p.bands = L->rows_plain / 8;
+  }
   if (L->region) return kss::launch_step_aar<S>(p, mode, L->stream);
   // (the vector kernel recomputes its deferred cells itself, at the end of each CTA; FP16
   // deviation storage has the vector kernel only)
@@ -404,13 +407,18 @@ int kss_create(const kss_config* cfg, kss_lattice** out) {
       return kss::step_grid<typename decltype(tag)::type>(cfg->nx, cfg->ny, cfg->tile, bands);
     });
   };
-  // Steps without outputs have no epilogue to amortise: they keep 32 rows up to 8 waves of
-  // 64-row CTAs (4096^2 FP32 plain step 0.181 vs 0.185 ms with 64 rows).
-  L->bands = L->bands_plain = kss::step_bands(cfg->tile);
+  // Steps without outputs have no epilogue to amortise and no tile counts: 64 rows from 8
+  // waves of such CTAs up (4096^2 FP32 plain step 0.181 vs 0.185 ms with 64 rows), else the
+  // tallest CTA of 32, 16 or 8 rows that gives two CTAs per SM (small lattices fill the GPU).
+  L->bands = kss::step_bands(cfg->tile);
+  const int cols = with_storage(cfg->precision, [](auto tag) {
+    return 32 * kss::Vec<typename decltype(tag)::type>::N;
+  });
+  L->rows_plain = kss::fill_rows(cfg->nx, cfg->ny, cols, L->nsm);
   if (cfg->tile <= 64 && 64 % cfg->tile == 0 && 64 / cfg->tile <= kss::kMaxBands) {
     const dim3 g64 = grid_for(64 / cfg->tile);
     if ((long long)g64.x * g64.y >= 4LL * 3 * L->nsm) L->bands = 64 / cfg->tile;
-    if ((long long)g64.x * g64.y >= 8LL * 3 * L->nsm) L->bands_plain = 64 / cfg->tile;
+    if ((long long)g64.x * g64.y >= 8LL * 3 * L->nsm) L->rows_plain = 64;
   }
   const dim3 g = grid_for(L->bands);
   L->nblocks = int(g.x * g.y);

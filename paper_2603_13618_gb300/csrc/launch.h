@@ -70,10 +70,20 @@ cudaError_t launch_step_tma(const StepParams<T>& p, int mode, TmaPlan plan, int 
 template <class T>
 cudaError_t launch_fixup(const StepParams<T>& p, bool pull, int ctas, cudaStream_t stream);
 
-// Adjoint kernels (adjoint_kernel.cuh) on the grid adj_grid(nx, ny).
-inline dim3 adj_grid(int nx, int ny) {
+// Rows per CTA (32, 16 or 8) for CTAs `cols` columns wide: the tallest that still gives
+// at least two CTAs per SM, else 8.  Steps without outputs and the adjoint kernels use it
+// (their results do not depend on the CTA shape, or are reduced in a fixed order).
+inline int fill_rows(int nx, int ny, int cols, int nsm) {
+  const long long gx = (nx + cols - 1) / cols;
+  for (int r = 32; r >= 16; r /= 2)
+    if (gx * ((ny + r - 1) / r) >= 2LL * nsm) return r;
+  return 8;
+}
+
+// Adjoint kernels (adjoint_kernel.cuh) on the grid adj_grid(nx, ny, rows).
+inline dim3 adj_grid(int nx, int ny, int rows = kAdjRows) {
   return dim3((unsigned)((nx + 32 * kAdjV - 1) / (32 * kAdjV)),
-              (unsigned)((ny + kAdjRows - 1) / kAdjRows), 1u);
+              (unsigned)((ny + rows - 1) / rows), 1u);
 }
 template <class T>
 cudaError_t launch_adj_objective(const AdjParams<T>& p, cudaStream_t stream);

@@ -146,19 +146,19 @@ cudaError_t launch_batch_step<KSS_T>(const StepParams<KSS_T>* table, const Batch
 #ifndef KSS_STORAGE_HALF
 template <>
 cudaError_t launch_adj_objective<KSS_T>(const AdjParams<KSS_T>& p, cudaStream_t stream) {
-  adj_objective_kernel<KSS_T><<<adj_grid(p.nx, p.ny), kThreads, 0, stream>>>(p);
+  adj_objective_kernel<KSS_T><<<adj_grid(p.nx, p.ny, p.rows), kThreads, 0, stream>>>(p);
   return cudaGetLastError();
 }
 
 template <>
 cudaError_t launch_adj_step<KSS_T>(const AdjParams<KSS_T>& p, cudaStream_t stream) {
-  adj_step_kernel<KSS_T><<<adj_grid(p.nx, p.ny), kThreads, 0, stream>>>(p);
+  adj_step_kernel<KSS_T><<<adj_grid(p.nx, p.ny, p.rows), kThreads, 0, stream>>>(p);
   return cudaGetLastError();
 }
 
 template <>
 cudaError_t launch_adj_final<KSS_T>(const AdjParams<KSS_T>& p, cudaStream_t stream) {
-  adj_final_kernel<KSS_T><<<adj_grid(p.nx, p.ny), kThreads, 0, stream>>>(p);
+  adj_final_kernel<KSS_T><<<adj_grid(p.nx, p.ny, p.rows), kThreads, 0, stream>>>(p);
   return cudaGetLastError();
 }
 

@@ -39,7 +39,7 @@ struct kss_lattice {
   long long plane = 0;      // elements per plane
   int ntx = 0, nty = 0, nblocks = 0;
   int bands = 0;            // tile bands per CTA of the vector step (CTA height bands * tile)
-  int bands_plain = 0;      // the same for steps without outputs
+  int rows_plain = 0;       // CTA height of steps without outputs (any multiple of 8)
   int nsm = 0;              // SMs of the device (persistent grid of the TMA kernel)
   void* f[2] = {nullptr, nullptr};
   int cur = 0;              // f[cur] holds the stored state
