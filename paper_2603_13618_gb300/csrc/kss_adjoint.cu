@@ -37,6 +37,12 @@ struct kss_adjoint {
   int lam_cur = 0;         // lam[lam_cur] holds lt^{N-1} after the forward pass
   bool have_forward = false;
   bool have_weight = false;
+  // the forward and the backward launch sequences replayed as CUDA graphs, recorded on a
+  // stream of their own for the (tau, weight) they were taken with
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t g_fwd = nullptr, g_bwd = nullptr;
+  double g_tau = 0;
+  int g_weight = -1;
   std::string msg;
 };
 
@@ -62,6 +68,9 @@ void free_all(kss_adjoint* A) {
                   A->wplane, A->fields, A->grad,    A->part,    A->small};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  if (A->g_fwd) cudaGraphExecDestroy(A->g_fwd);
+  if (A->g_bwd) cudaGraphExecDestroy(A->g_bwd);
+  if (A->cap) cudaStreamDestroy(A->cap);
   if (A->own_stream && A->stream) cudaStreamDestroy(A->stream);
   delete A;
 }
@@ -72,7 +81,7 @@ unsigned char* state_at(kss_adjoint* A, unsigned char* base, long long k) {
 
 // One plain forward step (stream + collide, no outputs) from src to dst.
 template <class T>
-cudaError_t plain_step(const kss_adjoint* A, const void* src, void* dst) {
+cudaError_t plain_step(const kss_adjoint* A, const void* src, void* dst, cudaStream_t s) {
   kss::StepParams<T> p{};
   p.src = static_cast<const T*>(src);
   p.dst = static_cast<T*>(dst);
@@ -87,7 +96,7 @@ cudaError_t plain_step(const kss_adjoint* A, const void* src, void* dst) {
   p.omega = T(1.0 / A->tau);
   p.tau = T(A->tau);
   for (int s = 0; s < KSS_S_COUNT; ++s) p.rec_slot[s] = -1;
-  return kss::launch_step<T>(p, kss::MODE_PLAIN, true, true, A->stream);
+  return kss::launch_step<T>(p, kss::MODE_PLAIN, true, true, s);
 }
 
 template <class T>
@@ -106,55 +115,57 @@ kss::AdjParams<T> adj_params(kss_adjoint* A) {
 
 double* acc_at(kss_adjoint* A, int k) { return reinterpret_cast<double*>(A->small + 64) + k; }
 
+// The launches of the forward pass on stream s: f^0, f^1 .. f^{N-1} (checkpoints in their
+// slots) and the objective with its seed lt^{N-1}.
 template <class T>
-int forward_impl(kss_adjoint* A, double* J) {
+cudaError_t forward_launches(kss_adjoint* A, cudaStream_t s) {
   const int N = A->cfg.nsteps, E = A->cfg.checkpoint_every;
   const size_t n = size_t(A->cfg.nx) * A->cfg.ny;
-  KSS_ACUDA(A, kss::launch_init_equilibrium<T>(A->fields, A->fields + n, A->fields + 2 * n,
-                                               reinterpret_cast<T*>(A->ck), A->plane, A->pitch,
-                                               A->cfg.nx, A->cfg.ny, kss::codec_t<T>{},
-                                               A->stream));
+  cudaError_t e = kss::launch_init_equilibrium<T>(A->fields, A->fields + n, A->fields + 2 * n,
+                                                  reinterpret_cast<T*>(A->ck), A->plane,
+                                                  A->pitch, A->cfg.nx, A->cfg.ny,
+                                                  kss::codec_t<T>{}, s);
   // f^k for k = 1 .. N-1: checkpoints land in their slot, the others alternate in work[]
   const void* cur = A->ck;
-  for (int k = 1; k < N; ++k) {
+  for (int k = 1; k < N && e == cudaSuccess; ++k) {
     void* dst = (k % E == 0) ? state_at(A, A->ck, k / E) : A->work[k & 1];
-    KSS_ACUDA(A, plain_step<T>(A, cur, dst));
+    e = plain_step<T>(A, cur, dst, s);
     cur = dst;
   }
-  KSS_ACUDA(A, cudaMemsetAsync(A->small + 64, 0, 2 * sizeof(double), A->stream));
+  if (e == cudaSuccess) e = cudaMemsetAsync(A->small + 64, 0, 2 * sizeof(double), s);
   kss::AdjParams<T> p = adj_params<T>(A);
   p.f = static_cast<const T*>(cur);
   p.lam_out = reinterpret_cast<T*>(A->lam[0]);
   p.weight = A->have_weight ? static_cast<const T*>(A->wplane) : nullptr;
   p.acc = acc_at(A, 0);
-  KSS_ACUDA(A, kss::launch_adj_objective<T>(p, A->stream));
-  KSS_ACUDA(A, cudaMemcpyAsync(J, acc_at(A, 0), sizeof(double), cudaMemcpyDeviceToHost, A->stream));
-  KSS_ACUDA(A, cudaStreamSynchronize(A->stream));
-  A->lam_cur = 0;
-  return KSS_OK;
+  if (e == cudaSuccess) e = kss::launch_adj_objective<T>(p, s);
+  return e;
 }
 
+// The launches of the reverse sweep on stream s (from the seed lam[0] the forward pass
+// leaves), ending with the projection on rho0 and the tau accumulator.
 template <class T>
-int backward_impl(kss_adjoint* A, double* grad_tau) {
+cudaError_t backward_launches(kss_adjoint* A, cudaStream_t s) {
   const int N = A->cfg.nsteps, E = A->cfg.checkpoint_every;
-  int lc = A->lam_cur;
+  int lc = 0;
   kss::AdjParams<T> p = adj_params<T>(A);
   p.acc = acc_at(A, 1);
+  cudaError_t e = cudaSuccess;
   // segments [s0, last] of the states f^0 .. f^{N-2} that the reverse sweep needs,
   // last segment first; slot 0 of a segment is its checkpoint
-  for (int s0 = N >= 2 ? ((N - 2) / E) * E : -1; s0 >= 0; s0 -= E) {
+  for (int s0 = N >= 2 ? ((N - 2) / E) * E : -1; s0 >= 0 && e == cudaSuccess; s0 -= E) {
     const int last = std::min(s0 + E - 1, N - 2);
     auto state = [&](int k) -> const void* {
       return k == s0 ? static_cast<const void*>(state_at(A, A->ck, s0 / E))
                      : static_cast<const void*>(state_at(A, A->seg, k - s0));
     };
-    for (int k = s0 + 1; k <= last; ++k)
-      KSS_ACUDA(A, plain_step<T>(A, state(k - 1), const_cast<void*>(state(k))));
-    for (int k = last; k >= s0; --k) {
+    for (int k = s0 + 1; k <= last && e == cudaSuccess; ++k)
+      e = plain_step<T>(A, state(k - 1), const_cast<void*>(state(k)), s);
+    for (int k = last; k >= s0 && e == cudaSuccess; --k) {
       p.f = static_cast<const T*>(state(k));
       p.lam_in = reinterpret_cast<const T*>(A->lam[lc]);
       p.lam_out = reinterpret_cast<T*>(A->lam[lc ^ 1]);
-      KSS_ACUDA(A, kss::launch_adj_step<T>(p, A->stream));
+      e = kss::launch_adj_step<T>(p, s);
       lc ^= 1;
     }
   }
@@ -163,7 +174,56 @@ int backward_impl(kss_adjoint* A, double* grad_tau) {
   p.ux0 = A->fields + n;
   p.uy0 = A->fields + 2 * n;
   p.grad = A->grad;
-  KSS_ACUDA(A, kss::launch_adj_final<T>(p, A->stream));
+  if (e == cudaSuccess) e = kss::launch_adj_final<T>(p, s);
+  return e;
+}
+
+// Replay the graph of fn's launches (recorded when tau or the weight option changed).
+template <class F>
+int run_graph(kss_adjoint* A, cudaGraphExec_t* exec, F&& fn) {
+  if (A->g_tau != A->tau || A->g_weight != int(A->have_weight)) {
+    for (cudaGraphExec_t* g : {&A->g_fwd, &A->g_bwd})
+      if (*g) {
+        cudaGraphExecDestroy(*g);
+        *g = nullptr;
+      }
+    A->g_tau = A->tau;
+    A->g_weight = int(A->have_weight);
+  }
+  if (!*exec) {
+    if (!A->cap) KSS_ACUDA(A, cudaStreamCreateWithFlags(&A->cap, cudaStreamNonBlocking));
+    KSS_ACUDA(A, cudaStreamBeginCapture(A->cap, cudaStreamCaptureModeThreadLocal));
+    const cudaError_t le = fn(A->cap);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(A->cap, &graph);
+    if (le != cudaSuccess || ee != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return afail(A, KSS_ERR_CUDA, std::string("graph capture: ") +
+                                        cudaGetErrorString(le != cudaSuccess ? le : ee));
+    }
+    const cudaError_t ie = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    KSS_ACUDA(A, ie);
+  }
+  KSS_ACUDA(A, cudaGraphLaunch(*exec, A->stream));
+  return KSS_OK;
+}
+
+template <class T>
+int forward_impl(kss_adjoint* A, double* J) {
+  int rc = run_graph(A, &A->g_fwd, [&](cudaStream_t s) { return forward_launches<T>(A, s); });
+  if (rc) return rc;
+  KSS_ACUDA(A, cudaMemcpyAsync(J, acc_at(A, 0), sizeof(double), cudaMemcpyDeviceToHost, A->stream));
+  KSS_ACUDA(A, cudaStreamSynchronize(A->stream));
+  A->lam_cur = 0;
+  return KSS_OK;
+}
+
+template <class T>
+int backward_impl(kss_adjoint* A, double* grad_tau) {
+  int rc = run_graph(A, &A->g_bwd, [&](cudaStream_t s) { return backward_launches<T>(A, s); });
+  if (rc) return rc;
   double s = 0;
   KSS_ACUDA(A, cudaMemcpyAsync(&s, acc_at(A, 1), sizeof(double), cudaMemcpyDeviceToHost, A->stream));
   KSS_ACUDA(A, cudaStreamSynchronize(A->stream));

@@ -102,6 +102,11 @@ cudaError_t launch_one_step(kss_lattice* L, bool out) {
 
 constexpr int kMultiRing = 8;  // partial-sum slots of the multi-step kernel
 
+// Runs of steps without outputs as replayed CUDA graphs (KSS_PLAIN_GRAPHS, default on).
+#ifndef KSS_PLAIN_GRAPHS
+#define KSS_PLAIN_GRAPHS 1
+#endif
+
 int multi_workspace(kss_lattice* L) {
   if (L->multi) return KSS_OK;
   const size_t nb = size_t(L->nblocks), R = kMultiRing;
@@ -224,6 +229,53 @@ const double* pinned_device_view(const double* host) {
   return static_cast<const double*>(a.devicePointer);
 }
 
+// nsteps >= 2 steps without outputs from buffer L->cur, as one replayed CUDA graph: a
+// small lattice's steps are a few microseconds each, about the launch overhead.  The graph
+// is recorded on the lattice's capture stream the first time a (step count, buffer) pair
+// comes up and replayed on its stream afterwards.
+int plain_steps_graph(kss_lattice* L, int nsteps) {
+  for (const auto& g : L->plain_graphs) {
+    if (g.exec && g.nsteps == nsteps && g.cur == L->cur) {
+      KSS_CUDA(L, cudaGraphLaunch(g.exec, L->stream));
+      return KSS_OK;
+    }
+  }
+  if (!L->cap) KSS_CUDA(L, cudaStreamCreateWithFlags(&L->cap, cudaStreamNonBlocking));
+  KSS_CUDA(L, cudaStreamBeginCapture(L->cap, cudaStreamCaptureModeThreadLocal));
+  const cudaStream_t keep = L->stream;
+  const int cur0 = L->cur;
+  L->stream = L->cap;
+  cudaError_t le = cudaSuccess;
+  for (int s = 0; s < nsteps && le == cudaSuccess; ++s) {
+    le = with_storage(L->cfg.precision, [&](auto tag) {
+      return launch_one_step<typename decltype(tag)::type>(L, false);
+    });
+    L->cur ^= 1;
+  }
+  L->stream = keep;
+  L->cur = cur0;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(L->cap, &graph);
+  if (le != cudaSuccess || ee != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return fail(L, KSS_ERR_CUDA, std::string("graph capture: ") +
+                                     cudaGetErrorString(le != cudaSuccess ? le : ee));
+  }
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  KSS_CUDA(L, ie);
+  auto& slot = L->plain_graphs[L->plain_graph_next];
+  L->plain_graph_next = (L->plain_graph_next + 1) % kss_lattice::kPlainGraphs;
+  if (slot.exec) cudaGraphExecDestroy(slot.exec);
+  slot.nsteps = nsteps;
+  slot.cur = L->cur;
+  slot.exec = exec;
+  KSS_CUDA(L, cudaGraphLaunch(exec, L->stream));
+  return KSS_OK;
+}
+
 int ensure_staging(kss_lattice* L, size_t elems) {
   if (L->staging_elems >= elems) return KSS_OK;
   if (L->staging) {
@@ -306,6 +358,9 @@ void release(kss_lattice* L) {
   if (L->multi) cudaFree(L->multi);
   if (L->region) cudaFree(L->region);
   if (L->eval_out) cudaFree(L->eval_out);
+  for (auto& g : L->plain_graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (L->cap) cudaStreamDestroy(L->cap);
   void* bufs[] = {L->f[0], L->f[1], L->rec, L->evalplane, L->flags, L->tiles, L->part_sum,
                   L->part_cnt, L->small, L->staging, L->defer_list};
   for (void* b : bufs)
@@ -609,6 +664,16 @@ int kss_step(kss_lattice* L, int32_t nsteps) {
     L->cur ^= nsteps & 1;
     L->step += nsteps;
     if (every == 1) L->out_step = L->rec_step = L->step;
+    return KSS_OK;
+  }
+  // a run of steps without outputs: one replayed graph
+  bool any_out = false;
+  for (int32_t s = 0; s < nsteps && !any_out; ++s)
+    any_out = every > 0 && (L->step + s + 1) % every == 0;
+  if (KSS_PLAIN_GRAPHS && nsteps >= 2 && !any_out) {
+    if ((rc = plain_steps_graph(L, nsteps))) return rc;
+    L->cur ^= nsteps & 1;
+    L->step += nsteps;
     return KSS_OK;
   }
   for (int32_t s = 0; s < nsteps; ++s) {

@@ -135,3 +135,26 @@ def test_backward_needs_a_forward_pass():
         assert e.value.code == -5
         with pytest.raises(kss.KssError):
             adj.forward(r, u, v, 0.5)
+
+
+def test_repeated_calls_replay_the_recorded_sweeps():
+    """The forward and backward sweeps are recorded as graphs for the (tau, weight) of the
+    call and replayed: repeated calls, and calls after tau or the weight changed, give
+    exactly what a fresh object gives."""
+    kss = _kss()
+    nx, ny, N = 40, 36, 9
+    r, u, v = inputs.random_smooth(nx, ny, seed=4, kmax=3)
+    w = np.random.default_rng(4).uniform(0.5, 1.5, (ny, nx))
+
+    def fresh(tau, weight):
+        with kss.Adjoint(nx, ny, N, precision="fp32", checkpoint_every=4) as a:
+            J = a.forward(r, u, v, tau, weight=weight)
+            return (J,) + a.backward()
+
+    with kss.Adjoint(nx, ny, N, precision="fp32", checkpoint_every=4) as adj:
+        for tau, weight in ((0.8, None), (0.8, None), (0.9, None), (0.9, w), (0.8, None)):
+            J = adj.forward(r, u, v, tau, weight=weight)
+            g, gt = adj.backward()
+            J0, g0, gt0 = fresh(tau, weight)
+            assert J == J0 and gt == gt0
+            np.testing.assert_array_equal(g, g0)

@@ -541,3 +541,26 @@ def test_multi_step_launch_equals_single_steps(prec, every, nx, ny, nsteps):
         np.testing.assert_array_equal(a.read_sensor("kl"), b.read_sensor("kl"))
     for lat in lats:
         lat.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "fp16dev"])
+def test_runs_of_plain_steps_replayed_as_graphs(prec):
+    """kss_step(n) without output steps replays one recorded graph per (n, buffer): the
+    same calls repeated (recorded, then replayed from either buffer) equal single steps
+    bit for bit, and an output step after them sees the same state."""
+    kss = _kss()
+    nx, ny = 96, 70
+    rho, ux, uy = inputs.smooth_jump(nx, ny, seed=23, kmax=4)
+    a = kss.Lattice(nx, ny, precision=prec, tau=0.7, output_every=0)
+    b = kss.Lattice(nx, ny, precision=prec, tau=0.7, output_every=0)
+    for lat in (a, b):
+        lat.set_fields(rho, ux, uy)
+    for n in (5, 5, 3, 5, 5, 2):
+        a.step(n)
+        for _ in range(n):
+            b.step(1)
+        np.testing.assert_array_equal(a.get_populations(), b.get_populations())
+    assert a.step_count == b.step_count == 25
+    np.testing.assert_array_equal(a.read_sensor("kl"), b.read_sensor("kl"))
+    a.close()
+    b.close()
