@@ -588,21 +588,53 @@ def run_reference(args):
     return 0
 
 
+# ---- replicas (N > 1 under torchrun): one independent lattice per rank ----
+
+def dist_env():
+    """(world size, rank, local rank) from the torchrun environment (1, 0, 0 without it)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def init_replicas(world, backend="nccl", device=None):
+    """The process group of an N > 1 run (None for one process).  The ranks exchange no
+    lattice data: only the timing barrier and the maximum of the timings."""
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+
+    if device is not None:
+        dist.init_process_group(backend, device_id=device)
+    else:
+        dist.init_process_group(backend)
+    return dist
+
+
+def max_over_ranks(value, dist, device="cpu"):
+    """The largest of the ranks' values (the job's time is that of its slowest rank)."""
+    if dist is None:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world, cells, steps, ms):
+    """Lattice updates of all ranks per second (weak scaling: each rank a full lattice)."""
+    return world * cells * steps / (ms * 1e-3) / 1e6
+
+
 def run_gpu(args):
     import numpy as np
     import torch
 
     from paper_2603_13618_gb300 import kss
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = dist_env()
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dist = init_replicas(world, "nccl", torch.device("cuda", local))
 
     def barrier():
         if dist is not None:
@@ -634,13 +666,9 @@ def run_gpu(args):
         barrier()
         t_host = time.perf_counter() - t_host
     clocks = clk.summary()
-    total_ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     cells = NX * NY
-    value = world * cells * K / (total_ms * 1e-3) / 1e6
+    value = whole_job_mlups(world, cells, K, total_ms)
     kern_ms = total_ms / K  # per step (the launch covers all K steps)
     achieved = BYTES_PER_LUP * cells / (kern_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
@@ -683,10 +711,10 @@ def run_gpu(args):
             lat.read_flags(out=(fl, tl))
             lat.read_stats()
         barrier()
-        el = time.perf_counter() - t0
+        el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         h2d = 3 * 8 * cells
         d2h = cells + 4 * 2 * lat.nty * lat.ntx + 8 * 3 + 8 * 3 + 8 * 3
-        e2e = {"value": world * cells * ke / el / 1e6, "unit": "MLUPS",
+        e2e = {"value": whole_job_mlups(world, cells, ke, el * 1e3), "unit": "MLUPS",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "steps": ke, "calls_per_step": ["kss_set_fields(host)", "kss_step(1)",
                                                "kss_read_flags(host)", "kss_read_stats"]}
