@@ -49,6 +49,12 @@ namespace kss {
 #define KSS_STEP_MIN_BLOCKS 3
 #endif
 
+// The same for the all-sensor steps (much more per-cell state): two CTAs per SM (at most
+// 128 registers) against one (158 registers): KSS_FULL_MIN_BLOCKS.
+#ifndef KSS_FULL_MIN_BLOCKS
+#define KSS_FULL_MIN_BLOCKS 2
+#endif
+
 constexpr int kWarps = 8;
 constexpr int kThreads = 32 * kWarps;
 constexpr int kMaxBands = 8;  // tile bands per CTA of step_kernel (rows = bands * tile)
@@ -728,7 +734,6 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
   if constexpr (MODE == MODE_FULL) {
     // ---- all sensors of Table 1: cell-major, generic per-cell arithmetic ----
     T fo[9][V];
-    T rv[S_COUNT][V];
 #pragma unroll
     for (int k = 0; k < V; ++k) {
       T c[9], o9[9];
@@ -751,8 +756,15 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
       const bool sw = valid && p.switch_on && (pick<T>(co.sv, p.switch_s) > p.thr_s);
       const bool np = valid && co.nonpos;
       fbits |= (uint32_t(r) | (uint32_t(sw) << 1) | (uint32_t(np) << 7)) << (8 * k);
+      // recorded sensors: one value per cell as soon as it is known (the lanes of a warp
+      // still cover contiguous bytes), so no sensor values stay live across the cells
+      if (valid) {
 #pragma unroll
-      for (int sid = 0; sid < S_COUNT; ++sid) rv[sid][k] = co.sv[sid];
+        for (int sid = 0; sid < S_COUNT; ++sid) {
+          const int slot = p.rec_slot[sid];
+          if (slot >= 0) p.rec[slot * p.plane + off + k] = co.sv[sid];
+        }
+      }
     }
     if (STORE && cv) {
 #pragma unroll
@@ -761,11 +773,6 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
     if (cv) {
       store_flags<V>(p.flags + off, fbits);
       if (AAR && STORE) store_flags<V>(p.region + off, (fbits >> 1) & 0x01010101u);
-#pragma unroll
-      for (int sid = 0; sid < S_COUNT; ++sid) {
-        const int slot = p.rec_slot[sid];
-        if (slot >= 0) vstore<T>(p.rec + slot * p.plane + off, rv[sid]);
-      }
     }
   } else {
     // ---- plain stream + collide, or with the {Kn, KL, neq} sensor set:
@@ -1122,7 +1129,7 @@ __device__ __forceinline__ void step_cta(const StepParams<S>& p, const int bx, c
 
 // AAR: the step with the two-relaxation collision in the region p.region (pull + store).
 template <class S, int MODE, bool PULL, bool STORE, bool AAR = false>
-__global__ void __launch_bounds__(kThreads, MODE == MODE_FULL ? 1 : KSS_STEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(kThreads, MODE == MODE_FULL ? KSS_FULL_MIN_BLOCKS : KSS_STEP_MIN_BLOCKS)
 step_kernel(const StepParams<S> p) {
   step_cta<S, MODE, PULL, STORE, AAR>(p, blockIdx.x, blockIdx.y, gridDim.x,
                                       gridDim.x * gridDim.y);
@@ -1133,7 +1140,7 @@ step_kernel(const StepParams<S> p) {
 // retired between blocks and the completion counter is taken once per CTA.  Each block's
 // partials keep their slot, so the sums are those of step_kernel bit for bit.
 template <class S, int MODE, bool PULL, bool STORE>
-__global__ void __launch_bounds__(kThreads, MODE == MODE_FULL ? 1 : KSS_STEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(kThreads, MODE == MODE_FULL ? KSS_FULL_MIN_BLOCKS : KSS_STEP_MIN_BLOCKS)
 step_kernel_persistent(const StepParams<S> p, int gx, int nblocks) {
   for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
     const int by = b / gx;
@@ -1287,7 +1294,7 @@ struct BatchItem {
 // MODE: MODE_PLAIN (no outputs), MODE_STD (every lattice with {Kn, KL, neq}) or
 // MODE_FULL (each lattice with its own set: p.mode, MODE_STD or MODE_FULL).
 template <class S, int MODE>
-__global__ void __launch_bounds__(kThreads, MODE == MODE_FULL ? 1 : KSS_STEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(kThreads, MODE == MODE_FULL ? KSS_FULL_MIN_BLOCKS : KSS_STEP_MIN_BLOCKS)
 batch_step_kernel(const StepParams<S>* __restrict__ table, const BatchItem* __restrict__ items,
                   int nitems) {
   static_assert(sizeof(StepParams<S>) % 8 == 0, "parameter copy in 8-byte words");
