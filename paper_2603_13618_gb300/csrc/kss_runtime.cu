@@ -100,6 +100,11 @@ cudaError_t launch_one_step(kss_lattice* L, bool out) {
 #define KSS_MULTISTEP 1
 #endif
 
+// FP16-deviation lattices in multi-step launches too (KSS_MULTISTEP_F16).
+#ifndef KSS_MULTISTEP_F16
+#define KSS_MULTISTEP_F16 0
+#endif
+
 constexpr int kMultiRing = 8;  // partial-sum slots of the multi-step kernel
 
 // Runs of steps without outputs as replayed CUDA graphs (KSS_PLAIN_GRAPHS, default on).
@@ -656,7 +661,8 @@ int kss_step(kss_lattice* L, int32_t nsteps) {
   const int every = L->cfg.output_every;
   const int mode = every == 1 ? mode_for(needed_mask(L, L->cfg.record_mask)) : MODE_PLAIN;
   if (KSS_MULTISTEP && nsteps >= 2 && every == 1 && mode == MODE_STD &&
-      L->cfg.precision != KSS_FP16DEV && !use_tma(L, mode) && !L->region &&
+      (KSS_MULTISTEP_F16 || L->cfg.precision != KSS_FP16DEV) && !use_tma(L, mode) &&
+      !L->region &&
       (long long)nsteps * L->nblocks < (1LL << 30)) {
     KSS_CUDA(L, with_storage(L->cfg.precision, [&](auto tag) {
                return launch_multi<typename decltype(tag)::type>(L, mode, nsteps);

@@ -328,11 +328,12 @@ __device__ __forceinline__ void pop_vload(const S* p, bool ok, arith_t<S> (&v)[V
     using VT = typename VecT<S, V>::type;
     const VT raw = ld_pop<CG>(reinterpret_cast<const VT*>(p));
     const __half2* h = reinterpret_cast<const __half2*>(&raw);
+    // two codes per paired FMA (each half rounded as fmaf rounds it)
+    const F2 inv = pack2(c.inv[q], c.inv[q]), base = pack2(c.base[q], c.base[q]);
 #pragma unroll
     for (int k = 0; k < V / 2; ++k) {
       const float2 a = __half22float2(h[k]);
-      v[2 * k] = fmaf(a.x, c.inv[q], c.base[q]);
-      v[2 * k + 1] = fmaf(a.y, c.inv[q], c.base[q]);
+      unpack2(fma2(pack2(a.x, a.y), inv, base), v[2 * k], v[2 * k + 1]);
     }
   } else {
     vload<S, V, CG>(p, ok, v);
@@ -346,10 +347,14 @@ __device__ __forceinline__ void pop_vstore(S* p, const arith_t<S> (&v)[V], int q
     using VT = typename VecT<S, V>::type;
     VT raw;
     __half2* h = reinterpret_cast<__half2*>(&raw);
+    // (f - b_q) s_q for two cells per paired subtract and multiply (the scalar roundings)
+    const F2 base = pack2(c.base[q], c.base[q]), scale = pack2(c.scale[q], c.scale[q]);
 #pragma unroll
-    for (int k = 0; k < V / 2; ++k)
-      h[k] = __floats2half2_rn((v[2 * k] - c.base[q]) * c.scale[q],
-                               (v[2 * k + 1] - c.base[q]) * c.scale[q]);
+    for (int k = 0; k < V / 2; ++k) {
+      float d0, d1;
+      unpack2(mul2(sub2(pack2(v[2 * k], v[2 * k + 1]), base), scale), d0, d1);
+      h[k] = __floats2half2_rn(d0, d1);
+    }
     __stcs(reinterpret_cast<VT*>(p), raw);
   } else {
     vstore<S, V>(p, v);
