@@ -206,6 +206,16 @@ int kss_read_stats(kss_lattice* lat, double sums[3], int64_t counts[3], int64_t*
 int kss_set_aar_region(kss_lattice* lat, const uint8_t* region, int on_device);
 int kss_get_aar_region(kss_lattice* lat, uint8_t* region, int on_device);
 
+/* Test support for failure detection (no counterpart in the paper).  Every device-side
+ * wait of the library (the multi-step launches' dependency waits, the TMA kernel's
+ * barrier waits) gives up after a deadline, sets the lattice's error word and returns,
+ * so that a lost dependency ends in an error instead of a hang.  This call runs that
+ * bounded wait on the lattice's stream for a device word that nothing ever sets, with a
+ * deadline of deadline_cycles (1 .. 1e9 clock cycles, about 0.5 s at most): the wait
+ * runs out, and the next synchronising call on the lattice returns KSS_ERR_TIMEOUT
+ * (sticky, as for a real expiry).  Nothing faults; the GPU context stays usable. */
+int kss_testing_expire_wait(kss_lattice* lat, int64_t deadline_cycles);
+
 /* Steps taken since the last set. */
 int kss_get_step(const kss_lattice* lat, int64_t* step);
 /* Wait for the lattice's stream; reports KSS_ERR_TIMEOUT (sticky) if a bounded device

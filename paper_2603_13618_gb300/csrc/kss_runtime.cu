@@ -209,6 +209,19 @@ cudaError_t launch_eval(kss_lattice* L, int sensor, bool keep) {
   return kss::launch_step<S>(p, mode_for(needed_mask(L, extra)), pull, false, L->stream);
 }
 
+// A device word that nothing ever writes: the bounded wait of kss_testing_expire_wait
+// waits on it.
+__device__ uint32_t g_never_set = 0u;
+
+// One thread waits, with the multi-step kernels' own bounded wait, for g_never_set to reach
+// 1; after `deadline` cycles the wait gives up and sets bit 1 of the lattice's error word.
+__global__ void expire_wait_kernel(uint32_t* err, long long deadline) {
+  kss::MultiState m{};
+  m.err = err;
+  m.deadline = deadline;
+  kss::wait_at_least(m, &g_never_set, 1u);
+}
+
 // Region bytes as the kernels write them: 1 for a switched cell, 0 otherwise.
 __global__ void region_to_01_kernel(uint8_t* r, int pitch, int nx, int ny) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -823,6 +836,17 @@ int kss_get_aar_region(kss_lattice* L, uint8_t* region, int on_device) {
                                 L->stream));
   KSS_CUDA(L, cudaStreamSynchronize(L->stream));
   return device_error(L);
+}
+
+int kss_testing_expire_wait(kss_lattice* L, int64_t deadline_cycles) {
+  int rc = enter(L);
+  if (rc) return rc;
+  if (deadline_cycles < 1 || deadline_cycles > 1000000000LL)
+    return fail(L, KSS_ERR_ARG, "deadline must be 1 .. 1e9 cycles");
+  DeviceGuard g(L->device);
+  expire_wait_kernel<<<1, 1, 0, L->stream>>>(L->err_word, (long long)deadline_cycles);
+  KSS_CUDA(L, cudaGetLastError());
+  return KSS_OK;
 }
 
 int kss_get_step(const kss_lattice* L, int64_t* step) {

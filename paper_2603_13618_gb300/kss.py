@@ -87,6 +87,7 @@ _SIGNATURES = {
     "kss_read_stats": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "kss_get_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "kss_set_aar_region": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "kss_testing_expire_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "kss_get_aar_region": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "kss_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "kss_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(Config),
