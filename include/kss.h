@@ -201,8 +201,9 @@ int kss_read_stats(kss_lattice* lat, double sums[3], int64_t counts[3], int64_t*
  * empty after kss_create, kss_set_fields and kss_set_populations, and
  * kss_set_aar_region replaces it (nx*ny bytes, nonzero = two-relaxation; get returns
  * 0 / 1).  KSS_ERR_STATE on a lattice with tau2 = 0.  AAR steps run on the vector
- * kernel, one launch per step; batch members must have tau2 = 0 (else
- * KSS_ERR_UNSUPPORTED from kss_batch_create). */
+ * kernel, one launch per step; in a batch, members with tau2 > 0 take the two-
+ * relaxation collision in their regions and the others step as BGK (the batch then
+ * runs one launch per step, no multi-step launch). */
 int kss_set_aar_region(kss_lattice* lat, const uint8_t* region, int on_device);
 int kss_get_aar_region(kss_lattice* lat, uint8_t* region, int on_device);
 

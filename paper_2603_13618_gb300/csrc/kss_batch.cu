@@ -39,6 +39,8 @@ struct kss_batch {
   int max_tile = 8;
   int mode_out = kss::MODE_STD;   // kernel of output steps: MODE_FULL if a member needs all
                                   // sensors (each member then runs its own set)
+  bool aar = false;               // some member has the two-relaxation model (AAR kernels,
+                                  // one launch per step)
   // device data
   void* table[2] = {nullptr, nullptr};  // StepParams<T>[n]; table[par] reads the stored states
   kss::BatchItem* items = nullptr;
@@ -299,7 +301,7 @@ cudaError_t launch_one(kss_batch* B, int tbl, int mode, cudaStream_t s) {
   return with_storage(B->prec, [&](auto tag) {
     using S = typename decltype(tag)::type;
     return kss::launch_batch_step<S>(static_cast<const kss::StepParams<S>*>(B->table[tbl]),
-                                     B->items, B->nitems, ctas, mode, s);
+                                     B->items, B->nitems, ctas, mode, s, B->aar);
   });
 }
 
@@ -424,10 +426,6 @@ int kss_batch_create(int32_t n, const kss_config* cfgs, kss_batch** out) {
   if (n < 1 || !cfgs) return KSS_ERR_ARG;
   for (int k = 1; k < n; ++k)
     if (cfgs[k].precision != cfgs[0].precision) return KSS_ERR_ARG;
-  // batched steps run the BGK collision only (adaptive algorithm refinement is a
-  // single-lattice option)
-  for (int k = 0; k < n; ++k)
-    if (cfgs[k].tau2 != 0.0) return KSS_ERR_UNSUPPORTED;
   kss_batch* B = new (std::nothrow) kss_batch();
   if (!B) return KSS_ERR_OOM;
   B->n = n;
@@ -464,6 +462,7 @@ int kss_batch_create(int32_t n, const kss_config* cfgs, kss_batch** out) {
       return rc;
     }
     B->mem[k]->owner = B;
+    if (c.tau2 > 0.0) B->aar = true;
     B->max_tile = std::max(B->max_tile, c.tile);
     if (mode_for(needed_mask(B->mem[k], c.record_mask)) == kss::MODE_FULL) B->mode_out = kss::MODE_FULL;
   }
@@ -563,7 +562,7 @@ int kss_batch_step(kss_batch* B, int32_t nsteps) {
       }
     }
   }
-  const bool all_std = B->mode_out == kss::MODE_STD &&
+  const bool all_std = B->mode_out == kss::MODE_STD && !B->aar &&
                        modes.find_first_not_of('S') == std::string::npos;
   if (B->tun.multi_step && nsteps >= 2 && all_std &&
       (long long)nsteps * B->nitems < (1LL << 30)) {
@@ -602,7 +601,7 @@ int kss_batch_autotune(kss_batch* B, const char* cache_path, int32_t steps,
   int rc = KSS_OK;
   // multi-step launches are timed too when the members' steps qualify for them (every
   // member an output step of the {Kn, KL, neq} set every step) and they are enabled
-  bool multi_ok = B->tun.multi_step && B->mode_out == kss::MODE_STD;
+  bool multi_ok = B->tun.multi_step && B->mode_out == kss::MODE_STD && !B->aar;
   for (const kss_lattice* L : B->mem) multi_ok = multi_ok && L->cfg.output_every == 1;
   if (cache_path && cache_lookup(cache_path, key, &best) && valid_rows(B, best.rows) &&
       best.ctas_per_sm >= 0 && best.ctas_per_sm <= 64) {

@@ -36,7 +36,7 @@ cudaError_t launch_step_aar(const StepParams<T>& p, int mode, cudaStream_t strea
 // stride over the items.  mode MODE_PLAIN / MODE_STD / MODE_FULL; always pull + store.
 template <class T>
 cudaError_t launch_batch_step(const StepParams<T>* table, const BatchItem* items, int nitems,
-                              int ctas, int mode, cudaStream_t stream);
+                              int ctas, int mode, cudaStream_t stream, bool aar = false);
 
 // nsteps batched steps in one cooperative launch (batch_kernel_multi): ta / tb are the
 // parameter tables of even / odd steps, mtab each lattice's MultiState, work the shared

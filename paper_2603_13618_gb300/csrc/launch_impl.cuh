@@ -131,9 +131,19 @@ cudaError_t launch_batch_multi<KSS_T>(const StepParams<KSS_T>* ta, const StepPar
 
 template <>
 cudaError_t launch_batch_step<KSS_T>(const StepParams<KSS_T>* table, const BatchItem* items,
-                                     int nitems, int ctas, int mode, cudaStream_t stream) {
+                                     int nitems, int ctas, int mode, cudaStream_t stream,
+                                     bool aar) {
   if (nitems < 1 || ctas < 1) return cudaErrorInvalidValue;
   const dim3 grid(unsigned(ctas < nitems ? ctas : nitems)), block(kThreads);
+  if (aar) {
+    switch (mode) {
+      case MODE_PLAIN: batch_step_kernel<KSS_T, MODE_PLAIN, true><<<grid, block, 0, stream>>>(table, items, nitems); break;
+      case MODE_STD: batch_step_kernel<KSS_T, MODE_STD, true><<<grid, block, 0, stream>>>(table, items, nitems); break;
+      case MODE_FULL: batch_step_kernel<KSS_T, MODE_FULL, true><<<grid, block, 0, stream>>>(table, items, nitems); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
   switch (mode) {
     case MODE_PLAIN: batch_step_kernel<KSS_T, MODE_PLAIN><<<grid, block, 0, stream>>>(table, items, nitems); break;
     case MODE_STD: batch_step_kernel<KSS_T, MODE_STD><<<grid, block, 0, stream>>>(table, items, nitems); break;

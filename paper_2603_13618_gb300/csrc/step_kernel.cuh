@@ -777,7 +777,7 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
     }
     if (cv) {
       store_flags<V>(p.flags + off, fbits);
-      if (AAR && STORE) store_flags<V>(p.region + off, (fbits >> 1) & 0x01010101u);
+      if (AAR && STORE && p.region) store_flags<V>(p.region + off, (fbits >> 1) & 0x01010101u);
     }
   } else {
     // ---- plain stream + collide, or with the {Kn, KL, neq} sensor set:
@@ -877,7 +877,7 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
       if (cv) {
         store_flags<V>(p.flags + off, fbits);
         // (a deferred cell's byte is 0x40: its region byte is set by the epilogue)
-        if (AAR && STORE) store_flags<V>(p.region + off, (fbits >> 1) & 0x01010101u);
+        if (AAR && STORE && p.region) store_flags<V>(p.region + off, (fbits >> 1) & 0x01010101u);
         if (p.rec_slot[S_KN] >= 0) vstore<T>(p.rec + p.rec_slot[S_KN] * p.plane + off, a.kn);
         if (p.rec_slot[S_KL] >= 0) vstore<T>(p.rec + p.rec_slot[S_KL] * p.plane + off, a.kl);
         if (p.rec_slot[S_NEQ] >= 0) vstore<T>(p.rec + p.rec_slot[S_NEQ] * p.plane + off, a.neq);
@@ -932,7 +932,8 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
     // overlaps theirs; output steps replace it with their own flags
     uint32_t mbits = 0;
     if constexpr (AAR && STORE) {
-      if (cv) mbits = load_bytes<V>(p.region + (long long)j * p.pitch + i0);
+      // (in a batch, a member without the model has no region: it steps as BGK)
+      if (cv && p.region) mbits = load_bytes<V>(p.region + (long long)j * p.pitch + i0);
     }
     if (PULL) {
       const long long up = (long long)((j == 0 ? p.ny : j) - 1 - j) * p.pitch;    // row j-1
@@ -1054,7 +1055,7 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
         const int rl = o / (32 * V), cl = o - rl * (32 * V);
         const int j = j0 + rl, i = bx * 32 * V + cl;
         const uint32_t tags = fix_cell<S, PULL, CG>(p, pr, ps, i, j);
-        if (AAR && STORE) p.region[(long long)j * p.pitch + i] = uint8_t((tags >> 1) & 1u);
+        if (AAR && STORE && p.region) p.region[(long long)j * p.pitch + i] = uint8_t((tags >> 1) & 1u);
         const int b = rl / p.tile, tl = cl / p.tile;
         if (tags & 1u) {
           atomicAdd(&s_cx[0], 1u);
@@ -1298,7 +1299,9 @@ struct BatchItem {
 
 // MODE: MODE_PLAIN (no outputs), MODE_STD (every lattice with {Kn, KL, neq}) or
 // MODE_FULL (each lattice with its own set: p.mode, MODE_STD or MODE_FULL).
-template <class S, int MODE>
+// AAR: members with a region take the two-relaxation collision there (members without
+// one step as BGK).
+template <class S, int MODE, bool AAR = false>
 __global__ void __launch_bounds__(kThreads, MODE == MODE_FULL ? KSS_FULL_MIN_BLOCKS : KSS_STEP_MIN_BLOCKS)
 batch_step_kernel(const StepParams<S>* __restrict__ table, const BatchItem* __restrict__ items,
                   int nitems) {
@@ -1311,10 +1314,11 @@ batch_step_kernel(const StepParams<S>* __restrict__ table, const BatchItem* __re
     for (int k = threadIdx.x; k < int(sizeof(StepParams<S>) / 8); k += kThreads) s_raw[k] = src[k];
     __syncthreads();
     if (MODE != MODE_FULL || sp.mode != MODE_FULL)
-      step_cta<S, MODE == MODE_FULL ? MODE_STD : MODE, true, true>(sp, int(it.bx), int(it.by),
-                                                                  sp.grid_x, sp.nblocks);
+      step_cta<S, MODE == MODE_FULL ? MODE_STD : MODE, true, true, AAR>(
+          sp, int(it.bx), int(it.by), sp.grid_x, sp.nblocks);
     else
-      step_cta<S, MODE_FULL, true, true>(sp, int(it.bx), int(it.by), sp.grid_x, sp.nblocks);
+      step_cta<S, MODE_FULL, true, true, AAR>(sp, int(it.bx), int(it.by), sp.grid_x,
+                                              sp.nblocks);
     __syncthreads();  // the CTA's shared memory is reused by the next item
   }
 }

@@ -275,6 +275,43 @@ def test_region_api():
         lat.set_aar_region(dev)
         out = lat.get_aar_region(device=True)
         np.testing.assert_array_equal(out.cpu().numpy(), (reg != 0).astype(np.uint8))
-    with pytest.raises(kss.KssError) as e:
-        kss.Batch([dict(nx=32, ny=32, tau2=1.0)])
-    assert e.value.code == -6
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "fp16dev"])
+def test_batch_members_with_and_without_the_model(prec):
+    """A batch mixing AAR members (prescribed regions, neq or qe as the switch, one with
+    plain steps between its output steps) and BGK members: every member equals the same
+    lattice stepped alone, bit for bit (populations, flags, regions)."""
+    kss = _kss()
+    specs = [dict(nx=37, ny=21, tau=0.7, tau2=1.3, switch_sensor="qe"),
+             dict(nx=130, ny=67, tau=1.0),
+             dict(nx=64, ny=64, tau=0.55, tau2=0.9, output_every=3),
+             dict(nx=200, ny=9, tau=0.6, tau2=2.0, record=("kl", "qe")),
+             dict(nx=5, ny=1, tau=1.3)]
+    thr = {"qe": 2e-4, "neq": 1e-3}
+    for sp in specs:
+        sp.setdefault("switch_sensor", "neq")
+        sp["switch_threshold"] = thr[sp["switch_sensor"]]
+    b = kss.Batch(specs, precision=prec)
+    singles = []
+    for k, sp in enumerate(specs):
+        fld = inputs.smooth_jump(sp["nx"], sp["ny"], seed=60 + k, kmax=4)
+        lat = kss.Lattice(precision=prec, **sp)
+        for x in (b[k], lat):
+            x.set_fields(*fld)
+            if sp.get("tau2"):
+                x.set_aar_region(inputs.random_region(sp["nx"], sp["ny"], seed=k))
+        singles.append(lat)
+    for n in (7, 1, 5):
+        b.step(n)
+        for lat in singles:
+            lat.step(n)
+        for k, sp in enumerate(specs):
+            a, c = b[k], singles[k]
+            np.testing.assert_array_equal(a.get_populations(), c.get_populations())
+            np.testing.assert_array_equal(a.read_flags()[0], c.read_flags()[0])
+            if sp.get("tau2"):
+                np.testing.assert_array_equal(a.get_aar_region(), c.get_aar_region())
+    for lat in singles:
+        lat.close()
+    b.close()
