@@ -203,7 +203,9 @@ int kss_read_stats(kss_lattice* lat, double sums[3], int64_t counts[3], int64_t*
  * 0 / 1).  KSS_ERR_STATE on a lattice with tau2 = 0.  AAR steps run on the vector
  * kernel, one launch per step; in a batch, members with tau2 > 0 take the two-
  * relaxation collision in their regions and the others step as BGK (the batch then
- * runs one launch per step, no multi-step launch). */
+ * runs one launch per step, no multi-step launch).  Because an output step rewrites the
+ * region, a batch with such members needs one output_every for all members
+ * (KSS_ERR_UNSUPPORTED from kss_batch_create otherwise). */
 int kss_set_aar_region(kss_lattice* lat, const uint8_t* region, int on_device);
 int kss_get_aar_region(kss_lattice* lat, uint8_t* region, int on_device);
 

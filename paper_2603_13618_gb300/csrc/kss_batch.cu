@@ -426,6 +426,12 @@ int kss_batch_create(int32_t n, const kss_config* cfgs, kss_batch** out) {
   if (n < 1 || !cfgs) return KSS_ERR_ARG;
   for (int k = 1; k < n; ++k)
     if (cfgs[k].precision != cfgs[0].precision) return KSS_ERR_ARG;
+  // a batched step is an output step for every member when it is one for any, and an
+  // AAR member's output steps rewrite its region: with AAR members, one shared cadence
+  bool any_aar = false;
+  for (int k = 0; k < n; ++k) any_aar = any_aar || cfgs[k].tau2 != 0.0;
+  for (int k = 1; any_aar && k < n; ++k)
+    if (cfgs[k].output_every != cfgs[0].output_every) return KSS_ERR_UNSUPPORTED;
   kss_batch* B = new (std::nothrow) kss_batch();
   if (!B) return KSS_ERR_OOM;
   B->n = n;

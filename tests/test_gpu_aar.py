@@ -277,21 +277,26 @@ def test_region_api():
         np.testing.assert_array_equal(out.cpu().numpy(), (reg != 0).astype(np.uint8))
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64", "fp16dev"])
-def test_batch_members_with_and_without_the_model(prec):
-    """A batch mixing AAR members (prescribed regions, neq or qe as the switch, one with
-    plain steps between its output steps) and BGK members: every member equals the same
-    lattice stepped alone, bit for bit (populations, flags, regions)."""
+@pytest.mark.parametrize("prec,every", [("fp32", 1), ("fp32", 3), ("fp64", 1),
+                                        ("fp16dev", 2)])
+def test_batch_members_with_and_without_the_model(prec, every):
+    """A batch mixing AAR members (prescribed regions, neq or qe as the switch) and BGK
+    members, all with one output cadence: every member equals the same lattice stepped
+    alone, bit for bit (populations, flags, regions).  Mixed cadences are refused."""
     kss = _kss()
     specs = [dict(nx=37, ny=21, tau=0.7, tau2=1.3, switch_sensor="qe"),
              dict(nx=130, ny=67, tau=1.0),
-             dict(nx=64, ny=64, tau=0.55, tau2=0.9, output_every=3),
+             dict(nx=64, ny=64, tau=0.55, tau2=0.9),
              dict(nx=200, ny=9, tau=0.6, tau2=2.0, record=("kl", "qe")),
              dict(nx=5, ny=1, tau=1.3)]
     thr = {"qe": 2e-4, "neq": 1e-3}
     for sp in specs:
         sp.setdefault("switch_sensor", "neq")
         sp["switch_threshold"] = thr[sp["switch_sensor"]]
+        sp["output_every"] = every
+    with pytest.raises(kss.KssError) as e:
+        kss.Batch([dict(specs[0]), dict(specs[1], output_every=every + 1)], precision=prec)
+    assert e.value.code == -6
     b = kss.Batch(specs, precision=prec)
     singles = []
     for k, sp in enumerate(specs):
