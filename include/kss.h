@@ -205,7 +205,9 @@ int kss_read_stats(kss_lattice* lat, double sums[3], int64_t counts[3], int64_t*
  * relaxation collision in their regions and the others step as BGK (the batch then
  * runs one launch per step, no multi-step launch).  Because an output step rewrites the
  * region, a batch with such members needs one output_every for all members
- * (KSS_ERR_UNSUPPORTED from kss_batch_create otherwise). */
+ * (KSS_ERR_UNSUPPORTED from kss_batch_create otherwise) and, when it is above 1, the
+ * members in phase: kss_batch_step returns KSS_ERR_STATE if their step counts differ
+ * modulo output_every (after a member was set or stepped on its own). */
 int kss_set_aar_region(kss_lattice* lat, const uint8_t* region, int on_device);
 int kss_get_aar_region(kss_lattice* lat, uint8_t* region, int on_device);
 

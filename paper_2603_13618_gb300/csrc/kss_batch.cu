@@ -555,6 +555,14 @@ int kss_batch_step(kss_batch* B, int32_t nsteps) {
     if (rc) return rc;
   }
   if (nsteps == 0) return KSS_OK;
+  if (B->aar) {
+    // the output steps of AAR members must be theirs: members in phase
+    const int every = B->mem[0]->cfg.output_every;
+    for (const kss_lattice* L : B->mem)
+      if (every > 1 && L->step % every != B->mem[0]->step % every)
+        return bfail(B, KSS_ERR_STATE, "members with the two-relaxation model are out of "
+                                       "phase with the batch's output steps");
+  }
   DeviceGuard g(B->device);
   int rc = check_tables(B);
   if (rc) return rc;

@@ -317,6 +317,11 @@ def test_batch_members_with_and_without_the_model(prec, every):
             np.testing.assert_array_equal(a.read_flags()[0], c.read_flags()[0])
             if sp.get("tau2"):
                 np.testing.assert_array_equal(a.get_aar_region(), c.get_aar_region())
+    if every > 1:  # a member set again is out of phase with the others
+        b[1].set_fields(*inputs.smooth_jump(130, 67, seed=61, kmax=4))
+        with pytest.raises(kss.KssError) as e:
+            b.step(1)
+        assert e.value.code == -5
     for lat in singles:
         lat.close()
     b.close()
