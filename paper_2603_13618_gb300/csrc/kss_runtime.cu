@@ -151,7 +151,8 @@ cudaError_t launch_multi(kss_lattice* L, int mode, int nsteps) {
   m.gx = int(g.x);
   m.gy = int(g.y);
   m.nblocks = nb;
-  const int resident = kss::multi_resident_ctas<S>(mode);
+  const bool aar = L->region != nullptr;
+  const int resident = kss::multi_resident_ctas<S>(mode, aar);
   if (resident < 1) return cudaErrorInvalidConfiguration;
   // as many CTAs as keep the blocks per CTA even
   const int per = (nb + resident - 1) / resident;
@@ -160,7 +161,7 @@ cudaError_t launch_multi(kss_lattice* L, int mode, int nsteps) {
   if (e != cudaSuccess) return e;
   const kss::StepParams<S> pa = make_params<S>(L, L->f[L->cur], L->f[L->cur ^ 1]);
   const kss::StepParams<S> pb = make_params<S>(L, L->f[L->cur ^ 1], L->f[L->cur]);
-  return kss::launch_step_multi<S>(pa, pb, m, mode, ctas, L->stream);
+  return kss::launch_step_multi<S>(pa, pb, m, mode, ctas, L->stream, aar);
 }
 
 // Scratch outputs of an evaluation that only a sensor field is wanted from: flags
@@ -672,10 +673,11 @@ int kss_step(kss_lattice* L, int32_t nsteps) {
   // launch (measured on GB300 at 4096^2 FP32: 0.232 vs 0.244 ms per step; plain steps and
   // FP16-deviation storage gain nothing from it: 0.179 vs 0.179, 0.224 vs 0.221 ms)
   const int every = L->cfg.output_every;
-  const int mode = every == 1 ? mode_for(needed_mask(L, L->cfg.record_mask)) : MODE_PLAIN;
+  const int mode =
+      every == 1 ? mode_for(needed_mask(L, L->cfg.record_mask), L->region != nullptr) : MODE_PLAIN;
   if (KSS_MULTISTEP && nsteps >= 2 && every == 1 && mode == MODE_STD &&
-      (KSS_MULTISTEP_F16 || L->cfg.precision != KSS_FP16DEV) && !use_tma(L, mode) &&
-      !L->region &&
+      (KSS_MULTISTEP_F16 || L->cfg.precision != KSS_FP16DEV) &&
+      (L->region || !use_tma(L, mode)) &&
       (long long)nsteps * L->nblocks < (1LL << 30)) {
     KSS_CUDA(L, with_storage(L->cfg.precision, [&](auto tag) {
                return launch_multi<typename decltype(tag)::type>(L, mode, nsteps);

@@ -54,10 +54,11 @@ int batch_multi_resident_ctas(int mode);
 // ctas <= multi_resident_ctas.
 template <class T>
 cudaError_t launch_step_multi(const StepParams<T>& pa, const StepParams<T>& pb,
-                              const MultiState& m, int mode, int ctas, cudaStream_t stream);
+                              const MultiState& m, int mode, int ctas, cudaStream_t stream,
+                              bool aar = false);
 // CTAs of the multi-step kernel resident on the current device at once (0 on error).
 template <class T>
-int multi_resident_ctas(int mode);
+int multi_resident_ctas(int mode, bool aar = false);
 
 // The TMA-staged step (step_tma.cuh): mode MODE_PLAIN or MODE_STD, always pull + store;
 // `ctas` persistent CTAs (one per SM).

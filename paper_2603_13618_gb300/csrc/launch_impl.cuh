@@ -91,19 +91,22 @@ cudaError_t launch_step_aar<KSS_T>(const StepParams<KSS_T>& p, int mode, cudaStr
 }
 
 template <>
-int multi_resident_ctas<KSS_T>(int mode) {
-  return mode == MODE_STD ? resident_ctas<step_kernel_multi<KSS_T, MODE_STD>>() : 0;
+int multi_resident_ctas<KSS_T>(int mode, bool aar) {
+  if (mode != MODE_STD) return 0;
+  return aar ? resident_ctas<step_kernel_multi<KSS_T, MODE_STD, true>>()
+             : resident_ctas<step_kernel_multi<KSS_T, MODE_STD>>();
 }
 
 template <>
 cudaError_t launch_step_multi<KSS_T>(const StepParams<KSS_T>& pa, const StepParams<KSS_T>& pb,
                                      const MultiState& m, int mode, int ctas,
-                                     cudaStream_t stream) {
+                                     cudaStream_t stream, bool aar) {
   StepParams<KSS_T> a = pa, b = pb;
   MultiState ms = m;
   void* args[] = {&a, &b, &ms};
   if (mode != MODE_STD) return cudaErrorInvalidValue;
-  const void* fn = reinterpret_cast<const void*>(step_kernel_multi<KSS_T, MODE_STD>);
+  const void* fn = aar ? reinterpret_cast<const void*>(step_kernel_multi<KSS_T, MODE_STD, true>)
+                       : reinterpret_cast<const void*>(step_kernel_multi<KSS_T, MODE_STD>);
   return cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(kThreads), args, 0, stream);
 }
 

@@ -1210,7 +1210,7 @@ __device__ __forceinline__ bool wait_at_least(const MultiState& m, const uint32_
 
 // Work item (step s, block b); returns false if a wait ran out.  s_next receives the
 // CTA's next work item (taken early, so that the counter's latency is hidden).
-template <class S, int MODE>
+template <class S, int MODE, bool AAR = false>
 __device__ __forceinline__ bool multi_block(const StepParams<S>& p, const MultiState& m, int s,
                                             int b, int* s_next) {
   constexpr bool OUT = MODE != MODE_PLAIN;
@@ -1239,7 +1239,9 @@ __device__ __forceinline__ bool multi_block(const StepParams<S>& p, const MultiS
   }
   __syncthreads();
   if (!s_go) return false;
-  step_block<S, MODE, true, true, true>(p, bx, by, m.gx, psum, pcnt);
+  // (AAR: block b's region bytes of step s - 1 were written before its release, which
+  // the wait on block b itself -- part of its 3 x 3 neighbourhood -- acquired)
+  step_block<S, MODE, true, true, true, AAR>(p, bx, by, m.gx, psum, pcnt);
   __syncthreads();  // every store of the block precedes thread 0's release
   if (threadIdx.x == 0) {
     __threadfence();
@@ -1262,8 +1264,9 @@ __device__ __forceinline__ bool multi_block(const StepParams<S>& p, const MultiS
   return true;
 }
 
-// pa: buffer A -> B (even steps); pb: B -> A (odd steps).
-template <class S, int MODE>
+// pa: buffer A -> B (even steps); pb: B -> A (odd steps).  AAR: the two-relaxation
+// collision in the region (adaptive algorithm refinement).
+template <class S, int MODE, bool AAR = false>
 __global__ void __launch_bounds__(kThreads, KSS_STEP_MIN_BLOCKS)
 step_kernel_multi(const StepParams<S> pa, const StepParams<S> pb, const MultiState m) {
   __shared__ int s_next;
@@ -1274,8 +1277,8 @@ step_kernel_multi(const StepParams<S> pa, const StepParams<S> pb, const MultiSta
   while (w < total) {
     const int s = w / m.nblocks, b = w - s * m.nblocks;
     __syncthreads();  // every thread has read s_next before thread 0 rewrites it
-    const bool ok = (s & 1) ? multi_block<S, MODE>(pb, m, s, b, &s_next)
-                            : multi_block<S, MODE>(pa, m, s, b, &s_next);
+    const bool ok = (s & 1) ? multi_block<S, MODE, AAR>(pb, m, s, b, &s_next)
+                            : multi_block<S, MODE, AAR>(pa, m, s, b, &s_next);
     if (!ok) return;
     __syncthreads();
     w = s_next;

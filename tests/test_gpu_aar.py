@@ -325,3 +325,37 @@ def test_batch_members_with_and_without_the_model(prec, every):
     for lat in singles:
         lat.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("switch", ["neq", "qe"])
+@pytest.mark.parametrize("nx,ny,n", [(37, 21, 6), (1024, 640, 7)])
+def test_multi_step_launch_equals_single_steps(prec, switch, nx, ny, n):
+    """kss_step(n) of an AAR lattice with every step an output step runs as one
+    cooperative multi-step launch: a block reads the region its own block wrote at the
+    previous step (possibly in another CTA).  It must equal n single launches bit for bit:
+    populations, regions, flags, counts, sums and the recorded fields."""
+    kss = _kss()
+    rho, ux, uy = inputs.smooth_jump(nx, ny, seed=nx + n, kmax=6)
+    thr = {"neq": 1e-3, "qe": 3e-5}[switch]
+    lats = []
+    for _ in range(2):
+        lat = kss.Lattice(nx, ny, precision=prec, tau=0.62, tau2=1.4, switch_sensor=switch,
+                          switch_threshold=thr, record=("kl", "qe"))
+        lat.set_fields(rho, ux, uy)
+        lat.set_aar_region(inputs.random_region(nx, ny, seed=n))
+        lats.append(lat)
+    lats[0].step(n)
+    for _ in range(n):
+        lats[1].step(1)
+    a, b = lats
+    np.testing.assert_array_equal(a.get_populations(), b.get_populations())
+    np.testing.assert_array_equal(a.get_aar_region(), b.get_aar_region())
+    assert 0 < a.get_aar_region().sum() < nx * ny
+    for x, y in zip(a.read_flags(), b.read_flags()):
+        np.testing.assert_array_equal(x, y)
+    np.testing.assert_array_equal(a.read_stats()[0], b.read_stats()[0])
+    for name in ("kl", "qe"):
+        np.testing.assert_array_equal(a.read_sensor(name), b.read_sensor(name))
+    for lat in lats:
+        lat.close()
