@@ -337,7 +337,9 @@ def test_multi_step_launch_equals_single_steps(prec, switch, nx, ny, n):
     populations, regions, flags, counts, sums and the recorded fields."""
     kss = _kss()
     rho, ux, uy = inputs.smooth_jump(nx, ny, seed=nx + n, kmax=6)
-    thr = {"neq": 1e-3, "qe": 3e-5}[switch]
+    sens, _ = oracle.sensor_fields(oracle.init_equilibrium(rho, ux, uy), 0.62, pull=True,
+                                   two_relax=True)
+    thr = _split(sens[oracle.SENSOR_ID[switch]])  # about half the cells switch
     lats = []
     for _ in range(2):
         lat = kss.Lattice(nx, ny, precision=prec, tau=0.62, tau2=1.4, switch_sensor=switch,
