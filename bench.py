@@ -15,6 +15,7 @@ previous step); the same steps as one launch each are timed alongside.
   python bench.py --workload adjoint512 # the adjoint workload (below)
   python bench.py --workload fp16dev8192 [--fp16-error]  # the precision workload (below)
   python bench.py --workload aar4096    # adaptive algorithm refinement (below)
+  python bench.py --workload shear128   # the FP64 correctness case (below)
 
 Batched workload (--workload batch64): 64 uneven periodic lattices (sizes 64^2 ..
 1024^2, tau ~ U[0.51, 1.5], Mach ~ U[0.01, 0.15], seed 13618, 15.8 M cells in all), the
@@ -28,6 +29,11 @@ output steps with the {Kn, KL, neq} set and neq as the switch sensor (the region
 follows the flags), the same with the quasi-equilibrium sensor as the switch, all of
 Table 1 with that switch, and plain steps in a fixed 40 % region, each against the same
 steps with BGK only.
+
+Correctness workload (--workload shear128): the decaying shear wave on a 128^2 FP64
+lattice (u_x = 0.01 sin(2 pi y / 128), tau = 0.8), 2000 steps in one call with the Kn and
+KL sensors, flags (Kn > 1e-3), tile counts and sums every 10 steps.  The lattice (1.2 MB per
+buffer) lives in L2, so its rate is reported as it is, with no bandwidth fraction.
 
 N > 1 (launched by torchrun) runs one independent lattice per rank (replicas, weak
 scaling); rank 0 prints one JSON line.  --impl reference times the CPU oracle on the
@@ -518,6 +524,52 @@ def run_aar(args):
     return 0
 
 
+SHEAR_METRIC = "MLUPS, 128^2 FP64 shear wave, sensors and flags every 10 steps, 1xGB300"
+
+
+def run_shear(args):
+    """The FP64 correctness workload, timed as one 2000-step call."""
+    import torch
+
+    from paper_2603_13618_gb300 import inputs, kss
+
+    torch.cuda.set_device(0)
+    n, tau, steps = 128, 0.8, 2000
+    rho, ux, uy = inputs.shear_wave(n, n, 0.01)
+    lat = kss.Lattice(n, n, precision="fp64", tau=tau, refine_sensor="kn",
+                      refine_threshold=1e-3, switch_sensor="neq", switch_threshold=1e-4,
+                      record=("kn", "kl"), output_every=10)
+    stream = torch.cuda.current_stream()
+    times = []
+    for rep_ in range(1 + max(1, args.warmup // 10)):
+        lat.set_fields(rho, ux, uy)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    t = min(times[1:])  # the first call records the step graphs
+    _, counts, step = lat.read_stats()
+    line = {
+        "metric": SHEAR_METRIC, "value": n * n * steps / (t * 1e-3) / 1e6, "unit": "MLUPS",
+        "n_gpus": 1, "steps": steps, "warmup": 1, "ms_per_step": t / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "D2Q9 FP64 128x128 periodic shear wave u_x = 0.01 sin(2 pi y/128), "
+                               "tau = 0.8, 2000 steps in one call; Kn (refine 1e-3) and KL "
+                               "fields, flags, tile counts and sums every 10 steps",
+                   "nx": n, "ny": n, "l2": "the lattice lives in L2 (1.2 MB per buffer): no "
+                                           "bandwidth fraction is meaningful"},
+        "refine_count_at_step_2000": int(counts[0]), "step": int(step),
+        "gpu_launches": steps,
+    }
+    print(json.dumps(line), flush=True)
+    lat.close()
+    return 0
+
+
 def fp16_error(n, tau, kexp, gen, steps=500, window=256):
     """Errors of FP16 deviation and FP32 storage after `steps` steps against the FP64
     oracle on the central window (the oracle runs the window's domain of dependence)."""
@@ -781,7 +833,8 @@ def main():
     ap.add_argument("--fp16-error", action="store_true",
                     help="fp16dev8192: also measure the error against the FP64 oracle")
     ap.add_argument("--workload", default="single",
-                    choices=["single", "batch64", "adjoint512", "fp16dev8192", "aar4096"],
+                    choices=["single", "batch64", "adjoint512", "fp16dev8192", "aar4096",
+                             "shear128"],
                     help="single: the 4096^2 lattice (default); batch64: 64 uneven "
                          "lattices; adjoint512: the gradient of the KL objective")
     ap.add_argument("--no-tune", action="store_true",
@@ -801,6 +854,8 @@ def main():
         return run_fp16(args)
     if args.workload == "aar4096":
         return run_aar(args)
+    if args.workload == "shear128":
+        return run_shear(args)
     return run_gpu(args)
 
 

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <limits>
 #include <new>
+#include <numeric>
 #include <string>
 
 #include "runtime.h"
@@ -107,10 +108,12 @@ cudaError_t launch_one_step(kss_lattice* L, bool out) {
 
 constexpr int kMultiRing = 8;  // partial-sum slots of the multi-step kernel
 
-// Runs of steps without outputs as replayed CUDA graphs (KSS_PLAIN_GRAPHS, default on).
-#ifndef KSS_PLAIN_GRAPHS
-#define KSS_PLAIN_GRAPHS 1
+// Runs of single-step launches as replayed CUDA graphs (KSS_STEP_GRAPHS, default on), of
+// at most kGraphChunk steps each.
+#ifndef KSS_STEP_GRAPHS
+#define KSS_STEP_GRAPHS 1
 #endif
+constexpr int32_t kGraphChunk = 512;
 
 int multi_workspace(kss_lattice* L) {
   if (L->multi) return KSS_OK;
@@ -248,13 +251,19 @@ const double* pinned_device_view(const double* host) {
   return static_cast<const double*>(a.devicePointer);
 }
 
-// nsteps >= 2 steps without outputs from buffer L->cur, as one replayed CUDA graph: a
-// small lattice's steps are a few microseconds each, about the launch overhead.  The graph
-// is recorded on the lattice's capture stream the first time a (step count, buffer) pair
-// comes up and replayed on its stream afterwards.
-int plain_steps_graph(kss_lattice* L, int nsteps) {
+// Is step n (counted from the last set) an output step?
+bool is_output_step(const kss_lattice* L, int64_t n) {
+  return L->cfg.output_every > 0 && n % L->cfg.output_every == 0;
+}
+
+// The next nsteps >= 2 steps from buffer L->cur, one launch each, as one replayed CUDA
+// graph: a small lattice's steps are a few microseconds each, about the launch overhead.
+// The graph is recorded on the lattice's capture stream the first time a (step count,
+// buffer, output phase) triple comes up and replayed on its stream afterwards.
+int steps_graph(kss_lattice* L, int nsteps) {
+  const int64_t phase = L->cfg.output_every > 0 ? L->step % L->cfg.output_every : 0;
   for (const auto& g : L->plain_graphs) {
-    if (g.exec && g.nsteps == nsteps && g.cur == L->cur) {
+    if (g.exec && g.nsteps == nsteps && g.cur == L->cur && g.phase == phase) {
       KSS_CUDA(L, cudaGraphLaunch(g.exec, L->stream));
       return KSS_OK;
     }
@@ -266,8 +275,9 @@ int plain_steps_graph(kss_lattice* L, int nsteps) {
   L->stream = L->cap;
   cudaError_t le = cudaSuccess;
   for (int s = 0; s < nsteps && le == cudaSuccess; ++s) {
+    const bool out = is_output_step(L, L->step + s + 1);
     le = with_storage(L->cfg.precision, [&](auto tag) {
-      return launch_one_step<typename decltype(tag)::type>(L, false);
+      return launch_one_step<typename decltype(tag)::type>(L, out);
     });
     L->cur ^= 1;
   }
@@ -290,6 +300,7 @@ int plain_steps_graph(kss_lattice* L, int nsteps) {
   if (slot.exec) cudaGraphExecDestroy(slot.exec);
   slot.nsteps = nsteps;
   slot.cur = L->cur;
+  slot.phase = phase;
   slot.exec = exec;
   KSS_CUDA(L, cudaGraphLaunch(exec, L->stream));
   return KSS_OK;
@@ -687,28 +698,30 @@ int kss_step(kss_lattice* L, int32_t nsteps) {
     if (every == 1) L->out_step = L->rec_step = L->step;
     return KSS_OK;
   }
-  // a run of steps without outputs: one replayed graph
-  bool any_out = false;
-  for (int32_t s = 0; s < nsteps && !any_out; ++s)
-    any_out = every > 0 && (L->step + s + 1) % every == 0;
-  if (KSS_PLAIN_GRAPHS && nsteps >= 2 && !any_out) {
-    if ((rc = plain_steps_graph(L, nsteps))) return rc;
-    L->cur ^= nsteps & 1;
-    L->step += nsteps;
-    return KSS_OK;
-  }
-  for (int32_t s = 0; s < nsteps; ++s) {
-    const int64_t n = L->step + 1;
-    const bool out = L->cfg.output_every > 0 && (n % L->cfg.output_every) == 0;
-    KSS_CUDA(L, with_storage(L->cfg.precision, [&](auto tag) {
-               return launch_one_step<typename decltype(tag)::type>(L, out);
-             }));
-    L->cur ^= 1;
-    L->step = n;
-    if (out) {
-      L->out_step = n;
-      L->rec_step = n;
+  // any other run of steps: one launch each, replayed as graphs of at most kGraphChunk
+  // steps; longer runs go in chunks of whole output periods and an even step count, so that
+  // every chunk has the same (count, buffer, phase) key and replays the same graph
+  int32_t left = nsteps;
+  while (left > 0) {
+    int32_t c = 1;
+    if (KSS_STEP_GRAPHS && left >= 2) {
+      c = std::min<int32_t>(left, kGraphChunk);
+      const int64_t period = every > 0 ? std::lcm<int64_t>(2, every) : 2;
+      if (c < left && period <= kGraphChunk) c = int32_t(c / period * period);
     }
+    if (c >= 2) {
+      if ((rc = steps_graph(L, c))) return rc;
+    } else {
+      const bool out = is_output_step(L, L->step + 1);
+      KSS_CUDA(L, with_storage(L->cfg.precision, [&](auto tag) {
+                 return launch_one_step<typename decltype(tag)::type>(L, out);
+               }));
+    }
+    for (int32_t s = 0; s < c; ++s)
+      if (is_output_step(L, L->step + s + 1)) L->out_step = L->rec_step = L->step + s + 1;
+    L->cur ^= c & 1;
+    L->step += c;
+    left -= c;
   }
   return KSS_OK;
 }

@@ -74,11 +74,13 @@ struct kss_lattice {
   uint8_t* region = nullptr;   // two-relaxation region [ny][pitch] (cfg.tau2 > 0 only)
   void* eval_out = nullptr;    // flags, tiles, sums and counts of on-demand evaluations
                                // while the step's own outputs are current, made on first use
-  // runs of steps without outputs, replayed as CUDA graphs (kss_runtime.cu), keyed by the
-  // step count and the buffer holding the state; recorded on a stream of their own
-  static constexpr int kPlainGraphs = 4;
+  // runs of single-step launches replayed as CUDA graphs (kss_runtime.cu), keyed by the
+  // step count, the buffer holding the state and the phase of the output steps; recorded
+  // on a stream of their own
+  static constexpr int kPlainGraphs = 8;
   struct PlainGraph {
     int nsteps = 0, cur = 0;
+    int64_t phase = 0;
     cudaGraphExec_t exec = nullptr;
   } plain_graphs[kPlainGraphs];
   int plain_graph_next = 0;

@@ -543,24 +543,31 @@ def test_multi_step_launch_equals_single_steps(prec, every, nx, ny, nsteps):
         lat.close()
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64", "fp16dev"])
-def test_runs_of_plain_steps_replayed_as_graphs(prec):
-    """kss_step(n) without output steps replays one recorded graph per (n, buffer): the
-    same calls repeated (recorded, then replayed from either buffer) equal single steps
-    bit for bit, and an output step after them sees the same state."""
+@pytest.mark.parametrize("prec,every", [("fp32", 0), ("fp64", 0), ("fp16dev", 0), ("fp32", 3),
+                                        ("fp64", 4)])
+def test_runs_of_steps_replayed_as_graphs(prec, every):
+    """kss_step(n) that is not one multi-step launch replays one recorded graph per
+    (n, buffer, output phase): the same calls repeated (recorded, then replayed) equal
+    single steps bit for bit, outputs included; a run longer than one graph (512 steps)
+    goes in chunks of whole output periods."""
     kss = _kss()
     nx, ny = 96, 70
     rho, ux, uy = inputs.smooth_jump(nx, ny, seed=23, kmax=4)
-    a = kss.Lattice(nx, ny, precision=prec, tau=0.7, output_every=0)
-    b = kss.Lattice(nx, ny, precision=prec, tau=0.7, output_every=0)
+    a = kss.Lattice(nx, ny, precision=prec, tau=0.7, output_every=every, record=("kl",))
+    b = kss.Lattice(nx, ny, precision=prec, tau=0.7, output_every=every, record=("kl",))
     for lat in (a, b):
         lat.set_fields(rho, ux, uy)
-    for n in (5, 5, 3, 5, 5, 2):
+    for n in (5, 5, 3, 5, 5, 2, 1100):
         a.step(n)
         for _ in range(n):
             b.step(1)
         np.testing.assert_array_equal(a.get_populations(), b.get_populations())
-    assert a.step_count == b.step_count == 25
-    np.testing.assert_array_equal(a.read_sensor("kl"), b.read_sensor("kl"))
+        for x, y in zip(a.read_flags(), b.read_flags()):
+            np.testing.assert_array_equal(x, y)
+        sa, sb = a.read_stats(), b.read_stats()
+        np.testing.assert_array_equal(sa[0], sb[0])
+        assert sa[2] == sb[2]
+        np.testing.assert_array_equal(a.read_sensor("kl"), b.read_sensor("kl"))
+    assert a.step_count == b.step_count == 1125
     a.close()
     b.close()
