@@ -135,16 +135,18 @@ def test_trajectory_follows_the_oracle_codec():
     lat.close()
 
 
-def test_error_against_fp64_on_a_window_of_1024():
+@pytest.mark.parametrize("N", [1024, 8192])
+def test_error_against_fp64_on_a_window(N):
     """The precision workload's inputs (smooth perturbations of amplitude 1e-3 in density
-    and velocity) on a 1024^2 lattice, 100 steps: FP16 deviations (K = 20) against the
-    unrounded FP64 oracle on the central 128^2 window (the oracle runs the window's
-    domain of dependence, 328^2).  Each step rounds each population to 2^-12 of its
-    deviation (< 4e-3 w_q here), so after n steps the density error stays below
+    and velocity) on an N^2 lattice (8192^2: the benchmark's size and launch
+    configuration), 100 steps: FP16 deviations (K = 20) against the unrounded FP64 oracle
+    on the central 128^2 window (the oracle runs the window's domain of dependence,
+    328^2).  Each step rounds each population to 2^-12 of its deviation (< 4e-3 w_q
+    here), so after n steps the density error stays below
     sqrt(n) * 9 * 2^-12 * 4e-3 / 9 = 1e-5; the Kn sensor (about 1e-5 here) carries that
     noise relative to its size."""
     kss = _kss()
-    N, n, W, k = 1024, 100, 128, 20
+    n, W, k = 100, 128, 20
     amp = 1e-3
     gen = dict(seed=8192, kmax=8, drho_amp=amp, mach=amp / inputs.CS, jump=1.0)
     rho, ux, uy = inputs.smooth_jump(N, N, **gen)
