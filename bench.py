@@ -268,7 +268,8 @@ def run_batch(args):
                    "cells": cells, "lattices": len(specs), "tuning": tuning,
                    "l2": "inputs larger than L2: 1.14 GB of populations per step"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": profile_traffic(BATCH_PROFILE) if multi else None,
                      "algorithmic_bytes_per_launch": BYTES_PER_LUP * cells,
                      "kernel_ms": kern_ms,
                      "kernel": ("batch_kernel_multi<float, MODE_STD> (all steps in one "
@@ -430,6 +431,7 @@ def run_fp16(args):
 
 
 AAR_PROFILE = os.path.join(ROOT, "profiles", "step_aar_std_f32_4096.md")
+BATCH_PROFILE = os.path.join(ROOT, "profiles", "batch_multi_f32_64lattices.md")
 AAR_METRIC = ("MLUPS with adaptive algorithm refinement (two-relaxation collision in the "
               "switched region) and sensors fused, 1xGB300")
 
