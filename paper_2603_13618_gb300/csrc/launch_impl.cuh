@@ -11,9 +11,31 @@ inline dim3 helper_grid(int nx, long long rows) {
   return dim3((unsigned)((nx + 255) / 256), (unsigned)(rows < 65535 ? rows : 65535));
 }
 
-// CTAs of `kernel` resident on the current device at once (its occupancy times the SM
-// count), looked up once per device.
-template <auto kernel>
+// Let `kernel` take DYN bytes of dynamic shared memory on the current device (beyond the
+// default 48 KB of static plus dynamic memory an opt-in is needed), once per device.
+template <auto kernel, int DYN>
+cudaError_t allow_dynamic_smem() {
+  if constexpr (DYN == 0) {
+    return cudaSuccess;
+  } else {
+    constexpr int kMaxDev = 64;
+    static bool done[kMaxDev] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    if (!done[dev]) {
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, DYN);
+      if (e != cudaSuccess) return e;
+      done[dev] = true;
+    }
+    return cudaSuccess;
+  }
+}
+
+// CTAs of `kernel` (with DYN bytes of dynamic shared memory) resident on the current
+// device at once (its occupancy times the SM count), looked up once per device.
+template <auto kernel, int DYN = 0>
 int resident_ctas() {
   constexpr int kMaxDev = 64;
   static int cache[kMaxDev] = {};  // one per kernel: `kernel` is a template argument
@@ -21,8 +43,9 @@ int resident_ctas() {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 0;
   if (!cache[dev]) {
     int nsm = 0, per = 0;
-    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kThreads, 0) != cudaSuccess)
+    if (allow_dynamic_smem<kernel, DYN>() != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kThreads, DYN) != cudaSuccess)
       return 0;
     cache[dev] = nsm * per;
   }
@@ -93,8 +116,10 @@ cudaError_t launch_step_aar<KSS_T>(const StepParams<KSS_T>& p, int mode, cudaStr
 template <>
 int multi_resident_ctas<KSS_T>(int mode, bool aar) {
   if (mode != MODE_STD) return 0;
-  return aar ? resident_ctas<step_kernel_multi<KSS_T, MODE_STD, true>>()
-             : resident_ctas<step_kernel_multi<KSS_T, MODE_STD>>();
+  return aar ? resident_ctas<step_kernel_multi<KSS_T, MODE_STD, true>,
+                             multi_prefetch_smem<KSS_T, MODE_STD, true>()>()
+             : resident_ctas<step_kernel_multi<KSS_T, MODE_STD>,
+                             multi_prefetch_smem<KSS_T, MODE_STD, false>()>();
 }
 
 template <>
@@ -105,9 +130,16 @@ cudaError_t launch_step_multi<KSS_T>(const StepParams<KSS_T>& pa, const StepPara
   MultiState ms = m;
   void* args[] = {&a, &b, &ms};
   if (mode != MODE_STD) return cudaErrorInvalidValue;
+  constexpr int dyn_aar = multi_prefetch_smem<KSS_T, MODE_STD, true>();
+  constexpr int dyn_bgk = multi_prefetch_smem<KSS_T, MODE_STD, false>();
+  const int dyn = aar ? dyn_aar : dyn_bgk;
+  const cudaError_t e =
+      aar ? allow_dynamic_smem<step_kernel_multi<KSS_T, MODE_STD, true>, dyn_aar>()
+          : allow_dynamic_smem<step_kernel_multi<KSS_T, MODE_STD>, dyn_bgk>();
+  if (e != cudaSuccess) return e;
   const void* fn = aar ? reinterpret_cast<const void*>(step_kernel_multi<KSS_T, MODE_STD, true>)
                        : reinterpret_cast<const void*>(step_kernel_multi<KSS_T, MODE_STD>);
-  return cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(kThreads), args, 0, stream);
+  return cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(kThreads), args, dyn, stream);
 }
 
 template <>

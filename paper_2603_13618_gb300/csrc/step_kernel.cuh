@@ -272,6 +272,53 @@ __device__ __forceinline__ void assemble_from_right(T (&v)[V], T halo, int i0, i
   }
 }
 
+// ---------------------------------------------------------------- row prefetch ----
+// The single-lattice multi-step kernel with the BGK collision and FP32 storage stages
+// each warp's next row in shared memory with asynchronous copies (cp.async), issued
+// before the current row's arithmetic, so that a row's loads are in flight while the
+// previous row is computed; the register file holds no second row.  A warp's slots are
+// written only by its own lanes' copies and read back by the same lanes, so the copies
+// need no CTA barrier, only the wait for their own group and a warp barrier that orders
+// the reads of a row before the copies of the next one.  Measured at 4096^2: 0.2202 vs
+// 0.2284 ms per step.  The two-relaxation kernel (0.2932 vs 0.2563 ms) and the batched
+// kernel (0.2302 vs 0.2194 ms) were slower with it and load their rows directly.
+// Build knob: -DKSS_MULTI_PREFETCH=0 loads every row directly.
+#ifndef KSS_MULTI_PREFETCH
+#define KSS_MULTI_PREFETCH 1
+#endif
+
+struct PfWarp {
+  float4 pop[9][32];  // the nine population vectors of each lane
+  float hr[3][32];    // right halo of q = 3, 6, 7 (lane 31 and the row's tail lanes)
+  float hl[4];        // left halo of q = 1, 5, 8 (lane 0)
+};
+constexpr int kPfBytes = kWarps * int(sizeof(PfWarp));
+static_assert(sizeof(PfWarp) % 16 == 0, "16-byte aligned warp slots");
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// Dynamic shared memory of step_kernel_multi<S, MODE, AAR>: the row prefetch slots, or 0
+// where the kernel loads its rows directly.
+template <class S, int MODE, bool AAR>
+__host__ __device__ constexpr int multi_prefetch_smem() {
+  return (KSS_MULTI_PREFETCH && std::is_same<S, float>::value && MODE == MODE_STD && !AAR)
+             ? kPfBytes
+             : 0;
+}
+
 // ---------------------------------------------------------------- accumulators ----
 // FP32 storage: a thread adds its few cells (at most 4 rows x 4 cells) in plain FP32,
 // then the warp combines the partials as double-floats (hi + lo, Knuth two-sum), so
@@ -896,7 +943,8 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
 // Block (bx, by) of a lattice whose step grid is gx blocks wide: its rows, then (output
 // modes) its tile counts and its partial sums and counts in slot bid.  Called by every
 // thread of the CTA; the CTA's shared memory is free again when it returns.
-template <class S, int MODE, bool PULL, bool STORE, bool CG = false, bool AAR = false>
+template <class S, int MODE, bool PULL, bool STORE, bool CG = false, bool AAR = false,
+          bool PREFETCH = false>
 __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx, const int by,
                                            const int gx, double* part_sum, uint32_t* part_cnt) {
   using T = arith_t<S>;
@@ -924,6 +972,52 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
   uint32_t n_ref = 0, n_sw = 0, n_np = 0;
   uint32_t wn = 0;  // deferred cells gathered by this warp (warp-uniform)
 
+  // row prefetch (see PfWarp): the warp's slots in dynamic shared memory, and the copies
+  // of row jj into them
+  constexpr bool PF = PREFETCH && CG && PULL && STORE;
+  static_assert(!PF || (std::is_same<S, float>::value && !AAR), "prefetch: FP32 BGK rows");
+  extern __shared__ __align__(16) unsigned char kss_dyn_smem[];
+  PfWarp* const pw = reinterpret_cast<PfWarp*>(kss_dyn_smem) + warp;
+  auto pf_issue = [&](int jj) {
+    if (cv) {
+      const S* base = p.src + (long long)jj * p.pitch;
+      const long long up = (long long)((jj == 0 ? p.ny : jj) - 1 - jj) * p.pitch;
+      const long long dn = (long long)((jj + 1 == p.ny ? 0 : jj + 1) - jj) * p.pitch;
+      const S* r1 = base + 1 * p.plane;
+      const S* r3 = base + 3 * p.plane;
+      const S* r5 = base + 5 * p.plane + up;
+      const S* r6 = base + 6 * p.plane + up;
+      const S* r7 = base + 7 * p.plane + dn;
+      const S* r8 = base + 8 * p.plane + dn;
+      cp_async16(&pw->pop[0][lane], base + i0);
+      cp_async16(&pw->pop[1][lane], r1 + i0);
+      cp_async16(&pw->pop[2][lane], base + 2 * p.plane + up + i0);
+      cp_async16(&pw->pop[3][lane], r3 + i0);
+      cp_async16(&pw->pop[4][lane], base + 4 * p.plane + dn + i0);
+      cp_async16(&pw->pop[5][lane], r5 + i0);
+      cp_async16(&pw->pop[6][lane], r6 + i0);
+      cp_async16(&pw->pop[7][lane], r7 + i0);
+      cp_async16(&pw->pop[8][lane], r8 + i0);
+      if (lane == 0) {
+        const int c = i0 == 0 ? p.nx - 1 : i0 - 1;
+        cp_async4(&pw->hl[0], r1 + c);
+        cp_async4(&pw->hl[1], r5 + c);
+        cp_async4(&pw->hl[2], r8 + c);
+      }
+      const bool tail = i0 + V >= p.nx;
+      if (lane == 31 || tail) {
+        const int c = tail ? 0 : i0 + V;
+        cp_async4(&pw->hr[0][lane], r3 + c);
+        cp_async4(&pw->hr[1][lane], r6 + c);
+        cp_async4(&pw->hr[2][lane], r7 + c);
+      }
+    }
+    cp_async_commit();
+  };
+  if constexpr (PF) {
+    if (j0 + warp < j1) pf_issue(j0 + warp);
+  }
+
   for (int j = j0 + warp; j < j1; j += kWarps) {
     T ft[9][V];
     const S* base = p.src + (long long)j * p.pitch;
@@ -931,47 +1025,79 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
     // recent output step before it), loaded ahead of the populations so that its latency
     // overlaps theirs; output steps replace it with their own flags
     uint32_t mbits = 0;
-    if constexpr (AAR && STORE) {
-      // (in a batch, a member without the model has no region: it steps as BGK)
-      if (cv && p.region) mbits = load_bytes<V>(p.region + (long long)j * p.pitch + i0);
-    }
-    if (PULL) {
-      const long long up = (long long)((j == 0 ? p.ny : j) - 1 - j) * p.pitch;    // row j-1
-      const long long dn = (long long)((j + 1 == p.ny ? 0 : j + 1) - j) * p.pitch;  // row j+1
-      // source rows of q = 0..8 (pull: row j - cy_q)
-      const S* r0 = base;
-      const S* r1 = base + 1 * p.plane;
-      const S* r2 = base + 2 * p.plane + up;
-      const S* r3 = base + 3 * p.plane;
-      const S* r4 = base + 4 * p.plane + dn;
-      const S* r5 = base + 5 * p.plane + up;
-      const S* r6 = base + 6 * p.plane + up;
-      const S* r7 = base + 7 * p.plane + dn;
-      const S* r8 = base + 8 * p.plane + dn;
-      pop_vload<S, V, CG>(r0 + i0, cv, ft[0], 0, p.codec);
-      pop_vload<S, V, CG>(r1 + i0, cv, ft[1], 1, p.codec);
-      pop_vload<S, V, CG>(r2 + i0, cv, ft[2], 2, p.codec);
-      pop_vload<S, V, CG>(r3 + i0, cv, ft[3], 3, p.codec);
-      pop_vload<S, V, CG>(r4 + i0, cv, ft[4], 4, p.codec);
-      pop_vload<S, V, CG>(r5 + i0, cv, ft[5], 5, p.codec);
-      pop_vload<S, V, CG>(r6 + i0, cv, ft[6], 6, p.codec);
-      pop_vload<S, V, CG>(r7 + i0, cv, ft[7], 7, p.codec);
-      pop_vload<S, V, CG>(r8 + i0, cv, ft[8], 8, p.codec);
-      const T h1 = decode<S>(load_left_halo<S, CG>(r1, i0, p.nx, lane, cv), 1, p.codec);
-      const T h5 = decode<S>(load_left_halo<S, CG>(r5, i0, p.nx, lane, cv), 5, p.codec);
-      const T h8 = decode<S>(load_left_halo<S, CG>(r8, i0, p.nx, lane, cv), 8, p.codec);
-      const T h3 = decode<S>(load_right_halo<S, V, CG>(r3, i0, p.nx, lane, cv), 3, p.codec);
-      const T h6 = decode<S>(load_right_halo<S, V, CG>(r6, i0, p.nx, lane, cv), 6, p.codec);
-      const T h7 = decode<S>(load_right_halo<S, V, CG>(r7, i0, p.nx, lane, cv), 7, p.codec);
-      assemble_from_left<T>(ft[1], h1, lane);
-      assemble_from_left<T>(ft[5], h5, lane);
-      assemble_from_left<T>(ft[8], h8, lane);
-      assemble_from_right<T>(ft[3], h3, i0, p.nx, lane);
-      assemble_from_right<T>(ft[6], h6, i0, p.nx, lane);
-      assemble_from_right<T>(ft[7], h7, i0, p.nx, lane);
-    } else {
+    if constexpr (PF) {
+      cp_async_wait_all();
+      T hl[3] = {T(0), T(0), T(0)}, hr[3] = {T(0), T(0), T(0)};
+      if (cv) {
 #pragma unroll
-      for (int q = 0; q < 9; ++q) pop_vload<S, V, CG>(base + q * p.plane + i0, cv, ft[q], q, p.codec);
+        for (int q = 0; q < 9; ++q) {
+          const float4 a = pw->pop[q][lane];
+          ft[q][0] = a.x; ft[q][1] = a.y; ft[q][2] = a.z; ft[q][3] = a.w;
+        }
+        if (lane == 0) {
+          hl[0] = pw->hl[0]; hl[1] = pw->hl[1]; hl[2] = pw->hl[2];
+        }
+        if (lane == 31 || i0 + V >= p.nx) {
+          hr[0] = pw->hr[0][lane]; hr[1] = pw->hr[1][lane]; hr[2] = pw->hr[2][lane];
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+#pragma unroll
+          for (int k = 0; k < V; ++k) ft[q][k] = T(0);
+      }
+      __syncwarp();  // the row's reads precede the copies of the next row into the slots
+      if (j + kWarps < j1) pf_issue(j + kWarps);
+      assemble_from_left<T>(ft[1], hl[0], lane);
+      assemble_from_left<T>(ft[5], hl[1], lane);
+      assemble_from_left<T>(ft[8], hl[2], lane);
+      assemble_from_right<T>(ft[3], hr[0], i0, p.nx, lane);
+      assemble_from_right<T>(ft[6], hr[1], i0, p.nx, lane);
+      assemble_from_right<T>(ft[7], hr[2], i0, p.nx, lane);
+    } else {
+      if constexpr (AAR && STORE) {
+        // (in a batch, a member without the model has no region: it steps as BGK)
+        if (cv && p.region) mbits = load_bytes<V>(p.region + (long long)j * p.pitch + i0);
+      }
+      if (PULL) {
+        const long long up = (long long)((j == 0 ? p.ny : j) - 1 - j) * p.pitch;    // row j-1
+        const long long dn = (long long)((j + 1 == p.ny ? 0 : j + 1) - j) * p.pitch;  // row j+1
+        // source rows of q = 0..8 (pull: row j - cy_q)
+        const S* r0 = base;
+        const S* r1 = base + 1 * p.plane;
+        const S* r2 = base + 2 * p.plane + up;
+        const S* r3 = base + 3 * p.plane;
+        const S* r4 = base + 4 * p.plane + dn;
+        const S* r5 = base + 5 * p.plane + up;
+        const S* r6 = base + 6 * p.plane + up;
+        const S* r7 = base + 7 * p.plane + dn;
+        const S* r8 = base + 8 * p.plane + dn;
+        pop_vload<S, V, CG>(r0 + i0, cv, ft[0], 0, p.codec);
+        pop_vload<S, V, CG>(r1 + i0, cv, ft[1], 1, p.codec);
+        pop_vload<S, V, CG>(r2 + i0, cv, ft[2], 2, p.codec);
+        pop_vload<S, V, CG>(r3 + i0, cv, ft[3], 3, p.codec);
+        pop_vload<S, V, CG>(r4 + i0, cv, ft[4], 4, p.codec);
+        pop_vload<S, V, CG>(r5 + i0, cv, ft[5], 5, p.codec);
+        pop_vload<S, V, CG>(r6 + i0, cv, ft[6], 6, p.codec);
+        pop_vload<S, V, CG>(r7 + i0, cv, ft[7], 7, p.codec);
+        pop_vload<S, V, CG>(r8 + i0, cv, ft[8], 8, p.codec);
+        const T h1 = decode<S>(load_left_halo<S, CG>(r1, i0, p.nx, lane, cv), 1, p.codec);
+        const T h5 = decode<S>(load_left_halo<S, CG>(r5, i0, p.nx, lane, cv), 5, p.codec);
+        const T h8 = decode<S>(load_left_halo<S, CG>(r8, i0, p.nx, lane, cv), 8, p.codec);
+        const T h3 = decode<S>(load_right_halo<S, V, CG>(r3, i0, p.nx, lane, cv), 3, p.codec);
+        const T h6 = decode<S>(load_right_halo<S, V, CG>(r6, i0, p.nx, lane, cv), 6, p.codec);
+        const T h7 = decode<S>(load_right_halo<S, V, CG>(r7, i0, p.nx, lane, cv), 7, p.codec);
+        assemble_from_left<T>(ft[1], h1, lane);
+        assemble_from_left<T>(ft[5], h5, lane);
+        assemble_from_left<T>(ft[8], h8, lane);
+        assemble_from_right<T>(ft[3], h3, i0, p.nx, lane);
+        assemble_from_right<T>(ft[6], h6, i0, p.nx, lane);
+        assemble_from_right<T>(ft[7], h7, i0, p.nx, lane);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+          pop_vload<S, V, CG>(base + q * p.plane + i0, cv, ft[q], q, p.codec);
+      }
     }
 
     const uint32_t fbits =
@@ -1210,7 +1336,7 @@ __device__ __forceinline__ bool wait_at_least(const MultiState& m, const uint32_
 
 // Work item (step s, block b); returns false if a wait ran out.  s_next receives the
 // CTA's next work item (taken early, so that the counter's latency is hidden).
-template <class S, int MODE, bool AAR = false>
+template <class S, int MODE, bool AAR = false, bool PREFETCH = false>
 __device__ __forceinline__ bool multi_block(const StepParams<S>& p, const MultiState& m, int s,
                                             int b, int* s_next) {
   constexpr bool OUT = MODE != MODE_PLAIN;
@@ -1241,7 +1367,7 @@ __device__ __forceinline__ bool multi_block(const StepParams<S>& p, const MultiS
   if (!s_go) return false;
   // (AAR: block b's region bytes of step s - 1 were written before its release, which
   // the wait on block b itself -- part of its 3 x 3 neighbourhood -- acquired)
-  step_block<S, MODE, true, true, true, AAR>(p, bx, by, m.gx, psum, pcnt);
+  step_block<S, MODE, true, true, true, AAR, PREFETCH>(p, bx, by, m.gx, psum, pcnt);
   __syncthreads();  // every store of the block precedes thread 0's release
   if (threadIdx.x == 0) {
     __threadfence();
@@ -1277,8 +1403,9 @@ step_kernel_multi(const StepParams<S> pa, const StepParams<S> pb, const MultiSta
   while (w < total) {
     const int s = w / m.nblocks, b = w - s * m.nblocks;
     __syncthreads();  // every thread has read s_next before thread 0 rewrites it
-    const bool ok = (s & 1) ? multi_block<S, MODE, AAR>(pb, m, s, b, &s_next)
-                            : multi_block<S, MODE, AAR>(pa, m, s, b, &s_next);
+    constexpr bool pf = multi_prefetch_smem<S, MODE, AAR>() > 0;
+    const bool ok = (s & 1) ? multi_block<S, MODE, AAR, pf>(pb, m, s, b, &s_next)
+                            : multi_block<S, MODE, AAR, pf>(pa, m, s, b, &s_next);
     if (!ok) return;
     __syncthreads();
     w = s_next;
