@@ -417,7 +417,8 @@ def run_fp16(args):
                          "per step"},
         "roofline": {"bound": "hbm", "achieved": main["achieved_gbs"], "peak": peak,
                      "unit": "GB/s", "frac": main["frac"], "peak_kind": peak_kind,
-                     "traffic": None, "algorithmic_bytes_per_launch": main["bytes_per_lup"] * cells,
+                     "traffic": profile_traffic(FP16_PROFILE) if n == 8192 else None,
+                     "algorithmic_bytes_per_launch": main["bytes_per_lup"] * cells,
                      "kernel_ms": main["kernel_ms"],
                      "kernel": "step_kernel<__half, MODE_STD, pull, store>"},
         "variants": runs,
@@ -432,6 +433,7 @@ def run_fp16(args):
 
 AAR_PROFILE = os.path.join(ROOT, "profiles", "step_aar_std_f32_4096.md")
 BATCH_PROFILE = os.path.join(ROOT, "profiles", "batch_multi_f32_64lattices.md")
+FP16_PROFILE = os.path.join(ROOT, "profiles", "step_std_f16dev_8192.md")
 AAR_METRIC = ("MLUPS with adaptive algorithm refinement (two-relaxation collision in the "
               "switched region) and sensors fused, 1xGB300")
 
