@@ -273,15 +273,17 @@ __device__ __forceinline__ void assemble_from_right(T (&v)[V], T halo, int i0, i
 }
 
 // ---------------------------------------------------------------- row prefetch ----
-// The single-lattice multi-step kernel with the BGK collision and FP32 storage stages
+// The single-lattice multi-step kernels with FP32 storage (BGK and two-relaxation) stage
 // each warp's next row in shared memory with asynchronous copies (cp.async), issued
 // before the current row's arithmetic, so that a row's loads are in flight while the
 // previous row is computed; the register file holds no second row.  A warp's slots are
 // written only by its own lanes' copies and read back by the same lanes, so the copies
 // need no CTA barrier, only the wait for their own group and a warp barrier that orders
-// the reads of a row before the copies of the next one.  Measured at 4096^2: 0.2202 vs
-// 0.2284 ms per step.  The two-relaxation kernel (0.2932 vs 0.2563 ms) and the batched
-// kernel (0.2302 vs 0.2194 ms) were slower with it and load their rows directly.
+// the reads of a row before the copies of the next one.  Measured at 4096^2: BGK 0.2202
+// vs 0.2284 ms per step (three CTAs per SM); two-relaxation 0.2207 vs 0.2561 ms with two
+// CTAs per SM at up to 128 registers (at three CTAs and 80 registers it spills, and the
+// slots leave too little L1 for the spills: 0.2932 ms).  The batched kernel (0.2302 vs
+// 0.2194 ms) loads its rows directly.
 // Build knob: -DKSS_MULTI_PREFETCH=0 loads every row directly.
 #ifndef KSS_MULTI_PREFETCH
 #define KSS_MULTI_PREFETCH 1
@@ -291,6 +293,7 @@ struct PfWarp {
   float4 pop[9][32];  // the nine population vectors of each lane
   float hr[3][32];    // right halo of q = 3, 6, 7 (lane 31 and the row's tail lanes)
   float hl[4];        // left halo of q = 1, 5, 8 (lane 0)
+  uint32_t rg[32];    // region bytes of each lane's cells (two-relaxation steps)
 };
 constexpr int kPfBytes = kWarps * int(sizeof(PfWarp));
 static_assert(sizeof(PfWarp) % 16 == 0, "16-byte aligned warp slots");
@@ -311,10 +314,10 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // Dynamic shared memory of step_kernel_multi<S, MODE, AAR>: the row prefetch slots, or 0
-// where the kernel loads its rows directly.
+// where the kernel loads its rows directly (either collision takes the slots).
 template <class S, int MODE, bool AAR>
 __host__ __device__ constexpr int multi_prefetch_smem() {
-  return (KSS_MULTI_PREFETCH && std::is_same<S, float>::value && MODE == MODE_STD && !AAR)
+  return (KSS_MULTI_PREFETCH && std::is_same<S, float>::value && MODE == MODE_STD)
              ? kPfBytes
              : 0;
 }
@@ -975,7 +978,7 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
   // row prefetch (see PfWarp): the warp's slots in dynamic shared memory, and the copies
   // of row jj into them
   constexpr bool PF = PREFETCH && CG && PULL && STORE;
-  static_assert(!PF || (std::is_same<S, float>::value && !AAR), "prefetch: FP32 BGK rows");
+  static_assert(!PF || std::is_same<S, float>::value, "prefetch: FP32 rows");
   extern __shared__ __align__(16) unsigned char kss_dyn_smem[];
   PfWarp* const pw = reinterpret_cast<PfWarp*>(kss_dyn_smem) + warp;
   auto pf_issue = [&](int jj) {
@@ -1011,6 +1014,7 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
         cp_async4(&pw->hr[1][lane], r6 + c);
         cp_async4(&pw->hr[2][lane], r7 + c);
       }
+      if (AAR && p.region) cp_async4(&pw->rg[lane], p.region + (long long)jj * p.pitch + i0);
     }
     cp_async_commit();
   };
@@ -1040,6 +1044,7 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
         if (lane == 31 || i0 + V >= p.nx) {
           hr[0] = pw->hr[0][lane]; hr[1] = pw->hr[1][lane]; hr[2] = pw->hr[2][lane];
         }
+        if (AAR && p.region) mbits = pw->rg[lane];
       } else {
 #pragma unroll
         for (int q = 0; q < 9; ++q)
@@ -1391,9 +1396,10 @@ __device__ __forceinline__ bool multi_block(const StepParams<S>& p, const MultiS
 }
 
 // pa: buffer A -> B (even steps); pb: B -> A (odd steps).  AAR: the two-relaxation
-// collision in the region (adaptive algorithm refinement).
+// collision in the region (adaptive algorithm refinement), two CTAs per SM (its per-cell
+// state needs more than 80 registers).
 template <class S, int MODE, bool AAR = false>
-__global__ void __launch_bounds__(kThreads, KSS_STEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(kThreads, AAR ? 2 : KSS_STEP_MIN_BLOCKS)
 step_kernel_multi(const StepParams<S> pa, const StepParams<S> pb, const MultiState m) {
   __shared__ int s_next;
   if (threadIdx.x == 0) s_next = int(atomicAdd(m.work, 1u));
