@@ -2,6 +2,8 @@
 // storage precision by launch_f32.cu / launch_f64.cu with KSS_T defined.
 #pragma once
 
+#include <atomic>
+
 #include "launch.h"
 
 namespace kss {
@@ -13,43 +15,47 @@ inline dim3 helper_grid(int nx, long long rows) {
 
 // Let `kernel` take DYN bytes of dynamic shared memory on the current device (beyond the
 // default 48 KB of static plus dynamic memory an opt-in is needed), once per device.
+// Threads that race here at most repeat the (idempotent) attribute call.
 template <auto kernel, int DYN>
 cudaError_t allow_dynamic_smem() {
   if constexpr (DYN == 0) {
     return cudaSuccess;
   } else {
     constexpr int kMaxDev = 64;
-    static bool done[kMaxDev] = {};
+    static std::atomic<bool> done[kMaxDev] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
-    if (!done[dev]) {
+    if (!done[dev].load(std::memory_order_acquire)) {
       e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, DYN);
       if (e != cudaSuccess) return e;
-      done[dev] = true;
+      done[dev].store(true, std::memory_order_release);
     }
     return cudaSuccess;
   }
 }
 
 // CTAs of `kernel` (with DYN bytes of dynamic shared memory) resident on the current
-// device at once (its occupancy times the SM count), looked up once per device.
+// device at once (its occupancy times the SM count), looked up once per device (racing
+// threads at most repeat the query).
 template <auto kernel, int DYN = 0>
 int resident_ctas() {
   constexpr int kMaxDev = 64;
-  static int cache[kMaxDev] = {};  // one per kernel: `kernel` is a template argument
+  static std::atomic<int> cache[kMaxDev] = {};  // one per kernel: a template argument
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 0;
-  if (!cache[dev]) {
+  int n = cache[dev].load(std::memory_order_acquire);
+  if (!n) {
     int nsm = 0, per = 0;
     if (allow_dynamic_smem<kernel, DYN>() != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kThreads, DYN) != cudaSuccess)
       return 0;
-    cache[dev] = nsm * per;
+    n = nsm * per;
+    cache[dev].store(n, std::memory_order_release);
   }
-  return cache[dev];
+  return n;
 }
 
 // Persistent steps: when the step grid exceeds one wave of resident CTAs, one wave that
