@@ -154,3 +154,25 @@ def test_noalloc_rejects_bad_arguments_before_touching_the_gpu(change, code):
     a = dict(_NOALLOC_OK, **change)
     rc = lib.kss_step_f32_noalloc(*a.values())
     assert rc == {"arg": -1, "capacity": -7}[code], (change, rc)
+
+
+@pytest.mark.parametrize("field,value,code", [
+    ("nx", 0, -1), ("ny", -3, -1), ("nsteps", 0, -1), ("checkpoint_every", 0, -1),
+    ("own_stream", 2, -1), ("precision", 2, -6), ("nx", 1 << 16, -1),
+])
+def test_adjoint_create_rejects_bad_config_before_touching_the_gpu(field, value, code):
+    """kss_adjoint_create checks its configuration before its first CUDA call (FP16
+    deviations have no adjoint: KSS_ERR_UNSUPPORTED)."""
+    import ctypes
+
+    from paper_2603_13618_gb300 import kss
+
+    lib = kss.load()
+    cfg = kss.AdjointConfig(nx=64, ny=48, precision=kss.FP32, nsteps=20, checkpoint_every=5,
+                            stream=None, own_stream=0)
+    setattr(cfg, field, value)
+    if field == "nx" and value == 1 << 16:
+        cfg.ny = 1 << 16  # 2^32 cells: beyond the 32-bit cell index
+    out = ctypes.c_void_p(1)
+    assert lib.kss_adjoint_create(ctypes.byref(cfg), ctypes.byref(out)) == code
+    assert out.value is None
