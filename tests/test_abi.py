@@ -176,3 +176,30 @@ def test_adjoint_create_rejects_bad_config_before_touching_the_gpu(field, value,
     out = ctypes.c_void_p(1)
     assert lib.kss_adjoint_create(ctypes.byref(cfg), ctypes.byref(out)) == code
     assert out.value is None
+
+
+@pytest.mark.parametrize("case,code", [("empty", -1), ("mixed_precision", -1),
+                                       ("aar_cadences", -6)])
+def test_batch_create_rejects_before_touching_the_gpu(case, code):
+    """kss_batch_create: no members, members of different storage precisions, or members with
+    the two-relaxation model (tau2 > 0) and different output cadences are refused before the
+    first CUDA call."""
+    import ctypes
+
+    from paper_2603_13618_gb300 import kss
+
+    lib = kss.load()
+    cfgs = (kss.Config * 2)()
+    for k in range(2):
+        assert lib.kss_config_default(cfgs[k], 64 + 32 * k, 48, kss.FP32) == 0
+    n = 2
+    if case == "empty":
+        n = 0
+    elif case == "mixed_precision":
+        cfgs[1].precision = kss.FP64
+    else:
+        cfgs[0].tau2 = cfgs[1].tau2 = 1.3
+        cfgs[1].output_every = 3
+    out = ctypes.c_void_p(1)
+    assert lib.kss_batch_create(n, cfgs, ctypes.byref(out)) == code
+    assert out.value is None
