@@ -25,19 +25,62 @@ SENSOR_NAMES = ("tau_ns", "c", "s", "e", "qh", "kn", "neq", "qe", "hr", "kl",
 SENSOR_ID = {n: k for k, n in enumerate(SENSOR_NAMES)}
 
 
-def build(verbose: bool = False) -> str:
-    """Compile orc.c into _build/liborc.so with gcc (plain -O2, no fast-math)."""
-    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    src = os.path.join(_HERE, "orc.c")
+def build(verbose: bool = False, src: str | None = None, out: str | None = None) -> str:
+    """Compile orc.c (or another copy of it, `src`) into _build/liborc.so (or `out`) with
+    gcc (plain -O2, no fast-math)."""
+    out = out or _LIB_PATH
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    src = src or os.path.join(_HERE, "orc.c")
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
-           "-ffp-contract=off", "-Wall", "-Wextra", "-o", _LIB_PATH, src, "-lm"]
+           "-ffp-contract=off", "-Wall", "-Wextra", "-I", _HERE, "-o", out, src, "-lm"]
     if verbose:
         print(" ".join(cmd))
     subprocess.run(cmd, check=True)
-    return _LIB_PATH
+    return out
 
 
 _lib = None
+
+
+def load_library(path: str) -> ctypes.CDLL:
+    """A compiled oracle library at `path`, with the ctypes signatures of its functions."""
+    L = ctypes.CDLL(path)
+    dp = ctypes.POINTER(ctypes.c_double)
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    ci, cd = ctypes.c_int, ctypes.c_double
+    sig = {
+        "orc_equilibrium": (None, [cd, cd, cd, dp]),
+        "orc_init_equilibrium": (None, [ci, ci, dp, dp, dp, dp]),
+        "orc_stream": (None, [ci, ci, dp, dp]),
+        "orc_collide": (None, [ci, ci, cd, dp, dp]),
+        "orc_step": (None, [ci, ci, cd, dp, dp]),
+        "orc_moments": (None, [ci, ci, dp, dp, dp, dp]),
+        "orc_cell_sensors": (ci, [dp, cd, dp]),
+        "orc_cell_sensors_model": (ci, [dp, cd, ci, dp]),
+        "orc_quasi_equilibrium": (None, [dp, dp]),
+        "orc_collide_aar": (None, [ci, ci, cd, cd, u8p, dp, dp]),
+        "orc_sensor_fields_model": (None, [ci, ci, cd, ci, dp, ci, dp, u8p]),
+        "orc_cell_log_sensors_literal": (None, [dp, cd, dp, dp]),
+        "orc_alpha_poly": (cd, [dp, dp]),
+        "orc_alpha_exact": (cd, [dp]),
+        "orc_sensor_fields": (None, [ci, ci, cd, dp, ci, dp, u8p]),
+        "orc_flags": (None, [ci, ci, dp, cd, dp, cd, u8p, ci, u8p, i32p, i64p]),
+        "orc_sums": (None, [ci, ci, dp, dp]),
+        "orc_mac_sensors": (None, [ci, ci, cd, dp, dp, dp, dp]),
+        "orc_run": (ctypes.c_int64, [ci, ci, cd, dp, dp, ci, ci, cd, ci, cd, ci,
+                                      dp, u8p, i32p, i64p, dp]),
+        "orc_adjoint_kl": (ci, [ci, ci, cd, ci, ci, dp, dp, dp, dp, dp, dp, dp]),
+        "orc_fp16_round": (cd, [cd]),
+        "orc_dev16_encode": (None, [ci, ci, cd, ci, ci, dp, dp]),
+        "orc_dev16_decode": (None, [ci, ci, cd, ci, ci, dp, dp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
 
 
 def lib():
@@ -47,43 +90,7 @@ def lib():
         if (not os.path.exists(_LIB_PATH)
                 or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src)):
             build()
-        L = ctypes.CDLL(_LIB_PATH)
-        dp = ctypes.POINTER(ctypes.c_double)
-        u8p = ctypes.POINTER(ctypes.c_uint8)
-        i32p = ctypes.POINTER(ctypes.c_int32)
-        i64p = ctypes.POINTER(ctypes.c_int64)
-        ci, cd = ctypes.c_int, ctypes.c_double
-        sig = {
-            "orc_equilibrium": (None, [cd, cd, cd, dp]),
-            "orc_init_equilibrium": (None, [ci, ci, dp, dp, dp, dp]),
-            "orc_stream": (None, [ci, ci, dp, dp]),
-            "orc_collide": (None, [ci, ci, cd, dp, dp]),
-            "orc_step": (None, [ci, ci, cd, dp, dp]),
-            "orc_moments": (None, [ci, ci, dp, dp, dp, dp]),
-            "orc_cell_sensors": (ci, [dp, cd, dp]),
-            "orc_cell_sensors_model": (ci, [dp, cd, ci, dp]),
-            "orc_quasi_equilibrium": (None, [dp, dp]),
-            "orc_collide_aar": (None, [ci, ci, cd, cd, u8p, dp, dp]),
-            "orc_sensor_fields_model": (None, [ci, ci, cd, ci, dp, ci, dp, u8p]),
-            "orc_cell_log_sensors_literal": (None, [dp, cd, dp, dp]),
-            "orc_alpha_poly": (cd, [dp, dp]),
-            "orc_alpha_exact": (cd, [dp]),
-            "orc_sensor_fields": (None, [ci, ci, cd, dp, ci, dp, u8p]),
-            "orc_flags": (None, [ci, ci, dp, cd, dp, cd, u8p, ci, u8p, i32p, i64p]),
-            "orc_sums": (None, [ci, ci, dp, dp]),
-            "orc_mac_sensors": (None, [ci, ci, cd, dp, dp, dp, dp]),
-            "orc_run": (ctypes.c_int64, [ci, ci, cd, dp, dp, ci, ci, cd, ci, cd, ci,
-                                          dp, u8p, i32p, i64p, dp]),
-            "orc_adjoint_kl": (ci, [ci, ci, cd, ci, ci, dp, dp, dp, dp, dp, dp, dp]),
-            "orc_fp16_round": (cd, [cd]),
-            "orc_dev16_encode": (None, [ci, ci, cd, ci, ci, dp, dp]),
-            "orc_dev16_decode": (None, [ci, ci, cd, ci, ci, dp, dp]),
-        }
-        for name, (res, args) in sig.items():
-            fn = getattr(L, name)
-            fn.restype = res
-            fn.argtypes = args
-        _lib = L
+        _lib = load_library(_LIB_PATH)
     return _lib
 
 

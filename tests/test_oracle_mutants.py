@@ -1,0 +1,89 @@
+"""The oracle's pins catch plausible mistakes.  Each case plants one mistake in a copy of
+oracle/orc.c (a wrong coefficient, a flipped sign or direction, a swapped index or
+operand, a dropped term, a different rounding rule), compiles it into a temporary library,
+and runs one existing pin against that library: the pin must fail.  The unchanged source,
+built the same way, passes the same pins (the control case).  Everything runs on the CPU.
+"""
+import os
+
+import pytest
+
+import oracle
+from tests import test_oracle_adjoint as t_adj
+from tests import test_oracle_fp16dev as t_f16
+from tests import test_oracle_lattice as t_lat
+from tests import test_oracle_sensors as t_sen
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "orc.c")
+
+PINS = {
+    "equilibrium_moments": lambda: t_lat.test_equilibrium_moments(oracle),
+    "stream_by_cq": lambda: t_lat.test_stream_moves_population_q_by_cq(oracle),
+    "push_scheme_8x8": lambda: t_lat.test_brute_force_push_scheme_8x8(oracle),
+    "sums": lambda: t_lat.test_sums_brute_force(oracle),
+    "hand_modes": lambda: t_sen.test_hand_derived_modes(oracle, 1.3, 0.6),
+    "printed_log_forms": lambda: t_sen.test_log_sensors_match_printed_forms(oracle),
+    "flags_tiles": lambda: t_sen.test_flags_and_tiles_brute_force(oracle),
+    "fp16_numpy": lambda: t_f16.test_fp16_rounding_matches_numpy_float16(),
+    "adjoint_tau_fd": lambda: t_adj.test_tau_derivative_matches_central_differences(0.8),
+    "adjoint_rho_fd": lambda: t_adj.test_full_density_gradient_matches_central_differences(),
+}
+
+# (planted mistake, text in orc.c, replacement, pin that must catch it)
+MUTANTS = [
+    ("equilibrium second-order term halved",
+     "h2 / (2.0 * CS2 * CS2)", "h2 / (4.0 * CS2 * CS2)", "equilibrium_moments"),
+    ("streaming pushes instead of pulls",
+     "ft[at(nx, ny, q, i, j)] = f[at(nx, ny, q, wrap(i - CX[q], nx), wrap(j - CY[q], ny))];",
+     "ft[at(nx, ny, q, i, j)] = f[at(nx, ny, q, wrap(i + CX[q], nx), wrap(j + CY[q], ny))];",
+     "stream_by_cq"),
+    ("relaxation time taken as tau - 1/2",
+     "const double omega = -(c[q] - feq[q]) / tau;",
+     "const double omega = -(c[q] - feq[q]) / (tau - 0.5);", "push_scheme_8x8"),
+    ("x and y momenta swapped in the moments",
+     "    jx += CX[q] * ft[q];\n    jy += CY[q] * ft[q];\n  }\n  *rho = r;",
+     "    jx += CY[q] * ft[q];\n    jy += CX[q] * ft[q];\n  }\n  *rho = r;", "push_scheme_8x8"),
+    ("Kn normalised by f instead of f^eq",
+     "kn += fabs(fneq[q] / feq[q]);", "kn += fabs(fneq[q] / ft[q]);", "hand_modes"),
+    ("absolute value dropped from the neq sensor",
+     "neq += fabs(fneq[q]);", "neq += fneq[q];", "hand_modes"),
+    ("KL weighted by f instead of f^eq",
+     "kl += feq[q] * phi(x);", "kl += ft[q] * phi(x);", "printed_log_forms"),
+    ("tile index transposed",
+     "const int t = (j / tile) * ntx + (i / tile);",
+     "const int t = (i / tile) * nty + (j / tile);", "flags_tiles"),
+    ("binary16 rounding ties away from zero",
+     "rint(a / quantum)", "floor(a / quantum + 0.5)", "fp16_numpy"),
+    ("sign of the dtau partial flipped",
+     "kahan_add(&gs, &gc, l[q] * (c[q] - feq[q]) / (tau * tau));",
+     "kahan_add(&gs, &gc, -l[q] * (c[q] - feq[q]) / (tau * tau));", "adjoint_tau_fd"),
+    ("1/tau dropped from the equilibrium part of the collision Jacobian",
+     "lt[at(nx, ny, p, i, j)] = (1.0 - 1.0 / tau) * l[p] + s / tau;",
+     "lt[at(nx, ny, p, i, j)] = (1.0 - 1.0 / tau) * l[p] + s;", "adjoint_rho_fd"),
+]
+
+
+def _build(tmp_path, text, name):
+    src = tmp_path / f"{name}.c"
+    src.write_text(text)
+    return oracle.load_library(oracle.build(src=str(src), out=str(tmp_path / f"{name}.so")))
+
+
+@pytest.fixture(scope="module")
+def source():
+    with open(SRC) as fh:
+        return fh.read()
+
+
+def test_control_unchanged_source_passes_every_pin(tmp_path, source, monkeypatch):
+    monkeypatch.setattr(oracle, "_lib", _build(tmp_path, source, "control"))
+    for pin in PINS.values():
+        pin()
+
+
+@pytest.mark.parametrize("what,old,new,pin", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(tmp_path, source, monkeypatch, what, old, new, pin):
+    assert source.count(old) == 1, f"the text to mutate must occur once: {old!r}"
+    monkeypatch.setattr(oracle, "_lib", _build(tmp_path, source.replace(old, new), "mutant"))
+    with pytest.raises(AssertionError):
+        PINS[pin]()
