@@ -4,17 +4,26 @@ operand, a dropped term, a different rounding rule), compiles it into a temporar
 and runs one existing pin against that library: the pin must fail.  The unchanged source,
 built the same way, passes the same pins (the control case).  Everything runs on the CPU.
 """
+import json
 import os
 
 import pytest
 
 import oracle
+from tests import test_oracle_aar as t_aar
 from tests import test_oracle_adjoint as t_adj
 from tests import test_oracle_fp16dev as t_f16
+from tests import test_oracle_golden as t_gold
 from tests import test_oracle_lattice as t_lat
 from tests import test_oracle_sensors as t_sen
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "orc.c")
+
+
+def _gold():
+    with open(os.path.join(t_gold.GOLDEN, "alpha_polynomial.json")) as fh:
+        return json.load(fh)
+
 
 PINS = {
     "equilibrium_moments": lambda: t_lat.test_equilibrium_moments(oracle),
@@ -27,6 +36,10 @@ PINS = {
     "fp16_numpy": lambda: t_f16.test_fp16_rounding_matches_numpy_float16(),
     "adjoint_tau_fd": lambda: t_adj.test_tau_derivative_matches_central_differences(0.8),
     "adjoint_rho_fd": lambda: t_adj.test_full_density_gradient_matches_central_differences(),
+    "aar_eigenmodes": lambda: t_aar.test_relaxation_eigenmodes(oracle, 0.8, 1.3),
+    "alpha_printed": lambda: t_gold.test_alpha_is_the_printed_polynomial_of_its_a_n(
+        oracle, _gold(), 1e-2),
+    "codec_scales": lambda: t_f16.test_codec_roundtrip_and_scales(),
 }
 
 # (planted mistake, text in orc.c, replacement, pin that must catch it)
@@ -60,6 +73,19 @@ MUTANTS = [
     ("1/tau dropped from the equilibrium part of the collision Jacobian",
      "lt[at(nx, ny, p, i, j)] = (1.0 - 1.0 / tau) * l[p] + s / tau;",
      "lt[at(nx, ny, p, i, j)] = (1.0 - 1.0 / tau) * l[p] + s;", "adjoint_rho_fd"),
+    ("quasi-equilibrium keeps the even part instead of the odd part",
+     "const double odd = 0.5 * ((ft[q] - feq[q]) - (ft[OPP[q]] - feq[OPP[q]]));",
+     "const double odd = 0.5 * ((ft[q] - feq[q]) + (ft[OPP[q]] - feq[OPP[q]]));",
+     "aar_eigenmodes"),
+    ("tau1 and tau2 swapped in the two-relaxation collision",
+     "const double omega = -(c[q] - fstar[q]) / tau1 - (fstar[q] - feq[q]) / tau2;",
+     "const double omega = -(c[q] - fstar[q]) / tau2 - (fstar[q] - feq[q]) / tau1;",
+     "aar_eigenmodes"),
+    ("a coefficient of the entropic-estimate polynomial changed",
+     "- 8.0 * a3 / a1 +", "- 4.0 * a3 / a1 +", "alpha_printed"),
+    ("binary16 deviation scale of one diagonal population wrong",
+     "static const int K[9] = {1, 3, 3, 3, 3, 5, 5, 5, 5};",
+     "static const int K[9] = {1, 3, 3, 3, 3, 5, 5, 5, 3};", "codec_scales"),
 ]
 
 
