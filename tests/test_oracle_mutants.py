@@ -113,3 +113,59 @@ def test_planted_mistake_is_caught(tmp_path, source, monkeypatch, what, old, new
     monkeypatch.setattr(oracle, "_lib", _build(tmp_path, source.replace(old, new), "mutant"))
     with pytest.raises(AssertionError):
         PINS[pin]()
+
+
+# ---- the regrid oracle (plain Python): mutants are loaded from a mutated copy of
+# oracle/regrid.py in place of the module the pins use
+from tests import test_oracle_regrid as t_reg  # noqa: E402
+
+REGRID_SRC = os.path.join(os.path.dirname(oracle.__file__), "regrid.py")
+
+REGRID_PINS = {
+    "rolled_dilation": lambda: t_reg.test_tile_mask_against_rolled_dilation(),
+    "blobs": lambda: t_reg.test_empty_full_and_separated_blobs(),
+    "hole_centre": lambda: t_reg.test_hole_nearest_the_centre_wins(),
+    "l_shape": lambda: t_reg.test_l_shape_splits_at_the_inflection(),
+}
+
+REGRID_MUTANTS = [
+    ("buffer one cell short below and left",
+     "np.arange(ty * tile - buffer, min((ty + 1) * tile, ny) + buffer) % ny",
+     "np.arange(ty * tile - buffer + 1, min((ty + 1) * tile, ny) + buffer) % ny",
+     "rolled_dilation"),
+    ("efficiency test made strict",
+     "if total >= efficiency * (w * h) or (w == 1 and h == 1):",
+     "if total > efficiency * (w * h) or (w == 1 and h == 1):", "hole_centre"),
+    ("hole distance measured from the wrong centre",
+     "return abs(2 * i - (lo + hi - 1))", "return abs(2 * i - (lo + hi - 3))", "hole_centre"),
+    ("inflection test on equal signs",
+     "if d[k] * d[k + 1] < 0:", "if d[k] * d[k + 1] > 0:", "l_shape"),
+]
+
+
+def _load_regrid(tmp_path, text, name):
+    import importlib.util
+
+    path = tmp_path / f"{name}.py"
+    path.write_text(text)
+    spec = importlib.util.spec_from_file_location(f"regrid_{name}", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_regrid_control_unchanged_source_passes_every_pin(tmp_path, monkeypatch):
+    with open(REGRID_SRC) as fh:
+        monkeypatch.setattr(t_reg, "regrid", _load_regrid(tmp_path, fh.read(), "control"))
+    for pin in REGRID_PINS.values():
+        pin()
+
+
+@pytest.mark.parametrize("what,old,new,pin", REGRID_MUTANTS, ids=[m[0] for m in REGRID_MUTANTS])
+def test_planted_regrid_mistake_is_caught(tmp_path, monkeypatch, what, old, new, pin):
+    with open(REGRID_SRC) as fh:
+        text = fh.read()
+    assert text.count(old) == 1, f"the text to mutate must occur once: {old!r}"
+    monkeypatch.setattr(t_reg, "regrid", _load_regrid(tmp_path, text.replace(old, new), "mut"))
+    with pytest.raises(AssertionError):
+        REGRID_PINS[pin]()
