@@ -40,6 +40,7 @@ PINS = {
     "alpha_printed": lambda: t_gold.test_alpha_is_the_printed_polynomial_of_its_a_n(
         oracle, _gold(), 1e-2),
     "codec_scales": lambda: t_f16.test_codec_roundtrip_and_scales(),
+    "symmetries": lambda: t_sen.test_lattice_symmetries(oracle),
 }
 
 # (planted mistake, text in orc.c, replacement, pin that must catch it)
@@ -83,6 +84,18 @@ MUTANTS = [
      "aar_eigenmodes"),
     ("a coefficient of the entropic-estimate polynomial changed",
      "- 8.0 * a3 / a1 +", "- 4.0 * a3 / a1 +", "alpha_printed"),
+    ("trace part of the S sensor not divided by D",
+     "M[a][b] = ((a == b ? trP / D : 0.0) - P[a][b]) / mu;",
+     "M[a][b] = ((a == b ? trP : 0.0) - P[a][b]) / mu;", "hand_modes"),
+    ("factor sqrt(D) dropped from the C sensor",
+     "out[ORC_C] = sqrt(D) * fabs(-trP / (2.0 * mu + D * lambda));",
+     "out[ORC_C] = fabs(-trP / (2.0 * mu + D * lambda));", "hand_modes"),
+    ("indices of u . P^neq swapped in the q_H sensor",
+     "qh[b] += u[a] * P[a][b];", "qh[b] += u[b] * P[a][b];", "symmetries"),
+    ("sigma_KL weighted by f^eq instead of f^neq",
+     "sig += fneq[q] * log1p(x);", "sig += feq[q] * log1p(x);", "printed_log_forms"),
+    ("sign of the linear term of HR flipped",
+     "lin += fneq[q] * L;", "lin -= fneq[q] * L;", "printed_log_forms"),
     ("binary16 deviation scale of one diagonal population wrong",
      "static const int K[9] = {1, 3, 3, 3, 3, 5, 5, 5, 5};",
      "static const int K[9] = {1, 3, 3, 3, 3, 5, 5, 5, 3};", "codec_scales"),
