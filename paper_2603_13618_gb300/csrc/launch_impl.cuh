@@ -150,7 +150,9 @@ cudaError_t launch_step_multi<KSS_T>(const StepParams<KSS_T>& pa, const StepPara
 
 template <>
 int batch_multi_resident_ctas<KSS_T>(int mode) {
-  return mode == MODE_STD ? resident_ctas<batch_kernel_multi<KSS_T, MODE_STD>>() : 0;
+  return mode == MODE_STD ? resident_ctas<batch_kernel_multi<KSS_T, MODE_STD>,
+                                         multi_prefetch_smem<KSS_T, MODE_STD, false>()>()
+                          : 0;
 }
 
 template <>
@@ -166,8 +168,11 @@ cudaError_t launch_batch_multi<KSS_T>(const StepParams<KSS_T>* ta, const StepPar
   int ni = nitems, ns = nsteps;
   uint32_t* w = work;
   void* args[] = {&a, &b, &m, &it, &ni, &ns, &w};
+  constexpr int dyn = multi_prefetch_smem<KSS_T, MODE_STD, false>();
+  const cudaError_t e = allow_dynamic_smem<batch_kernel_multi<KSS_T, MODE_STD>, dyn>();
+  if (e != cudaSuccess) return e;
   const void* fn = reinterpret_cast<const void*>(batch_kernel_multi<KSS_T, MODE_STD>);
-  return cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(kThreads), args, 0, stream);
+  return cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(kThreads), args, dyn, stream);
 }
 
 template <>

@@ -273,17 +273,17 @@ __device__ __forceinline__ void assemble_from_right(T (&v)[V], T halo, int i0, i
 }
 
 // ---------------------------------------------------------------- row prefetch ----
-// The single-lattice multi-step kernels with FP32 storage (BGK and two-relaxation) stage
-// each warp's next row in shared memory with asynchronous copies (cp.async), issued
-// before the current row's arithmetic, so that a row's loads are in flight while the
-// previous row is computed; the register file holds no second row.  A warp's slots are
-// written only by its own lanes' copies and read back by the same lanes, so the copies
-// need no CTA barrier, only the wait for their own group and a warp barrier that orders
-// the reads of a row before the copies of the next one.  Measured at 4096^2: BGK 0.2202
-// vs 0.2284 ms per step (three CTAs per SM); two-relaxation 0.2207 vs 0.2561 ms with two
-// CTAs per SM at up to 128 registers (at three CTAs and 80 registers it spills, and the
-// slots leave too little L1 for the spills: 0.2932 ms).  The batched kernel (0.2302 vs
-// 0.2194 ms) loads its rows directly.
+// The multi-step kernels with FP32 storage (single lattices with BGK or two-relaxation,
+// and batches) stage each warp's next row in shared memory with asynchronous copies
+// (cp.async), issued before the current row's arithmetic, so that a row's loads are in
+// flight while the previous row is computed; the register file holds no second row.  A
+// warp's slots are written only by its own lanes' copies and read back by the same
+// lanes, so the copies need no CTA barrier, only the wait for their own group and a warp
+// barrier that orders the reads of a row before the copies of the next one.  Measured at
+// 4096^2: BGK 0.2202 vs 0.2284 ms per step (three CTAs per SM); two-relaxation 0.2207 vs
+// 0.2561 ms with two CTAs per SM at up to 128 registers (at three CTAs and 80 registers
+// it spills, and the slots leave too little L1 for the spills: 0.2932 ms); the 64-lattice
+// batch 0.2015 vs 0.2194 ms, also at two CTAs per SM (at three it was slower, 0.2302 ms).
 // Build knob: -DKSS_MULTI_PREFETCH=0 loads every row directly.
 #ifndef KSS_MULTI_PREFETCH
 #define KSS_MULTI_PREFETCH 1
@@ -1460,14 +1460,15 @@ batch_step_kernel(const StepParams<S>* __restrict__ table, const BatchItem* __re
 }
 
 // ---------------------------------------------------------------- batched multi-step ----
-// nsteps steps of a whole batch in one cooperative launch: work item w = s * nitems + i is
+// nsteps steps of a whole batch in one cooperative launch (two CTAs per SM, rows staged
+// by the row prefetch for FP32 storage): work item w = s * nitems + i is
 // block items[i] of step s.  Each lattice has its own MultiState (its blocks' step
 // counters, ring of partial sums, ticket and slot counters); all share the work counter,
 // so items are handed out in (step, work-list) order and, as in step_kernel_multi, every
 // item waits only for items of its own lattice handed out before it.  mtab[k] is lattice
 // k's state; ta / tb its parameters for even / odd steps.
 template <class S, int MODE>
-__global__ void __launch_bounds__(kThreads, KSS_STEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(kThreads, 2)
 batch_kernel_multi(const StepParams<S>* __restrict__ ta, const StepParams<S>* __restrict__ tb,
                    const MultiState* __restrict__ mtab, const BatchItem* __restrict__ items,
                    int nitems, int nsteps, uint32_t* work) {
@@ -1495,7 +1496,9 @@ batch_kernel_multi(const StepParams<S>* __restrict__ ta, const StepParams<S>* __
     // the table is shared by calls of any length: the launch's step count goes in here
     // (other threads read it only after multi_block's barriers)
     if (threadIdx.x == 0) reinterpret_cast<MultiState*>(s_m)->nsteps = nsteps;
-    if (!multi_block<S, MODE>(sp, sm, s, int(it.by) * sm.gx + int(it.bx), &s_next)) return;
+    if (!multi_block<S, MODE, false, (multi_prefetch_smem<S, MODE, false>() > 0)>(
+            sp, sm, s, int(it.by) * sm.gx + int(it.bx), &s_next))
+      return;
     __syncthreads();
     w = s_next;
   }
