@@ -97,8 +97,9 @@ def profile_traffic(path=PROFILE):
 def kernel_name(choice: str) -> str:
     tma = choice == "tma"
     return ("step_tma_kernel<float, MODE_STD> (bulk-copy staged), one launch per step" if tma
-            else "step_kernel_multi<float, MODE_STD> (vector loads; all steps in one "
-                 "cooperative launch, blocks waiting on their neighbours' previous step)")
+            else "step_kernel_multi<float, MODE_STD> (each warp's next row staged in shared "
+                 "memory by cp.async; all steps in one cooperative launch, blocks waiting on "
+                 "their neighbours' previous step)")
 
 
 def measured_peak():
@@ -273,7 +274,8 @@ def run_batch(args):
                      "algorithmic_bytes_per_launch": BYTES_PER_LUP * cells,
                      "kernel_ms": kern_ms,
                      "kernel": ("batch_kernel_multi<float, MODE_STD> (all steps in one "
-                                "cooperative launch)" if multi
+                                "cooperative launch, rows staged in shared memory by "
+                                "cp.async)" if multi
                                 else "batch_step_kernel<float, MODE_STD>")},
         "multi_step_ms_by_rows": multi_rows,
         "graph_of_per_step_launches": {"value": cells * K / (graph_ms * 1e-3) / 1e6,
@@ -518,7 +520,8 @@ def run_aar(args):
                      "algorithmic_bytes_per_launch": main["bytes_per_lup"] * cells,
                      "kernel_ms_per_step": main["ms_per_step"],
                      "kernel": "step_kernel_multi<float, MODE_STD, AAR> (all K steps in one "
-                               "cooperative launch)"},
+                               "cooperative launch, rows staged in shared memory by "
+                               "cp.async)"},
         "variants": runs,
         "aar_cost_vs_bgk": main["ms_per_step"] / runs["bgk_std"]["ms_per_step"],
         "gpu_launches": 1,
