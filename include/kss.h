@@ -390,8 +390,10 @@ const char* kss_adjoint_last_error(const kss_adjoint* adj);
  * nothing (no cudaMalloc, cudaFree or allocating library routine).
  *
  * Buffers (device memory of the current device, owned by the caller):
- *   f_in, f_out   populations [9][ny][pitch] floats, 16-byte aligned, distinct; the
- *                 step reads f_in and writes f_out; pitch >= nx, a multiple of 32
+ *   f_in, f_out   populations [9][ny][pitch] floats, 16-byte aligned; the step reads
+ *                 f_in and writes f_out, and the two ranges must not overlap (an
+ *                 overlap, an in-place call included, is KSS_ERR_ARG); pitch >= nx, a
+ *                 multiple of 32
  *   sensor_out    the record_sensor field [ny][pitch] floats (16-byte aligned), or NULL
  *   flags         [ny][pitch] bytes (KSS_FLAG_*), 4-byte aligned
  *   tile_counts   int32 [2][ceil(ny/tile)][ceil(nx/tile)] (refine, switch)

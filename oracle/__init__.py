@@ -33,9 +33,15 @@ def build(verbose: bool = False, src: str | None = None, out: str | None = None)
     src = src or os.path.join(_HERE, "orc.c")
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
            "-ffp-contract=off", "-Wall", "-Wextra", "-I", _HERE, "-o", out, src, "-lm"]
+    # the row-parallel sweeps use OpenMP where the compiler has it (one thread unless
+    # set_threads asks for more); without it the same source builds serial
+    omp = cmd[:-1] + ["-fopenmp", "-lm"]
     if verbose:
-        print(" ".join(cmd))
-    subprocess.run(cmd, check=True)
+        print(" ".join(omp))
+    if subprocess.run(omp, capture_output=True).returncode != 0:
+        if verbose:
+            print(" ".join(cmd))
+        subprocess.run(cmd, check=True)
     return out
 
 
@@ -70,11 +76,15 @@ def load_library(path: str) -> ctypes.CDLL:
         "orc_sums": (None, [ci, ci, dp, dp]),
         "orc_mac_sensors": (None, [ci, ci, cd, dp, dp, dp, dp]),
         "orc_run": (ctypes.c_int64, [ci, ci, cd, dp, dp, ci, ci, cd, ci, cd, ci,
-                                      dp, u8p, i32p, i64p, dp]),
+                                      dp, u8p, i32p, i64p, dp, ci]),
+        "orc_cell_sensors_set": (ci, [dp, cd, ci, ci, dp]),
         "orc_adjoint_kl": (ci, [ci, ci, cd, ci, ci, dp, dp, dp, dp, dp, dp, dp]),
         "orc_fp16_round": (cd, [cd]),
         "orc_dev16_encode": (None, [ci, ci, cd, ci, ci, dp, dp]),
         "orc_dev16_decode": (None, [ci, ci, cd, ci, ci, dp, dp]),
+        "orc_set_threads": (None, [ci]),
+        "orc_get_threads": (ci, []),
+        "orc_have_openmp": (ci, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -101,6 +111,27 @@ def _p(a: np.ndarray, ct=ctypes.c_double):
 
 def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def set_threads(n: int) -> int:
+    """Split the row sweeps of later calls over n threads (1 = the serial oracle; results
+    are the same bit for bit at any count).  Returns the count in force, which stays 1
+    when the library was built without OpenMP."""
+    L = lib()
+    L.orc_set_threads(int(n) if L.orc_have_openmp() else 1)
+    return L.orc_get_threads()
+
+
+def get_threads() -> int:
+    return lib().orc_get_threads()
+
+
+def host_cores() -> int:
+    """Cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def equilibrium(rho: float, ux: float, uy: float) -> np.ndarray:
@@ -148,12 +179,16 @@ def moments(f):
     return rho, ux, uy
 
 
-def cell_sensors(ft, tau: float, two_relax: bool = False):
+def cell_sensors(ft, tau: float, two_relax: bool = False, full: bool = True):
     """All sensors of one cell's populations ft[9]; two_relax: the collision model is
-    the two-relaxation one (its quasi-equilibrium enters eps_qe), else BGK."""
+    the two-relaxation one (its quasi-equilibrium enters eps_qe), else BGK.  full=False:
+    only Kn, neq, qe and KL (the others NaN)."""
     ft = _f64(ft)
     out = np.empty(NSENS)
-    nonpos = lib().orc_cell_sensors_model(_p(ft), tau, int(two_relax), _p(out))
+    if full:
+        nonpos = lib().orc_cell_sensors_model(_p(ft), tau, int(two_relax), _p(out))
+    else:
+        nonpos = lib().orc_cell_sensors_set(_p(ft), tau, int(two_relax), 0, _p(out))
     return out, bool(nonpos)
 
 
@@ -242,8 +277,9 @@ def mac_sensors(rho, ux, uy, tau: float) -> np.ndarray:
 
 
 def run(f, tau: float, nsteps: int, sensor_r: int, thr_r: float, sensor_s: int,
-        thr_s: float, tile: int = 16):
-    """nsteps fused reference steps in place on a copy of f; returns a dict."""
+        thr_s: float, tile: int = 16, full: bool = True):
+    """nsteps fused reference steps in place on a copy of f; returns a dict.  full=False
+    evaluates only the {Kn, KL, neq} set (flags on one of them)."""
     f = _f64(f).copy()
     ny, nx = f.shape[1:]
     work = np.empty_like(f)
@@ -255,7 +291,7 @@ def run(f, tau: float, nsteps: int, sensor_r: int, thr_r: float, sensor_s: int,
     sm = np.empty(3)
     lib().orc_run(nx, ny, tau, _p(f), _p(work), nsteps, sensor_r, thr_r, sensor_s,
                   thr_s, tile, _p(rec), _p(fl, ctypes.c_uint8),
-                  _p(tiles, ctypes.c_int32), _p(counts, ctypes.c_int64), _p(sm))
+                  _p(tiles, ctypes.c_int32), _p(counts, ctypes.c_int64), _p(sm), int(full))
     return {"f": f, "eps_r": rec, "flags": fl, "tiles": tiles, "counts": counts,
             "sums": sm}
 

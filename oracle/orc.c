@@ -24,6 +24,31 @@ static const double W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 /
 /* Reference temperature of the lattice, R T_ref = c_s^2 = 1/3. */
 static const double CS2 = 1.0 / 3.0;
 
+/* Row-parallel sweeps.  The per-cell loops below that write only their own cell's
+ * outputs split their rows over g_threads OpenMP threads (1 by default, set by
+ * orc_set_threads); no arithmetic depends on the split, so the results are the same
+ * bit for bit at any thread count.  Loops that accumulate (flags and tile counts,
+ * the compensated sums, the adjoint) stay serial. */
+static int g_threads = 1;
+#ifdef _OPENMP
+#include <omp.h>
+#define ORC_ROWS _Pragma("omp parallel for schedule(static) num_threads(g_threads)")
+#else
+#define ORC_ROWS
+#endif
+
+void orc_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
+
+int orc_get_threads(void) { return g_threads; }
+
+int orc_have_openmp(void) {
+#ifdef _OPENMP
+  return 1;
+#else
+  return 0;
+#endif
+}
+
 static size_t at(int nx, int ny, int q, int i, int j) {
   return ((size_t)q * (size_t)ny + (size_t)j) * (size_t)nx + (size_t)i;
 }
@@ -53,6 +78,7 @@ void orc_equilibrium(double rho, double ux, double uy, double feq[9]) {
 
 void orc_init_equilibrium(int nx, int ny, const double* rho, const double* ux,
                           const double* uy, double* f) {
+  ORC_ROWS
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       const size_t c = (size_t)j * nx + i;
@@ -67,6 +93,7 @@ void orc_init_equilibrium(int nx, int ny, const double* rho, const double* ux,
  * it comes from, periodic in both directions. */
 void orc_stream(int nx, int ny, const double* f, double* ft) {
   for (int q = 0; q < 9; ++q)
+    ORC_ROWS
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i)
         ft[at(nx, ny, q, i, j)] = f[at(nx, ny, q, wrap(i - CX[q], nx), wrap(j - CY[q], ny))];
@@ -88,6 +115,7 @@ static void cell_moments(const double ft[9], double* rho, double* ux, double* uy
 /* Eq. new_collision_fi with tau1 = tau2 = tau (f* = f^eq): the discrete
  * collision operator Omega_i = -(f_i - f^eq_i)/tau, added with dt = 1. */
 void orc_collide(int nx, int ny, double tau, const double* ft, double* fnext) {
+  ORC_ROWS
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       double c[9], feq[9], rho, ux, uy;
@@ -141,6 +169,7 @@ void orc_quasi_equilibrium(const double ft[9], double fstar[9]) {
  * elsewhere the BGK operator of orc_collide (computed by the same expression). */
 void orc_collide_aar(int nx, int ny, double tau1, double tau2, const uint8_t* region,
                      const double* ft, double* fnext) {
+  ORC_ROWS
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       double c[9], feq[9], rho, ux, uy;
@@ -164,6 +193,7 @@ void orc_collide_aar(int nx, int ny, double tau1, double tau2, const uint8_t* re
 }
 
 void orc_moments(int nx, int ny, const double* f, double* rho, double* ux, double* uy) {
+  ORC_ROWS
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       double c[9];
@@ -290,6 +320,13 @@ int orc_cell_sensors(const double ft[9], double tau, double out[ORC_NSENS]) {
 
 int orc_cell_sensors_model(const double ft[9], double tau, int two_relax,
                            double out[ORC_NSENS]) {
+  return orc_cell_sensors_set(ft, tau, two_relax, 1, out);
+}
+
+/* full = 0: only Kn, neq, qe and KL (the sensor set that the flags of a production run
+ * use), by the same lines as the full evaluation; the other entries are NaN. */
+int orc_cell_sensors_set(const double ft[9], double tau, int two_relax, int full,
+                         double out[ORC_NSENS]) {
   double rho, ux, uy, feq[9], fneq[9];
   cell_moments(ft, &rho, &ux, &uy);
   orc_equilibrium(rho, ux, uy, feq);
@@ -299,6 +336,8 @@ int orc_cell_sensors_model(const double ft[9], double tau, int two_relax,
     if (ft[q] <= 0.0 || feq[q] <= 0.0) nonpos = 1;
   }
 
+  for (int k = 0; k < ORC_NSENS; ++k) out[k] = NAN;
+  if (full) {
   /* Non-equilibrium pressure tensor P^neq = sum v v f^neq. */
   double P[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
   for (int q = 0; q < 9; ++q) {
@@ -341,6 +380,7 @@ int orc_cell_sensors_model(const double ft[9], double tau, int two_relax,
       for (int a = 0; a < 2; ++a) qh[b] += u[a] * P[a][b];
     out[ORC_QH] = sqrt(qh[0] * qh[0] + qh[1] * qh[1]);
   }
+  }
   {
     /* f*: the equilibrium itself for BGK, else the quasi-equilibrium of the
      * two-relaxation model (orc_quasi_equilibrium) */
@@ -360,20 +400,26 @@ int orc_cell_sensors_model(const double ft[9], double tau, int two_relax,
     out[ORC_QE] = qe;
   }
   {
-    double kl = 0.0, lin = 0.0, sig = 0.0;
+    double kl = 0.0;
     for (int q = 0; q < 9; ++q) {
       const double x = fneq[q] / feq[q];
-      const double L = log(feq[q] / (W[q] * rho));
       kl += feq[q] * phi(x);
-      lin += fneq[q] * L;
-      sig += fneq[q] * log1p(x);
     }
     out[ORC_KL] = fabs(kl);
-    out[ORC_HR] = fabs(lin + kl);
-    out[ORC_SIGMA_H] = (lin + sig) / tau;
-    out[ORC_SIGMA_KL] = sig / tau;
+    if (full) {
+      double lin = 0.0, sig = 0.0;
+      for (int q = 0; q < 9; ++q) {
+        const double x = fneq[q] / feq[q];
+        const double L = log(feq[q] / (W[q] * rho));
+        lin += fneq[q] * L;
+        sig += fneq[q] * log1p(x);
+      }
+      out[ORC_HR] = fabs(lin + kl);
+      out[ORC_SIGMA_H] = (lin + sig) / tau;
+      out[ORC_SIGMA_KL] = sig / tau;
+    }
   }
-  {
+  if (full) {
     /* |2 - alpha| of Eq. sensor-alpha-kin with alpha of Eq. alpha-polynomial-1;
      * the constant 2 cancels exactly, so the correction terms are summed directly */
     double a[4];
@@ -388,11 +434,13 @@ int orc_cell_sensors_model(const double ft[9], double tau, int two_relax,
   }
   if (nonpos) {
     out[ORC_KN] = INFINITY;
-    out[ORC_HR] = INFINITY;
     out[ORC_KL] = INFINITY;
-    out[ORC_SIGMA_H] = INFINITY;
-    out[ORC_SIGMA_KL] = INFINITY;
-    out[ORC_ALPHA] = INFINITY;
+    if (full) {
+      out[ORC_HR] = INFINITY;
+      out[ORC_SIGMA_H] = INFINITY;
+      out[ORC_SIGMA_KL] = INFINITY;
+      out[ORC_ALPHA] = INFINITY;
+    }
   }
   return nonpos;
 }
@@ -443,6 +491,7 @@ void orc_sensor_fields(int nx, int ny, double tau, const double* f, int pull, do
 
 void orc_sensor_fields_model(int nx, int ny, double tau, int two_relax, const double* f,
                              int pull, double* out, uint8_t* nonpos) {
+  ORC_ROWS
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       double c[9], s[ORC_NSENS];
@@ -509,6 +558,7 @@ void orc_sums(int nx, int ny, const double* f, double sums[3]) {
 void orc_mac_sensors(int nx, int ny, double tau, const double* rho, const double* ux,
                      const double* uy, double* out) {
   const size_t n = (size_t)nx * ny;
+  ORC_ROWS
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       const size_t c = (size_t)j * nx + i;
@@ -532,17 +582,18 @@ void orc_mac_sensors(int nx, int ny, double tau, const double* rho, const double
 int64_t orc_run(int nx, int ny, double tau, double* f, double* work, int nsteps,
                 int sensor_r, double thr_r, int sensor_s, double thr_s, int tile,
                 double* rec_field, uint8_t* flags, int32_t* tiles, int64_t counts[3],
-                double sums[3]) {
+                double sums[3], int full) {
   const size_t n = (size_t)nx * ny;
   double* eps_s = (double*)malloc(sizeof(double) * n);
   uint8_t* np = (uint8_t*)malloc(n);
   for (int step = 0; step < nsteps; ++step) {
     orc_stream(nx, ny, f, work);
+    ORC_ROWS
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
         double c[9], s[ORC_NSENS];
         for (int q = 0; q < 9; ++q) c[q] = work[at(nx, ny, q, i, j)];
-        np[(size_t)j * nx + i] = (uint8_t)orc_cell_sensors(c, tau, s);
+        np[(size_t)j * nx + i] = (uint8_t)orc_cell_sensors_set(c, tau, 0, full, s);
         rec_field[(size_t)j * nx + i] = s[sensor_r];
         eps_s[(size_t)j * nx + i] = s[sensor_s];
       }

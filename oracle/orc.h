@@ -48,6 +48,15 @@ enum {
   ORC_NSENS = 13
 };
 
+/* Threads of the row-parallel per-cell sweeps (init, stream, collide, moments, sensor
+ * fields, the sensor pass of orc_run): 1 by default.  Every cell's arithmetic is
+ * independent of the split, so results are identical at any count.  Reductions
+ * (flags, tile counts, sums) and the adjoint stay serial.  orc_have_openmp() is 0
+ * when the library was built without OpenMP (the count then stays 1). */
+void orc_set_threads(int n);
+int orc_get_threads(void);
+int orc_have_openmp(void);
+
 /* Equilibrium, Grad-Hermite expansion to order N = 2 at T_ref = c_s^2 = 1/3
  * (section "Discrete kinetic model", unnumbered GH expansion). */
 void orc_equilibrium(double rho, double ux, double uy, double feq[9]);
@@ -89,6 +98,11 @@ int orc_cell_sensors(const double ft[9], double tau, double out[ORC_NSENS]);
  * with the quasi-equilibrium of orc_quasi_equilibrium). */
 int orc_cell_sensors_model(const double ft[9], double tau, int two_relax,
                            double out[ORC_NSENS]);
+/* The same, with full = 0 evaluating only ORC_KN, ORC_NEQ, ORC_QE and ORC_KL (the
+ * refine/switch set of a production run) by the same lines; the other entries are
+ * NaN.  full = 1 is orc_cell_sensors_model. */
+int orc_cell_sensors_set(const double ft[9], double tau, int two_relax, int full,
+                         double out[ORC_NSENS]);
 
 /* The four logarithmic sensors (HR, KL, SIGMA_H, SIGMA_KL) evaluated in their
  * literal printed form, for the consistency check of the cancellation-free
@@ -135,13 +149,14 @@ void orc_mac_sensors(int nx, int ny, double tau, const double* rho, const double
                      const double* uy, double* out);
 
 /* Full fused reference run (used for the CPU timing baseline): nsteps of
- * stream, all sensors, flags on sensor_r / sensor_s, sums, collide; work is
+ * stream, the sensors (all of them, or with full = 0 the set of
+ * orc_cell_sensors_set), flags on sensor_r / sensor_s, sums, collide; work is
  * scratch of the size of f and the result ends in f.  rec_field receives the
  * sensor_r field of the last step.  Returns the last step's non-positive count. */
 int64_t orc_run(int nx, int ny, double tau, double* f, double* work, int nsteps,
                 int sensor_r, double thr_r, int sensor_s, double thr_s, int tile,
                 double* rec_field, uint8_t* flags, int32_t* tiles, int64_t counts[3],
-                double sums[3]);
+                double sums[3], int full);
 
 /* Discrete adjoint of the sensor objective
  *   J = sum_x W(x) eps_KL(ft(x)),  ft = stream(f^{N-1}),

@@ -73,6 +73,13 @@ extern "C" int kss_step_f32_noalloc(const float* f_in, float* f_out, int32_t nx,
   if (sensor_out && !std_sensor(record_sensor)) return KSS_ERR_ARG;
   if (((uintptr_t)f_in | (uintptr_t)f_out | (uintptr_t)sensor_out) % 16 != 0) return KSS_ERR_ARG;
   if ((uintptr_t)flags % 4 != 0) return KSS_ERR_ARG;
+  // the pull step reads neighbouring rows of f_in while other CTAs write f_out, so the
+  // two population ranges must not overlap (an in-place step would read new values)
+  {
+    const uintptr_t bytes = uintptr_t(9) * uintptr_t(pitch) * uintptr_t(ny) * sizeof(float);
+    const uintptr_t a = reinterpret_cast<uintptr_t>(f_in), b = reinterpret_cast<uintptr_t>(f_out);
+    if (a < b + bytes && b < a + bytes) return KSS_ERR_ARG;
+  }
 
   const dim3 grid = kss::step_grid<float>(nx, ny, tile);
   const long long nblocks = (long long)grid.x * grid.y;

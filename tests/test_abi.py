@@ -134,7 +134,8 @@ def test_create_rejects_bad_fp16_deviation_config(field, value):
 # before its first CUDA call.  The pointers below are 16-byte aligned stand-ins that the
 # call never dereferences: it returns before any memory access.
 _A = 0x10000
-_NOALLOC_OK = dict(f_in=_A, f_out=_A, nx=64, ny=64, pitch=64, tau=0.8, refine_sensor=5,
+_B = 0x1000000  # beyond f_in's 9 x 64 x 64 floats: a distinct output range
+_NOALLOC_OK = dict(f_in=_A, f_out=_B, nx=64, ny=64, pitch=64, tau=0.8, refine_sensor=5,
                    refine_threshold=1e-3, switch_sensor=6, switch_threshold=1e-4, tile=16,
                    record_sensor=9, sensor_out=_A, flags=_A, tile_counts=_A, sums=_A,
                    counts=_A, stream=None)
@@ -144,8 +145,10 @@ _NOALLOC_OK = dict(f_in=_A, f_out=_A, nx=64, ny=64, pitch=64, tau=0.8, refine_se
     (dict(f_in=None), "arg"), (dict(sums=None), "arg"), (dict(nx=0), "arg"),
     (dict(pitch=48), "arg"), (dict(pitch=32), "arg"), (dict(tau=0.5), "arg"),
     (dict(tile=12), "arg"), (dict(refine_sensor=0), "arg"), (dict(switch_sensor=12), "arg"),
-    (dict(record_sensor=0), "arg"), (dict(f_out=_A + 8), "arg"), (dict(flags=_A + 2), "arg"),
-    (dict(nx=16384, ny=16384, pitch=16384), "capacity"),
+    (dict(record_sensor=0), "arg"), (dict(f_out=_B + 8), "arg"), (dict(flags=_A + 2), "arg"),
+    (dict(f_out=_A), "arg"), (dict(f_out=_A + 9 * 64 * 64 * 4 - 16), "arg"),
+    (dict(f_in=_B + 16), "arg"),
+    (dict(nx=16384, ny=16384, pitch=16384, f_out=_A + 9 * 16384 * 16384 * 4), "capacity"),
 ])
 def test_noalloc_rejects_bad_arguments_before_touching_the_gpu(change, code):
     from paper_2603_13618_gb300 import kss

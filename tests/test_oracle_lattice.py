@@ -183,3 +183,28 @@ def test_sums_brute_force(orc):
     s = orc.sums(f)
     np.testing.assert_allclose(s, [f.sum(), (CX[:, None, None] * f).sum(),
                                    (CY[:, None, None] * f).sum()], rtol=1e-13, atol=1e-13)
+
+
+def test_row_parallel_sweeps_are_bitwise_serial(orc):
+    """The oracle's per-cell sweeps split over threads give the single-thread results bit
+    for bit (no arithmetic depends on the split; reductions stay serial)."""
+    rho, ux, uy = inputs.smooth_jump(96, 70, seed=61, kmax=6)
+    out = []
+    for th in (1, 4):
+        orc.set_threads(th)
+        try:
+            f = orc.init_equilibrium(rho, ux, uy)
+            g = orc.step(f, 0.7, 3)
+            s, n = orc.sensor_fields(g, 0.7, pull=True)
+            m = orc.moments(g)
+            run = orc.run(g, 0.7, 2, orc.SENSOR_ID["kn"], 1e-3,
+                             orc.SENSOR_ID["neq"], 1e-4, 16)
+        finally:
+            orc.set_threads(1)
+        out.append((f, g, s, n, *m, run))
+    for a, b in zip(*out):
+        if isinstance(a, dict):
+            for k in a:
+                np.testing.assert_array_equal(a[k], b[k])
+        else:
+            np.testing.assert_array_equal(a, b)

@@ -290,3 +290,32 @@ def test_class1_kinetic_vs_macroscopic_smooth_2d(orc):
         scale = np.max(np.abs(mac[mac_id]))
         err = np.max(np.abs(sens[kin_id] - mac[mac_id]))
         assert err <= 5e-2 * max(scale, np.max(np.abs(mac[2]))), (kin_id, err, scale)
+
+
+def test_sensor_subset_evaluates_the_same_lines(orc):
+    """The {Kn, KL, neq, qe} evaluation (the production refine/switch set, used by the CPU
+    timing baseline) gives those sensors bit for bit as the full evaluation, NaN for the
+    others, the +Inf convention for non-positive cells, and the same fused run."""
+    rng = np.random.default_rng(5)
+    for k in range(200):
+        ft = orc.equilibrium(rng.uniform(0.5, 2), *rng.uniform(-0.1, 0.1, 2))
+        ft = ft * (1 + 0.2 * rng.uniform(-1, 1, 9))
+        if k % 17 == 0:
+            ft[k % 9] = -abs(ft[k % 9])
+        for two in (False, True):
+            full, np_full = orc.cell_sensors(ft, 0.7, two_relax=two)
+            sub, np_sub = orc.cell_sensors(ft, 0.7, two_relax=two, full=False)
+            assert np_full == np_sub
+            for name in ("kn", "neq", "qe", "kl"):
+                i = orc.SENSOR_ID[name]
+                assert full[i] == sub[i] or (math.isinf(full[i]) and math.isinf(sub[i]))
+            others = [orc.SENSOR_ID[n] for n in orc.SENSOR_NAMES
+                      if n not in ("kn", "neq", "qe", "kl")]
+            assert np.all(np.isnan(sub[others]))
+    rho, ux, uy = inputs.smooth_jump(40, 30, seed=2, kmax=4)
+    f = orc.init_equilibrium(rho, ux, uy)
+    a = orc.run(f, 0.6, 3, orc.SENSOR_ID["kn"], 1e-3, orc.SENSOR_ID["neq"], 1e-4, 16)
+    b = orc.run(f, 0.6, 3, orc.SENSOR_ID["kn"], 1e-3, orc.SENSOR_ID["neq"], 1e-4, 16,
+                full=False)
+    for key in a:
+        np.testing.assert_array_equal(a[key], b[key])

@@ -93,11 +93,22 @@ def test_noalloc_rejects_problems_beyond_its_scratch(torch_cuda):
     i32 = torch.zeros(64, dtype=torch.int32, device="cuda")
     d = torch.zeros(3, dtype=torch.float64, device="cuda")
     c = torch.zeros(3, dtype=torch.int64, device="cuda")
-    rc = lib.kss_step_f32_noalloc(_ptr(buf), _ptr(buf), 16384, 16384, 16384, 0.8, KN, 1e-3,
+    # (the output address is a stand-in past the input's 9 x 16384^2 floats: the call
+    # rejects the size before it touches either buffer)
+    far = buf.data_ptr() + 9 * 16384 * 16384 * 4
+    rc = lib.kss_step_f32_noalloc(_ptr(buf), far, 16384, 16384, 16384, 0.8, KN, 1e-3,
                                   NEQ, 1e-4, 8, KL, _ptr(buf), _ptr(b8), _ptr(i32), _ptr(d),
                                   _ptr(c), None)
     assert rc == -7
+    # an in-place step (f_out = f_in), or overlapping population ranges, is an argument
+    # error: the pull step would read populations that other CTAs already overwrote
+    big = torch.zeros(2 * 9 * 64 * 8, dtype=torch.float32, device="cuda")
+    for dst in (big.data_ptr(), big.data_ptr() + 4 * 9 * 64 * 8 - 16):
+        rc = lib.kss_step_f32_noalloc(_ptr(big), dst, 64, 8, 64, 0.8, KN, 1e-3, NEQ, 1e-4, 8,
+                                      KL, None, _ptr(b8), _ptr(i32), _ptr(d), _ptr(c), None)
+        assert rc == -1
     # a non-{Kn, KL, neq} sensor is an argument error
-    rc = lib.kss_step_f32_noalloc(_ptr(buf), _ptr(buf), 64, 8, 64, 0.8, 0, 1e-3, NEQ, 1e-4, 8,
+    rc = lib.kss_step_f32_noalloc(_ptr(big), big.data_ptr() + 4 * 9 * 64 * 8, 64, 8, 64, 0.8, 0,
+                                  1e-3, NEQ, 1e-4, 8,
                                   KL, _ptr(buf), _ptr(b8), _ptr(i32), _ptr(d), _ptr(c), None)
     assert rc == -1
