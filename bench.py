@@ -67,16 +67,20 @@ WORKLOAD = ("D2Q9 FP32 4096x4096 periodic, tau=0.6, smooth perturbations (amp 1e
             "Mach<=0.1) + density step 2:1 at x=2048; fused stream+collide+sensors "
             "(Kn refine 1e-3, neq switch 1e-4, KL field) + flags + tile counts + sums "
             "every step")
-KERNEL_SOURCES = ("paper_2603_13618_gb300/csrc/d2q9.cuh",
-                  "paper_2603_13618_gb300/csrc/step_kernel.cuh")
+CSRC = os.path.join(ROOT, "paper_2603_13618_gb300", "csrc")
 PROFILE = os.path.join(ROOT, "profiles", "step_std_f32_4096.md")
 
 
 def kernel_hash() -> str:
+    """sha256 (first 16 hex digits) over every file of the CUDA sources (kernels, launch
+    decisions, runtimes), by name in sorted order: any edit there changes it."""
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, p), "rb") as fh:
-            h.update(fh.read())
+    for name in sorted(os.listdir(CSRC)):
+        path = os.path.join(CSRC, name)
+        if os.path.isfile(path):
+            h.update(name.encode() + b"\0")
+            with open(path, "rb") as fh:
+                h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -168,25 +172,45 @@ def workload_fields(nx=NX, ny=NY, x0=0, y0=0, wx=None, wy=None):
     return inputs.smooth_jump(NX, NY, seed=2603, kmax=8, x0=x0, y0=y0, wx=wx, wy=wy)
 
 
-def cpu_baseline(seconds: float = 10.0, window: int = 1024):
-    """The oracle as it stands (single thread) on a window of the workload."""
+def _oracle_rate(f, seconds, threads, max_steps=1 << 30):
+    """Fused oracle steps ({Kn, KL, neq}: Kn refine, neq switch, KL field, flags, tile
+    counts, sums, collide) on the state f for about `seconds`; (MLUPS, steps, s)."""
+    import oracle
+
+    oracle.set_threads(threads)
+    try:
+        steps, t0 = 0, time.perf_counter()
+        while steps < max_steps:
+            oracle.run(f, TAU, 1, oracle.SENSOR_ID["kn"], THR_R, oracle.SENSOR_ID["neq"], THR_S,
+                       TILE, full=False)
+            steps += 1
+            el = time.perf_counter() - t0
+            if el >= seconds:
+                break
+    finally:
+        oracle.set_threads(1)
+    return f.shape[1] * f.shape[2] * steps / el / 1e6, steps, el
+
+
+def cpu_baseline(seconds: float = 8.0, window: int = 1024):
+    """The oracle as it stands on a window of the workload, with the GPU headline's
+    sensor set: on all host cores (the reported value) and on one thread."""
     import oracle
 
     rho, ux, uy = workload_fields(x0=NX // 2 - window // 2, y0=NY // 2 - window // 2,
                                   wx=window, wy=window)
     f = oracle.init_equilibrium(rho, ux, uy)
-    steps, t0 = 0, time.perf_counter()
-    while True:
-        oracle.run(f, TAU, 1, oracle.SENSOR_ID["kn"], THR_R, oracle.SENSOR_ID["neq"], THR_S, TILE)
-        steps += 1
-        el = time.perf_counter() - t0
-        if el >= seconds:
-            break
-    return {"value": window * window * steps / el / 1e6, "unit": "MLUPS", "cores": 1,
-            "kind": "oracle",
-            "sample": f"{steps} fused oracle step(s) (all 13 sensors, flags, tile counts, "
-                      f"sums) on the central {window}x{window} window of the workload, "
-                      f"{el:.1f} s, 1 thread"}
+    cores = oracle.host_cores()
+    threads = cores if oracle.lib().orc_have_openmp() else 1
+    v1, n1, t1 = _oracle_rate(f, seconds, 1)
+    vn, nn, tn = _oracle_rate(f, seconds, threads)
+    return {"value": vn, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+            "sample": f"{nn} fused oracle step(s) ({{Kn, KL, neq}}: Kn refine 1e-3, neq switch "
+                      f"1e-4, KL field, flags, tile counts, sums) on the central "
+                      f"{window}x{window} window of the workload, {tn:.1f} s, {threads} "
+                      f"threads (row sweeps split over the host cores)",
+            "single_thread": {"value": v1, "unit": "MLUPS", "cores": 1,
+                              "sample": f"{n1} step(s) of the same, {t1:.1f} s, 1 thread"}}
 
 
 BATCH_METRIC = "MLUPS with sensors fused, 64 uneven lattices batched, 1xGB300"
@@ -624,22 +648,33 @@ def fp16_error(n, tau, kexp, gen, steps=500, window=256):
 
 
 def run_reference(args):
+    """The oracle on the host cores, one bounded window of the workload per step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import oracle
 
-    window = 128
+    window = 256
     rho, ux, uy = workload_fields(x0=NX // 2 - window // 2, y0=NY // 2 - window // 2,
                                   wx=window, wy=window)
     f = oracle.init_equilibrium(rho, ux, uy)
+    threads = oracle.host_cores() if oracle.lib().orc_have_openmp() else 1
+    oracle.set_threads(threads)
+
+    def one():
+        oracle.run(f, TAU, 1, oracle.SENSOR_ID["kn"], THR_R, oracle.SENSOR_ID["neq"], THR_S,
+                   TILE, full=False)
+
     for _ in range(args.warmup):
-        oracle.run(f, TAU, 1, 5, THR_R, 6, THR_S, TILE)
+        one()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.run(f, TAU, 1, 5, THR_R, 6, THR_S, TILE)
+        one()
     el = time.perf_counter() - t0
+    oracle.set_threads(1)
     value = window * window * args.steps / el / 1e6
+    sample = (f"each step: one fused oracle step ({{Kn, KL, neq}}, flags, tile counts, sums) "
+              f"on the central {window}x{window} window, {threads} threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -647,9 +682,8 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nx": NX, "ny": NY,
                    "sample": f"{window}x{window} central window per step"},
-        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                         "sample": f"each step: one fused oracle step on the central "
-                                   f"{window}x{window} window, 1 thread"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -692,6 +726,52 @@ def max_over_ranks(value, dist, device="cpu"):
 def whole_job_mlups(world, cells, steps, ms):
     """Lattice updates of all ranks per second (weak scaling: each rank a full lattice)."""
     return world * cells * steps / (ms * 1e-3) / 1e6
+
+
+def deferred_fraction(lat):
+    """Share of the last step's cells that the fused pass defers to the exact per-cell
+    recomputation: Kn >= 1/16 or a non-positive population (Kn = +Inf); the fused
+    pass's other condition (|u|^2 >= 0.3) does not occur at Mach 0.1."""
+    import numpy as np
+
+    kn = lat.read_sensor("kn")
+    return float(np.mean(~(kn < 0.0625)))
+
+
+def tau_sweep(lat0, k, warmup, stream, peak, barrier):
+    """The timed call (one kss_step(k), all steps fused output steps) at each tau of the
+    configuration on a fresh lattice, with the deferred share of its last step."""
+    import torch
+
+    from paper_2603_13618_gb300 import kss
+
+    rho, ux, uy = workload_fields()
+    out = {}
+    for tau in (0.51, 0.6, 0.8, 1.0):
+        if tau == TAU:
+            lat = lat0
+            lat.set_fields(rho, ux, uy)
+        else:
+            lat = kss.Lattice(NX, NY, precision="fp32", tau=tau, refine_sensor="kn",
+                              refine_threshold=THR_R, switch_sensor="neq",
+                              switch_threshold=THR_S, record=("kl",), output_every=1,
+                              tile=TILE, stream="torch")
+            lat.set_fields(rho, ux, uy)
+        lat.step(warmup)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(k)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1) / k
+        gbs = BYTES_PER_LUP * NX * NY / (ms * 1e-3) / 1e9
+        out[str(tau)] = {"ms_per_step": ms, "frac": gbs / peak, "steps": k,
+                         "deferred_fraction": deferred_fraction(lat),
+                         "refine_count": int(lat.read_stats()[1][0])}
+        if lat is not lat0:
+            lat.close()
+    return out
 
 
 def run_gpu(args):
@@ -787,6 +867,40 @@ def run_gpu(args):
                "steps": ke, "calls_per_step": ["kss_set_fields(host)", "kss_step(1)",
                                                "kss_read_flags(host)", "kss_read_stats"]}
 
+    # end to end for a caller that keeps the state on the device: K steps, each followed
+    # by reading its flags, tile counts, KL field and sums back to pinned host memory
+    e2e_stepping = None
+    if rank == 0 or world > 1:
+        ks = max(3, min(20, K // 10))
+        klh = torch.empty((NY, NX), dtype=torch.float64).pin_memory()
+        lat.set_fields(*pin)
+        for _ in range(2):
+            lat.step(1)
+            lat.read_flags(out=(fl, tl))
+            lat.read_sensor("kl", out=klh)
+            lat.read_stats()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ks):
+            lat.step(1)
+            lat.read_flags(out=(fl, tl))
+            lat.read_sensor("kl", out=klh)
+            lat.read_stats()
+        barrier()
+        el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+        d2h = cells + 8 * cells + 4 * 2 * lat.nty * lat.ntx + 8 * 3 + 8 * 3 + 8 * 3
+        e2e_stepping = {"value": whole_job_mlups(world, cells, ks, el * 1e3), "unit": "MLUPS",
+                        "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h, "steps": ks,
+                        "calls_per_step": ["kss_step(1)", "kss_read_flags(host)",
+                                           "kss_read_sensor(kl, host)", "kss_read_stats"]}
+
+    # the kernel's work depends on the data: cells it cannot prove exact in the fused pass
+    # (Kn >= 1/16, or a non-positive population) are recomputed in the CTA epilogue; the
+    # same workload at the other relaxation times of the configuration, K' steps each
+    sweep = None
+    if rank == 0 and not args.no_tau_sweep:
+        sweep = tau_sweep(lat, min(K, 100), args.warmup, stream, peak, barrier)
+
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline()
@@ -812,6 +926,8 @@ def run_gpu(args):
             "single_step_launches": single,
             "cpu_baseline": base,
             "e2e": e2e,
+            "e2e_stepping": e2e_stepping,
+            "tau_sweep": sweep,
             "gpu_launches": 1 if multi else K,
             "clocks": clocks,
             "host_s": t_host,
@@ -832,6 +948,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tau-sweep", action="store_true",
+                    help="skip the timed calls at the other relaxation times")
     ap.add_argument("--kernel", default="auto", choices=["auto", "vector", "tma"],
                     help="step kernel (auto: the library's choice)")
     ap.add_argument("--size", type=int, default=None,

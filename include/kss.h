@@ -211,6 +211,33 @@ int kss_read_stats(kss_lattice* lat, double sums[3], int64_t counts[3], int64_t*
 int kss_set_aar_region(kss_lattice* lat, const uint8_t* region, int on_device);
 int kss_get_aar_region(kss_lattice* lat, uint8_t* region, int on_device);
 
+/* ---- Domain decomposition into y-slabs (section "Adaptive refinement and parallel
+ * processing": the lattice is shared out between processes) --------------------------
+ * A lattice of NX x NY cells split into slabs of whole rows, one per process or device;
+ * slab r owns rows [y_r, y_r + ny_r) and is a lattice of nx = NX, ny = ny_r created by
+ * kss_slab_create.  Within a slab the step is the one of kss_step, except at its two
+ * faces: pull streaming reads row -1 for the populations with c_y = +1 (q = 2, 5, 6) and
+ * row ny for those with c_y = -1 (q = 4, 7, 8), which are halo rows the caller fills
+ * before every step instead of wrapping periodically inside the slab.  Per step:
+ *   kss_slab_edges      the rows leaving the slab: to_below = q 4, 7, 8 of row 0 (they
+ *                       stream into the slab below), to_above = q 2, 5, 6 of row ny - 1;
+ *   kss_slab_set_halos  from_below = the slab below's to_above, from_above = the slab
+ *                       above's to_below (for one slab, its own rows: periodic);
+ *   kss_step(lat, 1)    one step (a slab takes one step per call: KSS_ERR_ARG otherwise).
+ * Buffers hold 3 rows of nx elements in the storage type (double, float, or the binary16
+ * codes of KSS_FP16DEV), q in the order given, raw so that the exchange is exact; host
+ * or device memory (on_device), owned by the caller.  kss_slab_edges synchronises for
+ * host buffers.  The slab's sums and counts are those of its own rows; the lattice's are
+ * their sums over the slabs (an all-reduce), its flags and sensor fields the slabs'
+ * rows in order, and its tile counts too when every slab but the last has a multiple of
+ * tile rows.  A slab steps on the vector kernel (no TMA kernel, no multi-step launch);
+ * sensors read on demand after a step use the halo rows that step read, so read them
+ * before the next kss_slab_set_halos. */
+int kss_slab_create(const kss_config* cfg, kss_lattice** out);
+int kss_slab_edges(kss_lattice* lat, void* to_below, void* to_above, int on_device);
+int kss_slab_set_halos(kss_lattice* lat, const void* from_below, const void* from_above,
+                       int on_device);
+
 /* Test support for failure detection (no counterpart in the paper).  Every device-side
  * wait of the library (the multi-step launches' dependency waits, the TMA kernel's
  * barrier waits) gives up after a deadline, sets the lattice's error word and returns,
@@ -220,6 +247,21 @@ int kss_get_aar_region(kss_lattice* lat, uint8_t* region, int on_device);
  * runs out, and the next synchronising call on the lattice returns KSS_ERR_TIMEOUT
  * (sticky, as for a real expiry).  Nothing faults; the GPU context stays usable. */
 int kss_testing_expire_wait(kss_lattice* lat, int64_t deadline_cycles);
+/* The same for the TMA kernel's bounded mbarrier wait: an mbarrier whose phase never
+ * completes (one of two arrivals, no copy ever issued to it), waited on with a deadline of
+ * deadline_cycles (1 .. 1e9); the next synchronising call returns KSS_ERR_TIMEOUT. */
+int kss_testing_expire_mbarrier(kss_lattice* lat, int64_t deadline_cycles);
+
+/* Test support: host-side fault injection (no counterpart in the paper).  kind 0: the n-th
+ * device allocation of the library from now (n >= 0, 0 = the next) fails as if the device
+ * were out of memory, without calling the CUDA allocator; kind 1: the n-th kss_step call
+ * from now fails as if its launch had failed (KSS_ERR_CUDA, sticky on that lattice)
+ * before it launches anything.  One event at a time; it disarms when it fires, and n < 0
+ * disarms it.  kss_testing_live_allocations: device allocations the library holds now
+ * (a failed kss_create or kss_batch_create must release everything it took).
+ * Returns KSS_OK, or KSS_ERR_ARG for another kind. */
+int kss_testing_fail_after(int32_t kind, int64_t n);
+int64_t kss_testing_live_allocations(void);
 
 /* Steps taken since the last set. */
 int kss_get_step(const kss_lattice* lat, int64_t* step);

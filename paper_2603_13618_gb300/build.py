@@ -7,6 +7,7 @@ allocation-free entry point) compile in parallel and link into one shared librar
 from __future__ import annotations
 
 import concurrent.futures as cf
+import hashlib
 import os
 import shutil
 import subprocess
@@ -38,11 +39,27 @@ def cuda_lib_dir() -> str:
     return os.path.join(root, "lib64")
 
 
+def source_hash() -> str:
+    """sha256 (first 16 hex digits) of the CUDA sources and the build flags from the
+    environment: the autotuner's cache entries carry it, so an entry measured on other
+    kernels is not reused."""
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(CSRC)):
+        path = os.path.join(CSRC, name)
+        if os.path.isfile(path):
+            h.update(name.encode() + b"\0")
+            with open(path, "rb") as fh:
+                h.update(fh.read())
+    h.update(os.environ.get("KSS_NVCC_EXTRA", "").encode())
+    return h.hexdigest()[:16]
+
+
 def flags(extra=()) -> list[str]:
     # KSS_NVCC_EXTRA: additional nvcc flags (tuning macros such as -DKSS_STEP_MIN_BLOCKS=3)
     env = os.environ.get("KSS_NVCC_EXTRA", "").split()
     return ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
-                   "-I", os.path.join(ROOT, "include"), *env, *extra]
+                   "-I", os.path.join(ROOT, "include"), f"-DKSS_SOURCE_HASH=\"{source_hash()}\"",
+                   *env, *extra]
 
 
 def build(verbose: bool = False, ptxas_info: bool = False) -> str:

@@ -67,7 +67,7 @@ void free_all(kss_adjoint* A) {
   void* bufs[] = {A->ck,     A->seg,    A->work[0], A->work[1], A->lam[0], A->lam[1],
                   A->wplane, A->fields, A->grad,    A->part,    A->small};
   for (void* b : bufs)
-    if (b) cudaFree(b);
+    if (b) kss_rt::dev_free(b);
   if (A->g_fwd) cudaGraphExecDestroy(A->g_fwd);
   if (A->g_bwd) cudaGraphExecDestroy(A->g_bwd);
   if (A->cap) cudaStreamDestroy(A->cap);
@@ -295,7 +295,7 @@ int kss_adjoint_create(const kss_adjoint_config* cfg, kss_adjoint** out) {
       {reinterpret_cast<void**>(&A->small), 256},
   };
   for (auto& a : allocs) {
-    if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
+    if (kss_rt::dev_malloc(a.p, a.bytes) != cudaSuccess) {
       cudaGetLastError();
       free_all(A);
       return KSS_ERR_OOM;

@@ -197,10 +197,10 @@ int write_items(kss_batch* B) {
   if (host.size() > B->items_cap) {
     drop_graphs(B);  // graphs hold the old list's address
     KSS_BCUDA(B, cudaStreamSynchronize(B->stream));
-    if (B->items) cudaFree(B->items);
+    if (B->items) kss_rt::dev_free(B->items);
     B->items = nullptr;
     B->items_cap = 0;
-    if (cudaMalloc(&B->items, host.size() * sizeof(kss::BatchItem)) != cudaSuccess) {
+    if (kss_rt::dev_malloc(&B->items, host.size() * sizeof(kss::BatchItem)) != cudaSuccess) {
       cudaGetLastError();
       return bfail(B, KSS_ERR_OOM, "work list allocation failed");
     }
@@ -362,14 +362,20 @@ void destroy_batch(kss_batch* B) {
   void* bufs[] = {B->table[0], B->table[1], B->items, B->part_sum, B->part_cnt, B->multi,
                   B->mtab};
   for (void* b : bufs)
-    if (b) cudaFree(b);
+    if (b) kss_rt::dev_free(b);
   if (B->cap) cudaStreamDestroy(B->cap);
   if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
   delete B;
 }
 
 // ---- autotuner cache: "key<TAB>rows<TAB>ctas_per_sm<TAB>ms<TAB>multi_step" lines (a
-// line without the last field is a per-step choice) ----
+// line without the last field is a per-step choice).  The key ends with a hash of the
+// CUDA sources and build flags of this library, so entries measured on other kernels
+// are never reused. ----
+#ifndef KSS_SOURCE_HASH
+#define KSS_SOURCE_HASH "unhashed"
+#endif
+constexpr const char* kSourceHash = KSS_SOURCE_HASH;
 std::string tune_key(const kss_batch* B) {
   cudaDeviceProp prop{};
   std::string name = "unknown";
@@ -381,7 +387,7 @@ std::string tune_key(const kss_batch* B) {
   const int lc = int(std::lround(std::log2(double(std::max(1LL, cells)))));
   const int ln = int(std::lround(std::log2(double(B->n))));
   return name + "|" + std::to_string(B->nsm) + "|" + (B->prec == KSS_FP64 ? "fp64" : (B->prec == KSS_FP32 ? "fp32" : "fp16dev")) + "|" +
-         std::to_string(lc) + "|" + std::to_string(ln);
+         std::to_string(lc) + "|" + std::to_string(ln) + "|" + kSourceHash;
 }
 
 bool cache_lookup(const char* path, const std::string& key, kss_batch_tuning* t) {
@@ -500,7 +506,7 @@ int kss_batch_create(int32_t n, const kss_config* cfgs, kss_batch** out) {
       {reinterpret_cast<void**>(&B->mtab), sizeof(kss::MultiState) * size_t(n)},
   };
   for (auto& a : allocs) {
-    if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
+    if (kss_rt::dev_malloc(a.p, a.bytes) != cudaSuccess) {
       cudaGetLastError();
       destroy_batch(B);
       return KSS_ERR_OOM;
@@ -672,7 +678,7 @@ int kss_batch_autotune(kss_batch* B, const char* cache_path, int32_t steps,
     size_t total = 0;
     for (const kss_lattice* L : B->mem) total += 9 * size_t(L->plane) * L->esz;
     unsigned char* snap = nullptr;
-    if (cudaMalloc(&snap, total) != cudaSuccess) {
+    if (kss_rt::dev_malloc(&snap, total) != cudaSuccess) {
       cudaGetLastError();
       rc = bfail(B, KSS_ERR_OOM, "autotune: state snapshot allocation failed");
     }
@@ -719,7 +725,7 @@ int kss_batch_autotune(kss_batch* B, const char* cache_path, int32_t steps,
         o += bytes;
       }
       cudaStreamSynchronize(B->stream);
-      cudaFree(snap);
+      kss_rt::dev_free(snap);
     }
   }
   cudaEventDestroy(e0);

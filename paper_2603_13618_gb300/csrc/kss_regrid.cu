@@ -282,7 +282,7 @@ struct Workspace {
   void release() {
     void* b[] = {level[0], level[1], acc, kids, result, counts, eff, mask, pc, pr};
     for (void* p : b)
-      if (p) cudaFree(p);
+      if (p) kss_rt::dev_free(p);
     *this = Workspace{};
   }
 };
@@ -292,16 +292,16 @@ cudaError_t ws_alloc(Workspace& ws, int ntx, int nty) {
   ws.cap = ntiles + 1;
   const size_t bb = sizeof(Box) * size_t(ws.cap);
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = cudaMalloc(&ws.level[0], 2 * bb);
-  if (e == cudaSuccess) e = cudaMalloc(&ws.level[1], 2 * bb);
-  if (e == cudaSuccess) e = cudaMalloc(&ws.acc, bb);
-  if (e == cudaSuccess) e = cudaMalloc(&ws.kids, 2 * bb);
-  if (e == cudaSuccess) e = cudaMalloc(&ws.result, bb);
-  if (e == cudaSuccess) e = cudaMalloc(&ws.counts, 2 * sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&ws.eff, sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&ws.mask, size_t(ntiles));
-  if (e == cudaSuccess) e = cudaMalloc(&ws.pc, sizeof(int) * size_t(nty + 1) * ntx);
-  if (e == cudaSuccess) e = cudaMalloc(&ws.pr, sizeof(int) * size_t(nty) * (ntx + 1));
+  if (e == cudaSuccess) e = kss_rt::dev_malloc(&ws.level[0], 2 * bb);
+  if (e == cudaSuccess) e = kss_rt::dev_malloc(&ws.level[1], 2 * bb);
+  if (e == cudaSuccess) e = kss_rt::dev_malloc(&ws.acc, bb);
+  if (e == cudaSuccess) e = kss_rt::dev_malloc(&ws.kids, 2 * bb);
+  if (e == cudaSuccess) e = kss_rt::dev_malloc(&ws.result, bb);
+  if (e == cudaSuccess) e = kss_rt::dev_malloc(&ws.counts, 2 * sizeof(int));
+  if (e == cudaSuccess) e = kss_rt::dev_malloc(&ws.eff, sizeof(double));
+  if (e == cudaSuccess) e = kss_rt::dev_malloc(&ws.mask, size_t(ntiles));
+  if (e == cudaSuccess) e = kss_rt::dev_malloc(&ws.pc, sizeof(int) * size_t(nty + 1) * ntx);
+  if (e == cudaSuccess) e = kss_rt::dev_malloc(&ws.pr, sizeof(int) * size_t(nty) * (ntx + 1));
   if (e != cudaSuccess) {
     cudaGetLastError();
     ws.release();
@@ -478,13 +478,13 @@ int kss_regrid_flags(const uint8_t* flags, int32_t nx, int32_t ny, int32_t tile,
   uint8_t* staged = nullptr;
   const size_t bytes = size_t(nx) * ny;
   if (!on_device) {
-    if (cudaMalloc(&staged, bytes) != cudaSuccess) {
+    if (kss_rt::dev_malloc(&staged, bytes) != cudaSuccess) {
       cudaGetLastError();
       return KSS_ERR_OOM;
     }
     if (cudaMemcpyAsync(staged, flags, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) {
       cudaGetLastError();
-      cudaFree(staged);
+      kss_rt::dev_free(staged);
       return KSS_ERR_CUDA;
     }
     d = staged;
@@ -494,7 +494,7 @@ int kss_regrid_flags(const uint8_t* flags, int32_t nx, int32_t ny, int32_t tile,
                             nboxes, on_device, s, nullptr);
   cudaStreamSynchronize(s);
   R.destroy();
-  if (staged) cudaFree(staged);
+  if (staged) kss_rt::dev_free(staged);
   return rc;
 }
 

@@ -10,7 +10,11 @@
 #include <numeric>
 #include <string>
 
+#include <atomic>
+#include <mutex>
+
 #include "runtime.h"
+#include "step_tma.cuh"
 
 using namespace kss_rt;
 
@@ -51,7 +55,7 @@ int check_config(const kss_config* c) {
 // one at every size measured (plain steps 0.179 vs 0.209 ms, sensor steps 0.25 vs
 // 0.28 ms at 4096^2 FP32); the TMA kernel is used only when asked for.
 bool use_tma(const kss_lattice* L, int mode) {
-  return mode != MODE_FULL && L->cfg.kernel == KSS_KERNEL_TMA;
+  return mode != MODE_FULL && L->cfg.kernel == KSS_KERNEL_TMA && !L->slab;
 }
 
 // CTAs of the fixup pass (2 per SM, grid-striding over the deferred cells).
@@ -121,7 +125,7 @@ int multi_workspace(kss_lattice* L) {
   const size_t bytes = sizeof(uint32_t) * (nb + 2 * R + 1) + 256 +  // done, ticket, fin, work
                        sizeof(double) * R * nb * 3 + sizeof(uint32_t) * R * nb * 4 +  // partials
                        (sizeof(double) + sizeof(unsigned long long)) * R * 3;        // step sums
-  if (cudaMalloc(&L->multi, bytes) != cudaSuccess) {
+  if (kss_rt::dev_malloc(&L->multi, bytes) != cudaSuccess) {
     cudaGetLastError();
     L->multi = nullptr;
     return fail(L, KSS_ERR_OOM, "multi-step workspace");
@@ -176,7 +180,7 @@ size_t eval_out_small(const kss_lattice* L) {
 
 int ensure_eval_out(kss_lattice* L) {
   if (L->eval_out) return KSS_OK;
-  if (cudaMalloc(&L->eval_out, eval_out_small(L) + 256) != cudaSuccess) {
+  if (kss_rt::dev_malloc(&L->eval_out, eval_out_small(L) + 256) != cudaSuccess) {
     cudaGetLastError();
     L->eval_out = nullptr;
     return fail(L, KSS_ERR_OOM, "evaluation scratch allocation failed");
@@ -224,6 +228,19 @@ __global__ void expire_wait_kernel(uint32_t* err, long long deadline) {
   m.err = err;
   m.deadline = deadline;
   kss::wait_at_least(m, &g_never_set, 1u);
+}
+
+// The TMA kernel's bounded mbarrier wait, on a barrier whose phase never completes (two
+// arrivals expected, one made; no copy is ever issued to it): after `deadline` cycles the
+// wait gives up and sets bit 0 of the error word, as the TMA kernel does.
+__global__ void expire_mbarrier_kernel(uint32_t* err, long long deadline) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    kss::mbar_init(&bar, 2);
+    kss::fence_mbarrier_init();
+    kss::mbar_arrive(&bar);
+    if (!kss::mbar_wait_bounded(&bar, 0u, deadline)) atomicOr(err, 1u);
+  }
 }
 
 // Region bytes as the kernels write them: 1 for a switched cell, 0 otherwise.
@@ -310,12 +327,12 @@ int ensure_staging(kss_lattice* L, size_t elems) {
   if (L->staging_elems >= elems) return KSS_OK;
   if (L->staging) {
     KSS_CUDA(L, cudaStreamSynchronize(L->stream));
-    cudaFree(L->staging);
+    kss_rt::dev_free(L->staging);
     L->staging = nullptr;
     L->staging_elems = 0;
   }
   void* p = nullptr;
-  if (cudaMalloc(&p, elems * sizeof(double)) != cudaSuccess) {
+  if (kss_rt::dev_malloc(&p, elems * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return fail(L, KSS_ERR_OOM, "staging allocation failed");
   }
@@ -381,20 +398,65 @@ int device_error(kss_lattice* L) {
   return KSS_OK;
 }
 
+// ---- counted device allocations and host-side fault injection (test support) ----
+namespace inject {
+std::atomic<long long> g_live_allocs{0};
+std::mutex g_inject_mutex;
+long long g_fail_alloc = -1;   // allocations to pass before one fails (-1: disarmed)
+long long g_fail_launch = -1;  // kss_step calls to pass before one fails (-1: disarmed)
+
+// Is the armed event of this counter due now?  (then it disarms)
+bool injection_due(long long& counter) {
+  std::lock_guard<std::mutex> lock(g_inject_mutex);
+  if (counter < 0) return false;
+  if (counter-- == 0) {
+    counter = -1;
+    return true;
+  }
+  return false;
+}
+}  // namespace inject
+using inject::g_fail_alloc;
+using inject::g_fail_launch;
+using inject::g_inject_mutex;
+using inject::g_live_allocs;
+using inject::injection_due;
+
+cudaError_t dev_malloc_raw(void** p, size_t bytes) {
+  if (injection_due(g_fail_alloc)) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) ++g_live_allocs;
+  return e;
+}
+
+cudaError_t dev_free(void* p) {
+  if (!p) return cudaSuccess;
+  const cudaError_t e = cudaFree(p);
+  if (e == cudaSuccess) --g_live_allocs;
+  return e;
+}
+
+cudaError_t injected_launch_error() {
+  return injection_due(g_fail_launch) ? cudaErrorLaunchFailure : cudaSuccess;
+}
+
 void release(kss_lattice* L) {
   if (!L) return;
   cudaStreamSynchronize(L->stream);
   regrid_release(L);
-  if (L->multi) cudaFree(L->multi);
-  if (L->region) cudaFree(L->region);
-  if (L->eval_out) cudaFree(L->eval_out);
+  if (L->multi) kss_rt::dev_free(L->multi);
+  if (L->region) kss_rt::dev_free(L->region);
+  if (L->eval_out) kss_rt::dev_free(L->eval_out);
   for (auto& g : L->plain_graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   if (L->cap) cudaStreamDestroy(L->cap);
-  void* bufs[] = {L->f[0], L->f[1], L->rec, L->evalplane, L->flags, L->tiles, L->part_sum,
+  void* bufs[] = {L->f_alloc[0], L->f_alloc[1], L->rec, L->evalplane, L->flags, L->tiles, L->part_sum,
                   L->part_cnt, L->small, L->staging, L->defer_list};
   for (void* b : bufs)
-    if (b) cudaFree(b);
+    if (b) kss_rt::dev_free(b);
   if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
   delete L;
 }
@@ -445,7 +507,7 @@ int kss_config_default(kss_config* c, int32_t nx, int32_t ny, int32_t precision)
   return KSS_OK;
 }
 
-int kss_create(const kss_config* cfg, kss_lattice** out) {
+static int create_lattice(const kss_config* cfg, bool slab, kss_lattice** out) {
   if (!out) return KSS_ERR_ARG;
   *out = nullptr;
   const int rc = check_config(cfg);
@@ -453,6 +515,7 @@ int kss_create(const kss_config* cfg, kss_lattice** out) {
   kss_lattice* L = new (std::nothrow) kss_lattice();
   if (!L) return KSS_ERR_OOM;
   L->cfg = *cfg;
+  L->slab = slab;
   if (cudaGetDevice(&L->device) != cudaSuccess) {
     cudaGetLastError();
     delete L;
@@ -474,7 +537,8 @@ int kss_create(const kss_config* cfg, kss_lattice** out) {
   }
   const int align = int(128 / L->esz);
   L->pitch = (cfg->nx + align - 1) / align * align;
-  L->plane = (long long)L->pitch * cfg->ny;
+  // a slab's planes hold its two halo rows too (row -1 before its rows, row ny after)
+  L->plane = (long long)L->pitch * (cfg->ny + (slab ? 2 : 0));
   L->ntx = (cfg->nx + cfg->tile - 1) / cfg->tile;
   L->nty = (cfg->ny + cfg->tile - 1) / cfg->tile;
   if (cudaDeviceGetAttribute(&L->nsm, cudaDevAttrMultiProcessorCount, L->device) != cudaSuccess ||
@@ -530,8 +594,8 @@ int kss_create(const kss_config* cfg, kss_lattice** out) {
     void** p;
     size_t bytes;
   } allocs[] = {
-      {&L->f[0], pop_bytes},
-      {&L->f[1], pop_bytes},
+      {&L->f_alloc[0], pop_bytes},
+      {&L->f_alloc[1], pop_bytes},
       {&L->rec, plane_bytes * (nrec > 0 ? nrec : 1)},
       {&L->evalplane, plane_bytes},
       {reinterpret_cast<void**>(&L->flags), size_t(L->pitch) * cfg->ny},
@@ -542,7 +606,7 @@ int kss_create(const kss_config* cfg, kss_lattice** out) {
       {reinterpret_cast<void**>(&L->defer_list), sizeof(uint32_t) * size_t(L->defer_cap)},
   };
   for (auto& a : allocs) {
-    if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
+    if (kss_rt::dev_malloc(a.p, a.bytes) != cudaSuccess) {
       cudaGetLastError();
       release(L);
       return KSS_ERR_OOM;
@@ -555,7 +619,7 @@ int kss_create(const kss_config* cfg, kss_lattice** out) {
   }
   if (cfg->tau2 > 0.0) {
     const size_t bytes = size_t(L->pitch) * cfg->ny;
-    if (cudaMalloc(&L->region, bytes) != cudaSuccess) {
+    if (kss_rt::dev_malloc(&L->region, bytes) != cudaSuccess) {
       cudaGetLastError();
       L->region = nullptr;
       release(L);
@@ -567,6 +631,8 @@ int kss_create(const kss_config* cfg, kss_lattice** out) {
       return KSS_ERR_CUDA;
     }
   }
+  for (int b = 0; b < 2; ++b)  // row 0 of plane 0 (a slab's halo row -1 precedes it)
+    L->f[b] = static_cast<unsigned char*>(L->f_alloc[b]) + (slab ? size_t(L->pitch) * L->esz : 0);
   L->done = reinterpret_cast<uint32_t*>(L->small);
   L->stat_sums = reinterpret_cast<double*>(L->small + 64);
   L->stat_counts = reinterpret_cast<unsigned long long*>(L->small + 128);
@@ -578,6 +644,14 @@ int kss_create(const kss_config* cfg, kss_lattice** out) {
   }
   *out = L;
   return KSS_OK;
+}
+
+int kss_create(const kss_config* cfg, kss_lattice** out) {
+  return create_lattice(cfg, false, out);
+}
+
+int kss_slab_create(const kss_config* cfg, kss_lattice** out) {
+  return create_lattice(cfg, true, out);
 }
 
 void kss_destroy(kss_lattice* L) {
@@ -679,6 +753,10 @@ int kss_step(kss_lattice* L, int32_t nsteps) {
   int rc = enter(L);
   if (rc) return rc;
   if (nsteps < 0) return fail(L, KSS_ERR_ARG, "negative step count");
+  if (L->slab && nsteps > 1)
+    return fail(L, KSS_ERR_ARG, "a slab steps once per call: its halo rows change every step");
+  if (injected_launch_error() != cudaSuccess)
+    return fail(L, KSS_ERR_CUDA, "injected launch failure (kss_testing_fail_after)");
   DeviceGuard g(L->device);
   // several output steps of the {Kn, KL, neq} set on FP32 or FP64 storage: one multi-step
   // launch (measured on GB300 at 4096^2 FP32: 0.232 vs 0.244 ms per step; plain steps and
@@ -863,6 +941,76 @@ int kss_testing_expire_wait(kss_lattice* L, int64_t deadline_cycles) {
   KSS_CUDA(L, cudaGetLastError());
   return KSS_OK;
 }
+
+// ---- y-slab decomposition: the rows that cross a slab's faces ----
+// Pull streaming moves population q from row j - cy_q to row j: a slab's row 0 takes the
+// c_y = +1 populations (q = 2, 5, 6) of the row below it, its row ny - 1 the c_y = -1
+// populations (q = 4, 7, 8) of the row above it.  Each is a row of nx elements of one
+// plane, contiguous in memory; a buffer of the exchange holds three such rows.
+static const int kUpQ[3] = {2, 5, 6};    // cross the face above a slab, upwards
+static const int kDownQ[3] = {4, 7, 8};  // cross the face below a slab, downwards
+
+static int slab_rows(kss_lattice* L, const int* qs, int row, void* buf, bool to_buf) {
+  const size_t row_bytes = size_t(L->cfg.nx) * L->esz;
+  unsigned char* base = static_cast<unsigned char*>(L->f[L->cur]);
+  for (int k = 0; k < 3; ++k) {
+    unsigned char* r =
+        base + (size_t(qs[k]) * size_t(L->plane) + (long long)row * L->pitch) * L->esz;
+    unsigned char* b = static_cast<unsigned char*>(buf) + size_t(k) * row_bytes;
+    KSS_CUDA(L, cudaMemcpyAsync(to_buf ? b : r, to_buf ? r : b, row_bytes, cudaMemcpyDefault,
+                                L->stream));
+  }
+  return KSS_OK;
+}
+
+int kss_slab_edges(kss_lattice* L, void* to_below, void* to_above, int on_device) {
+  int rc = enter(L);
+  if (rc) return rc;
+  if (!L->slab) return fail(L, KSS_ERR_ARG, "not a slab lattice (kss_slab_create)");
+  if (!to_below || !to_above) return fail(L, KSS_ERR_ARG, "null buffer");
+  DeviceGuard g(L->device);
+  rc = slab_rows(L, kDownQ, 0, to_below, true);
+  if (rc) return rc;
+  rc = slab_rows(L, kUpQ, L->cfg.ny - 1, to_above, true);
+  if (rc) return rc;
+  if (!on_device) KSS_CUDA(L, cudaStreamSynchronize(L->stream));
+  return KSS_OK;
+}
+
+int kss_slab_set_halos(kss_lattice* L, const void* from_below, const void* from_above,
+                       int on_device) {
+  int rc = enter(L);
+  if (rc) return rc;
+  if (!L->slab) return fail(L, KSS_ERR_ARG, "not a slab lattice (kss_slab_create)");
+  if (!from_below || !from_above) return fail(L, KSS_ERR_ARG, "null buffer");
+  DeviceGuard g(L->device);
+  rc = slab_rows(L, kUpQ, -1, const_cast<void*>(from_below), false);
+  if (rc) return rc;
+  rc = slab_rows(L, kDownQ, L->cfg.ny, const_cast<void*>(from_above), false);
+  if (rc) return rc;
+  if (!on_device) KSS_CUDA(L, cudaStreamSynchronize(L->stream));
+  return KSS_OK;
+}
+
+int kss_testing_expire_mbarrier(kss_lattice* L, int64_t deadline_cycles) {
+  int rc = enter(L);
+  if (rc) return rc;
+  if (deadline_cycles < 1 || deadline_cycles > 1000000000LL)
+    return fail(L, KSS_ERR_ARG, "deadline must be 1 .. 1e9 cycles");
+  DeviceGuard g(L->device);
+  expire_mbarrier_kernel<<<1, 32, 0, L->stream>>>(L->err_word, (long long)deadline_cycles);
+  KSS_CUDA(L, cudaGetLastError());
+  return KSS_OK;
+}
+
+int kss_testing_fail_after(int32_t kind, int64_t n) {
+  if (kind != 0 && kind != 1) return KSS_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_inject_mutex);
+  (kind == 0 ? g_fail_alloc : g_fail_launch) = n < 0 ? -1 : (long long)n;
+  return KSS_OK;
+}
+
+int64_t kss_testing_live_allocations(void) { return g_live_allocs.load(); }
 
 int kss_get_step(const kss_lattice* L, int64_t* step) {
   if (!L || !step) return KSS_ERR_ARG;

@@ -42,6 +42,10 @@ struct kss_lattice {
   int rows_plain = 0;       // CTA height of steps without outputs (any multiple of 8)
   int nsm = 0;              // SMs of the device (persistent grid of the TMA kernel)
   void* f[2] = {nullptr, nullptr};
+  void* f_alloc[2] = {nullptr, nullptr};  // the allocations behind f (a slab's start one
+                                          // halo row before f)
+  bool slab = false;        // a y-slab of a decomposed lattice (kss_slab_create): halo rows
+                            // -1 and ny next to its own rows, no periodic wrap in y
   int cur = 0;              // f[cur] holds the stored state
   void* rec = nullptr;      // recorded sensor planes
   int rec_slot[KSS_S_COUNT];
@@ -157,6 +161,7 @@ kss::StepParams<S> make_params(const kss_lattice* L, const void* src, void* dst)
   p.stat_sums = L->stat_sums;
   p.stat_counts = L->stat_counts;
   p.err = L->err_word;
+  p.slab = L->slab ? 1 : 0;
   p.plane = L->plane;
   p.pitch = L->pitch;
   p.nx = L->cfg.nx;
@@ -196,6 +201,18 @@ inline auto with_storage(int precision, F&& f) {
   if (precision == KSS_FP16DEV) return f(Tag<__half>{});
   return f(Tag<float>{});
 }
+
+// Device allocations of the library's host runtimes go through these two calls: they
+// count the live allocations and, for tests, can be made to fail (kss_testing_fail_after:
+// the n-th allocation or launch from now reports an error without touching the GPU).
+cudaError_t dev_malloc_raw(void** p, size_t bytes);
+template <class T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc_raw(reinterpret_cast<void**>(p), bytes);
+}
+cudaError_t dev_free(void* p);
+// Launch injection point: cudaErrorLaunchFailure when an armed launch failure is due.
+cudaError_t injected_launch_error();
 
 // Sticky error of a lattice, if any (KSS_ERR_ARG for NULL).
 inline int enter(kss_lattice* L) {

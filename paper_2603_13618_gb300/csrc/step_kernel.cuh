@@ -41,19 +41,41 @@
 
 namespace kss {
 
-// Minimum resident CTAs per SM requested from the register allocator for the plain
-// and {Kn, KL, neq} steps (a build-time tuning knob, -DKSS_STEP_MIN_BLOCKS=n).  Three
-// 256-thread CTAs (80 registers) hide the load latency far better than two (~128
-// registers) at the price of a few spilled registers.
+// Minimum resident CTAs per SM requested from the register allocator (build-time tuning
+// knobs, -DKSS_..._MIN_BLOCKS=n):
+//   KSS_F32_MIN_BLOCKS   FP32 plain and {Kn, KL, neq} steps (one-step, multi-step and
+//                        batched kernels): two 256-thread CTAs at up to 128 registers.  With
+//                        the paired row and warp-uniform row arithmetic, 4096^2 multi-step
+//                        launches take 0.2029 ms per step against 0.2241 ms at three CTAs
+//                        (80 registers, spilling), one-step launches 0.838 against 0.725 of
+//                        the measured bandwidth.
+//   KSS_STEP_MIN_BLOCKS  FP64 and FP16-deviation plain steps, FP64 {Kn, KL, neq} steps: three
+//                        CTAs (80 registers).
+//   KSS_F16_MIN_BLOCKS   FP16-deviation {Kn, KL, neq} steps: three (0.659 ms per 8192^2 step
+//                        against 0.706 ms at two: its 8-byte rows need more warps in flight).
+//   KSS_FULL_MIN_BLOCKS  the all-sensor steps (much more per-cell state): two CTAs (at most
+//                        128 registers) against one (158 registers).
+#ifndef KSS_F32_MIN_BLOCKS
+#define KSS_F32_MIN_BLOCKS 2
+#endif
 #ifndef KSS_STEP_MIN_BLOCKS
 #define KSS_STEP_MIN_BLOCKS 3
 #endif
-
-// The same for the all-sensor steps (much more per-cell state): two CTAs per SM (at most
-// 128 registers) against one (158 registers): KSS_FULL_MIN_BLOCKS.
 #ifndef KSS_FULL_MIN_BLOCKS
 #define KSS_FULL_MIN_BLOCKS 2
 #endif
+#ifndef KSS_F16_MIN_BLOCKS
+#define KSS_F16_MIN_BLOCKS KSS_STEP_MIN_BLOCKS
+#endif
+
+// The knob of a step kernel with storage S and sensor set MODE.
+template <class S, int MODE>
+__host__ __device__ constexpr int step_min_blocks() {
+  return MODE == MODE_FULL ? KSS_FULL_MIN_BLOCKS
+         : std::is_same<S, float>::value ? KSS_F32_MIN_BLOCKS
+         : (std::is_same<S, __half>::value && MODE == MODE_STD) ? KSS_F16_MIN_BLOCKS
+                                                                : KSS_STEP_MIN_BLOCKS;
+}
 
 constexpr int kWarps = 8;
 constexpr int kThreads = 32 * kWarps;
@@ -187,6 +209,9 @@ struct StepParams {
   int grid_x, nblocks;   // step grid of the lattice: CTAs per block row, CTAs in all
                          // (read by the batched step only; step_kernel uses its grid)
   int mode;              // the lattice's sensor set on output steps (batched step only)
+  T zero;                // 0, read at run time (see product2): every builder value-initialises
+  int slab;              // 0: periodic in y; 1: a y-slab of a decomposed lattice, whose rows
+                         // -1 and ny are halo rows held next to its own (kss_slab_create)
   int rec_slot[S_COUNT];  // plane index of each recorded sensor, -1 if not recorded
   codec_t<S> codec;      // FP16 deviation codec (empty for float / double storage)
   uint8_t* region;       // two-relaxation region [ny][pitch], a byte per cell (AAR steps):
@@ -194,6 +219,16 @@ struct StepParams {
                          // (0 / 1) on output steps
   Trt<T> trt;            // two-relaxation coefficients, and the model of eps_qe
 };
+
+// Offsets (elements) of rows j - 1 and j + 1 from row j: periodic in y, or, in a slab
+// (p.slab), the halo rows -1 and ny that sit next to the slab's own rows.
+template <class S>
+__device__ __forceinline__ void row_neighbours(const StepParams<S>& p, int j, long long& up,
+                                               long long& dn) {
+  const bool lo = (j == 0) & (p.slab == 0), hi = (j + 1 == p.ny) & (p.slab == 0);
+  up = (long long)((lo ? p.ny : j) - 1 - j) * p.pitch;
+  dn = (long long)((hi ? 0 : j + 1) - j) * p.pitch;
+}
 
 // ---------------------------------------------------------------- loads ----
 // Population loads: through the read-only data path (CG = false; the source buffer is
@@ -608,7 +643,7 @@ __device__ __forceinline__ void reload_cell(const StepParams<S>& p, int i, int j
       si = i - cx[q];
       sj = j - cy[q];
       si = si < 0 ? si + p.nx : (si >= p.nx ? si - p.nx : si);
-      sj = sj < 0 ? sj + p.ny : (sj >= p.ny ? sj - p.ny : sj);
+      if (!p.slab) sj = sj < 0 ? sj + p.ny : (sj >= p.ny ? sj - p.ny : sj);
     }
     c[q] = decode<S>(ld_pop<CG>(p.src + q * p.plane + (long long)sj * p.pitch + si), q, p.codec);
   }
@@ -768,6 +803,249 @@ __device__ __forceinline__ uint32_t fix_cell(const StepParams<S>& p, const Pick3
   return uint32_t(rr) | (uint32_t(ss) << 1) | (uint32_t(np) << 2);
 }
 
+// ---------------------------------------------------------------- one row, paired ----
+// The plain and {Kn, KL, neq} rows of FP32 arithmetic (FP32 storage and FP16 deviations)
+// with every operation that is the same for two cells issued as one paired instruction
+// (f32x2.cuh): moments, velocities, the equilibrium, the relaxation, the Kullback-Leibler
+// series and the codec.  Each operation and its rounding are exactly those of the scalar
+// row (fused_row below and cell_update), so the populations, sensors, flags and sums are
+// the same bit for bit; only the instruction count differs.  A lane's V = 4 cells are the
+// pairs (0, 1) and (2, 3).  Build knob: -DKSS_ROW_PAIRED=0 takes the scalar row.
+#ifndef KSS_ROW_PAIRED
+#define KSS_ROW_PAIRED 1
+#endif
+
+__device__ __forceinline__ F2 splat2(float c) { return pack2(c, c); }
+
+// |a| of both halves (the sign bits cleared).
+__device__ __forceinline__ F2 abs2(F2 a) {
+  F2 r;
+  r.v = a.v & 0x7fffffff7fffffffull;
+  return r;
+}
+
+// Reciprocal of both halves (the hardware approximation of Num<float>::rcp).
+__device__ __forceinline__ F2 rcp2(F2 a) {
+  float x, y;
+  unpack2(a, x, y);
+  return pack2(Num<float>::rcp(x), Num<float>::rcp(y));
+}
+
+// Codec constants of one weight class (all populations of equal weight share b_q and s_q):
+// decode f = b + h / s as one FMA per value, encode (f - b) s as f s - s b (s a power of
+// two, so that is (f - b) s with the same single rounding).
+template <class S>
+struct PairCodec {
+  __device__ PairCodec(const codec_t<S>&, int) {}
+};
+template <>
+struct PairCodec<__half> {
+  F2 inv, base, scale, nsb;
+  __device__ PairCodec(const codec_t<__half>& c, int q)
+      : inv(splat2(c.inv[q])), base(splat2(c.base[q])), scale(splat2(c.scale[q])),
+        nsb(splat2(-(c.scale[q] * c.base[q]))) {}
+};
+
+// Store the four cells of one population (two pairs), encoded for FP16 deviations.
+template <class S>
+__device__ __forceinline__ void pop_store2(S* p, const F2 (&f)[2], const PairCodec<S>& pc) {
+  if constexpr (std::is_same<S, __half>::value) {
+    uint2 raw;
+    float a, b;
+    unpack2(fma2(f[0], pc.scale, pc.nsb), a, b);
+    const __half2 h0 = __floats2half2_rn(a, b);
+    unpack2(fma2(f[1], pc.scale, pc.nsb), a, b);
+    const __half2 h1 = __floats2half2_rn(a, b);
+    raw.x = *reinterpret_cast<const unsigned int*>(&h0);
+    raw.y = *reinterpret_cast<const unsigned int*>(&h1);
+    __stcs(reinterpret_cast<uint2*>(p), raw);
+  } else {
+    float a, b, c, d;
+    unpack2(f[0], a, b);
+    unpack2(f[1], c, d);
+    __stcs(reinterpret_cast<float4*>(p), make_float4(a, b, c, d));
+  }
+}
+
+// a b rounded once, for a product whose only use is a subtraction.  The device compiler
+// contracts a paired multiply into a following paired subtract (one rounding instead of
+// two) even with explicit round-to-nearest modifiers; an FMA whose addend is a zero it
+// cannot see (a kernel parameter) is the same rounded product and cannot be contracted.
+// This keeps f^eq rounded exactly as the scalar arithmetic rounds it (Num<T>::mul).
+__device__ __forceinline__ F2 product2(F2 a, F2 b, F2 zero) { return fma2(a, b, zero); }
+
+// Per-cell accumulators of the paired row: Kn and neq per pair, KL per pair.
+struct PairAcc {
+  F2 kn[2], neq[2], kl[2];
+};
+
+// Relax one population (two pairs) toward its equilibrium feq and accumulate the sensor
+// terms, as relax_pop does per pair.
+template <bool OUT>
+__device__ __forceinline__ void relax2(F2 (&f)[2], const F2 (&feq)[2], F2 nom, PairAcc& a) {
+  constexpr int N = Num<float>::kPhiFastOrder;
+  static_assert(N == 5, "series order of the paired row");
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const F2 fneq = sub2(f[m], feq[m]);
+    if (OUT) {
+      const F2 x = mul2(fneq, rcp2(feq[m]));
+      // |x| and |f^neq| accumulate per cell (a scalar add with the absolute value as an
+      // operand modifier is one instruction; the paired add would need the sign bits
+      // cleared first)
+      float x0, x1, n0, n1, k0, k1, e0, e1;
+      unpack2(x, x0, x1);
+      unpack2(fneq, n0, n1);
+      unpack2(a.kn[m], k0, k1);
+      unpack2(a.neq[m], e0, e1);
+      a.kn[m] = pack2(k0 + fabsf(x0), k1 + fabsf(x1));
+      a.neq[m] = pack2(e0 + fabsf(n0), e1 + fabsf(n1));
+      F2 acc = splat2(float(PhiCoef<5>::value));
+      acc = fma2(acc, x, splat2(float(PhiCoef<4>::value)));
+      acc = fma2(acc, x, splat2(float(PhiCoef<3>::value)));
+      acc = fma2(acc, x, splat2(float(PhiCoef<2>::value)));
+      a.kl[m] = fma2(mul2(fneq, x), acc, a.kl[m]);
+    }
+    f[m] = fma2(nom, fneq, f[m]);
+  }
+}
+
+// The opposite pair (QP, QM) with c.u = cu: f^eq = w rho (base + 9/2 cu^2 +- 3 cu),
+// relaxed and (STORE) written.
+template <class S, bool OUT, bool STORE>
+__device__ __forceinline__ void pair2(F2 (&fp)[2], F2 (&fm)[2], const F2 (&cu)[2],
+                                      const F2 (&base)[2], const F2 (&rw)[2], F2 nom, F2 zero,
+                                      PairAcc& a, S* dst_p, S* dst_m, const PairCodec<S>& pc,
+                                      bool cv) {
+  F2 ep[2], em[2];
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const F2 t = fma2(mul2(splat2(4.5f), cu[m]), cu[m], base[m]);
+    ep[m] = product2(rw[m], fma2(splat2(3.f), cu[m], t), zero);
+    em[m] = product2(rw[m], fma2(splat2(-3.f), cu[m], t), zero);
+  }
+  relax2<OUT>(fp, ep, nom, a);
+  if (STORE && cv) pop_store2<S>(dst_p, fp, pc);
+  relax2<OUT>(fm, em, nom, a);
+  if (STORE && cv) pop_store2<S>(dst_m, fm, pc);
+}
+
+template <class S, int MODE, bool STORE>
+__device__ __forceinline__ uint32_t fused_row_paired(const StepParams<S>& p,
+                                                     F2 (&f)[9][2], int i0, int j, bool cv,
+                                                     Acc<float>& a_rho, Acc<float>& a_jx,
+                                                     Acc<float>& a_jy) {
+  constexpr bool OUT = MODE != MODE_PLAIN;
+  // row parts are the same for the whole warp (one row per warp): the lane's column is
+  // added last, so that they stay warp-uniform
+  const long long row = (long long)j * p.pitch;
+  // cells past the row end hold padding or stale data: zeroed (they add nothing to the
+  // sums, and their NaN sensors raise no flag)
+  const int nvalid = cv ? min(4, p.nx - i0) : 0;
+  if (nvalid < 4) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      float c0, c1, c2, c3;
+      unpack2(f[q][0], c0, c1);
+      unpack2(f[q][1], c2, c3);
+      f[q][0] = pack2(nvalid > 0 ? c0 : 0.f, nvalid > 1 ? c1 : 0.f);
+      f[q][1] = pack2(nvalid > 2 ? c2 : 0.f, 0.f);
+    }
+  }
+  F2 rw1[2], ux[2], uy[2], base[2];
+  float rs[4], xs[4], ys[4];
+  PairAcc a;
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const F2 rho = add2(add2(add2(add2(f[0][m], f[1][m]), add2(f[2][m], f[3][m])),
+                             add2(add2(f[4][m], f[5][m]), add2(f[6][m], f[7][m]))),
+                        f[8][m]);
+    const F2 jx = sub2(add2(add2(f[1][m], f[5][m]), f[8][m]),
+                       add2(add2(f[3][m], f[6][m]), f[7][m]));
+    const F2 jy = sub2(add2(add2(f[2][m], f[5][m]), f[6][m]),
+                       add2(add2(f[4][m], f[7][m]), f[8][m]));
+    const F2 ir = rcp2(rho);
+    ux[m] = mul2(jx, ir);
+    uy[m] = mul2(jy, ir);
+    base[m] = fma2(splat2(-1.5f), fma2(ux[m], ux[m], mul2(uy[m], uy[m])), splat2(1.f));
+    rw1[m] = mul2(rho, splat2(float(1.0 / 9.0)));
+    unpack2(rho, rs[2 * m], rs[2 * m + 1]);
+    unpack2(jx, xs[2 * m], xs[2 * m + 1]);
+    unpack2(jy, ys[2 * m], ys[2 * m + 1]);
+    a.kn[m] = a.neq[m] = a.kl[m] = splat2(0.f);
+  }
+  if (OUT) {  // the row's moments, cell by cell in order (as the scalar row adds them)
+    a_rho.add(((rs[0] + rs[1]) + rs[2]) + rs[3]);
+    a_jx.add(((xs[0] + xs[1]) + xs[2]) + xs[3]);
+    a_jy.add(((ys[0] + ys[1]) + ys[2]) + ys[3]);
+  }
+  const F2 nom = splat2(-p.omega), zero = splat2(p.zero);
+  const PairCodec<S> c0(p.codec, 0), c1(p.codec, 1), c5(p.codec, 5);
+  S* const dst = p.dst + row;
+  {
+    F2 feq[2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) feq[m] = product2(mul2(splat2(4.f), rw1[m]), base[m], zero);
+    relax2<OUT>(f[0], feq, nom, a);
+    if (STORE && cv) pop_store2<S>(dst + i0, f[0], c0);
+  }
+  pair2<S, OUT, STORE>(f[1], f[3], ux, base, rw1, nom, zero, a, dst + 1 * p.plane + i0,
+                       dst + 3 * p.plane + i0, c1, cv);
+  pair2<S, OUT, STORE>(f[2], f[4], uy, base, rw1, nom, zero, a, dst + 2 * p.plane + i0,
+                       dst + 4 * p.plane + i0, c1, cv);
+  {
+    F2 sd[2], rw2[2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      sd[m] = add2(ux[m], uy[m]);
+      rw2[m] = mul2(splat2(0.25f), rw1[m]);
+    }
+    pair2<S, OUT, STORE>(f[5], f[7], sd, base, rw2, nom, zero, a, dst + 5 * p.plane + i0,
+                         dst + 7 * p.plane + i0, c5, cv);
+#pragma unroll
+    for (int m = 0; m < 2; ++m) sd[m] = sub2(uy[m], ux[m]);
+    pair2<S, OUT, STORE>(f[6], f[8], sd, base, rw2, nom, zero, a, dst + 6 * p.plane + i0,
+                         dst + 8 * p.plane + i0, c5, cv);
+  }
+  uint32_t fbits = 0;
+  if (OUT) {
+    const Pick3 pr(p.refine_s), ps(p.switch_s);
+    float kn[4], neq[4], kl[4], rw[4], bs[4];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      unpack2(a.kn[m], kn[2 * m], kn[2 * m + 1]);
+      unpack2(a.neq[m], neq[2 * m], neq[2 * m + 1]);
+      unpack2(abs2(a.kl[m]), kl[2 * m], kl[2 * m + 1]);
+      unpack2(rw1[m], rw[2 * m], rw[2 * m + 1]);
+      unpack2(base[m], bs[2 * m], bs[2 * m + 1]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      // rho > 0 and |u|^2 < 0.3 make every f^eq_q >= 0.05 w_q rho > 0, and Kn < 1/16
+      // bounds every |x_q| (see fused_row): otherwise the cell is deferred
+      const bool fast = (rw[k] > 0.f) & (bs[k] > 0.55f) & (kn[k] < 0.0625f);
+      const bool r = pr(kn[k], kl[k], neq[k]) > p.thr_r;
+      const bool sw = p.switch_on && (ps(kn[k], kl[k], neq[k]) > p.thr_s);
+      const uint32_t b = fast ? (uint32_t(r) | (uint32_t(sw) << 1)) : kFlagDeferred;
+      fbits |= b << (8 * k);
+    }
+    if (nvalid < 4) fbits &= nvalid > 0 ? 0xffffffffu >> (32 - 8 * nvalid) : 0u;
+    if (cv) {
+      store_flags<4>(p.flags + row + i0, fbits);
+      if (p.rec_slot[S_KN] >= 0)
+        __stcs(reinterpret_cast<float4*>(p.rec + p.rec_slot[S_KN] * p.plane + row + i0),
+               make_float4(kn[0], kn[1], kn[2], kn[3]));
+      if (p.rec_slot[S_KL] >= 0)
+        __stcs(reinterpret_cast<float4*>(p.rec + p.rec_slot[S_KL] * p.plane + row + i0),
+               make_float4(kl[0], kl[1], kl[2], kl[3]));
+      if (p.rec_slot[S_NEQ] >= 0)
+        __stcs(reinterpret_cast<float4*>(p.rec + p.rec_slot[S_NEQ] * p.plane + row + i0),
+               make_float4(neq[0], neq[1], neq[2], neq[3]));
+    }
+  }
+  return fbits;
+}
+
 // ---------------------------------------------------------------- one row ----
 // Everything after the loads for one row of V-cell vectors: moments, equilibrium,
 // sensors of the compiled set, flags, BGK collision, and the stores of the new
@@ -829,6 +1107,15 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
       store_flags<V>(p.flags + off, fbits);
       if (AAR && STORE && p.region) store_flags<V>(p.region + off, (fbits >> 1) & 0x01010101u);
     }
+  } else if constexpr (KSS_ROW_PAIRED && std::is_same<T, float>::value && !AAR && V == 4) {
+    // ---- the same row in paired instructions (fused_row_paired) ----
+    F2 f[9][2];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      f[q][0] = pack2(ft[q][0], ft[q][1]);
+      f[q][1] = pack2(ft[q][2], ft[q][3]);
+    }
+    fbits = fused_row_paired<S, MODE, STORE>(p, f, i0, j, cv, a_rho, a_jx, a_jy);
   } else {
     // ---- plain stream + collide, or with the {Kn, KL, neq} sensor set:
     //      population-major so each population's vector is stored as soon as it
@@ -938,6 +1225,76 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
   return fbits;
 }
 
+// One row of FP16 deviation codes, pulled and decoded into pairs: the nine 8-byte code
+// vectors of the lane's 4 cells (rows j - cy_q), shifted along x as binary16 words (a cx =
+// +1 population takes the code left of each cell: the left lane's last code by one
+// shuffle of a 32-bit word, or lane 0's halo code; cx = -1 the mirror image, with the
+// periodic seam and a row end inside the vector taking the halo code), then decoded
+// f = b_q + h / s_q two codes per paired FMA.  The values are those of pop_vload and
+// assemble_from_left / _right (the same codes, decoded by the same FMA).
+__device__ __forceinline__ uint32_t half_bits(__half h) { return __half_as_ushort(h); }
+
+template <bool CG>
+__device__ __forceinline__ void load_half_row(const StepParams<__half>& p, int j, int i0,
+                                              int lane, bool cv, F2 (&f)[9][2]) {
+  const __half* base = p.src + (long long)j * p.pitch;
+  long long up, dn;  // rows j - 1 and j + 1
+  row_neighbours(p, j, up, dn);
+  const __half* r[9] = {base,
+                        base + 1 * p.plane,
+                        base + 2 * p.plane + up,
+                        base + 3 * p.plane,
+                        base + 4 * p.plane + dn,
+                        base + 5 * p.plane + up,
+                        base + 6 * p.plane + up,
+                        base + 7 * p.plane + dn,
+                        base + 8 * p.plane + dn};
+  uint2 w[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q)
+    w[q] = cv ? ld_pop<CG>(reinterpret_cast<const uint2*>(r[q] + i0)) : make_uint2(0u, 0u);
+  const bool tail = i0 + 4 >= p.nx;
+  const int cl = i0 == 0 ? p.nx - 1 : i0 - 1, cr = tail ? 0 : i0 + 4;
+  const bool hl = lane == 0 && cv, hr = cv && (lane == 31 || tail);
+  uint32_t h[9];
+  h[1] = hl ? half_bits(ld_pop<CG>(r[1] + cl)) : 0u;
+  h[5] = hl ? half_bits(ld_pop<CG>(r[5] + cl)) : 0u;
+  h[8] = hl ? half_bits(ld_pop<CG>(r[8] + cl)) : 0u;
+  h[3] = hr ? half_bits(ld_pop<CG>(r[3] + cr)) : 0u;
+  h[6] = hr ? half_bits(ld_pop<CG>(r[6] + cr)) : 0u;
+  h[7] = hr ? half_bits(ld_pop<CG>(r[7] + cr)) : 0u;
+  // cx = +1 (q = 1, 5, 8): codes [left, h0, h1, h2]
+#pragma unroll
+  for (int q : {1, 5, 8}) {
+    uint32_t left = __shfl_up_sync(kFull, w[q].y, 1);
+    if (lane == 0) left = h[q] << 16;
+    const uint32_t x0 = __byte_perm(left, w[q].x, 0x5432), x1 = __byte_perm(w[q].x, w[q].y, 0x5432);
+    w[q] = make_uint2(x0, x1);
+  }
+  // cx = -1 (q = 3, 6, 7): codes [h1, h2, h3, right]; cell nx - 1 takes column 0
+#pragma unroll
+  for (int q : {3, 6, 7}) {
+    uint32_t right = __shfl_down_sync(kFull, w[q].x, 1);
+    if (lane == 31 || tail) right = h[q];
+    uint32_t x0 = __byte_perm(w[q].x, w[q].y, 0x5432), x1 = __byte_perm(w[q].y, right, 0x5432);
+    if (tail) {  // a row end inside the vector (nx not a multiple of 4)
+      if (i0 + 0 == p.nx - 1) x0 = (x0 & 0xffff0000u) | h[q];
+      if (i0 + 1 == p.nx - 1) x0 = (x0 & 0x0000ffffu) | (h[q] << 16);
+      if (i0 + 2 == p.nx - 1) x1 = (x1 & 0xffff0000u) | h[q];
+    }
+    w[q] = make_uint2(x0, x1);
+  }
+  const PairCodec<__half> c0(p.codec, 0), c1(p.codec, 1), c5(p.codec, 5);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    const PairCodec<__half>& c = q == 0 ? c0 : (q <= 4 ? c1 : c5);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&w[q].x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&w[q].y));
+    f[q][0] = fma2(pack2(a.x, a.y), c.inv, c.base);
+    f[q][1] = fma2(pack2(b.x, b.y), c.inv, c.base);
+  }
+}
+
 // ---------------------------------------------------------------- the fused step ----
 // MODE:  MODE_PLAIN (stream + collide only), MODE_STD / MODE_FULL (plus sensors,
 //        flags, tile counts, sums).
@@ -953,7 +1310,7 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
   using T = arith_t<S>;
   constexpr int V = Vec<S>::N;
   constexpr bool OUT = MODE != MODE_PLAIN;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = __shfl_sync(kFull, int(threadIdx.x >> 5), 0);
   const int i0 = (bx * 32 + lane) * V;
   const bool cv = i0 < p.nx;
   const int j0 = by * p.tile * p.bands;
@@ -974,6 +1331,10 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
   Acc<T> a_rho, a_jx, a_jy;
   uint32_t n_ref = 0, n_sw = 0, n_np = 0;
   uint32_t wn = 0;  // deferred cells gathered by this warp (warp-uniform)
+  // tile = 2^tshift rows and columns, covered by lpt = 2^lshift lanes of V cells
+  const int tshift = __ffs(p.tile) - 1;
+  const int lshift = tshift - (V == 4 ? 2 : (V == 2 ? 1 : 0));
+  const int lpt = 1 << lshift;
 
   // row prefetch (see PfWarp): the warp's slots in dynamic shared memory, and the copies
   // of row jj into them
@@ -984,8 +1345,8 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
   auto pf_issue = [&](int jj) {
     if (cv) {
       const S* base = p.src + (long long)jj * p.pitch;
-      const long long up = (long long)((jj == 0 ? p.ny : jj) - 1 - jj) * p.pitch;
-      const long long dn = (long long)((jj + 1 == p.ny ? 0 : jj + 1) - jj) * p.pitch;
+      long long up, dn;  // rows jj - 1 and jj + 1
+      row_neighbours(p, jj, up, dn);
       const S* r1 = base + 1 * p.plane;
       const S* r3 = base + 3 * p.plane;
       const S* r5 = base + 5 * p.plane + up;
@@ -1022,7 +1383,17 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
     if (j0 + warp < j1) pf_issue(j0 + warp);
   }
 
+  // FP16 deviations on the paired row: the pulled codes are assembled as binary16 words
+  // (load_half_row) and decoded in pairs
+  constexpr bool kHalfPaired = KSS_ROW_PAIRED && std::is_same<S, __half>::value &&
+                               MODE != MODE_FULL && !AAR && PULL && !PF && V == 4;
   for (int j = j0 + warp; j < j1; j += kWarps) {
+    uint32_t fbits;
+    if constexpr (kHalfPaired) {
+      F2 f[9][2];
+      load_half_row<CG>(p, j, i0, lane, cv, f);
+      fbits = fused_row_paired<S, MODE, STORE>(p, f, i0, j, cv, a_rho, a_jx, a_jy);
+    } else {
     T ft[9][V];
     const S* base = p.src + (long long)j * p.pitch;
     // AAR: the region in force for this step's collision (the switch flags of the most
@@ -1065,8 +1436,8 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
         if (cv && p.region) mbits = load_bytes<V>(p.region + (long long)j * p.pitch + i0);
       }
       if (PULL) {
-        const long long up = (long long)((j == 0 ? p.ny : j) - 1 - j) * p.pitch;    // row j-1
-        const long long dn = (long long)((j + 1 == p.ny ? 0 : j + 1) - j) * p.pitch;  // row j+1
+        long long up, dn;  // rows j - 1 and j + 1
+        row_neighbours(p, j, up, dn);
         // source rows of q = 0..8 (pull: row j - cy_q)
         const S* r0 = base;
         const S* r1 = base + 1 * p.plane;
@@ -1105,25 +1476,28 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
       }
     }
 
-    const uint32_t fbits =
-        fused_row<S, MODE, PULL, STORE, AAR>(p, ft, i0, j, cv, a_rho, a_jx, a_jy, mbits);
+    fbits = fused_row<S, MODE, PULL, STORE, AAR>(p, ft, i0, j, cv, a_rho, a_jx, a_jy, mbits);
+    }
     if (OUT) {
       n_ref += __popc(fbits & 0x01010101u);
       n_sw += __popc(fbits & 0x02020202u);
       n_np += __popc(fbits & 0x80808080u);
     }
-    // per-tile tag counts: this lane's cells all lie in tile (lane / lanes_per_tile)
+    // per-tile tag counts: this lane's cells all lie in tile (lane / lanes_per_tile);
+    // tile and lanes per tile are powers of two (tile 8, 16, 32 or 64)
     if (OUT) {
-      const int lpt = p.tile / V;
       int tr = __popc(fbits & 0x01010101u), ts = __popc(fbits & 0x02020202u);
-      for (int o = lpt >> 1; o > 0; o >>= 1) {
-        tr += __shfl_xor_sync(kFull, tr, o);
-        ts += __shfl_xor_sync(kFull, ts, o);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        if (o < lpt) {
+          tr += __shfl_xor_sync(kFull, tr, o);
+          ts += __shfl_xor_sync(kFull, ts, o);
+        }
       }
       if ((lane & (lpt - 1)) == 0 && (tr | ts)) {
-        const int b = (j - j0) / p.tile;
-        atomicAdd(&s_tiles[0][b][lane / lpt], tr);
-        atomicAdd(&s_tiles[1][b][lane / lpt], ts);
+        const int b = (j - j0) >> tshift;
+        atomicAdd(&s_tiles[0][b][lane >> lshift], tr);
+        atomicAdd(&s_tiles[1][b][lane >> lshift], ts);
       }
       if (MODE == MODE_STD) {
         // gather this row's deferred cells in the warp's region (CTA-local offsets)
@@ -1265,8 +1639,9 @@ __device__ __forceinline__ void step_cta(const StepParams<S>& p, const int bx, c
 }
 
 // AAR: the step with the two-relaxation collision in the region p.region (pull + store).
+
 template <class S, int MODE, bool PULL, bool STORE, bool AAR = false>
-__global__ void __launch_bounds__(kThreads, MODE == MODE_FULL ? KSS_FULL_MIN_BLOCKS : KSS_STEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(kThreads, step_min_blocks<S, MODE>())
 step_kernel(const StepParams<S> p) {
   step_cta<S, MODE, PULL, STORE, AAR>(p, blockIdx.x, blockIdx.y, gridDim.x,
                                       gridDim.x * gridDim.y);
@@ -1277,7 +1652,7 @@ step_kernel(const StepParams<S> p) {
 // retired between blocks and the completion counter is taken once per CTA.  Each block's
 // partials keep their slot, so the sums are those of step_kernel bit for bit.
 template <class S, int MODE, bool PULL, bool STORE>
-__global__ void __launch_bounds__(kThreads, MODE == MODE_FULL ? KSS_FULL_MIN_BLOCKS : KSS_STEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(kThreads, step_min_blocks<S, MODE>())
 step_kernel_persistent(const StepParams<S> p, int gx, int nblocks) {
   for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
     const int by = b / gx;
@@ -1399,7 +1774,7 @@ __device__ __forceinline__ bool multi_block(const StepParams<S>& p, const MultiS
 // collision in the region (adaptive algorithm refinement), two CTAs per SM (its per-cell
 // state needs more than 80 registers).
 template <class S, int MODE, bool AAR = false>
-__global__ void __launch_bounds__(kThreads, AAR ? 2 : KSS_STEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(kThreads, AAR ? 2 : step_min_blocks<S, MODE>())
 step_kernel_multi(const StepParams<S> pa, const StepParams<S> pb, const MultiState m) {
   __shared__ int s_next;
   if (threadIdx.x == 0) s_next = int(atomicAdd(m.work, 1u));
@@ -1438,7 +1813,7 @@ struct BatchItem {
 // AAR: members with a region take the two-relaxation collision there (members without
 // one step as BGK).
 template <class S, int MODE, bool AAR = false>
-__global__ void __launch_bounds__(kThreads, MODE == MODE_FULL ? KSS_FULL_MIN_BLOCKS : KSS_STEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(kThreads, step_min_blocks<S, MODE>())
 batch_step_kernel(const StepParams<S>* __restrict__ table, const BatchItem* __restrict__ items,
                   int nitems) {
   static_assert(sizeof(StepParams<S>) % 8 == 0, "parameter copy in 8-byte words");
@@ -1460,15 +1835,18 @@ batch_step_kernel(const StepParams<S>* __restrict__ table, const BatchItem* __re
 }
 
 // ---------------------------------------------------------------- batched multi-step ----
-// nsteps steps of a whole batch in one cooperative launch (two CTAs per SM, rows staged
-// by the row prefetch for FP32 storage): work item w = s * nitems + i is
+// nsteps steps of a whole batch in one cooperative launch (FP32 storage: rows staged by
+// the row prefetch, two CTAs per SM at up to 128 registers; other storage types load their
+// rows directly at the register budget of the one-step kernels): work item w = s * nitems + i is
 // block items[i] of step s.  Each lattice has its own MultiState (its blocks' step
 // counters, ring of partial sums, ticket and slot counters); all share the work counter,
 // so items are handed out in (step, work-list) order and, as in step_kernel_multi, every
 // item waits only for items of its own lattice handed out before it.  mtab[k] is lattice
 // k's state; ta / tb its parameters for even / odd steps.
 template <class S, int MODE>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads,
+                                  multi_prefetch_smem<S, MODE, false>() > 0 ? 2
+                                                                            : step_min_blocks<S, MODE>())
 batch_kernel_multi(const StepParams<S>* __restrict__ ta, const StepParams<S>* __restrict__ tb,
                    const MultiState* __restrict__ mtab, const BatchItem* __restrict__ items,
                    int nitems, int nsteps, uint32_t* work) {

@@ -88,8 +88,14 @@ _SIGNATURES = {
     "kss_get_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "kss_set_aar_region": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "kss_testing_expire_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "kss_testing_expire_mbarrier": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "kss_testing_fail_after": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64]),
+    "kss_testing_live_allocations": (ctypes.c_int64, []),
     "kss_get_aar_region": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "kss_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "kss_slab_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_void_p)]),
+    "kss_slab_edges": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int]),
+    "kss_slab_set_halos": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int]),
     "kss_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(Config),
                                         ctypes.POINTER(ctypes.c_void_p)]),
     "kss_batch_destroy": (None, [ctypes.c_void_p]),
@@ -202,14 +208,22 @@ def make_config(nx: int, ny: int, precision="fp32", tau: float = 0.8, refine_sen
     return cfg
 
 
+# storage element of each precision, as numpy / torch dtypes (the raw rows of the slab
+# exchange; FP16 deviations travel as their binary16 codes)
+STORAGE_NP = {FP64: np.float64, FP32: np.float32, FP16DEV: np.int16}
+
+
 class Lattice:
-    """A periodic D2Q9 lattice on the current CUDA device (see include/kss.h)."""
+    """A periodic D2Q9 lattice on the current CUDA device (see include/kss.h); with
+    slab=True one y-slab of a decomposed lattice, whose halo rows the caller sets before
+    each step (kss_slab_create)."""
 
     def __init__(self, nx: int, ny: int, precision="fp32", tau: float = 0.8,
                  refine_sensor="kn", refine_threshold: float = 1e-3, switch_sensor="neq",
                  switch_threshold: float = 1e-4, record=("kl",), output_every: int = 1,
                  tile: int = 16, stream="torch", kernel="auto", rho0: float = 1.0,
-                 dev_exp: int = 12, dev_unscaled: bool = False, tau2: float = 0.0):
+                 dev_exp: int = 12, dev_unscaled: bool = False, tau2: float = 0.0,
+                 slab: bool = False):
         self._lib = load()
         self._h = None
         cfg = make_config(nx, ny, precision=precision, tau=tau, refine_sensor=refine_sensor,
@@ -218,8 +232,10 @@ class Lattice:
                           output_every=output_every, tile=tile, stream=stream, kernel=kernel,
                           rho0=rho0, dev_exp=dev_exp, dev_unscaled=dev_unscaled, tau2=tau2)
         handle = ctypes.c_void_p()
-        self._check(self._lib.kss_create(ctypes.byref(cfg), ctypes.byref(handle)))
+        create = self._lib.kss_slab_create if slab else self._lib.kss_create
+        self._check(create(ctypes.byref(cfg), ctypes.byref(handle)))
         self._adopt(handle, cfg, owned=True)
+        self.slab = slab
 
     def _adopt(self, handle, cfg, owned: bool):
         self.cfg = cfg
@@ -308,8 +324,11 @@ class Lattice:
         self._check(self._lib.kss_read_moments(self._h, p0, p1, p2, d))
         return tuple(outs)
 
-    def read_sensor(self, sensor, device: bool = False):
-        out = self._alloc((self.ny, self.nx), np.float64, device)
+    def read_sensor(self, sensor, device: bool = False, out=None):
+        """The sensor field [ny, nx] (FP64) of the last output step; `out` = a buffer to
+        fill (host or device, float64, contiguous)."""
+        if out is None:
+            out = self._alloc((self.ny, self.nx), np.float64, device)
         p, d = _ptr(out, np.float64)
         self._check(self._lib.kss_read_sensor(self._h, _sensor(sensor), p, d))
         return out
@@ -326,6 +345,47 @@ class Lattice:
         pt, _ = _ptr(tiles, np.int32)
         self._check(self._lib.kss_read_flags(self._h, pf, pt, counts, d))
         return flags, tiles, np.array(list(counts), dtype=np.int64)
+
+    def _raw(self, a):
+        """(pointer, on_device) of a contiguous [3, nx] buffer of the storage type."""
+        want = STORAGE_NP[self.precision]
+        if _is_torch(a):
+            import torch
+
+            tdt = {np.float64: torch.float64, np.float32: torch.float32,
+                   np.int16: torch.int16}[want]
+            if a.dtype != tdt or not a.is_contiguous() or a.numel() != 3 * self.nx:
+                raise TypeError(f"halo rows must be a contiguous {tdt} tensor of 3 x {self.nx}")
+            return ctypes.c_void_p(a.data_ptr()), int(a.is_cuda)
+        if (not isinstance(a, np.ndarray) or a.dtype != want or not a.flags["C_CONTIGUOUS"]
+                or a.size != 3 * self.nx):
+            raise TypeError(f"halo rows must be a C-contiguous {np.dtype(want).name} array "
+                            f"of 3 x {self.nx}")
+        return ctypes.c_void_p(a.ctypes.data), 0
+
+    def slab_edges(self, device: bool = True, out=None):
+        """(to_below, to_above): the rows leaving the slab, [3, nx] each in the storage
+        type (q = 4, 7, 8 of row 0; q = 2, 5, 6 of row ny - 1)."""
+        if out is None:
+            want = STORAGE_NP[self.precision]
+            if device:
+                import torch
+
+                tdt = {np.float64: torch.float64, np.float32: torch.float32,
+                       np.int16: torch.int16}[want]
+                out = tuple(torch.empty((3, self.nx), dtype=tdt, device="cuda")
+                            for _ in range(2))
+            else:
+                out = (np.empty((3, self.nx), dtype=want), np.empty((3, self.nx), dtype=want))
+        (pb, d), (pa, _) = self._raw(out[0]), self._raw(out[1])
+        self._check(self._lib.kss_slab_edges(self._h, pb, pa, d))
+        return out
+
+    def set_halos(self, from_below, from_above) -> None:
+        """Halo rows of the next step: from_below = the slab below's to_above (its row
+        ny - 1, q = 2, 5, 6), from_above = the slab above's to_below."""
+        (pb, d), (pa, _) = self._raw(from_below), self._raw(from_above)
+        self._check(self._lib.kss_slab_set_halos(self._h, pb, pa, d))
 
     def read_stats(self):
         sums = (ctypes.c_double * 3)()

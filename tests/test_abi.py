@@ -206,3 +206,16 @@ def test_batch_create_rejects_before_touching_the_gpu(case, code):
     out = ctypes.c_void_p(1)
     assert lib.kss_batch_create(n, cfgs, ctypes.byref(out)) == code
     assert out.value is None
+
+
+def test_fault_injection_arms_and_disarms_without_a_gpu():
+    """kss_testing_fail_after takes kind 0 (allocations) or 1 (step launches) and any n;
+    arming and disarming touch no device, and nothing is allocated without a lattice."""
+    from paper_2603_13618_gb300 import kss
+
+    lib = kss.load()
+    assert lib.kss_testing_fail_after(2, 0) == -1
+    for kind in (0, 1):
+        assert lib.kss_testing_fail_after(kind, 5) == 0
+        assert lib.kss_testing_fail_after(kind, -1) == 0
+    assert lib.kss_testing_live_allocations() >= 0
