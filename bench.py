@@ -232,7 +232,11 @@ def run_batch(args):
                   stream="torch")
     for k, (s, _, mach, fs) in enumerate(specs):
         b[k].set_fields(*inputs.batch_fields(s, mach, fs))
-    tuning = b.autotune(None, steps=20) if not args.no_tune else b.tuning
+    if args.batch_rows:  # a fixed decomposition (profiling captures): multi-step launch
+        b.set_tuning(rows=args.batch_rows, ctas_per_sm=0, graph=1, multi_step=1)
+        tuning = b.tuning
+    else:
+        tuning = b.autotune(None, steps=20) if not args.no_tune else b.tuning
     stream = torch.cuda.current_stream()
     K = args.steps
     b.step(args.warmup)
@@ -321,6 +325,21 @@ def run_batch(args):
 ADJ_METRIC = "adjoint MLUPS (forward with checkpoints + reverse sweep), 1xGB300"
 
 
+def adjoint_launches(N, E, multi=True):
+    """Kernel launches of one gradient: the forward pass (equilibrium, N - 1 plain steps,
+    the objective), then per segment of the reverse sweep its recomputed plain steps and
+    its reverse steps (one cooperative launch and the ordered addition of its totals, or
+    one launch per reverse step), and the final projection."""
+    fwd = 1 + (N - 1) + 1
+    bwd = 1
+    s0 = ((N - 2) // E) * E if N >= 2 else -1
+    while s0 >= 0:
+        last = min(s0 + E - 1, N - 2)
+        bwd += (last - s0) + (2 if multi else last - s0 + 1)
+        s0 -= E
+    return fwd + bwd
+
+
 def run_adjoint(args):
     """The adjoint workload: time(forward + backward) against time(200 plain steps)."""
     import numpy as np
@@ -372,7 +391,8 @@ def run_adjoint(args):
                    "nx": n, "ny": n, "nsteps": N, "checkpoint_every": E},
         "ms_gradient": t_adj, "ms_forward_plain": t_fwd, "adjoint_over_forward": t_adj / t_fwd,
         "grad_tau": gt, "grad_rho0_norm": float(torch.linalg.vector_norm(g)),
-        "gpu_launches_per_gradient": 1 + (N - 1) + (N - 1 - (N - 2) // E - 1) + (N - 1) + 1 + 1,
+        "gpu_launches_per_gradient": adjoint_launches(N, E, multi=True),
+        "gpu_launches_per_gradient_one_launch_per_reverse_step": adjoint_launches(N, E, False),
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -419,11 +439,21 @@ def run_fp16(args):
             torch.cuda.synchronize()
             total = ev[0].elapsed_time(ev[-1])
             kern = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(K)) / K
+            # the same K steps as one kss_step(K) call (a multi-step launch where the
+            # library takes one, else a replayed graph of one-step launches)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.step(K)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            call = e0.elapsed_time(e1) / K
             bpl = (18 if prec == "fp16dev" else 36) * 2 + (5 if out else 0)
             achieved = bpl * cells / (kern * 1e-3) / 1e9
             runs[name] = {"value": cells * K / (total * 1e-3) / 1e6, "unit": "MLUPS",
                           "ms_per_step": total / K, "kernel_ms": kern, "bytes_per_lup": bpl,
-                          "achieved_gbs": achieved, "frac": achieved / peak}
+                          "achieved_gbs": achieved, "frac": achieved / peak,
+                          "one_call_ms_per_step": call,
+                          "one_call_frac": bpl * cells / (call * 1e-3) / 1e9 / peak}
             lat.close()
     clocks = clk.summary()
     err = None
@@ -964,6 +994,9 @@ def main():
                          "lattices; adjoint512: the gradient of the KL objective")
     ap.add_argument("--no-tune", action="store_true",
                     help="batch64: keep the default work decomposition")
+    ap.add_argument("--batch-rows", type=int, default=0,
+                    help="batch64: CTA height of a fixed multi-step decomposition instead of "
+                         "the autotuner's choice")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

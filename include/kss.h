@@ -419,6 +419,12 @@ int kss_adjoint_forward(kss_adjoint* adj, const double* rho0, const double* ux0,
 int kss_adjoint_backward(kss_adjoint* adj, double* grad_rho0, double* grad_tau, int on_device);
 
 const char* kss_adjoint_last_error(const kss_adjoint* adj);
+/* How the reverse sweep runs (no counterpart in the paper): on = 1 (the default) takes
+ * each segment's reverse steps in one cooperative launch whose blocks wait only on their
+ * neighbours' previous step (bounded waits: KSS_ERR_TIMEOUT from kss_adjoint_backward if
+ * one runs out); on = 0 one launch per reverse step.  The gradients are the same bit for
+ * bit.  KSS_ERR_ARG for another value. */
+int kss_adjoint_set_multistep(kss_adjoint* adj, int on);
 
 /* ---- Allocation-free fused step (no counterpart in the paper) ----------------------
  * For callers that cannot call cudaMalloc: code that owns all device memory itself

@@ -57,7 +57,7 @@ struct AdjParams {
 
 // Nine populations of V cells of row j pulled from src: forward (REV = false)
 // v_q(i, j) = src_q(i - cx_q, j - cy_q); reverse v_q(i, j) = src_q(i + cx_q, j + cy_q).
-template <class T, bool REV>
+template <class T, bool REV, bool CG = false>
 __device__ __forceinline__ void adj_pull_row(const T* src, long long plane, int pitch, int nx,
                                              int ny, int j, int i0, int lane, bool cv,
                                              T (&v)[9][kAdjV]) {
@@ -77,16 +77,16 @@ __device__ __forceinline__ void adj_pull_row(const T* src, long long plane, int 
                    base + 7 * plane + rm,
                    base + 8 * plane + rm};
 #pragma unroll
-  for (int q = 0; q < 9; ++q) vload<T, V>(r[q] + i0, cv, v[q]);
+  for (int q = 0; q < 9; ++q) vload<T, V, CG>(r[q] + i0, cv, v[q]);
   // cx = +1 planes (1, 5, 8) take column i - 1 forward, i + 1 in reverse; cx = -1
   // planes (3, 6, 7) the opposite
   if (!REV) {
-    const T h1 = load_left_halo<T>(r[1], i0, nx, lane, cv);
-    const T h5 = load_left_halo<T>(r[5], i0, nx, lane, cv);
-    const T h8 = load_left_halo<T>(r[8], i0, nx, lane, cv);
-    const T h3 = load_right_halo<T, V>(r[3], i0, nx, lane, cv);
-    const T h6 = load_right_halo<T, V>(r[6], i0, nx, lane, cv);
-    const T h7 = load_right_halo<T, V>(r[7], i0, nx, lane, cv);
+    const T h1 = load_left_halo<T, CG>(r[1], i0, nx, lane, cv);
+    const T h5 = load_left_halo<T, CG>(r[5], i0, nx, lane, cv);
+    const T h8 = load_left_halo<T, CG>(r[8], i0, nx, lane, cv);
+    const T h3 = load_right_halo<T, V, CG>(r[3], i0, nx, lane, cv);
+    const T h6 = load_right_halo<T, V, CG>(r[6], i0, nx, lane, cv);
+    const T h7 = load_right_halo<T, V, CG>(r[7], i0, nx, lane, cv);
     assemble_from_left<T, V>(v[1], h1, lane);
     assemble_from_left<T, V>(v[5], h5, lane);
     assemble_from_left<T, V>(v[8], h8, lane);
@@ -94,12 +94,12 @@ __device__ __forceinline__ void adj_pull_row(const T* src, long long plane, int 
     assemble_from_right<T, V>(v[6], h6, i0, nx, lane);
     assemble_from_right<T, V>(v[7], h7, i0, nx, lane);
   } else {
-    const T h3 = load_left_halo<T>(r[3], i0, nx, lane, cv);
-    const T h6 = load_left_halo<T>(r[6], i0, nx, lane, cv);
-    const T h7 = load_left_halo<T>(r[7], i0, nx, lane, cv);
-    const T h1 = load_right_halo<T, V>(r[1], i0, nx, lane, cv);
-    const T h5 = load_right_halo<T, V>(r[5], i0, nx, lane, cv);
-    const T h8 = load_right_halo<T, V>(r[8], i0, nx, lane, cv);
+    const T h3 = load_left_halo<T, CG>(r[3], i0, nx, lane, cv);
+    const T h6 = load_left_halo<T, CG>(r[6], i0, nx, lane, cv);
+    const T h7 = load_left_halo<T, CG>(r[7], i0, nx, lane, cv);
+    const T h1 = load_right_halo<T, V, CG>(r[1], i0, nx, lane, cv);
+    const T h5 = load_right_halo<T, V, CG>(r[5], i0, nx, lane, cv);
+    const T h8 = load_right_halo<T, V, CG>(r[8], i0, nx, lane, cv);
     assemble_from_left<T, V>(v[3], h3, lane);
     assemble_from_left<T, V>(v[6], h6, lane);
     assemble_from_left<T, V>(v[7], h7, lane);
@@ -253,24 +253,26 @@ __global__ void __launch_bounds__(kThreads) adj_objective_kernel(const AdjParams
   adj_reduce<T>(p, sum);
 }
 
-// lt^n from l^{n+1} = S^T lt^{n+1} and ft^n = S f^n; adds sum l^{n+1} . f^neq to *acc
-// (dJ/dtau = that sum over all steps / tau^2).
-template <class T>
-__global__ void __launch_bounds__(kThreads) adj_step_kernel(const AdjParams<T> p) {
+// lt^n from l^{n+1} = S^T lt^{n+1} and ft^n = S f^n for the block (bx, by) of the adjoint
+// grid; returns the block's sum l^{n+1} . f^neq per thread (dJ/dtau = that sum over all
+// steps / tau^2).  CG: the adjoint buffers are written by other CTAs of the same launch
+// (the multi-step reverse sweep), so they are read with ordinary cached loads.
+template <class T, bool CG>
+__device__ __forceinline__ Acc<T> adj_step_block(const AdjParams<T>& p, int bx, int by) {
   constexpr int V = kAdjV;
   constexpr int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
   constexpr int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i0 = (blockIdx.x * 32 + lane) * V;
+  const int i0 = (bx * 32 + lane) * V;
   const bool cv = i0 < p.nx;
   const int nvalid = cv ? min(V, p.nx - i0) : 0;
-  const int j0 = blockIdx.y * p.rows, j1 = min(j0 + p.rows, p.ny);
+  const int j0 = by * p.rows, j1 = min(j0 + p.rows, p.ny);
   const T om = p.omega, om1 = T(1) - p.omega;
   Acc<T> sum;
   for (int j = j0 + warp; j < j1; j += kWarps) {
     T ft[9][V], l[9][V];
     adj_pull_row<T, false>(p.f, p.plane, p.pitch, p.nx, p.ny, j, i0, lane, cv, ft);
-    adj_pull_row<T, true>(p.lam_in, p.plane, p.pitch, p.nx, p.ny, j, i0, lane, cv, l);
+    adj_pull_row<T, true, CG>(p.lam_in, p.plane, p.pitch, p.nx, p.ny, j, i0, lane, cv, l);
     adj_pad<T>(ft, nvalid, T(1));
     adj_pad<T>(l, nvalid, T(0));
     T rs = T(0);
@@ -285,11 +287,11 @@ __global__ void __launch_bounds__(kThreads) adj_step_kernel(const AdjParams<T> p
       adj_cell_eq<T>(c, ux, uy, feq);
 #pragma unroll
       for (int q = 0; q < 9; ++q) rs = fma(y[q], c[q] - feq[q], rs);
-      T A, bx, by;
-      adj_moment_pullback<T>(y, ux, uy, A, bx, by);
+      T A, bx_, by_;
+      adj_moment_pullback<T>(y, ux, uy, A, bx_, by_);
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
-        const T cb = T(cx[q]) * bx + T(cy[q]) * by;
+        const T cb = T(cx[q]) * bx_ + T(cy[q]) * by_;
         l[q][k] = fma(om1, y[q], om * (A + cb));
       }
     }
@@ -300,7 +302,139 @@ __global__ void __launch_bounds__(kThreads) adj_step_kernel(const AdjParams<T> p
         vstore<T, V>(p.lam_out + q * p.plane + (long long)j * p.pitch + i0, l[q]);
     }
   }
+  return sum;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) adj_step_kernel(const AdjParams<T> p) {
+  Acc<T> sum = adj_step_block<T, false>(p, blockIdx.x, blockIdx.y);
   adj_reduce<T>(p, sum);
+}
+
+// ---- the reverse sweep of one segment in one cooperative launch ----
+// Reverse iterations it = 0 .. nit - 1 (step k = last - it): work item w = it * nblocks + b
+// is block b of iteration it, handed out in order from an atomic counter.  Block b of
+// iteration it first waits until the blocks of its 3 x 3 neighbourhood (periodic) have
+// completed iteration it - 1: they wrote the adjoint cells its reverse pull reads, and have
+// read the cells it overwrites (the buffers alternate).  Every wait is bounded (bit 1 of the
+// error word on expiry).  Each block's partial of the dJ/dtau sum goes to part[it][b]; the
+// block completing iteration it last adds them as adj_reduce does and stores the
+// iteration's total in totals[it]; adj_add_totals then adds the totals in iteration order,
+// so the accumulator is that of one launch per step bit for bit.
+template <class T>
+struct AdjMulti {
+  const T* ck;         // the segment's checkpoint state (step s0)
+  const T* seg;        // recomputed states of steps s0 + 1 .. last, state_elems apart
+  long long state_elems;
+  const T* lam0;       // adjoint ping-pong: iteration it reads lam(lc + it), writes
+  const T* lam1;       // lam(lc + it + 1), lam(k) = lam0 for even k, lam1 for odd
+  uint32_t* done;      // [nblocks] iterations each block completed (0 at launch)
+  uint32_t* ticket;    // [nit] blocks of each iteration completed (0 at launch)
+  uint32_t* work;      // next work item (0 at launch)
+  double* part;        // [nit][nblocks]
+  double* totals;      // [nit]
+  uint32_t* err;       // bit 1: a wait ran out
+  long long deadline;  // clock64 cycles one wait may take
+  int s0, last, lc;
+  int gx, gy, nblocks;  // the adjoint grid (adj_grid): gx x gy blocks
+};
+
+__device__ __forceinline__ bool adj_wait_ge(const uint32_t* p, uint32_t want, uint32_t* err,
+                                            long long deadline) {
+  if (ld_acquire_u32(p) >= want) return true;
+  const long long t0 = clock64();
+  while (ld_acquire_u32(p) < want) {
+    if (clock64() - t0 > deadline) {
+      atomicOr(err, 2u);
+      return false;
+    }
+    __nanosleep(64);
+  }
+  return true;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) adj_multi_kernel(const AdjParams<T> base,
+                                                             const AdjMulti<T> m) {
+  __shared__ int s_next, s_go, s_fin;
+  __shared__ Red<T> s_red[kWarps];
+  __shared__ Red<T> s_tot[kWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gx = m.gx, gy = m.gy;
+  const int nit = m.last - m.s0 + 1;
+  const int total = nit * m.nblocks;
+  if (threadIdx.x == 0) s_next = int(atomicAdd(m.work, 1u));
+  __syncthreads();
+  int w = s_next;
+  while (w < total) {
+    const int it = w / m.nblocks, b = w - it * m.nblocks;
+    const int by = b / gx, bx = b - by * gx;
+    __syncthreads();  // every thread has read s_next before thread 0 rewrites it
+    if (threadIdx.x < 32) {
+      const int t = threadIdx.x;
+      if (t == 0) s_next = int(atomicAdd(m.work, 1u));
+      bool ok = true;
+      if (it > 0 && t < 9) {
+        const int dy = t / 3 - 1, dx = t - 3 * (t / 3) - 1;
+        const int yy = by + dy < 0 ? gy - 1 : (by + dy == gy ? 0 : by + dy);
+        const int xx = bx + dx < 0 ? gx - 1 : (bx + dx == gx ? 0 : bx + dx);
+        ok = adj_wait_ge(m.done + yy * gx + xx, uint32_t(it), m.err, m.deadline);
+      }
+      ok = __all_sync(kFull, ok);
+      if (t == 0) s_go = ok;
+    }
+    __syncthreads();
+    if (!s_go) return;
+    const int k = m.last - it;
+    AdjParams<T> p = base;
+    p.f = k == m.s0 ? m.ck : m.seg + (long long)(k - m.s0) * m.state_elems;
+    const bool odd = ((m.lc + it) & 1) != 0;
+    p.lam_in = odd ? m.lam1 : m.lam0;
+    p.lam_out = const_cast<T*>(odd ? m.lam0 : m.lam1);
+    Acc<T> sum = adj_step_block<T, true>(p, bx, by);
+    // the block's partial, as adj_reduce forms it
+    sum.warp_reduce();
+    if (lane == 0) s_red[warp] = Red<T>::of(sum);
+    __syncthreads();  // (also: every store of the block precedes thread 0's release)
+    double* part = m.part + (long long)it * m.nblocks;
+    if (threadIdx.x == 0) {
+      Red<T> t;
+      for (int q = 0; q < kWarps; ++q) t.add(s_red[q]);
+      t.store(part + b);
+      __threadfence();
+      st_release_u32(m.done + b, uint32_t(it + 1));
+      s_fin = atomicAdd(m.ticket + it, 1u) == uint32_t(m.nblocks - 1);
+    }
+    __syncthreads();
+    if (s_fin) {  // the iteration's total, in adj_reduce's order
+      __threadfence();
+      Red<T> t;
+      for (int q = threadIdx.x; q < m.nblocks; q += kThreads) t.add(Red<T>::load(part + q));
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) t.add(t.shfl_xor(off));
+      if (lane == 0) s_tot[warp] = t;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        Red<T> r = s_tot[0];
+        for (int q = 1; q < kWarps; ++q) r.add(s_tot[q]);
+        m.totals[it] = r.value();
+      }
+    }
+    __syncthreads();
+    w = s_next;
+  }
+}
+
+// *acc += totals[0] + ... in iteration order, one addition each (as one launch per step
+// adds its total).  (A template, instantiated per storage type, so that the header can be
+// included by several translation units.)
+template <class T>
+__global__ void adj_add_totals(const double* totals, int n, double* acc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double a = *acc;
+    for (int i = 0; i < n; ++i) a += totals[i];
+    *acc = a;
+  }
 }
 
 // dJ/drho0(x) = sum_q (S^T lt^0)_q(x) f^eq_q(1, u0(x)) (f^0 = f^eq(rho0, u0) is linear in

@@ -30,7 +30,15 @@ struct kss_adjoint {
   double* fields = nullptr;  // staging: rho0, ux0, uy0 (dense)
   double* grad = nullptr;    // dense dJ/drho0
   double* part = nullptr;    // per-CTA partials
-  unsigned char* small = nullptr;  // done counter @0, acc[2] @64
+  unsigned char* small = nullptr;  // done counter @0, acc[2] @64, error word @128
+  // the reverse sweep of a segment in one cooperative launch (adj_multi_kernel): its
+  // counters (block progress, iteration tickets, work counter: zeroed before each launch),
+  // the per-block partials and the iteration totals
+  bool multi = true;
+  int multi_ctas = 0;
+  uint32_t* mcount = nullptr;  // [nblocks] done, [E] tickets, [1] work
+  double* mpart = nullptr;     // [E][nblocks]
+  double* mtot = nullptr;      // [E]
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   double tau = 0;
@@ -65,7 +73,8 @@ void free_all(kss_adjoint* A) {
   DeviceGuard g(A->device);
   cudaStreamSynchronize(A->stream);
   void* bufs[] = {A->ck,     A->seg,    A->work[0], A->work[1], A->lam[0], A->lam[1],
-                  A->wplane, A->fields, A->grad,    A->part,    A->small};
+                  A->wplane, A->fields, A->grad,    A->part,    A->small,   A->mcount,
+                  A->mpart,  A->mtot};
   for (void* b : bufs)
     if (b) kss_rt::dev_free(b);
   if (A->g_fwd) cudaGraphExecDestroy(A->g_fwd);
@@ -161,6 +170,36 @@ cudaError_t backward_launches(kss_adjoint* A, cudaStream_t s) {
     };
     for (int k = s0 + 1; k <= last && e == cudaSuccess; ++k)
       e = plain_step<T>(A, state(k - 1), const_cast<void*>(state(k)), s);
+    if (A->multi && A->multi_ctas > 0 && e == cudaSuccess) {
+      // the segment's reverse steps in one cooperative launch (adj_multi_kernel)
+      const dim3 g = kss::adj_grid(A->cfg.nx, A->cfg.ny, A->adj_rows);
+      const int nblocks = int(g.x * g.y), nit = last - s0 + 1;
+      kss::AdjMulti<T> m{};
+      m.ck = static_cast<const T*>(state(s0));
+      m.seg = reinterpret_cast<const T*>(A->seg);
+      m.state_elems = (long long)(A->state_bytes / A->esz);
+      m.lam0 = reinterpret_cast<const T*>(A->lam[0]);
+      m.lam1 = reinterpret_cast<const T*>(A->lam[1]);
+      m.done = A->mcount;
+      m.ticket = A->mcount + nblocks;
+      m.work = A->mcount + nblocks + A->cfg.checkpoint_every;
+      m.part = A->mpart;
+      m.totals = A->mtot;
+      m.err = reinterpret_cast<uint32_t*>(A->small + 128);
+      m.deadline = 2000000000LL;  // about a second at 2 GHz
+      m.s0 = s0;
+      m.last = last;
+      m.lc = lc;
+      m.gx = int(g.x);
+      m.gy = int(g.y);
+      m.nblocks = nblocks;
+      e = cudaMemsetAsync(A->mcount, 0,
+                          sizeof(uint32_t) * (size_t(nblocks) + A->cfg.checkpoint_every + 1), s);
+      const int ctas = std::min(A->multi_ctas, nit * nblocks);
+      if (e == cudaSuccess) e = kss::launch_adj_multi<T>(p, m, ctas, p.acc, s);
+      lc ^= nit & 1;
+      continue;
+    }
     for (int k = last; k >= s0 && e == cudaSuccess; --k) {
       p.f = static_cast<const T*>(state(k));
       p.lam_in = reinterpret_cast<const T*>(A->lam[lc]);
@@ -225,8 +264,11 @@ int backward_impl(kss_adjoint* A, double* grad_tau) {
   int rc = run_graph(A, &A->g_bwd, [&](cudaStream_t s) { return backward_launches<T>(A, s); });
   if (rc) return rc;
   double s = 0;
+  uint32_t err = 0;
   KSS_ACUDA(A, cudaMemcpyAsync(&s, acc_at(A, 1), sizeof(double), cudaMemcpyDeviceToHost, A->stream));
+  KSS_ACUDA(A, cudaMemcpyAsync(&err, A->small + 128, sizeof(err), cudaMemcpyDeviceToHost, A->stream));
   KSS_ACUDA(A, cudaStreamSynchronize(A->stream));
+  if (err) return afail(A, KSS_ERR_TIMEOUT, "a bounded wait of the reverse sweep ran out");
   if (grad_tau) *grad_tau = s / (A->tau * A->tau);
   return KSS_OK;
 }
@@ -293,6 +335,11 @@ int kss_adjoint_create(const kss_adjoint_config* cfg, kss_adjoint** out) {
       {reinterpret_cast<void**>(&A->grad), n * sizeof(double)},
       {reinterpret_cast<void**>(&A->part), size_t(g.x) * g.y * sizeof(double)},
       {reinterpret_cast<void**>(&A->small), 256},
+      {reinterpret_cast<void**>(&A->mcount),
+       sizeof(uint32_t) * (size_t(g.x) * g.y + A->cfg.checkpoint_every + 1)},
+      {reinterpret_cast<void**>(&A->mpart),
+       sizeof(double) * size_t(g.x) * g.y * A->cfg.checkpoint_every},
+      {reinterpret_cast<void**>(&A->mtot), sizeof(double) * size_t(A->cfg.checkpoint_every)},
   };
   for (auto& a : allocs) {
     if (kss_rt::dev_malloc(a.p, a.bytes) != cudaSuccess) {
@@ -314,11 +361,23 @@ int kss_adjoint_create(const kss_adjoint_config* cfg, kss_adjoint** out) {
     free_all(A);
     return KSS_ERR_CUDA;
   }
+  A->multi_ctas = A->fp32 ? kss::adj_multi_resident_ctas<float>()
+                          : kss::adj_multi_resident_ctas<double>();
   *out = A;
   return KSS_OK;
 }
 
 void kss_adjoint_destroy(kss_adjoint* A) { free_all(A); }
+
+int kss_adjoint_set_multistep(kss_adjoint* A, int on) {
+  if (!A || (on != 0 && on != 1)) return KSS_ERR_ARG;
+  if (A->multi != (on != 0) && A->g_bwd) {  // the recorded reverse sweep is the other form
+    cudaGraphExecDestroy(A->g_bwd);
+    A->g_bwd = nullptr;
+  }
+  A->multi = on != 0;
+  return KSS_OK;
+}
 
 const char* kss_adjoint_last_error(const kss_adjoint* A) { return A ? A->msg.c_str() : "null adjoint"; }
 

@@ -92,6 +92,14 @@ template <class T>
 cudaError_t launch_adj_step(const AdjParams<T>& p, cudaStream_t stream);
 template <class T>
 cudaError_t launch_adj_final(const AdjParams<T>& p, cudaStream_t stream);
+// The reverse sweep of one segment in one cooperative launch of `ctas` persistent CTAs
+// (adj_multi_kernel), then its iteration totals added to *acc in order; and the CTAs of
+// that kernel the device holds at once.
+template <class T>
+cudaError_t launch_adj_multi(const AdjParams<T>& base, const AdjMulti<T>& m, int ctas,
+                             double* acc, cudaStream_t stream);
+template <class T>
+int adj_multi_resident_ctas();
 
 // Population conversions for any storage S (float, double, __half deviations); the
 // codec is that of the lattice (empty for float and double).

@@ -79,6 +79,14 @@ cudaError_t launch_step_mode(const StepParams<KSS_T>& p, dim3 grid, cudaStream_t
       return cudaGetLastError();
     }
   }
+  if constexpr (KSS_F16_PREFETCH && step_prefetch_smem<KSS_T, MODE, true>() > 0) {
+    // FP16 deviations, {Kn, KL, neq}: the row prefetch, with its dynamic shared memory
+    constexpr int dyn = step_prefetch_smem<KSS_T, MODE, true>();
+    const cudaError_t e = allow_dynamic_smem<step_kernel<KSS_T, MODE, true, true, false, true>, dyn>();
+    if (e != cudaSuccess) return e;
+    step_kernel<KSS_T, MODE, true, true, false, true><<<grid, kThreads, dyn, stream>>>(p);
+    return cudaGetLastError();
+  }
   step_kernel<KSS_T, MODE, true, true><<<grid, kThreads, 0, stream>>>(p);
   return cudaGetLastError();
 }
@@ -215,6 +223,33 @@ cudaError_t launch_adj_step<KSS_T>(const AdjParams<KSS_T>& p, cudaStream_t strea
 template <>
 cudaError_t launch_adj_final<KSS_T>(const AdjParams<KSS_T>& p, cudaStream_t stream) {
   adj_final_kernel<KSS_T><<<adj_grid(p.nx, p.ny, p.rows), kThreads, 0, stream>>>(p);
+  return cudaGetLastError();
+}
+
+template <>
+int adj_multi_resident_ctas<KSS_T>() {
+  return resident_ctas<adj_multi_kernel<KSS_T>>();
+}
+
+template <>
+cudaError_t launch_adj_multi<KSS_T>(const AdjParams<KSS_T>& base, const AdjMulti<KSS_T>& m,
+                                    int ctas, double* acc, cudaStream_t stream) {
+  if (ctas < 1) return cudaErrorInvalidValue;
+  // a cooperative launch (all CTAs resident: the waits need it), recorded as such when the
+  // stream is being captured into a graph
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, adj_multi_kernel<KSS_T>, base, m);
+  if (e != cudaSuccess) return e;
+  adj_add_totals<KSS_T><<<1, 32, 0, stream>>>(m.totals, m.last - m.s0 + 1, acc);
   return cudaGetLastError();
 }
 

@@ -348,13 +348,25 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
+// The same slots for FP16 deviation codes (see pf_issue_half): nine 8-byte vectors per lane
+// and the 4-byte words that hold the halo codes.
+struct PfWarpH {
+  uint2 pop[9][32];     // the nine code vectors of each lane
+  uint32_t hr[3][32];   // words holding the right halo of q = 3, 6, 7 (lane 31, tail lanes)
+  uint32_t hl[4];       // words holding the left halo of q = 1, 5, 8 (lane 0)
+};
+constexpr int kPfBytesH = kWarps * int(sizeof(PfWarpH));
+static_assert(sizeof(PfWarpH) % 16 == 0, "16-byte aligned warp slots");
+
 // Dynamic shared memory of step_kernel_multi<S, MODE, AAR>: the row prefetch slots, or 0
-// where the kernel loads its rows directly (either collision takes the slots).
+// where the kernel loads its rows directly (either collision takes the FP32 slots; FP16
+// deviations stage their codes with BGK).
 template <class S, int MODE, bool AAR>
 __host__ __device__ constexpr int multi_prefetch_smem() {
-  return (KSS_MULTI_PREFETCH && std::is_same<S, float>::value && MODE == MODE_STD)
-             ? kPfBytes
-             : 0;
+  return !KSS_MULTI_PREFETCH || MODE != MODE_STD ? 0
+         : std::is_same<S, float>::value ? kPfBytes
+         : (std::is_same<S, __half>::value && !AAR) ? kPfBytesH
+                                                    : 0;
 }
 
 // ---------------------------------------------------------------- accumulators ----
@@ -1234,35 +1246,51 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
 // assemble_from_left / _right (the same codes, decoded by the same FMA).
 __device__ __forceinline__ uint32_t half_bits(__half h) { return __half_as_ushort(h); }
 
-template <bool CG>
-__device__ __forceinline__ void load_half_row(const StepParams<__half>& p, int j, int i0,
-                                              int lane, bool cv, F2 (&f)[9][2]) {
+// Source rows of q = 0..8 for row j (pull: row j - cy_q), warp-uniform.
+__device__ __forceinline__ void half_rows(const StepParams<__half>& p, int j,
+                                          const __half* (&r)[9]) {
   const __half* base = p.src + (long long)j * p.pitch;
   long long up, dn;  // rows j - 1 and j + 1
   row_neighbours(p, j, up, dn);
-  const __half* r[9] = {base,
-                        base + 1 * p.plane,
-                        base + 2 * p.plane + up,
-                        base + 3 * p.plane,
-                        base + 4 * p.plane + dn,
-                        base + 5 * p.plane + up,
-                        base + 6 * p.plane + up,
-                        base + 7 * p.plane + dn,
-                        base + 8 * p.plane + dn};
-  uint2 w[9];
+  r[0] = base;
+  r[1] = base + 1 * p.plane;
+  r[2] = base + 2 * p.plane + up;
+  r[3] = base + 3 * p.plane;
+  r[4] = base + 4 * p.plane + dn;
+  r[5] = base + 5 * p.plane + up;
+  r[6] = base + 6 * p.plane + up;
+  r[7] = base + 7 * p.plane + dn;
+  r[8] = base + 8 * p.plane + dn;
+}
+
+// The lane's code vectors w[q] of row j and the halo codes h[q] of the populations with
+// cx = +1 (q = 1, 5, 8: column i0 - 1, periodic; lane 0) and cx = -1 (q = 3, 6, 7: column
+// i0 + 4, or 0 at the row end; lane 31 and the lanes whose vector reaches the row end).
+template <bool CG>
+__device__ __forceinline__ void gather_half_row(const StepParams<__half>& p, int j, int i0,
+                                                int lane, bool cv, uint2 (&w)[9],
+                                                uint32_t (&h)[9]) {
+  const __half* r[9];
+  half_rows(p, j, r);
 #pragma unroll
   for (int q = 0; q < 9; ++q)
     w[q] = cv ? ld_pop<CG>(reinterpret_cast<const uint2*>(r[q] + i0)) : make_uint2(0u, 0u);
   const bool tail = i0 + 4 >= p.nx;
   const int cl = i0 == 0 ? p.nx - 1 : i0 - 1, cr = tail ? 0 : i0 + 4;
   const bool hl = lane == 0 && cv, hr = cv && (lane == 31 || tail);
-  uint32_t h[9];
   h[1] = hl ? half_bits(ld_pop<CG>(r[1] + cl)) : 0u;
   h[5] = hl ? half_bits(ld_pop<CG>(r[5] + cl)) : 0u;
   h[8] = hl ? half_bits(ld_pop<CG>(r[8] + cl)) : 0u;
   h[3] = hr ? half_bits(ld_pop<CG>(r[3] + cr)) : 0u;
   h[6] = hr ? half_bits(ld_pop<CG>(r[6] + cr)) : 0u;
   h[7] = hr ? half_bits(ld_pop<CG>(r[7] + cr)) : 0u;
+}
+
+// Pull along x and decode: w and h as gather_half_row leaves them.
+__device__ __forceinline__ void assemble_half_row(const StepParams<__half>& p, int i0, int lane,
+                                                  uint2 (&w)[9], const uint32_t (&h)[9],
+                                                  F2 (&f)[9][2]) {
+  const bool tail = i0 + 4 >= p.nx;
   // cx = +1 (q = 1, 5, 8): codes [left, h0, h1, h2]
 #pragma unroll
   for (int q : {1, 5, 8}) {
@@ -1293,6 +1321,72 @@ __device__ __forceinline__ void load_half_row(const StepParams<__half>& p, int j
     f[q][0] = fma2(pack2(a.x, a.y), c.inv, c.base);
     f[q][1] = fma2(pack2(b.x, b.y), c.inv, c.base);
   }
+}
+
+// ---- row prefetch of FP16 codes (the one-step {Kn, KL, neq} kernel) ----
+// As the FP32 multi-step kernels stage rows (PfWarp), each warp copies its next row's
+// codes into shared memory with cp.async before it computes the current row: nine 8-byte
+// vectors per lane, and for each halo code the aligned 4-byte word that holds it (cp.async
+// copies 4, 8 or 16 bytes; the row pitch is a multiple of 64 codes, so the word's other
+// code is inside the row).  Build knob: -DKSS_F16_PREFETCH=0 loads every row directly.
+#ifndef KSS_F16_PREFETCH
+#define KSS_F16_PREFETCH 1
+#endif
+
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// Copies of row j's codes into the warp's slots (committed as one group).
+__device__ __forceinline__ void pf_issue_half(const StepParams<__half>& p, PfWarpH* pw, int j,
+                                              int i0, int lane, bool cv) {
+  if (cv) {
+    const __half* r[9];
+    half_rows(p, j, r);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) cp_async8(&pw->pop[q][lane], r[q] + i0);
+    const bool tail = i0 + 4 >= p.nx;
+    if (lane == 0) {
+      const int cl = (i0 == 0 ? p.nx - 1 : i0 - 1) & ~1;
+      cp_async4(&pw->hl[0], r[1] + cl);
+      cp_async4(&pw->hl[1], r[5] + cl);
+      cp_async4(&pw->hl[2], r[8] + cl);
+    }
+    if (lane == 31 || tail) {
+      const int cr = tail ? 0 : i0 + 4;  // even: the word starts at the code
+      cp_async4(&pw->hr[0][lane], r[3] + cr);
+      cp_async4(&pw->hr[1][lane], r[6] + cr);
+      cp_async4(&pw->hr[2][lane], r[7] + cr);
+    }
+  }
+  cp_async_commit();
+}
+
+// The staged row back from the slots (after the copies of this lane completed).
+__device__ __forceinline__ void pf_read_half(const StepParams<__half>& p, const PfWarpH* pw,
+                                             int i0, int lane, bool cv, uint2 (&w)[9],
+                                             uint32_t (&h)[9]) {
+#pragma unroll
+  for (int q = 0; q < 9; ++q) w[q] = cv ? pw->pop[q][lane] : make_uint2(0u, 0u);
+  const bool tail = i0 + 4 >= p.nx;
+  const int cl = i0 == 0 ? p.nx - 1 : i0 - 1;
+  const int sh = (cl & 1) ? 16 : 0;  // the code's half of its word
+  const bool hl = lane == 0 && cv, hr = cv && (lane == 31 || tail);
+  h[1] = hl ? (pw->hl[0] >> sh) & 0xffffu : 0u;
+  h[5] = hl ? (pw->hl[1] >> sh) & 0xffffu : 0u;
+  h[8] = hl ? (pw->hl[2] >> sh) & 0xffffu : 0u;
+  h[3] = hr ? pw->hr[0][lane] & 0xffffu : 0u;
+  h[6] = hr ? pw->hr[1][lane] & 0xffffu : 0u;
+  h[7] = hr ? pw->hr[2][lane] & 0xffffu : 0u;
+}
+
+// Dynamic shared memory of step_kernel<S, MODE, ..., PF>: the FP16 row prefetch slots of
+// the one-step {Kn, KL, neq} kernel, or 0.
+template <class S, int MODE, bool PF>
+__host__ __device__ constexpr int step_prefetch_smem() {
+  return (PF && std::is_same<S, __half>::value && MODE == MODE_STD) ? kPfBytesH : 0;
 }
 
 // ---------------------------------------------------------------- the fused step ----
@@ -1338,8 +1432,7 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
 
   // row prefetch (see PfWarp): the warp's slots in dynamic shared memory, and the copies
   // of row jj into them
-  constexpr bool PF = PREFETCH && CG && PULL && STORE;
-  static_assert(!PF || std::is_same<S, float>::value, "prefetch: FP32 rows");
+  constexpr bool PF = PREFETCH && CG && PULL && STORE && std::is_same<S, float>::value;
   extern __shared__ __align__(16) unsigned char kss_dyn_smem[];
   PfWarp* const pw = reinterpret_cast<PfWarp*>(kss_dyn_smem) + warp;
   auto pf_issue = [&](int jj) {
@@ -1384,14 +1477,30 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
   }
 
   // FP16 deviations on the paired row: the pulled codes are assembled as binary16 words
-  // (load_half_row) and decoded in pairs
+  // (gather_half_row / assemble_half_row) and decoded in pairs; with PREFETCH each warp's
+  // next row is staged in shared memory (PfWarpH)
   constexpr bool kHalfPaired = KSS_ROW_PAIRED && std::is_same<S, __half>::value &&
-                               MODE != MODE_FULL && !AAR && PULL && !PF && V == 4;
+                               MODE != MODE_FULL && !AAR && PULL && V == 4;
+  constexpr bool kHalfPF = kHalfPaired && PREFETCH && STORE;
+  PfWarpH* const pwh = reinterpret_cast<PfWarpH*>(kss_dyn_smem) + warp;
+  if constexpr (kHalfPF) {
+    if (j0 + warp < j1) pf_issue_half(p, pwh, j0 + warp, i0, lane, cv);
+  }
   for (int j = j0 + warp; j < j1; j += kWarps) {
     uint32_t fbits;
     if constexpr (kHalfPaired) {
       F2 f[9][2];
-      load_half_row<CG>(p, j, i0, lane, cv, f);
+      uint2 w[9];
+      uint32_t h[9];
+      if constexpr (kHalfPF) {
+        cp_async_wait_all();
+        pf_read_half(p, pwh, i0, lane, cv, w, h);
+        __syncwarp();  // the row's reads precede the copies of the next row into the slots
+        if (j + kWarps < j1) pf_issue_half(p, pwh, j + kWarps, i0, lane, cv);
+      } else {
+        gather_half_row<CG>(p, j, i0, lane, cv, w, h);
+      }
+      assemble_half_row(p, i0, lane, w, h, f);
       fbits = fused_row_paired<S, MODE, STORE>(p, f, i0, j, cv, a_rho, a_jx, a_jy);
     } else {
     T ft[9][V];
@@ -1630,21 +1739,23 @@ __device__ __forceinline__ void ticket_and_finalize(const StepParams<S>& p, int 
   finalize_partials<S, kThreads>(p, nblocks);
 }
 
-// One CTA per block (bx, by) of a grid gx blocks wide, nblocks in all.
-template <class S, int MODE, bool PULL, bool STORE, bool AAR = false>
+// One CTA per block (bx, by) of a grid gx blocks wide, nblocks in all.  PF: the FP16 row
+// prefetch (the launch then gives the kernel step_prefetch_smem bytes of dynamic shared
+// memory).
+template <class S, int MODE, bool PULL, bool STORE, bool AAR = false, bool PF = false>
 __device__ __forceinline__ void step_cta(const StepParams<S>& p, const int bx, const int by,
                                          const int gx, const int nblocks) {
-  step_block<S, MODE, PULL, STORE, false, AAR>(p, bx, by, gx, p.part_sum, p.part_cnt);
+  step_block<S, MODE, PULL, STORE, false, AAR, PF>(p, bx, by, gx, p.part_sum, p.part_cnt);
   if (MODE != MODE_PLAIN) ticket_and_finalize<S>(p, nblocks, nblocks);
 }
 
 // AAR: the step with the two-relaxation collision in the region p.region (pull + store).
 
-template <class S, int MODE, bool PULL, bool STORE, bool AAR = false>
+template <class S, int MODE, bool PULL, bool STORE, bool AAR = false, bool PF = false>
 __global__ void __launch_bounds__(kThreads, step_min_blocks<S, MODE>())
 step_kernel(const StepParams<S> p) {
-  step_cta<S, MODE, PULL, STORE, AAR>(p, blockIdx.x, blockIdx.y, gridDim.x,
-                                      gridDim.x * gridDim.y);
+  step_cta<S, MODE, PULL, STORE, AAR, PF>(p, blockIdx.x, blockIdx.y, gridDim.x,
+                                          gridDim.x * gridDim.y);
 }
 
 // The same step with a persistent grid: CTA c takes blocks c, c + gridDim.x, ... of the

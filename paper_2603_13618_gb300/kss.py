@@ -121,6 +121,7 @@ _SIGNATURES = {
                                                                     _DP]),
     "kss_adjoint_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _DP, ctypes.c_int]),
     "kss_adjoint_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "kss_adjoint_set_multistep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "kss_step_f32_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                             ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
@@ -543,6 +544,11 @@ class Adjoint:
         self._check(self._lib.kss_adjoint_forward(self._h, ptrs[0][0], ptrs[1][0], ptrs[2][0],
                                                   wp, float(tau), dev.pop(), ctypes.byref(J)))
         return J.value
+
+    def set_multistep(self, on: bool) -> None:
+        """Reverse sweep in one cooperative launch per segment (True, the default) or one
+        launch per reverse step; the gradients are the same bit for bit."""
+        self._check(self._lib.kss_adjoint_set_multistep(self._h, int(bool(on))))
 
     def backward(self, device: bool = False):
         """(dJ/drho0 [ny, nx] float64, dJ/dtau) of the last forward pass."""

@@ -158,3 +158,25 @@ def test_repeated_calls_replay_the_recorded_sweeps():
             J0, g0, gt0 = fresh(tau, weight)
             assert J == J0 and gt == gt0
             np.testing.assert_array_equal(g, g0)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("n,N,E", [(96, 23, 5), (512, 200, 20), (70, 9, 9)])
+def test_multistep_reverse_sweep_equals_one_launch_per_step(prec, n, N, E):
+    """The reverse sweep of each segment in one cooperative launch (blocks waiting on their
+    neighbours' previous reverse step) gives the gradients of one launch per reverse step
+    bit for bit: the same per-block arithmetic, the same partials and order of addition."""
+    from paper_2603_13618_gb300 import kss
+
+    r, u, v = inputs.random_smooth(n, n - 3, seed=n + N, kmax=6, drho_amp=1e-2, mach=0.1)
+    out = []
+    for multi in (True, False):
+        adj = kss.Adjoint(n, n - 3, N, precision=prec, checkpoint_every=E)
+        adj.set_multistep(multi)
+        J = adj.forward(r, u, v, 0.6)
+        g, gt = adj.backward()
+        out.append((J, g, gt))
+        adj.close()
+    assert out[0][0] == out[1][0]
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
