@@ -325,6 +325,28 @@ def run_batch(args):
 ADJ_METRIC = "adjoint MLUPS (forward with checkpoints + reverse sweep), 1xGB300"
 
 
+def adjoint_roofline(n, N, E, ms):
+    """Algorithmic bytes of one gradient over its time: the forward's N - 1 plain steps and
+    the recomputed ones (72 B/LUP), the N - 1 reverse steps (108 B/LUP: f read, lambda read
+    and written), the objective and the projection (72 B/LUP each).  The 512^2 working set
+    (9.4 MB per state) lives in L2, so HBM is not the limit: launches and the latency of
+    each dependent step are."""
+    peak, kind = measured_peak()
+    recompute = 0
+    s0 = ((N - 2) // E) * E if N >= 2 else -1
+    while s0 >= 0:
+        recompute += min(s0 + E - 1, N - 2) - s0
+        s0 -= E
+    lups = n * n
+    bytes_ = lups * (72 * (N - 1) + 72 * recompute + 108 * (N - 1) + 72 * 2)
+    achieved = bytes_ / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": kind, "traffic": None,
+            "algorithmic_bytes_per_gradient": bytes_,
+            "note": "working set in L2 (512^2: 9.4 MB per state): bound by launches and the "
+                    "latency of each dependent step, not by HBM"}
+
+
 def adjoint_launches(N, E, multi=True):
     """Kernel launches of one gradient: the forward pass (equilibrium, N - 1 plain steps,
     the objective), then per segment of the reverse sweep its recomputed plain steps and
@@ -389,6 +411,7 @@ def run_adjoint(args):
         "config": {"workload": "gradient of the summed KL sensor of step 200 in rho0 and "
                                "tau, 512x512 FP32, checkpoint every 20, tau=0.6, seed 1361",
                    "nx": n, "ny": n, "nsteps": N, "checkpoint_every": E},
+        "roofline": adjoint_roofline(n, N, E, t_adj),
         "ms_gradient": t_adj, "ms_forward_plain": t_fwd, "adjoint_over_forward": t_adj / t_fwd,
         "grad_tau": gt, "grad_rho0_norm": float(torch.linalg.vector_norm(g)),
         "gpu_launches_per_gradient": adjoint_launches(N, E, multi=True),
@@ -644,10 +667,14 @@ def fp16_error(n, tau, kexp, gen, steps=500, window=256):
     wr, wu, wv = inputs.smooth_jump(n, n, x0=x0 - halo, y0=x0 - halo, wx=window + 2 * halo,
                                     wy=window + 2 * halo, **gen)
     t0 = time.perf_counter()
-    f = oracle.step(oracle.init_equilibrium(wr, wu, wv), tau, steps - 1)
-    sens, nonpos = oracle.sensor_fields(f, tau, pull=True)
-    f = oracle.step(f, tau)
-    rr, ru, rv = oracle.moments(f)
+    oracle.set_threads(oracle.host_cores())  # (bit-identical to one thread)
+    try:
+        f = oracle.step(oracle.init_equilibrium(wr, wu, wv), tau, steps - 1)
+        sens, nonpos = oracle.sensor_fields(f, tau, pull=True)
+        f = oracle.step(f, tau)
+        rr, ru, rv = oracle.moments(f)
+    finally:
+        oracle.set_threads(1)
     t_orc = time.perf_counter() - t0
     c = slice(halo, halo + window)
     ref = {"rho": rr[c, c], "ux": ru[c, c], "uy": rv[c, c]}

@@ -353,9 +353,14 @@ __device__ __forceinline__ bool adj_wait_ge(const uint32_t* p, uint32_t want, ui
   return true;
 }
 
+// Resident CTAs per SM requested from the register allocator for adj_multi_kernel (a
+// build-time tuning knob; 0 leaves the choice to the compiler).
+#ifndef KSS_ADJ_MULTI_MIN_BLOCKS
+#define KSS_ADJ_MULTI_MIN_BLOCKS 0
+#endif
 template <class T>
-__global__ void __launch_bounds__(kThreads) adj_multi_kernel(const AdjParams<T> base,
-                                                             const AdjMulti<T> m) {
+__global__ void __launch_bounds__(kThreads, KSS_ADJ_MULTI_MIN_BLOCKS)
+adj_multi_kernel(const AdjParams<T> base, const AdjMulti<T> m) {
   __shared__ int s_next, s_go, s_fin;
   __shared__ Red<T> s_red[kWarps];
   __shared__ Red<T> s_tot[kWarps];

@@ -11,6 +11,12 @@
 
 using namespace kss_rt;
 
+// Rows per CTA of the adjoint kernels: 0 takes fill_rows (the tallest of 32, 16, 8 that
+// still gives two CTAs per SM); 8, 16 or 32 fix it (a build-time tuning knob).
+#ifndef KSS_ADJ_ROWS
+#define KSS_ADJ_ROWS 0
+#endif
+
 struct kss_adjoint {
   kss_adjoint_config cfg{};
   int device = 0;
@@ -317,7 +323,7 @@ int kss_adjoint_create(const kss_adjoint_config* cfg, kss_adjoint** out) {
     cudaGetLastError();
     nsm = 1;
   }
-  A->adj_rows = kss::fill_rows(cfg->nx, cfg->ny, 32 * kss::kAdjV, nsm);
+  A->adj_rows = KSS_ADJ_ROWS ? KSS_ADJ_ROWS : kss::fill_rows(cfg->nx, cfg->ny, 32 * kss::kAdjV, nsm);
   A->step_rows = kss::fill_rows(cfg->nx, cfg->ny, 32 * (A->fp32 ? kss::Vec<float>::N : kss::Vec<double>::N), nsm);
   const dim3 g = kss::adj_grid(cfg->nx, cfg->ny, A->adj_rows);
   struct {

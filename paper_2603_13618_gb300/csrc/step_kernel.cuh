@@ -889,11 +889,12 @@ __device__ __forceinline__ F2 product2(F2 a, F2 b, F2 zero) { return fma2(a, b, 
 // Per-cell accumulators of the paired row: Kn and neq per pair, KL per pair.
 struct PairAcc {
   F2 kn[2], neq[2], kl[2];
+  F2 qe[2];  // two-relaxation steps only: the quasi-equilibrium sensor
 };
 
 // Relax one population (two pairs) toward its equilibrium feq and accumulate the sensor
 // terms, as relax_pop does per pair.
-template <bool OUT>
+template <bool OUT, bool COLLIDE = true>
 __device__ __forceinline__ void relax2(F2 (&f)[2], const F2 (&feq)[2], F2 nom, PairAcc& a) {
   constexpr int N = Num<float>::kPhiFastOrder;
   static_assert(N == 5, "series order of the paired row");
@@ -918,7 +919,7 @@ __device__ __forceinline__ void relax2(F2 (&f)[2], const F2 (&feq)[2], F2 nom, P
       acc = fma2(acc, x, splat2(float(PhiCoef<2>::value)));
       a.kl[m] = fma2(mul2(fneq, x), acc, a.kl[m]);
     }
-    f[m] = fma2(nom, fneq, f[m]);
+    if (COLLIDE) f[m] = fma2(nom, fneq, f[m]);
   }
 }
 
@@ -942,11 +943,53 @@ __device__ __forceinline__ void pair2(F2 (&fp)[2], F2 (&fm)[2], const F2 (&cu)[2
   if (STORE && cv) pop_store2<S>(dst_m, fm, pc);
 }
 
-template <class S, int MODE, bool STORE>
+// The same pair on a two-relaxation step (adaptive algorithm refinement): the sensors of
+// relax2, then in the cells whose region byte (in mbits) is set the coupled update
+// f'_q = f_q - A f^neq_q - B f^neq_-q of cell_update, and in the others BGK (A = 1/tau,
+// B = 0, which adds a zero product): the operations and roundings of pair_pops.
+template <class S, bool OUT, bool STORE>
+__device__ __forceinline__ void pair2_aar(F2 (&fp)[2], F2 (&fm)[2], const F2 (&cu)[2],
+                                          const F2 (&base)[2], const F2 (&rw)[2], F2 nom,
+                                          F2 zero, PairAcc& a, S* dst_p, S* dst_m,
+                                          const PairCodec<S>& pc, bool cv, uint32_t mbits,
+                                          float omega, const Trt<float>& trt) {
+  F2 ep[2], em[2];
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const F2 t = fma2(mul2(splat2(4.5f), cu[m]), cu[m], base[m]);
+    ep[m] = product2(rw[m], fma2(splat2(3.f), cu[m], t), zero);
+    em[m] = product2(rw[m], fma2(splat2(-3.f), cu[m], t), zero);
+  }
+  relax2<OUT, false>(fp, ep, nom, a);  // the sensors only
+  relax2<OUT, false>(fm, em, nom, a);
+  if (!STORE) return;
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const bool s0 = ((mbits >> (16 * m)) & 0xffu) != 0u;
+    const bool s1 = ((mbits >> (16 * m + 8)) & 0xffu) != 0u;
+    const F2 nA = pack2(s0 ? -trt.a : -omega, s1 ? -trt.a : -omega);
+    const F2 nB = pack2(s0 ? -trt.b : -0.f, s1 ? -trt.b : -0.f);
+    const F2 np = sub2(fp[m], ep[m]), nm = sub2(fm[m], em[m]);
+    if (OUT) {
+      float d0, d1, q0, q1;
+      unpack2(sub2(np, nm), d0, d1);
+      unpack2(a.qe[m], q0, q1);
+      a.qe[m] = pack2(q0 + fabsf(d0), q1 + fabsf(d1));
+    }
+    fp[m] = fma2(nB, nm, fma2(nA, np, fp[m]));
+    fm[m] = fma2(nB, np, fma2(nA, nm, fm[m]));
+  }
+  if (cv) {
+    pop_store2<S>(dst_p, fp, pc);
+    pop_store2<S>(dst_m, fm, pc);
+  }
+}
+
+template <class S, int MODE, bool STORE, bool AAR = false>
 __device__ __forceinline__ uint32_t fused_row_paired(const StepParams<S>& p,
                                                      F2 (&f)[9][2], int i0, int j, bool cv,
                                                      Acc<float>& a_rho, Acc<float>& a_jx,
-                                                     Acc<float>& a_jy) {
+                                                     Acc<float>& a_jy, uint32_t mbits = 0) {
   constexpr bool OUT = MODE != MODE_PLAIN;
   // row parts are the same for the whole warp (one row per warp): the lane's column is
   // added last, so that they stay warp-uniform
@@ -984,7 +1027,7 @@ __device__ __forceinline__ uint32_t fused_row_paired(const StepParams<S>& p,
     unpack2(rho, rs[2 * m], rs[2 * m + 1]);
     unpack2(jx, xs[2 * m], xs[2 * m + 1]);
     unpack2(jy, ys[2 * m], ys[2 * m + 1]);
-    a.kn[m] = a.neq[m] = a.kl[m] = splat2(0.f);
+    a.kn[m] = a.neq[m] = a.kl[m] = a.qe[m] = splat2(0.f);
   }
   if (OUT) {  // the row's moments, cell by cell in order (as the scalar row adds them)
     a_rho.add(((rs[0] + rs[1]) + rs[2]) + rs[3]);
@@ -1001,10 +1044,21 @@ __device__ __forceinline__ uint32_t fused_row_paired(const StepParams<S>& p,
     relax2<OUT>(f[0], feq, nom, a);
     if (STORE && cv) pop_store2<S>(dst + i0, f[0], c0);
   }
-  pair2<S, OUT, STORE>(f[1], f[3], ux, base, rw1, nom, zero, a, dst + 1 * p.plane + i0,
-                       dst + 3 * p.plane + i0, c1, cv);
-  pair2<S, OUT, STORE>(f[2], f[4], uy, base, rw1, nom, zero, a, dst + 2 * p.plane + i0,
-                       dst + 4 * p.plane + i0, c1, cv);
+  // the four opposite pairs: (1, 3) c.u = +-ux; (2, 4) +-uy; (5, 7) +-(ux + uy);
+  // (6, 8) +-(uy - ux)
+  auto pair = [&](F2 (&fp)[2], F2 (&fm)[2], const F2 (&cu)[2], const F2 (&rw)[2], int qp,
+                  int qm, const PairCodec<S>& pc) {
+    if constexpr (AAR) {
+      pair2_aar<S, OUT, STORE>(fp, fm, cu, base, rw, nom, zero, a, dst + qp * p.plane + i0,
+                               dst + qm * p.plane + i0, pc, cv, p.region ? mbits : 0u,
+                               p.omega, p.trt);
+    } else {
+      pair2<S, OUT, STORE>(fp, fm, cu, base, rw, nom, zero, a, dst + qp * p.plane + i0,
+                           dst + qm * p.plane + i0, pc, cv);
+    }
+  };
+  pair(f[1], f[3], ux, rw1, 1, 3, c1);
+  pair(f[2], f[4], uy, rw1, 2, 4, c1);
   {
     F2 sd[2], rw2[2];
 #pragma unroll
@@ -1012,19 +1066,18 @@ __device__ __forceinline__ uint32_t fused_row_paired(const StepParams<S>& p,
       sd[m] = add2(ux[m], uy[m]);
       rw2[m] = mul2(splat2(0.25f), rw1[m]);
     }
-    pair2<S, OUT, STORE>(f[5], f[7], sd, base, rw2, nom, zero, a, dst + 5 * p.plane + i0,
-                         dst + 7 * p.plane + i0, c5, cv);
+    pair(f[5], f[7], sd, rw2, 5, 7, c5);
 #pragma unroll
     for (int m = 0; m < 2; ++m) sd[m] = sub2(uy[m], ux[m]);
-    pair2<S, OUT, STORE>(f[6], f[8], sd, base, rw2, nom, zero, a, dst + 6 * p.plane + i0,
-                         dst + 8 * p.plane + i0, c5, cv);
+    pair(f[6], f[8], sd, rw2, 6, 8, c5);
   }
   uint32_t fbits = 0;
   if (OUT) {
     const Pick3 pr(p.refine_s), ps(p.switch_s);
-    float kn[4], neq[4], kl[4], rw[4], bs[4];
+    float kn[4], neq[4], kl[4], rw[4], bs[4], qe[4];
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
+      unpack2(a.qe[m], qe[2 * m], qe[2 * m + 1]);
       unpack2(a.kn[m], kn[2 * m], kn[2 * m + 1]);
       unpack2(a.neq[m], neq[2 * m], neq[2 * m + 1]);
       unpack2(abs2(a.kl[m]), kl[2 * m], kl[2 * m + 1]);
@@ -1036,14 +1089,20 @@ __device__ __forceinline__ uint32_t fused_row_paired(const StepParams<S>& p,
       // rho > 0 and |u|^2 < 0.3 make every f^eq_q >= 0.05 w_q rho > 0, and Kn < 1/16
       // bounds every |x_q| (see fused_row): otherwise the cell is deferred
       const bool fast = (rw[k] > 0.f) & (bs[k] > 0.55f) & (kn[k] < 0.0625f);
-      const bool r = pr(kn[k], kl[k], neq[k]) > p.thr_r;
-      const bool sw = p.switch_on && (ps(kn[k], kl[k], neq[k]) > p.thr_s);
+      const bool r = (AAR ? pr(kn[k], kl[k], neq[k], qe[k]) : pr(kn[k], kl[k], neq[k])) > p.thr_r;
+      const bool sw = p.switch_on &&
+                      ((AAR ? ps(kn[k], kl[k], neq[k], qe[k]) : ps(kn[k], kl[k], neq[k])) > p.thr_s);
       const uint32_t b = fast ? (uint32_t(r) | (uint32_t(sw) << 1)) : kFlagDeferred;
       fbits |= b << (8 * k);
     }
     if (nvalid < 4) fbits &= nvalid > 0 ? 0xffffffffu >> (32 - 8 * nvalid) : 0u;
     if (cv) {
       store_flags<4>(p.flags + row + i0, fbits);
+      // (a deferred cell's byte is 0x40: its region byte is set by the epilogue)
+      if (AAR && STORE && p.region) store_flags<4>(p.region + row + i0, (fbits >> 1) & 0x01010101u);
+      if (AAR && p.rec_slot[S_QE] >= 0)
+        __stcs(reinterpret_cast<float4*>(p.rec + p.rec_slot[S_QE] * p.plane + row + i0),
+               make_float4(qe[0], qe[1], qe[2], qe[3]));
       if (p.rec_slot[S_KN] >= 0)
         __stcs(reinterpret_cast<float4*>(p.rec + p.rec_slot[S_KN] * p.plane + row + i0),
                make_float4(kn[0], kn[1], kn[2], kn[3]));
@@ -1063,8 +1122,12 @@ __device__ __forceinline__ uint32_t fused_row_paired(const StepParams<S>& p,
 // sensors of the compiled set, flags, BGK collision, and the stores of the new
 // populations, the flag bytes and the recorded sensor fields.  ft holds the
 // post-streaming populations of cells i0..i0+V-1 of row j.  Returns the lane's flag
-// word (one byte per cell); the row's moments are added to the accumulators.
-template <class S, int MODE, bool PULL, bool STORE, bool AAR = false>
+// word (one byte per cell); the row's moments are added to the accumulators.  MULTI: the
+// row of a multi-step launch (whose two-relaxation row keeps the scalar form: the paired
+// one spills there and measured slower, 0.2257 vs 0.2133 ms per 4096^2 step, while it is
+// faster in one-step launches, 0.2375 vs 0.2769 ms; both give the same results bit for
+// bit).
+template <class S, int MODE, bool PULL, bool STORE, bool AAR = false, bool MULTI = false>
 __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
                                               arith_t<S> (&ft)[9][Vec<S>::N], int i0, int j,
                                               bool cv, Acc<arith_t<S>>& a_rho,
@@ -1119,7 +1182,8 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
       store_flags<V>(p.flags + off, fbits);
       if (AAR && STORE && p.region) store_flags<V>(p.region + off, (fbits >> 1) & 0x01010101u);
     }
-  } else if constexpr (KSS_ROW_PAIRED && std::is_same<T, float>::value && !AAR && V == 4) {
+  } else if constexpr (KSS_ROW_PAIRED && std::is_same<T, float>::value && V == 4 &&
+                       !(AAR && MULTI)) {
     // ---- the same row in paired instructions (fused_row_paired) ----
     F2 f[9][2];
 #pragma unroll
@@ -1127,7 +1191,7 @@ __device__ __forceinline__ uint32_t fused_row(const StepParams<S>& p,
       f[q][0] = pack2(ft[q][0], ft[q][1]);
       f[q][1] = pack2(ft[q][2], ft[q][3]);
     }
-    fbits = fused_row_paired<S, MODE, STORE>(p, f, i0, j, cv, a_rho, a_jx, a_jy);
+    fbits = fused_row_paired<S, MODE, STORE, AAR>(p, f, i0, j, cv, a_rho, a_jx, a_jy, mbits);
   } else {
     // ---- plain stream + collide, or with the {Kn, KL, neq} sensor set:
     //      population-major so each population's vector is stored as soon as it
@@ -1585,7 +1649,7 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
       }
     }
 
-    fbits = fused_row<S, MODE, PULL, STORE, AAR>(p, ft, i0, j, cv, a_rho, a_jx, a_jy, mbits);
+    fbits = fused_row<S, MODE, PULL, STORE, AAR, CG>(p, ft, i0, j, cv, a_rho, a_jx, a_jy, mbits);
     }
     if (OUT) {
       n_ref += __popc(fbits & 0x01010101u);
