@@ -349,15 +349,22 @@ def adjoint_roofline(n, N, E, ms):
 
 def adjoint_launches(N, E, multi=True):
     """Kernel launches of one gradient: the forward pass (equilibrium, N - 1 plain steps,
-    the objective), then per segment of the reverse sweep its recomputed plain steps and
-    its reverse steps (one cooperative launch and the ordered addition of its totals, or
-    one launch per reverse step), and the final projection."""
+    the last segment's states among them, and the objective), then per segment of the
+    reverse sweep, last first: one cooperative launch of its reverse steps that also
+    recomputes the previous segment, and the ordered addition of its totals (multi); or
+    its recomputed plain steps (all but the last segment) and one launch per reverse step.
+    Then the final projection."""
     fwd = 1 + (N - 1) + 1
     bwd = 1
     s0 = ((N - 2) // E) * E if N >= 2 else -1
+    first = True
     while s0 >= 0:
         last = min(s0 + E - 1, N - 2)
-        bwd += (last - s0) + (2 if multi else last - s0 + 1)
+        if multi:
+            bwd += 2
+        else:
+            bwd += (0 if first else last - s0) + (last - s0 + 1)
+        first = False
         s0 -= E
     return fwd + bwd
 

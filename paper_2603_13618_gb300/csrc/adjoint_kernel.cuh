@@ -53,6 +53,7 @@ struct AdjParams {
   int pitch, nx, ny;
   int rows;              // rows per CTA (grid adj_grid(nx, ny, rows))
   T omega;
+  T zero;                // 0, read at run time (see product2)
 };
 
 // Nine populations of V cells of row j pulled from src: forward (REV = false)
@@ -253,54 +254,168 @@ __global__ void __launch_bounds__(kThreads) adj_objective_kernel(const AdjParams
   adj_reduce<T>(p, sum);
 }
 
-// lt^n from l^{n+1} = S^T lt^{n+1} and ft^n = S f^n for the block (bx, by) of the adjoint
-// grid; returns the block's sum l^{n+1} . f^neq per thread (dJ/dtau = that sum over all
-// steps / tau^2).  CG: the adjoint buffers are written by other CTAs of the same launch
-// (the multi-step reverse sweep), so they are read with ordinary cached loads.
+// Paired FP32 form of the reverse step's cell arithmetic (KSS_ADJ_PAIRED): a thread's two
+// cells are one pair of the f32x2 instructions.  Moments and f^eq are rounded as the
+// forward step's paired row rounds them (fused_row_paired); the vector-Jacobian product is
+// regrouped per opposite pair (p, -p) of populations, with S = w (y_p + y_-p) and
+// D = w (y_p - y_-p) (D_p = D_-p, c_-p = -c_p):
+//   A = w_0 y_0 g + sum_pairs S (g - 9/2 (c_p.u)^2),                 g = 1 + 3/2 u.u
+//   B = sum_pairs c_p (3 D + 9 (c_p.u) S) - 3 u (w_0 y_0 + sum_pairs S),
+// the same sums as adj_moment_pullback in another order of rounding.
+#ifndef KSS_ADJ_PAIRED
+#define KSS_ADJ_PAIRED 1
+#endif
+
+__device__ __forceinline__ void adj_cell_pairs(const F2 (&c)[9], const F2 (&y)[9], F2 om,
+                                               F2 om1, F2 zero, F2 (&lt)[9], F2& rs) {
+  const F2 rho = add2(add2(add2(add2(c[0], c[1]), add2(c[2], c[3])),
+                           add2(add2(c[4], c[5]), add2(c[6], c[7]))),
+                      c[8]);
+  const F2 jx = sub2(add2(add2(c[1], c[5]), c[8]), add2(add2(c[3], c[6]), c[7]));
+  const F2 jy = sub2(add2(add2(c[2], c[5]), c[6]), add2(add2(c[4], c[7]), c[8]));
+  const F2 ir = rcp2(rho);
+  const F2 ux = mul2(jx, ir), uy = mul2(jy, ir);
+  const F2 uu = fma2(ux, ux, mul2(uy, uy));
+  const F2 base = fma2(splat2(-1.5f), uu, splat2(1.f));
+  const F2 r1 = mul2(rho, splat2(float(1.0 / 9.0)));
+  const F2 r2 = mul2(splat2(0.25f), r1);
+  const F2 sd[2] = {add2(ux, uy), sub2(uy, ux)};
+  // f^eq, and the dtau partial sum y . (c - f^eq)
+  F2 feq[9];
+  feq[0] = product2(mul2(splat2(4.f), r1), base, zero);
+  const F2 cu[4] = {ux, uy, sd[0], sd[1]};
+  constexpr int qp[4] = {1, 2, 5, 6}, qm[4] = {3, 4, 7, 8};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const F2 rw = k < 2 ? r1 : r2;
+    const F2 t = fma2(mul2(splat2(4.5f), cu[k]), cu[k], base);
+    feq[qp[k]] = product2(rw, fma2(splat2(3.f), cu[k], t), zero);
+    feq[qm[k]] = product2(rw, fma2(splat2(-3.f), cu[k], t), zero);
+  }
+  F2 acc = splat2(0.f);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) acc = fma2(y[q], sub2(c[q], feq[q]), acc);
+  rs = acc;
+  // A and B
+  const F2 g = fma2(splat2(1.5f), uu, splat2(1.f));
+  const F2 wy0 = mul2(splat2(float(4.0 / 9.0)), y[0]);
+  F2 a = mul2(wy0, g), sw = wy0, bx = splat2(0.f), by = splat2(0.f);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const F2 w = splat2(k < 2 ? float(1.0 / 9.0) : float(1.0 / 36.0));
+    const F2 S = mul2(w, add2(y[qp[k]], y[qm[k]]));
+    const F2 D = mul2(w, sub2(y[qp[k]], y[qm[k]]));
+    a = fma2(fma2(mul2(splat2(-4.5f), cu[k]), cu[k], g), S, a);
+    const F2 t = fma2(mul2(splat2(9.f), cu[k]), S, mul2(splat2(3.f), D));
+    // c_p = (1, 0), (0, 1), (1, 1), (-1, 1)
+    if (k == 0 || k == 2) bx = add2(bx, t);
+    if (k == 3) bx = sub2(bx, t);
+    if (k >= 1) by = add2(by, t);
+    sw = add2(sw, S);
+  }
+  bx = fma2(mul2(splat2(-3.f), ux), sw, bx);
+  by = fma2(mul2(splat2(-3.f), uy), sw, by);
+  // lt_q = (1 - omega) y_q + omega (A + c_q . B)
+  const F2 oa = mul2(om, a), obx = mul2(om, bx), oby = mul2(om, by);
+  const F2 ob[4] = {obx, oby, add2(obx, oby), sub2(oby, obx)};
+  lt[0] = fma2(om1, y[0], oa);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    lt[qp[k]] = fma2(om1, y[qp[k]], add2(oa, ob[k]));
+    lt[qm[k]] = fma2(om1, y[qm[k]], sub2(oa, ob[k]));
+  }
+}
+
+// One row j of the reverse step: lt^n from l^{n+1} = S^T lt^{n+1} (pulled here) and
+// ft^n = S f^n (pulled by the caller into ft); adds the row's l^{n+1} . f^neq to sum.
+// CG: the adjoint buffers are written by other CTAs of the same launch (the multi-step
+// reverse sweep), so they are read with ordinary cached loads.
 template <class T, bool CG>
-__device__ __forceinline__ Acc<T> adj_step_block(const AdjParams<T>& p, int bx, int by) {
+__device__ __forceinline__ void adj_step_row(const AdjParams<T>& p, int j, int i0, int lane,
+                                             bool cv, int nvalid, T (&ft)[9][kAdjV],
+                                             Acc<T>& sum) {
   constexpr int V = kAdjV;
   constexpr int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
   constexpr int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  const T om = p.omega, om1 = T(1) - p.omega;
+  T l[9][V];
+  adj_pull_row<T, true, CG>(p.lam_in, p.plane, p.pitch, p.nx, p.ny, j, i0, lane, cv, l);
+  adj_pad<T>(ft, nvalid, T(1));
+  adj_pad<T>(l, nvalid, T(0));
+  if constexpr (KSS_ADJ_PAIRED && std::is_same<T, float>::value && V == 2) {
+    F2 c[9], y[9], lt[9], rs2;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      c[q] = pack2(ft[q][0], ft[q][1]);
+      y[q] = pack2(l[q][0], l[q][1]);
+    }
+    adj_cell_pairs(c, y, splat2(om), splat2(om1), splat2(p.zero), lt, rs2);
+    float r0, r1;
+    unpack2(rs2, r0, r1);
+    sum.add(r0 + r1);
+    if (cv) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        unpack2(lt[q], l[q][0], l[q][1]);
+        vstore<T, V>(p.lam_out + q * p.plane + (long long)j * p.pitch + i0, l[q]);
+      }
+    }
+    return;
+  }
+  T rs = T(0);
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    T c[9], y[9], feq[9], ux, uy;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      c[q] = ft[q][k];
+      y[q] = l[q][k];
+    }
+    adj_cell_eq<T>(c, ux, uy, feq);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) rs = fma(y[q], c[q] - feq[q], rs);
+    T A, bx_, by_;
+    adj_moment_pullback<T>(y, ux, uy, A, bx_, by_);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const T cb = T(cx[q]) * bx_ + T(cy[q]) * by_;
+      l[q][k] = fma(om1, y[q], om * (A + cb));
+    }
+  }
+  sum.add(rs);
+  if (cv) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+      vstore<T, V>(p.lam_out + q * p.plane + (long long)j * p.pitch + i0, l[q]);
+  }
+}
+
+// The reverse step for the block (bx, by) of the adjoint grid; returns the block's sum
+// l^{n+1} . f^neq per thread (dJ/dtau = that sum over all steps / tau^2).  PRE: the
+// warp's first row of ft^n was pulled by the caller into ft0 (the multi-step sweep issues
+// those loads before it waits for its neighbours: the forward state is not written in
+// the launch).
+template <class T, bool CG, bool PRE = false>
+__device__ __forceinline__ Acc<T> adj_step_block(const AdjParams<T>& p, int bx, int by,
+                                                 T (*ft0)[kAdjV] = nullptr) {
+  constexpr int V = kAdjV;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i0 = (bx * 32 + lane) * V;
   const bool cv = i0 < p.nx;
   const int nvalid = cv ? min(V, p.nx - i0) : 0;
   const int j0 = by * p.rows, j1 = min(j0 + p.rows, p.ny);
-  const T om = p.omega, om1 = T(1) - p.omega;
   Acc<T> sum;
   for (int j = j0 + warp; j < j1; j += kWarps) {
-    T ft[9][V], l[9][V];
-    adj_pull_row<T, false>(p.f, p.plane, p.pitch, p.nx, p.ny, j, i0, lane, cv, ft);
-    adj_pull_row<T, true, CG>(p.lam_in, p.plane, p.pitch, p.nx, p.ny, j, i0, lane, cv, l);
-    adj_pad<T>(ft, nvalid, T(1));
-    adj_pad<T>(l, nvalid, T(0));
-    T rs = T(0);
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-      T c[9], y[9], feq[9], ux, uy;
-#pragma unroll
-      for (int q = 0; q < 9; ++q) {
-        c[q] = ft[q][k];
-        y[q] = l[q][k];
-      }
-      adj_cell_eq<T>(c, ux, uy, feq);
-#pragma unroll
-      for (int q = 0; q < 9; ++q) rs = fma(y[q], c[q] - feq[q], rs);
-      T A, bx_, by_;
-      adj_moment_pullback<T>(y, ux, uy, A, bx_, by_);
-#pragma unroll
-      for (int q = 0; q < 9; ++q) {
-        const T cb = T(cx[q]) * bx_ + T(cy[q]) * by_;
-        l[q][k] = fma(om1, y[q], om * (A + cb));
-      }
-    }
-    sum.add(rs);
-    if (cv) {
+    T ft[9][V];
+    if (PRE && j == j0 + warp) {
 #pragma unroll
       for (int q = 0; q < 9; ++q)
-        vstore<T, V>(p.lam_out + q * p.plane + (long long)j * p.pitch + i0, l[q]);
+#pragma unroll
+        for (int k = 0; k < V; ++k) ft[q][k] = ft0[q][k];
+    } else {
+      adj_pull_row<T, false>(p.f, p.plane, p.pitch, p.nx, p.ny, j, i0, lane, cv, ft);
     }
+    adj_step_row<T, CG>(p, j, i0, lane, cv, nvalid, ft, sum);
   }
   return sum;
 }
@@ -312,15 +427,49 @@ __global__ void __launch_bounds__(kThreads) adj_step_kernel(const AdjParams<T> p
 }
 
 // ---- the reverse sweep of one segment in one cooperative launch ----
-// Reverse iterations it = 0 .. nit - 1 (step k = last - it): work item w = it * nblocks + b
-// is block b of iteration it, handed out in order from an atomic counter.  Block b of
-// iteration it first waits until the blocks of its 3 x 3 neighbourhood (periodic) have
-// completed iteration it - 1: they wrote the adjoint cells its reverse pull reads, and have
-// read the cells it overwrites (the buffers alternate).  Every wait is bounded (bit 1 of the
-// error word on expiry).  Each block's partial of the dJ/dtau sum goes to part[it][b]; the
-// block completing iteration it last adds them as adj_reduce does and stores the
-// iteration's total in totals[it]; adj_add_totals then adds the totals in iteration order,
-// so the accumulator is that of one launch per step bit for bit.
+// Reverse iterations it = 0 .. nit - 1 (step k = last - it), each over the nblocks blocks of
+// the adjoint grid.  Block b of iteration it first waits until the blocks of its 3 x 3
+// neighbourhood (periodic) have completed iteration it - 1: they wrote the adjoint cells its
+// reverse pull reads, and have read the cells it overwrites (the buffers alternate).  Each
+// block's partial of the dJ/dtau sum goes to part[it][b].  After the launch,
+// adj_iteration_totals adds each iteration's partials as adj_reduce does, and the
+// iteration totals to the accumulator in iteration order, so the accumulator is that of
+// one launch per step bit for bit (and no block of the sweep waits for a counter of its
+// iteration before it takes its next item).
+//
+// The same launch recomputes the previous segment (fsteps > 0): its plain forward steps
+// t = 1 .. fsteps from the checkpoint fck into the states fseg + t (the forward step's own
+// CTA body over the forward grid, fnblocks blocks).  Those states are not read by the
+// reverse iterations of this launch (they belong to the next launch), and the reverse
+// sweep's latency-bound waits leave the SMs idle enough to take them.  Forward block fb of
+// step t waits until its 3 x 3 neighbourhood has completed step t - 1 (the rows its pull
+// reads); every state has a slot of its own, so nothing else is overwritten.
+//
+// Work items are handed out in order from an atomic counter, in rounds: round r holds the
+// reverse iteration r (if r < nit) and the forward step r + 1 (if r < fsteps).  Every item
+// waits only for items handed out before it (in its own chain), so the smallest unfinished
+// item can always proceed: no deadlock, given co-residency (the cooperative launch).  Every
+// wait is bounded (bit 1 of the error word on expiry).
+// Resident CTAs per SM requested from the register allocator for the FP32 adj_multi_kernel
+// (a build-time tuning knob; FP64 takes the registers it needs).  Measured at 512^2 with
+// the paired cell arithmetic: three (80 registers, a little spilling) 2.551 ms per
+// gradient, four (64) 2.618 ms; with the scalar arithmetic three 2.609, four 2.634-2.698,
+// two (128 registers) 3.144 and five (48 registers, 484 bytes of spills) 3.492 ms.  The
+// sweep is bound by the latency of its dependent items, so more of them in flight pays
+// more than registers, up to the point where spills lengthen each item.
+#ifndef KSS_ADJ_MULTI_MIN_BLOCKS
+#define KSS_ADJ_MULTI_MIN_BLOCKS 3
+#endif
+// Sleep between two polls of a neighbour's counter, in nanoseconds (0: poll back to back).
+#ifndef KSS_ADJ_POLL_NS
+#define KSS_ADJ_POLL_NS 64
+#endif
+// Order within a round of adj_multi_kernel's work items: the reverse iteration first (0) or
+// the forward step first (1); either order keeps each chain's items in order.
+#ifndef KSS_ADJ_FWD_FIRST
+#define KSS_ADJ_FWD_FIRST 0
+#endif
+
 template <class T>
 struct AdjMulti {
   const T* ck;         // the segment's checkpoint state (step s0)
@@ -329,7 +478,7 @@ struct AdjMulti {
   const T* lam0;       // adjoint ping-pong: iteration it reads lam(lc + it), writes
   const T* lam1;       // lam(lc + it + 1), lam(k) = lam0 for even k, lam1 for odd
   uint32_t* done;      // [nblocks] iterations each block completed (0 at launch)
-  uint32_t* ticket;    // [nit] blocks of each iteration completed (0 at launch)
+  uint32_t* ticket;    // adj_iteration_totals' block counter (0 at launch)
   uint32_t* work;      // next work item (0 at launch)
   double* part;        // [nit][nblocks]
   double* totals;      // [nit]
@@ -337,7 +486,20 @@ struct AdjMulti {
   long long deadline;  // clock64 cycles one wait may take
   int s0, last, lc;
   int gx, gy, nblocks;  // the adjoint grid (adj_grid): gx x gy blocks
+  // the previous segment's recomputation (fsteps = 0: none)
+  StepParams<T> fp;    // plain step parameters (src and dst are set per step)
+  const T* fck;        // its checkpoint (state 0)
+  T* fseg;             // its states 1 .. fsteps at fseg + t state_elems
+  uint32_t* fdone;     // [fnblocks] forward steps each block completed (0 at launch)
+  int fsteps;
+  int fgx, fgy, fnblocks;  // the forward step grid (step_grid)
 };
+
+// Orders this thread's earlier memory operations, and those it observed (through the
+// CTA barrier before it), before its later ones at GPU scope (a release fence).
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
 
 __device__ __forceinline__ bool adj_wait_ge(const uint32_t* p, uint32_t want, uint32_t* err,
                                             long long deadline) {
@@ -348,96 +510,162 @@ __device__ __forceinline__ bool adj_wait_ge(const uint32_t* p, uint32_t want, ui
       atomicOr(err, 2u);
       return false;
     }
-    __nanosleep(64);
+    if (KSS_ADJ_POLL_NS > 0) __nanosleep(KSS_ADJ_POLL_NS);
   }
   return true;
 }
 
-// Resident CTAs per SM requested from the register allocator for adj_multi_kernel (a
-// build-time tuning knob; 0 leaves the choice to the compiler).
-#ifndef KSS_ADJ_MULTI_MIN_BLOCKS
-#define KSS_ADJ_MULTI_MIN_BLOCKS 0
-#endif
+// Warp 0: lanes 0..8 wait (bounded) until the 3 x 3 neighbourhood of block (bx, by) of a
+// gx x gy grid has done[] >= want; lane 0 also takes the CTA's next work item.  Returns,
+// to every thread after the barrier, whether all waits succeeded.
+__device__ __forceinline__ bool adj_wait_neighbours(const uint32_t* done, int bx, int by,
+                                                    int gx, int gy, uint32_t want, bool wait,
+                                                    uint32_t* work, int* s_next, int* s_go,
+                                                    uint32_t* err, long long deadline) {
+  if (threadIdx.x < 32) {
+    const int t = threadIdx.x;
+    if (t == 0) *s_next = int(atomicAdd(work, 1u));
+    bool ok = true;
+    if (wait && t < 9) {
+      const int dy = t / 3 - 1, dx = t - 3 * (t / 3) - 1;
+      const int yy = by + dy < 0 ? gy - 1 : (by + dy == gy ? 0 : by + dy);
+      const int xx = bx + dx < 0 ? gx - 1 : (bx + dx == gx ? 0 : bx + dx);
+      ok = adj_wait_ge(done + yy * gx + xx, want, err, deadline);
+    }
+    ok = __all_sync(kFull, ok);
+    if (t == 0) *s_go = ok;
+  }
+  __syncthreads();
+  return *s_go != 0;
+}
+
 template <class T>
-__global__ void __launch_bounds__(kThreads, KSS_ADJ_MULTI_MIN_BLOCKS)
+__global__ void __launch_bounds__(kThreads,
+                                  std::is_same<T, float>::value ? KSS_ADJ_MULTI_MIN_BLOCKS : 1)
 adj_multi_kernel(const AdjParams<T> base, const AdjMulti<T> m) {
-  __shared__ int s_next, s_go, s_fin;
+  __shared__ int s_next, s_go;
   __shared__ Red<T> s_red[kWarps];
-  __shared__ Red<T> s_tot[kWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gx = m.gx, gy = m.gy;
   const int nit = m.last - m.s0 + 1;
-  const int total = nit * m.nblocks;
+  const int both = min(nit, m.fsteps);
+  const int round = m.nblocks + m.fnblocks;
+  const int total = nit * m.nblocks + m.fsteps * m.fnblocks;
   if (threadIdx.x == 0) s_next = int(atomicAdd(m.work, 1u));
   __syncthreads();
   int w = s_next;
   while (w < total) {
-    const int it = w / m.nblocks, b = w - it * m.nblocks;
-    const int by = b / gx, bx = b - by * gx;
-    __syncthreads();  // every thread has read s_next before thread 0 rewrites it
-    if (threadIdx.x < 32) {
-      const int t = threadIdx.x;
-      if (t == 0) s_next = int(atomicAdd(m.work, 1u));
-      bool ok = true;
-      if (it > 0 && t < 9) {
-        const int dy = t / 3 - 1, dx = t - 3 * (t / 3) - 1;
-        const int yy = by + dy < 0 ? gy - 1 : (by + dy == gy ? 0 : by + dy);
-        const int xx = bx + dx < 0 ? gx - 1 : (bx + dx == gx ? 0 : bx + dx);
-        ok = adj_wait_ge(m.done + yy * gx + xx, uint32_t(it), m.err, m.deadline);
+    // the item: reverse iteration it, block b; or forward step t, block b
+    int it = -1, t = 0, b;
+    if (w < both * round) {
+      const int r = w / round, o = w - r * round;
+      if (KSS_ADJ_FWD_FIRST ? o >= m.fnblocks : o < m.nblocks) {
+        it = r;
+        b = KSS_ADJ_FWD_FIRST ? o - m.fnblocks : o;
+      } else {
+        t = r + 1;
+        b = KSS_ADJ_FWD_FIRST ? o : o - m.nblocks;
       }
-      ok = __all_sync(kFull, ok);
-      if (t == 0) s_go = ok;
+    } else {
+      const int w2 = w - both * round;
+      if (nit > both) {
+        it = both + w2 / m.nblocks;
+        b = w2 - (it - both) * m.nblocks;
+      } else {
+        const int r = w2 / m.fnblocks;
+        t = both + 1 + r;
+        b = w2 - r * m.fnblocks;
+      }
     }
-    __syncthreads();
-    if (!s_go) return;
+    if (it < 0) {  // ---- a forward step of the previous segment's recomputation
+      const int fby = b / m.fgx, fbx = b - fby * m.fgx;
+      __syncthreads();  // every thread has read s_next before thread 0 rewrites it
+      if (!adj_wait_neighbours(m.fdone, fbx, fby, m.fgx, m.fgy, uint32_t(t - 1), t > 1, m.work,
+                               &s_next, &s_go, m.err, m.deadline))
+        return;
+      StepParams<T> q = m.fp;
+      q.src = t == 1 ? m.fck : m.fseg + (long long)(t - 1) * m.state_elems;
+      q.dst = m.fseg + (long long)t * m.state_elems;
+      step_block<T, MODE_PLAIN, true, true, true>(q, fbx, fby, m.fgx, nullptr, nullptr);
+      __syncthreads();  // every store of the block precedes thread 0's release
+      w = s_next;
+      // (the other warps go on to their next item meanwhile; the barrier before its
+      // wait keeps s_next until everyone has read it)
+      if (threadIdx.x == 0) {
+        fence_acq_rel_gpu();
+        st_release_u32(m.fdone + b, uint32_t(t));
+      }
+      continue;
+    }
+    // ---- a reverse iteration of this segment
+    const int by = b / gx, bx = b - by * gx;
     const int k = m.last - it;
     AdjParams<T> p = base;
     p.f = k == m.s0 ? m.ck : m.seg + (long long)(k - m.s0) * m.state_elems;
     const bool odd = ((m.lc + it) & 1) != 0;
     p.lam_in = odd ? m.lam1 : m.lam0;
     p.lam_out = const_cast<T*>(odd ? m.lam0 : m.lam1);
-    Acc<T> sum = adj_step_block<T, true>(p, bx, by);
-    // the block's partial, as adj_reduce forms it
+    // the warp's first row of the forward state (written before the launch), pulled
+    // while the block waits for its neighbours
+    T ft0[9][kAdjV];
+    {
+      const int i0 = (bx * 32 + lane) * kAdjV, jf = by * p.rows + warp;
+      if (jf < min(by * p.rows + p.rows, p.ny))
+        adj_pull_row<T, false>(p.f, p.plane, p.pitch, p.nx, p.ny, jf, i0, lane, i0 < p.nx,
+                               ft0);
+    }
+    __syncthreads();  // every thread has read s_next before thread 0 rewrites it
+    if (!adj_wait_neighbours(m.done, bx, by, gx, gy, uint32_t(it), it > 0, m.work, &s_next,
+                             &s_go, m.err, m.deadline))
+      return;
+    Acc<T> sum = adj_step_block<T, true, true>(p, bx, by, ft0);
+    // the neighbours wait only for the adjoint stores: the release comes first, then the
+    // block's partial (read after the launch), as adj_reduce forms it
     sum.warp_reduce();
     if (lane == 0) s_red[warp] = Red<T>::of(sum);
-    __syncthreads();  // (also: every store of the block precedes thread 0's release)
-    double* part = m.part + (long long)it * m.nblocks;
-    if (threadIdx.x == 0) {
-      Red<T> t;
-      for (int q = 0; q < kWarps; ++q) t.add(s_red[q]);
-      t.store(part + b);
-      __threadfence();
-      st_release_u32(m.done + b, uint32_t(it + 1));
-      s_fin = atomicAdd(m.ticket + it, 1u) == uint32_t(m.nblocks - 1);
-    }
-    __syncthreads();
-    if (s_fin) {  // the iteration's total, in adj_reduce's order
-      __threadfence();
-      Red<T> t;
-      for (int q = threadIdx.x; q < m.nblocks; q += kThreads) t.add(Red<T>::load(part + q));
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) t.add(t.shfl_xor(off));
-      if (lane == 0) s_tot[warp] = t;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        Red<T> r = s_tot[0];
-        for (int q = 1; q < kWarps; ++q) r.add(s_tot[q]);
-        m.totals[it] = r.value();
-      }
-    }
-    __syncthreads();
+    __syncthreads();  // every store of the block precedes thread 0's release
     w = s_next;
+    // (as above; s_red is rewritten only after the next item's barriers)
+    if (threadIdx.x == 0) {
+      fence_acq_rel_gpu();
+      st_release_u32(m.done + b, uint32_t(it + 1));
+      Red<T> r;
+      for (int q = 0; q < kWarps; ++q) r.add(s_red[q]);
+      r.store(m.part + (long long)it * m.nblocks + b);
+    }
   }
 }
 
-// *acc += totals[0] + ... in iteration order, one addition each (as one launch per step
-// adds its total).  (A template, instantiated per storage type, so that the header can be
-// included by several translation units.)
+// Block it: the total of iteration it's per-block partials part[it][0 .. nblocks - 1],
+// added as adj_reduce adds one launch's partials, into totals[it].  The block finishing
+// last (count, 0 at launch) then does *acc += totals[0] + ... in iteration order, one
+// addition each (as one launch per step adds its total).
 template <class T>
-__global__ void adj_add_totals(const double* totals, int n, double* acc) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
+__global__ void __launch_bounds__(kThreads)
+adj_iteration_totals(const double* part, int nblocks, int nit, double* totals,
+                     uint32_t* count, double* acc) {
+  __shared__ Red<T> s_tot[kWarps];
+  __shared__ int s_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, it = blockIdx.x;
+  const double* pp = part + (long long)it * nblocks;
+  Red<T> r;
+  for (int q = threadIdx.x; q < nblocks; q += kThreads) r.add(Red<T>::load(pp + q));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) r.add(r.shfl_xor(off));
+  if (lane == 0) s_tot[warp] = r;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Red<T> r2 = s_tot[0];
+    for (int q = 1; q < kWarps; ++q) r2.add(s_tot[q]);
+    totals[it] = r2.value();
+    __threadfence();
+    s_last = atomicAdd(count, 1u) == uint32_t(nit - 1);
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
     double a = *acc;
-    for (int i = 0; i < n; ++i) a += totals[i];
+    for (int i = 0; i < nit; ++i) a += __ldcg(totals + i);
     *acc = a;
   }
 }

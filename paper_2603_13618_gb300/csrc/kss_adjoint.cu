@@ -29,7 +29,11 @@ struct kss_adjoint {
   int adj_rows = 32;       // rows per CTA of the adjoint kernels (fill_rows)
   int step_rows = 32;      // rows per CTA of the forward steps (fill_rows)
   unsigned char* ck = nullptr;   // nck states
-  unsigned char* seg = nullptr;  // checkpoint_every states: a recomputed segment
+  // two buffers of checkpoint_every states: a segment's states (slot k - s0 for step k,
+  // slot 0 unused: that state is the checkpoint), the last segment's written by the
+  // forward pass, the others recomputed; segment i (counted from the last) uses seg[i & 1]
+  unsigned char* seg = nullptr;
+  unsigned char* seg2 = nullptr;
   unsigned char* work[2] = {nullptr, nullptr};  // forward ping-pong
   unsigned char* lam[2] = {nullptr, nullptr};   // adjoint ping-pong
   void* wplane = nullptr;    // weights, one pitched plane of T
@@ -42,7 +46,7 @@ struct kss_adjoint {
   // the per-block partials and the iteration totals
   bool multi = true;
   int multi_ctas = 0;
-  uint32_t* mcount = nullptr;  // [nblocks] done, [E] tickets, [1] work
+  uint32_t* mcount = nullptr;  // [nblocks] done, [E] tickets, [1] work, [fnblocks] fdone
   double* mpart = nullptr;     // [E][nblocks]
   double* mtot = nullptr;      // [E]
   cudaStream_t stream = nullptr;
@@ -78,9 +82,9 @@ void free_all(kss_adjoint* A) {
   if (!A) return;
   DeviceGuard g(A->device);
   cudaStreamSynchronize(A->stream);
-  void* bufs[] = {A->ck,     A->seg,    A->work[0], A->work[1], A->lam[0], A->lam[1],
-                  A->wplane, A->fields, A->grad,    A->part,    A->small,   A->mcount,
-                  A->mpart,  A->mtot};
+  void* bufs[] = {A->ck,     A->seg,    A->seg2,  A->work[0], A->work[1],
+                  A->lam[0], A->lam[1], A->wplane, A->fields, A->grad,
+                  A->part,   A->small,  A->mcount, A->mpart,  A->mtot};
   for (void* b : bufs)
     if (b) kss_rt::dev_free(b);
   if (A->g_fwd) cudaGraphExecDestroy(A->g_fwd);
@@ -94,9 +98,9 @@ unsigned char* state_at(kss_adjoint* A, unsigned char* base, long long k) {
   return base + size_t(k) * A->state_bytes;
 }
 
-// One plain forward step (stream + collide, no outputs) from src to dst.
+// Parameters of a plain forward step (stream + collide, no outputs) from src to dst.
 template <class T>
-cudaError_t plain_step(const kss_adjoint* A, const void* src, void* dst, cudaStream_t s) {
+kss::StepParams<T> plain_params(const kss_adjoint* A, const void* src, void* dst) {
   kss::StepParams<T> p{};
   p.src = static_cast<const T*>(src);
   p.dst = static_cast<T*>(dst);
@@ -111,7 +115,25 @@ cudaError_t plain_step(const kss_adjoint* A, const void* src, void* dst, cudaStr
   p.omega = T(1.0 / A->tau);
   p.tau = T(A->tau);
   for (int s = 0; s < KSS_S_COUNT; ++s) p.rec_slot[s] = -1;
-  return kss::launch_step<T>(p, kss::MODE_PLAIN, true, true, s);
+  return p;
+}
+
+// One plain forward step from src to dst.
+template <class T>
+cudaError_t plain_step(const kss_adjoint* A, const void* src, void* dst, cudaStream_t s) {
+  return kss::launch_step<T>(plain_params<T>(A, src, dst), kss::MODE_PLAIN, true, true, s);
+}
+
+// The forward step grid of the plain steps (plain_params: tile 8, step_rows rows).
+template <class T>
+dim3 plain_grid(const kss_adjoint* A) {
+  return kss::step_grid<T>(A->cfg.nx, A->cfg.ny, 8, A->step_rows / 8);
+}
+
+// First step of the last segment of states f^0 .. f^{N-2} that the reverse sweep needs.
+int last_segment(const kss_adjoint* A) {
+  const int N = A->cfg.nsteps, E = A->cfg.checkpoint_every;
+  return N >= 2 ? ((N - 2) / E) * E : -1;
 }
 
 template <class T>
@@ -140,10 +162,15 @@ cudaError_t forward_launches(kss_adjoint* A, cudaStream_t s) {
                                                   reinterpret_cast<T*>(A->ck), A->plane,
                                                   A->pitch, A->cfg.nx, A->cfg.ny,
                                                   kss::codec_t<T>{}, s);
-  // f^k for k = 1 .. N-1: checkpoints land in their slot, the others alternate in work[]
+  // f^k for k = 1 .. N-1: checkpoints land in their slot, the last segment's states in
+  // seg[0] (the reverse sweep reads them without recomputing), the others alternate in
+  // work[]
+  const int sl = last_segment(A);
   const void* cur = A->ck;
   for (int k = 1; k < N && e == cudaSuccess; ++k) {
-    void* dst = (k % E == 0) ? state_at(A, A->ck, k / E) : A->work[k & 1];
+    void* dst = (k % E == 0)         ? state_at(A, A->ck, k / E)
+                : (sl >= 0 && k > sl && k <= N - 2) ? state_at(A, A->seg, k - sl)
+                                                    : A->work[k & 1];
     e = plain_step<T>(A, cur, dst, s);
     cur = dst;
   }
@@ -167,28 +194,40 @@ cudaError_t backward_launches(kss_adjoint* A, cudaStream_t s) {
   p.acc = acc_at(A, 1);
   cudaError_t e = cudaSuccess;
   // segments [s0, last] of the states f^0 .. f^{N-2} that the reverse sweep needs,
-  // last segment first; slot 0 of a segment is its checkpoint
-  for (int s0 = N >= 2 ? ((N - 2) / E) * E : -1; s0 >= 0 && e == cudaSuccess; s0 -= E) {
+  // last segment first (i = 0, 1, ...); slot 0 of a segment is its checkpoint, its other
+  // states are in seg[i & 1]: the last segment's from the forward pass, each other one
+  // recomputed -- by the previous segment's cooperative launch (fused), or by plain steps
+  // before its own reverse steps
+  const bool fused = A->multi && A->multi_ctas > 0;
+  const dim3 g = kss::adj_grid(A->cfg.nx, A->cfg.ny, A->adj_rows);
+  const dim3 fg = plain_grid<T>(A);
+  const int nblocks = int(g.x * g.y), fnblocks = int(fg.x * fg.y);
+  auto segbuf = [&](int i) { return (i & 1) ? A->seg2 : A->seg; };
+  int i = 0;
+  for (int s0 = last_segment(A); s0 >= 0 && e == cudaSuccess; s0 -= E, ++i) {
     const int last = std::min(s0 + E - 1, N - 2);
+    unsigned char* sb = segbuf(i);
     auto state = [&](int k) -> const void* {
       return k == s0 ? static_cast<const void*>(state_at(A, A->ck, s0 / E))
-                     : static_cast<const void*>(state_at(A, A->seg, k - s0));
+                     : static_cast<const void*>(state_at(A, sb, k - s0));
     };
-    for (int k = s0 + 1; k <= last && e == cudaSuccess; ++k)
-      e = plain_step<T>(A, state(k - 1), const_cast<void*>(state(k)), s);
-    if (A->multi && A->multi_ctas > 0 && e == cudaSuccess) {
-      // the segment's reverse steps in one cooperative launch (adj_multi_kernel)
-      const dim3 g = kss::adj_grid(A->cfg.nx, A->cfg.ny, A->adj_rows);
-      const int nblocks = int(g.x * g.y), nit = last - s0 + 1;
+    if (i > 0 && !fused)
+      for (int k = s0 + 1; k <= last && e == cudaSuccess; ++k)
+        e = plain_step<T>(A, state(k - 1), const_cast<void*>(state(k)), s);
+    if (fused && e == cudaSuccess) {
+      // the segment's reverse steps in one cooperative launch (adj_multi_kernel), which
+      // also recomputes the previous segment [s0 - E, s0 - 1] into seg[(i + 1) & 1]
+      const int nit = last - s0 + 1;
       kss::AdjMulti<T> m{};
       m.ck = static_cast<const T*>(state(s0));
-      m.seg = reinterpret_cast<const T*>(A->seg);
+      m.seg = reinterpret_cast<const T*>(sb);
       m.state_elems = (long long)(A->state_bytes / A->esz);
       m.lam0 = reinterpret_cast<const T*>(A->lam[0]);
       m.lam1 = reinterpret_cast<const T*>(A->lam[1]);
       m.done = A->mcount;
       m.ticket = A->mcount + nblocks;
       m.work = A->mcount + nblocks + A->cfg.checkpoint_every;
+      m.fdone = m.work + 1;
       m.part = A->mpart;
       m.totals = A->mtot;
       m.err = reinterpret_cast<uint32_t*>(A->small + 128);
@@ -199,9 +238,22 @@ cudaError_t backward_launches(kss_adjoint* A, cudaStream_t s) {
       m.gx = int(g.x);
       m.gy = int(g.y);
       m.nblocks = nblocks;
+      if (s0 > 0) {
+        unsigned char* nb = segbuf(i + 1);
+        m.fp = plain_params<T>(A, nullptr, nullptr);
+        m.fck = reinterpret_cast<const T*>(state_at(A, A->ck, s0 / E - 1));
+        m.fseg = reinterpret_cast<T*>(nb);
+        m.fsteps = E - 1;
+        m.fgx = int(fg.x);
+        m.fgy = int(fg.y);
+        m.fnblocks = fnblocks;
+      }
       e = cudaMemsetAsync(A->mcount, 0,
-                          sizeof(uint32_t) * (size_t(nblocks) + A->cfg.checkpoint_every + 1), s);
-      const int ctas = std::min(A->multi_ctas, nit * nblocks);
+                          sizeof(uint32_t) * (size_t(nblocks) + A->cfg.checkpoint_every + 1 +
+                                              size_t(fnblocks)),
+                          s);
+      const int items = nit * nblocks + m.fsteps * m.fnblocks;
+      const int ctas = std::min(A->multi_ctas, items);
       if (e == cudaSuccess) e = kss::launch_adj_multi<T>(p, m, ctas, p.acc, s);
       lc ^= nit & 1;
       continue;
@@ -326,12 +378,14 @@ int kss_adjoint_create(const kss_adjoint_config* cfg, kss_adjoint** out) {
   A->adj_rows = KSS_ADJ_ROWS ? KSS_ADJ_ROWS : kss::fill_rows(cfg->nx, cfg->ny, 32 * kss::kAdjV, nsm);
   A->step_rows = kss::fill_rows(cfg->nx, cfg->ny, 32 * (A->fp32 ? kss::Vec<float>::N : kss::Vec<double>::N), nsm);
   const dim3 g = kss::adj_grid(cfg->nx, cfg->ny, A->adj_rows);
+  const dim3 fg = A->fp32 ? plain_grid<float>(A) : plain_grid<double>(A);
   struct {
     void** p;
     size_t bytes;
   } allocs[] = {
       {reinterpret_cast<void**>(&A->ck), A->state_bytes * size_t(A->nck)},
       {reinterpret_cast<void**>(&A->seg), A->state_bytes * size_t(A->cfg.checkpoint_every)},
+      {reinterpret_cast<void**>(&A->seg2), A->state_bytes * size_t(A->cfg.checkpoint_every)},
       {reinterpret_cast<void**>(&A->work[0]), A->state_bytes},
       {reinterpret_cast<void**>(&A->work[1]), A->state_bytes},
       {reinterpret_cast<void**>(&A->lam[0]), A->state_bytes},
@@ -342,7 +396,7 @@ int kss_adjoint_create(const kss_adjoint_config* cfg, kss_adjoint** out) {
       {reinterpret_cast<void**>(&A->part), size_t(g.x) * g.y * sizeof(double)},
       {reinterpret_cast<void**>(&A->small), 256},
       {reinterpret_cast<void**>(&A->mcount),
-       sizeof(uint32_t) * (size_t(g.x) * g.y + A->cfg.checkpoint_every + 1)},
+       sizeof(uint32_t) * (size_t(g.x) * g.y + A->cfg.checkpoint_every + 1 + size_t(fg.x) * fg.y)},
       {reinterpret_cast<void**>(&A->mpart),
        sizeof(double) * size_t(g.x) * g.y * A->cfg.checkpoint_every},
       {reinterpret_cast<void**>(&A->mtot), sizeof(double) * size_t(A->cfg.checkpoint_every)},

@@ -249,7 +249,9 @@ cudaError_t launch_adj_multi<KSS_T>(const AdjParams<KSS_T>& base, const AdjMulti
   cfg.numAttrs = 1;
   cudaError_t e = cudaLaunchKernelEx(&cfg, adj_multi_kernel<KSS_T>, base, m);
   if (e != cudaSuccess) return e;
-  adj_add_totals<KSS_T><<<1, 32, 0, stream>>>(m.totals, m.last - m.s0 + 1, acc);
+  const int nit = m.last - m.s0 + 1;
+  adj_iteration_totals<KSS_T><<<nit, kThreads, 0, stream>>>(m.part, m.nblocks, nit, m.totals,
+                                                             m.ticket, acc);
   return cudaGetLastError();
 }
 

@@ -161,11 +161,14 @@ def test_repeated_calls_replay_the_recorded_sweeps():
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-@pytest.mark.parametrize("n,N,E", [(96, 23, 5), (512, 200, 20), (70, 9, 9)])
+@pytest.mark.parametrize("n,N,E", [(96, 23, 5), (512, 200, 20), (70, 9, 9), (64, 6, 1)])
 def test_multistep_reverse_sweep_equals_one_launch_per_step(prec, n, N, E):
     """The reverse sweep of each segment in one cooperative launch (blocks waiting on their
-    neighbours' previous reverse step) gives the gradients of one launch per reverse step
-    bit for bit: the same per-block arithmetic, the same partials and order of addition."""
+    neighbours' previous reverse step), which also recomputes the previous segment's states,
+    gives the gradients of one launch per reverse step after plain recomputing steps, bit
+    for bit: the same per-block arithmetic, the same partials and order of addition.  The
+    cases cover a partial last segment (fewer reverse iterations than recomputed steps),
+    full segments, one segment (nothing to recompute) and a checkpoint every step."""
     from paper_2603_13618_gb300 import kss
 
     r, u, v = inputs.random_smooth(n, n - 3, seed=n + N, kmax=6, drho_amp=1e-2, mach=0.1)
