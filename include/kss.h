@@ -51,6 +51,11 @@ extern "C" {
 #define KSS_ERR_TIMEOUT (-4)     /* a bounded device wait ran out                     */
 #define KSS_ERR_STATE (-5)       /* call not valid in the lattice's current state     */
 #define KSS_ERR_UNSUPPORTED (-6) /* precision or option not built into this library  */
+#define KSS_ERR_BOUNDS (-8)      /* a device bounds check failed: only in libraries built
+                                    with -DKSS_DEBUG_BOUNDS=1, where every step block checks
+                                    its coordinates, rows, deferred-cell slots and tile
+                                    indices and skips an access that would leave its buffer
+                                    (sticky, like KSS_ERR_TIMEOUT)                        */
 #define KSS_WARN_NONPOSITIVE 1   /* sensors evaluated; some cell had f_q <= 0 or f^eq_q <= 0 */
 
 /* Storage and arithmetic precision of a lattice:

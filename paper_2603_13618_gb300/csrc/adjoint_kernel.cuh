@@ -49,6 +49,7 @@ struct AdjParams {
   double* part;          // per-CTA partial sums [nblocks]
   uint32_t* done;        // CTA completion counter, 0 between launches
   double* acc;           // the launch's total is added to *acc (FP64)
+  uint32_t* err;         // error word (bit 2: a debug bounds check failed)
   long long plane;
   int pitch, nx, ny;
   int rows;              // rows per CTA (grid adj_grid(nx, ny, rows))
@@ -405,6 +406,7 @@ __device__ __forceinline__ Acc<T> adj_step_block(const AdjParams<T>& p, int bx, 
   const int nvalid = cv ? min(V, p.nx - i0) : 0;
   const int j0 = by * p.rows, j1 = min(j0 + p.rows, p.ny);
   Acc<T> sum;
+  if (!bounds_ok(bx >= 0 && by >= 0 && bx * 32 * V < p.pitch && j0 < p.ny, p.err)) return sum;
   for (int j = j0 + warp; j < j1; j += kWarps) {
     T ft[9][V];
     if (PRE && j == j0 + warp) {

@@ -147,6 +147,7 @@ kss::AdjParams<T> adj_params(kss_adjoint* A) {
   p.ny = A->cfg.ny;
   p.rows = A->adj_rows;
   p.omega = T(1.0 / A->tau);
+  p.err = reinterpret_cast<uint32_t*>(A->small + 128);
   return p;
 }
 
@@ -326,6 +327,8 @@ int backward_impl(kss_adjoint* A, double* grad_tau) {
   KSS_ACUDA(A, cudaMemcpyAsync(&s, acc_at(A, 1), sizeof(double), cudaMemcpyDeviceToHost, A->stream));
   KSS_ACUDA(A, cudaMemcpyAsync(&err, A->small + 128, sizeof(err), cudaMemcpyDeviceToHost, A->stream));
   KSS_ACUDA(A, cudaStreamSynchronize(A->stream));
+  if (err & kss::kErrBounds)
+    return afail(A, KSS_ERR_BOUNDS, "a device bounds check failed (debug build)");
   if (err) return afail(A, KSS_ERR_TIMEOUT, "a bounded wait of the reverse sweep ran out");
   if (grad_tau) *grad_tau = s / (A->tau * A->tau);
   return KSS_OK;
@@ -443,6 +446,7 @@ const char* kss_adjoint_last_error(const kss_adjoint* A) { return A ? A->msg.c_s
 
 int kss_adjoint_forward(kss_adjoint* A, const double* rho0, const double* ux0, const double* uy0,
                         const double* weight, double tau, int on_device, double* J) {
+  const kss_rt::NvtxRange nvtx_range("kss_adjoint_forward");
   if (!A) return KSS_ERR_ARG;
   if (!rho0 || !ux0 || !uy0 || !J) return afail(A, KSS_ERR_ARG, "null pointer");
   if (!(tau > 0.5) || !std::isfinite(tau)) return afail(A, KSS_ERR_ARG, "tau must be > 0.5");
@@ -474,6 +478,7 @@ int kss_adjoint_forward(kss_adjoint* A, const double* rho0, const double* ux0, c
 }
 
 int kss_adjoint_backward(kss_adjoint* A, double* grad_rho0, double* grad_tau, int on_device) {
+  const kss_rt::NvtxRange nvtx_range("kss_adjoint_backward");
   if (!A) return KSS_ERR_ARG;
   if (!A->have_forward) return afail(A, KSS_ERR_STATE, "backward needs a forward pass");
   DeviceGuard g(A->device);

@@ -554,6 +554,7 @@ int kss_batch_set_tuning(kss_batch* B, const kss_batch_tuning* t) {
 }
 
 int kss_batch_step(kss_batch* B, int32_t nsteps) {
+  const kss_rt::NvtxRange nvtx_range("kss_batch_step");
   if (!B) return KSS_ERR_ARG;
   if (nsteps < 0) return bfail(B, KSS_ERR_ARG, "negative step count");
   for (kss_lattice* L : B->mem) {

@@ -450,6 +450,7 @@ extern "C" {
 
 int kss_regrid(kss_lattice* L, int32_t buffer, double efficiency, uint8_t* tile_mask,
                kss_box* boxes, int32_t max_boxes, int32_t* nboxes, int on_device) {
+  const kss_rt::NvtxRange nvtx_range("kss_regrid");
   int rc = enter(L);
   if (rc) return rc;
   if (!valid_args(L->cfg.tile, buffer, efficiency, max_boxes, nboxes))

@@ -390,6 +390,11 @@ int device_error(kss_lattice* L) {
   uint32_t w = 0;
   KSS_CUDA(L, cudaMemcpyAsync(&w, L->err_word, sizeof(w), cudaMemcpyDeviceToHost, L->stream));
   KSS_CUDA(L, cudaStreamSynchronize(L->stream));
+  if (w & kss::kErrBounds) {
+    L->err = KSS_ERR_BOUNDS;
+    L->msg = "a device bounds check failed (debug build)";
+    return KSS_ERR_BOUNDS;
+  }
   if (w) {
     L->err = KSS_ERR_TIMEOUT;
     L->msg = "a bounded device wait ran out (bulk copy did not complete)";
@@ -474,6 +479,7 @@ const char* kss_strerror(int code) {
     case KSS_ERR_OOM: return "out of memory";
     case KSS_ERR_CUDA: return "CUDA error";
     case KSS_ERR_TIMEOUT: return "device wait timed out";
+    case KSS_ERR_BOUNDS: return "device bounds check failed";
     case KSS_ERR_STATE: return "invalid state";
     case KSS_ERR_UNSUPPORTED: return "unsupported option";
     case KSS_WARN_NONPOSITIVE: return "non-positive populations present";
@@ -750,6 +756,7 @@ int kss_get_populations(kss_lattice* L, double* f, int on_device) {
 }
 
 int kss_step(kss_lattice* L, int32_t nsteps) {
+  const kss_rt::NvtxRange nvtx_range("kss_step");
   int rc = enter(L);
   if (rc) return rc;
   if (nsteps < 0) return fail(L, KSS_ERR_ARG, "negative step count");

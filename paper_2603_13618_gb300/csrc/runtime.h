@@ -12,6 +12,30 @@
 #include "../../include/kss.h"
 #include "launch.h"
 
+// NVTX ranges around the compute entry points (kss_step, kss_batch_step, the adjoint's
+// forward and backward passes, kss_regrid), named as the calls: a profiler's timeline then
+// shows which call launched which kernels.  The header-only NVTX v3 API costs nothing when
+// no tool is attached.  -DKSS_NVTX=0 builds without it.
+#ifndef KSS_NVTX
+#define KSS_NVTX 1
+#endif
+#if KSS_NVTX
+#include <nvtx3/nvToolsExt.h>
+#endif
+
+namespace kss_rt {
+struct NvtxRange {
+#if KSS_NVTX
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+#else
+  explicit NvtxRange(const char*) {}
+#endif
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace kss_rt
+
 namespace kss_rt {
 
 struct DeviceGuard {

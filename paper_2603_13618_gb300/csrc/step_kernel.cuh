@@ -97,6 +97,21 @@ constexpr unsigned kFull = 0xffffffffu;
 // between the fused pass and fixup_kernel, which replaces the byte.
 constexpr uint32_t kFlagDeferred = 0x40u;
 
+// Debug builds (-DKSS_DEBUG_BOUNDS=1): a CTA block checks its coordinates and rows
+// against the lattice before it touches memory, and every deferred-cell slot and tile
+// index against its shared array.  A failed check sets bit 2 of the lattice's error word
+// and the access is skipped; the next synchronising call returns KSS_ERR_BOUNDS.  Release
+// builds compile the checks away.
+#ifndef KSS_DEBUG_BOUNDS
+#define KSS_DEBUG_BOUNDS 0
+#endif
+constexpr uint32_t kErrBounds = 4u;
+__device__ __forceinline__ bool bounds_ok(bool ok, uint32_t* err) {
+  if (!KSS_DEBUG_BOUNDS || ok) return true;
+  if (err) atomicOr(err, kErrBounds);
+  return false;
+}
+
 // Cells per thread and the vector type of one population's load/store.  FP32 takes
 // 4 cells (16-byte vectors) by default; -DKSS_F32_VEC=2 selects 8-byte vectors (half the
 // per-thread state, more resident warps).
@@ -1473,6 +1488,11 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
   const bool cv = i0 < p.nx;
   const int j0 = by * p.tile * p.bands;
   const int j1 = min(j0 + p.tile * p.bands, p.ny);
+  // (uniform over the CTA: every thread returns, before any barrier)
+  if (!bounds_ok(bx >= 0 && by >= 0 && bx < gx && bx * 32 * V < p.pitch && j0 < p.ny &&
+                     p.bands >= 1 && p.bands <= kMaxBands && p.tile * p.bands <= 64,
+                 p.err))
+    return;
 
   __shared__ int s_tiles[2][kMaxBands][32];
   __shared__ uint16_t s_dl[kWarps][kWarpDefer];  // each warp's deferred cells
@@ -1669,8 +1689,10 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
       }
       if ((lane & (lpt - 1)) == 0 && (tr | ts)) {
         const int b = (j - j0) >> tshift;
-        atomicAdd(&s_tiles[0][b][lane >> lshift], tr);
-        atomicAdd(&s_tiles[1][b][lane >> lshift], ts);
+        if (bounds_ok(b < kMaxBands && (lane >> lshift) < 32, p.err)) {
+          atomicAdd(&s_tiles[0][b][lane >> lshift], tr);
+          atomicAdd(&s_tiles[1][b][lane >> lshift], ts);
+        }
       }
       if (MODE == MODE_STD) {
         // gather this row's deferred cells in the warp's region (CTA-local offsets)
@@ -1687,7 +1709,11 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
           const int rowoff = (j - j0) * 32 * V + lane * V;
 #pragma unroll
           for (int k = 0; k < V; ++k) {
-            if ((dbits >> (8 * k)) & 0x40u) s_dl[warp][slot++] = uint16_t(rowoff + k);
+            if ((dbits >> (8 * k)) & 0x40u) {
+              if (bounds_ok(slot < uint32_t(kWarpDefer), p.err))
+                s_dl[warp][slot] = uint16_t(rowoff + k);
+              ++slot;
+            }
           }
           wn += uint32_t(__shfl_sync(kFull, incl, 31));
         }
@@ -1732,6 +1758,8 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
         const int o = s_dl[w][r];
         const int rl = o / (32 * V), cl = o - rl * (32 * V);
         const int j = j0 + rl, i = bx * 32 * V + cl;
+        if (!bounds_ok(j < j1 && i < p.nx && rl / p.tile < kMaxBands && cl / p.tile < 32, p.err))
+          continue;
         const uint32_t tags = fix_cell<S, PULL, CG>(p, pr, ps, i, j);
         if (AAR && STORE && p.region) p.region[(long long)j * p.pitch + i] = uint8_t((tags >> 1) & 1u);
         const int b = rl / p.tile, tl = cl / p.tile;

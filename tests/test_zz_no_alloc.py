@@ -1,5 +1,6 @@
 """The allocation-free fused step (kss_step_f32_noalloc) against the library's own
-lattice path (kss_step through a kss_lattice), on two calls in a row.
+lattice path (kss_step through a kss_lattice), on two calls in a row, and directly
+against the FP64 oracle (every cell, two ragged sizes).
 
 The entry point exists for callers that cannot allocate device memory (they own all
 buffers, or must not allocate while running); it keeps the kernel's scratch in a
@@ -13,7 +14,9 @@ import math
 import numpy as np
 import pytest
 
+import oracle
 from paper_2603_13618_gb300 import inputs
+from tests import parity
 
 pytestmark = pytest.mark.gpu
 
@@ -79,6 +82,56 @@ def test_noalloc_step_matches_lattice_step(torch_cuda):
         np.testing.assert_allclose(sums.cpu().numpy(), s_want, rtol=1e-12, atol=1e-9)
         src, dst = dst, src
     lat.close()
+
+
+@pytest.mark.parametrize("nx,ny,tau", [(300, 201, 0.6), (1031, 517, 1.0)])
+def test_noalloc_step_matches_the_oracle(torch_cuda, nx, ny, tau):
+    """One call from the FP32-rounded equilibrium of the smooth-jump fields: populations,
+    the recorded KL field, flags (outside the threshold band), tile counts, counts and
+    sums against the oracle's step of the same FP32 state, at every cell."""
+    torch = torch_cuda
+    from paper_2603_13618_gb300 import kss
+
+    lib = kss.load()
+    tile, thr_r, thr_s = 16, 1e-3, 1e-4
+    rho, ux, uy = inputs.smooth_jump(nx, ny, seed=nx + ny, kmax=6)
+    f0 = oracle.init_equilibrium(rho, ux, uy).astype(np.float32).astype(np.float64)
+    pitch = -(-nx // 32) * 32
+    dev = "cuda"
+    fa = torch.zeros((9, ny, pitch), dtype=torch.float32, device=dev)
+    fa[:, :, :nx] = torch.from_numpy(f0).to(dev, torch.float32)
+    fb = torch.zeros_like(fa)
+    sensor = torch.zeros((ny, pitch), dtype=torch.float32, device=dev)
+    flags = torch.zeros((ny, pitch), dtype=torch.uint8, device=dev)
+    tiles = torch.zeros((2, -(-ny // tile), -(-nx // tile)), dtype=torch.int32, device=dev)
+    sums = torch.zeros(3, dtype=torch.float64, device=dev)
+    counts = torch.zeros(3, dtype=torch.int64, device=dev)
+    rc = lib.kss_step_f32_noalloc(_ptr(fa), _ptr(fb), nx, ny, pitch, tau, KN, thr_r, NEQ,
+                                  thr_s, tile, KL, _ptr(sensor), _ptr(flags), _ptr(tiles),
+                                  _ptr(sums), _ptr(counts),
+                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0
+    torch.cuda.synchronize()
+    got_f = fb[:, :, :nx].double().cpu().numpy()
+
+    sens, nonpos = oracle.sensor_fields(f0, tau, pull=True)
+    ft = oracle.stream(f0)
+    r, u, v = oracle.moments(ft)
+    fin = oracle.collide(ft, tau)
+    u32 = parity.UNIT_ROUNDOFF["fp32"]
+    assert np.max(np.abs(got_f - fin) / fin) <= 64 * u32 * math.sqrt(2)
+    kn = sens[oracle.SENSOR_ID["kn"]]
+    parity.assert_sensor_close("kl", sensor[:, :nx].double().cpu().numpy(),
+                               sens[oracle.SENSOR_ID["kl"]], "fp32", 1, r, u, v, kn, tau,
+                               neq=parity.neq_field(ft), where=f"noalloc {nx}x{ny}")
+    es = sens[oracle.SENSOR_ID["neq"]]
+    rf, rt, rcnt = oracle.flags(kn, thr_r, es, thr_s, nonpos, tile)
+    band = parity.band_mask(kn, thr_r, es, thr_s)
+    parity.assert_flags_match(flags[:, :nx].cpu().numpy(), tiles.cpu().numpy(),
+                              counts.cpu().numpy(), rf, rt, rcnt, band, tile)
+    assert 0 < int(counts[0]) < nx * ny
+    want = oracle.sums(ft)
+    assert np.all(np.abs(sums.cpu().numpy() - want) <= 16 * u32 * want[0])
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch(torch_cuda):
