@@ -1099,16 +1099,29 @@ __device__ __forceinline__ uint32_t fused_row_paired(const StepParams<S>& p,
       unpack2(rw1[m], rw[2 * m], rw[2 * m + 1]);
       unpack2(base[m], bs[2 * m], bs[2 * m + 1]);
     }
+    // rho > 0 and |u|^2 < 0.3 make every f^eq_q >= 0.05 w_q rho > 0, and Kn < 1/16
+    // bounds every |x_q| (see fused_row): otherwise the cell is deferred.  The common
+    // choice (refine on Kn, switch on neq) takes its sensors without a selection.
+    if (!AAR && p.refine_s == S_KN && p.switch_s == S_NEQ) {  // (uniform)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      // rho > 0 and |u|^2 < 0.3 make every f^eq_q >= 0.05 w_q rho > 0, and Kn < 1/16
-      // bounds every |x_q| (see fused_row): otherwise the cell is deferred
-      const bool fast = (rw[k] > 0.f) & (bs[k] > 0.55f) & (kn[k] < 0.0625f);
-      const bool r = (AAR ? pr(kn[k], kl[k], neq[k], qe[k]) : pr(kn[k], kl[k], neq[k])) > p.thr_r;
-      const bool sw = p.switch_on &&
-                      ((AAR ? ps(kn[k], kl[k], neq[k], qe[k]) : ps(kn[k], kl[k], neq[k])) > p.thr_s);
-      const uint32_t b = fast ? (uint32_t(r) | (uint32_t(sw) << 1)) : kFlagDeferred;
-      fbits |= b << (8 * k);
+      for (int k = 0; k < 4; ++k) {
+        const bool fast = (rw[k] > 0.f) & (bs[k] > 0.55f) & (kn[k] < 0.0625f);
+        const bool r = kn[k] > p.thr_r;
+        const bool sw = p.switch_on && (neq[k] > p.thr_s);
+        const uint32_t b = fast ? (uint32_t(r) | (uint32_t(sw) << 1)) : kFlagDeferred;
+        fbits |= b << (8 * k);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const bool fast = (rw[k] > 0.f) & (bs[k] > 0.55f) & (kn[k] < 0.0625f);
+        const bool r =
+            (AAR ? pr(kn[k], kl[k], neq[k], qe[k]) : pr(kn[k], kl[k], neq[k])) > p.thr_r;
+        const bool sw = p.switch_on && ((AAR ? ps(kn[k], kl[k], neq[k], qe[k])
+                                             : ps(kn[k], kl[k], neq[k])) > p.thr_s);
+        const uint32_t b = fast ? (uint32_t(r) | (uint32_t(sw) << 1)) : kFlagDeferred;
+        fbits |= b << (8 * k);
+      }
     }
     if (nvalid < 4) fbits &= nvalid > 0 ? 0xffffffffu >> (32 - 8 * nvalid) : 0u;
     if (cv) {
@@ -1443,22 +1456,24 @@ __device__ __forceinline__ void pf_issue_half(const StepParams<__half>& p, PfWar
   cp_async_commit();
 }
 
-// The staged row back from the slots (after the copies of this lane completed).
+// The staged row back from the slots (after the copies of this lane completed).  Slots
+// that no copy filled (a lane past the row end; the halo words of lanes that take no halo
+// code) hold stale data: nothing reads it into a result (assemble_half_row takes halo codes
+// only in lane 0, lane 31 and the row-end lane, and fused_row_paired zeroes the cells past
+// the row end before any arithmetic), so it is read without a select.
 __device__ __forceinline__ void pf_read_half(const StepParams<__half>& p, const PfWarpH* pw,
                                              int i0, int lane, bool cv, uint2 (&w)[9],
                                              uint32_t (&h)[9]) {
 #pragma unroll
-  for (int q = 0; q < 9; ++q) w[q] = cv ? pw->pop[q][lane] : make_uint2(0u, 0u);
-  const bool tail = i0 + 4 >= p.nx;
+  for (int q = 0; q < 9; ++q) w[q] = pw->pop[q][lane];
   const int cl = i0 == 0 ? p.nx - 1 : i0 - 1;
   const int sh = (cl & 1) ? 16 : 0;  // the code's half of its word
-  const bool hl = lane == 0 && cv, hr = cv && (lane == 31 || tail);
-  h[1] = hl ? (pw->hl[0] >> sh) & 0xffffu : 0u;
-  h[5] = hl ? (pw->hl[1] >> sh) & 0xffffu : 0u;
-  h[8] = hl ? (pw->hl[2] >> sh) & 0xffffu : 0u;
-  h[3] = hr ? pw->hr[0][lane] & 0xffffu : 0u;
-  h[6] = hr ? pw->hr[1][lane] & 0xffffu : 0u;
-  h[7] = hr ? pw->hr[2][lane] & 0xffffu : 0u;
+  h[1] = (pw->hl[0] >> sh) & 0xffffu;
+  h[5] = (pw->hl[1] >> sh) & 0xffffu;
+  h[8] = (pw->hl[2] >> sh) & 0xffffu;
+  h[3] = pw->hr[0][lane] & 0xffffu;
+  h[6] = pw->hr[1][lane] & 0xffffu;
+  h[7] = pw->hr[2][lane] & 0xffffu;
 }
 
 // Dynamic shared memory of step_kernel<S, MODE, ..., PF>: the FP16 row prefetch slots of
