@@ -327,15 +327,19 @@ ADJ_METRIC = "adjoint MLUPS (forward with checkpoints + reverse sweep), 1xGB300"
 
 def adjoint_roofline(n, N, E, ms):
     """Algorithmic bytes of one gradient over its time: the forward's N - 1 plain steps and
-    the recomputed ones (72 B/LUP), the N - 1 reverse steps (108 B/LUP: f read, lambda read
-    and written), the objective and the projection (72 B/LUP each).  The 512^2 working set
-    (9.4 MB per state) lives in L2, so HBM is not the limit: launches and the latency of
-    each dependent step are."""
+    the recomputed ones (72 B/LUP; every segment but the last, whose states the forward
+    pass keeps), the N - 1 reverse steps (108 B/LUP: f read, lambda read and written), the
+    objective and the projection (72 B/LUP each).  The 512^2 working set (9.4 MB per
+    state) lives mostly in L2, so HBM is not the limit: the latency of each dependent
+    reverse step is (the cooperative sweep's blocks wait on their neighbours)."""
     peak, kind = measured_peak()
     recompute = 0
     s0 = ((N - 2) // E) * E if N >= 2 else -1
+    first = True
     while s0 >= 0:
-        recompute += min(s0 + E - 1, N - 2) - s0
+        if not first:
+            recompute += min(s0 + E - 1, N - 2) - s0
+        first = False
         s0 -= E
     lups = n * n
     bytes_ = lups * (72 * (N - 1) + 72 * recompute + 108 * (N - 1) + 72 * 2)
@@ -343,8 +347,8 @@ def adjoint_roofline(n, N, E, ms):
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": kind, "traffic": None,
             "algorithmic_bytes_per_gradient": bytes_,
-            "note": "working set in L2 (512^2: 9.4 MB per state): bound by launches and the "
-                    "latency of each dependent step, not by HBM"}
+            "note": "working set mostly in L2 (512^2: 9.4 MB per state): bound by the latency "
+                    "of the dependent reverse steps, not by HBM"}
 
 
 def adjoint_launches(N, E, multi=True):

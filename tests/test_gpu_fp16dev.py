@@ -213,3 +213,54 @@ def test_batched_fp16_members_equal_single_lattices():
         np.testing.assert_array_equal(b[k].read_sensor("kl"), singles[k].read_sensor("kl"))
         singles[k].close()
     b.close()
+
+
+@pytest.fixture(scope="module")
+def _all_cores():
+    n = oracle.set_threads(oracle.host_cores())
+    yield n
+    oracle.set_threads(1)
+
+
+def test_full_field_4096_one_step(_all_cores):
+    """The benchmark's FP16 launch geometry (4096^2 and up take 64-row CTAs, with the row
+    prefetch of the codes): one step from an exactly stored state, every cell against the
+    oracle's step and FP16 codec -- populations within a quantum, the recorded Kn, KL and
+    neq fields, flags outside the threshold band, tile counts, counts and sums."""
+    kss = _kss()
+    n, tau, tile = 4096, 0.6, 16
+    r0, u0, v0 = inputs.random_smooth(n, n, seed=2603, kmax=8, drho_amp=0.02, mach=0.1)
+    f = oracle.step(oracle.init_equilibrium(r0, u0, v0), tau, 3)
+    h = oracle.dev16_encode(f, rho0=1.0, dev_exp=K)
+    h[np.abs(h) < 1.0] = 0.0
+    X = oracle.dev16_decode(h, rho0=1.0, dev_exp=K)
+    del f, h, r0, u0, v0
+    lat = kss.Lattice(n, n, precision="fp16dev", tau=tau, tile=tile, dev_exp=K,
+                      refine_sensor="kn", refine_threshold=1e-3, switch_sensor="neq",
+                      switch_threshold=1e-4, record=("kl", "kn", "neq"), output_every=1)
+    lat.set_populations(X)
+    lat.step(1)
+    got = lat.get_populations()
+    sens_got = {s: lat.read_sensor(s) for s in ("kn", "kl", "neq")}
+    flags, tiles, counts = lat.read_flags()
+    sums, _, _ = lat.read_stats()
+    lat.close()
+    ho = oracle.dev16_encode(oracle.step(X, tau), rho0=1.0, dev_exp=K)
+    want = oracle.dev16_decode(ho, rho0=1.0, dev_exp=K)
+    assert np.all(np.abs(got - want) <= _quantum(ho) + 8 * 2.0 ** -24 * np.abs(want))
+    assert np.mean(got == want) > 0.95
+    del got, want, ho
+    ref, nonpos = oracle.sensor_fields(X, tau, pull=True)
+    ft = oracle.stream(X)
+    r, u, v = oracle.moments(ft)
+    kn = ref[oracle.SENSOR_ID["kn"]]
+    neq = parity.neq_field(ft)
+    for name, field in sens_got.items():
+        parity.assert_sensor_close(name, field, ref[oracle.SENSOR_ID[name]], "fp32", 0, r, u, v,
+                                   kn, tau, neq=neq, where="fp16dev 4096^2 one step")
+    es = ref[oracle.SENSOR_ID["neq"]]
+    rf, rt, rcnt = oracle.flags(kn, 1e-3, es, 1e-4, nonpos, tile)
+    band = parity.band_mask(kn, 1e-3, es, 1e-4)
+    parity.assert_flags_match(flags, tiles, counts, rf, rt, rcnt, band, tile)
+    want_s = oracle.sums(ft)
+    assert np.all(np.abs(sums - want_s) <= 64 * parity.UNIT_ROUNDOFF["fp32"] * want_s[0])
