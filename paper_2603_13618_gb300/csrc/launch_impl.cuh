@@ -66,6 +66,14 @@ int resident_ctas() {
 #ifndef KSS_PERSISTENT
 #define KSS_PERSISTENT 0
 #endif
+// Eight cells per lane for the FP16 {Kn, KL, neq} step (step_block<..., VC = 8>); 0 keeps
+// four.
+#ifndef KSS_F16_CELLS8
+#define KSS_F16_CELLS8 1
+#endif
+#ifndef KSS_H8_ROWS
+#define KSS_H8_ROWS 64
+#endif
 
 template <int MODE>
 cudaError_t launch_step_mode(const StepParams<KSS_T>& p, dim3 grid, cudaStream_t stream) {
@@ -80,7 +88,24 @@ cudaError_t launch_step_mode(const StepParams<KSS_T>& p, dim3 grid, cudaStream_t
     }
   }
   if constexpr (KSS_F16_PREFETCH && step_prefetch_smem<KSS_T, MODE, true>() > 0) {
-    // FP16 deviations, {Kn, KL, neq}: the row prefetch, with its dynamic shared memory
+    // FP16 deviations, {Kn, KL, neq}: the row prefetch, with its dynamic shared memory.
+    // Eight cells per lane: CTA blocks of 256 columns and at most KSS_H8_ROWS rows, where
+    // that grid has no more blocks than the four-cell one (whose count sized the partial
+    // sums)
+    if constexpr (KSS_F16_CELLS8) {
+      const int rows8 = p.tile * p.bands < KSS_H8_ROWS ? p.tile * p.bands : KSS_H8_ROWS;
+      const dim3 g8(unsigned((p.nx + 255) / 256), unsigned((p.ny + rows8 - 1) / rows8));
+      if (rows8 % p.tile == 0 && (long long)g8.x * g8.y <= nblocks) {
+        StepParams<KSS_T> q = p;
+        q.bands = rows8 / p.tile;
+        constexpr int dyn8 = step_prefetch_smem<KSS_T, MODE, true, 8>();
+        const cudaError_t e =
+            allow_dynamic_smem<step_kernel<KSS_T, MODE, true, true, false, true, 8>, dyn8>();
+        if (e != cudaSuccess) return e;
+        step_kernel<KSS_T, MODE, true, true, false, true, 8><<<g8, kThreads, dyn8, stream>>>(q);
+        return cudaGetLastError();
+      }
+    }
     constexpr int dyn = step_prefetch_smem<KSS_T, MODE, true>();
     const cudaError_t e = allow_dynamic_smem<step_kernel<KSS_T, MODE, true, true, false, true>, dyn>();
     if (e != cudaSuccess) return e;

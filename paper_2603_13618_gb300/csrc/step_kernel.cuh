@@ -67,6 +67,10 @@ namespace kss {
 #ifndef KSS_F16_MIN_BLOCKS
 #define KSS_F16_MIN_BLOCKS KSS_STEP_MIN_BLOCKS
 #endif
+//   KSS_H8_MIN_BLOCKS    the FP16 {Kn, KL, neq} step with eight cells per lane
+#ifndef KSS_H8_MIN_BLOCKS
+#define KSS_H8_MIN_BLOCKS 2
+#endif
 
 // The knob of a step kernel with storage S and sensor set MODE.
 template <class S, int MODE>
@@ -80,9 +84,11 @@ __host__ __device__ constexpr int step_min_blocks() {
 constexpr int kWarps = 8;
 constexpr int kThreads = 32 * kWarps;
 constexpr int kMaxBands = 8;  // tile bands per CTA of step_kernel (rows = bands * tile)
-// Deferred cells a warp of step_kernel can hold: all of its cells (at most 64 rows per
-// CTA / 8 warps, 32 * V <= 128 columns), as CTA-local offsets.
+// Deferred cells a warp of step_kernel can hold: all of its cells (at most 64 rows per CTA
+// / 8 warps, 32 * V <= 128 columns, or 256 with eight cells per lane), as CTA-local
+// offsets.
 constexpr int kWarpDefer = 8 * 128;
+constexpr int kWarpDefer8 = 8 * 256;
 
 // Tile bands per CTA: about KSS_STEP_ROWS rows per CTA (32: 4 per warp) amortise the
 // CTA's epilogue; taller CTAs would leave a longer tail of partly filled waves.
@@ -873,9 +879,47 @@ struct PairCodec<__half> {
         nsb(splat2(-(c.scale[q] * c.base[q]))) {}
 };
 
-// Store the four cells of one population (two pairs), encoded for FP16 deviations.
+// Stores of the paired row under a per-lane condition ok (the lane's cells lie in the
+// lattice).  With KSS_PRED_STORES each is one predicated store instruction, so the row
+// body has no branch per store and its arithmetic forms one block that the compiler can
+// schedule as a whole (the values are computed by every lane).  Build knob:
+// -DKSS_PRED_STORES=0 takes an ordinary conditional store.
+#ifndef KSS_PRED_STORES
+#define KSS_PRED_STORES 1
+#endif
+__device__ __forceinline__ void st_cs_if(uint2* p, uint2 v, bool ok) {
+#if KSS_PRED_STORES
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.b32 q, %3, 0;\n @q st.global.cs.v2.b32 [%0], {%1, %2};\n}"
+      ::"l"(p), "r"(v.x), "r"(v.y), "r"(int(ok)) : "memory");
+#else
+  if (ok) __stcs(p, v);
+#endif
+}
+__device__ __forceinline__ void st_cs_if(float4* p, float4 v, bool ok) {
+#if KSS_PRED_STORES
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.b32 q, %5, 0;\n"
+      " @q st.global.cs.v4.f32 [%0], {%1, %2, %3, %4};\n}"
+      ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(int(ok)) : "memory");
+#else
+  if (ok) __stcs(p, v);
+#endif
+}
+__device__ __forceinline__ void st_u32_if(uint8_t* p, uint32_t v, bool ok) {
+#if KSS_PRED_STORES
+  asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n @q st.global.b32 [%0], %1;\n}"
+               ::"l"(p), "r"(v), "r"(int(ok)) : "memory");
+#else
+  if (ok) *reinterpret_cast<uint32_t*>(p) = v;
+#endif
+}
+
+// Store the four cells of one population (two pairs), encoded for FP16 deviations, where
+// ok holds.
 template <class S>
-__device__ __forceinline__ void pop_store2(S* p, const F2 (&f)[2], const PairCodec<S>& pc) {
+__device__ __forceinline__ void pop_store2(S* p, const F2 (&f)[2], const PairCodec<S>& pc,
+                                           bool ok) {
   if constexpr (std::is_same<S, __half>::value) {
     uint2 raw;
     float a, b;
@@ -885,12 +929,12 @@ __device__ __forceinline__ void pop_store2(S* p, const F2 (&f)[2], const PairCod
     const __half2 h1 = __floats2half2_rn(a, b);
     raw.x = *reinterpret_cast<const unsigned int*>(&h0);
     raw.y = *reinterpret_cast<const unsigned int*>(&h1);
-    __stcs(reinterpret_cast<uint2*>(p), raw);
+    st_cs_if(reinterpret_cast<uint2*>(p), raw, ok);
   } else {
     float a, b, c, d;
     unpack2(f[0], a, b);
     unpack2(f[1], c, d);
-    __stcs(reinterpret_cast<float4*>(p), make_float4(a, b, c, d));
+    st_cs_if(reinterpret_cast<float4*>(p), make_float4(a, b, c, d), ok);
   }
 }
 
@@ -953,9 +997,9 @@ __device__ __forceinline__ void pair2(F2 (&fp)[2], F2 (&fm)[2], const F2 (&cu)[2
     em[m] = product2(rw[m], fma2(splat2(-3.f), cu[m], t), zero);
   }
   relax2<OUT>(fp, ep, nom, a);
-  if (STORE && cv) pop_store2<S>(dst_p, fp, pc);
+  if (STORE) pop_store2<S>(dst_p, fp, pc, cv);
   relax2<OUT>(fm, em, nom, a);
-  if (STORE && cv) pop_store2<S>(dst_m, fm, pc);
+  if (STORE) pop_store2<S>(dst_m, fm, pc, cv);
 }
 
 // The same pair on a two-relaxation step (adaptive algorithm refinement): the sensors of
@@ -994,10 +1038,8 @@ __device__ __forceinline__ void pair2_aar(F2 (&fp)[2], F2 (&fm)[2], const F2 (&c
     fp[m] = fma2(nB, nm, fma2(nA, np, fp[m]));
     fm[m] = fma2(nB, np, fma2(nA, nm, fm[m]));
   }
-  if (cv) {
-    pop_store2<S>(dst_p, fp, pc);
-    pop_store2<S>(dst_m, fm, pc);
-  }
+  pop_store2<S>(dst_p, fp, pc, cv);
+  pop_store2<S>(dst_m, fm, pc, cv);
 }
 
 template <class S, int MODE, bool STORE, bool AAR = false>
@@ -1057,7 +1099,7 @@ __device__ __forceinline__ uint32_t fused_row_paired(const StepParams<S>& p,
 #pragma unroll
     for (int m = 0; m < 2; ++m) feq[m] = product2(mul2(splat2(4.f), rw1[m]), base[m], zero);
     relax2<OUT>(f[0], feq, nom, a);
-    if (STORE && cv) pop_store2<S>(dst + i0, f[0], c0);
+    if (STORE) pop_store2<S>(dst + i0, f[0], c0, cv);
   }
   // the four opposite pairs: (1, 3) c.u = +-ux; (2, 4) +-uy; (5, 7) +-(ux + uy);
   // (6, 8) +-(uy - ux)
@@ -1124,23 +1166,23 @@ __device__ __forceinline__ uint32_t fused_row_paired(const StepParams<S>& p,
       }
     }
     if (nvalid < 4) fbits &= nvalid > 0 ? 0xffffffffu >> (32 - 8 * nvalid) : 0u;
-    if (cv) {
-      store_flags<4>(p.flags + row + i0, fbits);
-      // (a deferred cell's byte is 0x40: its region byte is set by the epilogue)
-      if (AAR && STORE && p.region) store_flags<4>(p.region + row + i0, (fbits >> 1) & 0x01010101u);
-      if (AAR && p.rec_slot[S_QE] >= 0)
-        __stcs(reinterpret_cast<float4*>(p.rec + p.rec_slot[S_QE] * p.plane + row + i0),
-               make_float4(qe[0], qe[1], qe[2], qe[3]));
-      if (p.rec_slot[S_KN] >= 0)
-        __stcs(reinterpret_cast<float4*>(p.rec + p.rec_slot[S_KN] * p.plane + row + i0),
-               make_float4(kn[0], kn[1], kn[2], kn[3]));
-      if (p.rec_slot[S_KL] >= 0)
-        __stcs(reinterpret_cast<float4*>(p.rec + p.rec_slot[S_KL] * p.plane + row + i0),
-               make_float4(kl[0], kl[1], kl[2], kl[3]));
-      if (p.rec_slot[S_NEQ] >= 0)
-        __stcs(reinterpret_cast<float4*>(p.rec + p.rec_slot[S_NEQ] * p.plane + row + i0),
-               make_float4(neq[0], neq[1], neq[2], neq[3]));
-    }
+    // (uniform conditions on the recorded set; the lane's own condition is the store's)
+    st_u32_if(p.flags + row + i0, fbits, cv);
+    // (a deferred cell's byte is 0x40: its region byte is set by the epilogue)
+    if (AAR && STORE && p.region)
+      st_u32_if(p.region + row + i0, (fbits >> 1) & 0x01010101u, cv);
+    if (AAR && p.rec_slot[S_QE] >= 0)
+      st_cs_if(reinterpret_cast<float4*>(p.rec + p.rec_slot[S_QE] * p.plane + row + i0),
+               make_float4(qe[0], qe[1], qe[2], qe[3]), cv);
+    if (p.rec_slot[S_KN] >= 0)
+      st_cs_if(reinterpret_cast<float4*>(p.rec + p.rec_slot[S_KN] * p.plane + row + i0),
+               make_float4(kn[0], kn[1], kn[2], kn[3]), cv);
+    if (p.rec_slot[S_KL] >= 0)
+      st_cs_if(reinterpret_cast<float4*>(p.rec + p.rec_slot[S_KL] * p.plane + row + i0),
+               make_float4(kl[0], kl[1], kl[2], kl[3]), cv);
+    if (p.rec_slot[S_NEQ] >= 0)
+      st_cs_if(reinterpret_cast<float4*>(p.rec + p.rec_slot[S_NEQ] * p.plane + row + i0),
+               make_float4(neq[0], neq[1], neq[2], neq[3]), cv);
   }
   return fbits;
 }
@@ -1476,11 +1518,110 @@ __device__ __forceinline__ void pf_read_half(const StepParams<__half>& p, const 
   h[7] = pw->hr[2][lane] & 0xffffu;
 }
 
-// Dynamic shared memory of step_kernel<S, MODE, ..., PF>: the FP16 row prefetch slots of
-// the one-step {Kn, KL, neq} kernel, or 0.
-template <class S, int MODE, bool PF>
+// ---- eight cells per lane (the one-step FP16 {Kn, KL, neq} kernel) ----
+// Each lane takes one 16-byte vector of eight codes per population, so a CTA row is 256
+// columns wide and the per-row work (the copies and their addresses, the neighbour codes
+// of the pull, tile counts, the deferred-cell gather, loop control) is shared by eight
+// cells instead of four; the eight cells are evaluated as two groups of four
+// (fused_row_paired), one after the other.  A warp's slots hold, per population, 34
+// vectors: index 0 the word with the left halo code (in .w; lane 0's left neighbour),
+// 1..32 the lanes' vectors, 33 the word with the right halo code (in .x; lane 31's right
+// neighbour).  Lane L reads its left neighbour's last code from index L and its right
+// neighbour's first code from index L + 2, so no lane selects among sources; the lane
+// whose vector reaches the row end copies its right halo (column 0) into index L + 2,
+// which no other copy fills (the lanes past the row end copy nothing).
+struct PfWarpH8 {
+  uint4 pop[9][34];
+};
+constexpr int kPfBytesH8 = kWarps * int(sizeof(PfWarpH8));
+static_assert(sizeof(PfWarpH8) % 16 == 0, "16-byte aligned warp slots");
+
+// Copies of row j's codes for the lane at column i0 (committed as one group).  tail: the
+// lane's vector reaches the row end.
+__device__ __forceinline__ void pf_issue_h8(const StepParams<__half>& p, PfWarpH8* pw, int j,
+                                            int i0, int lane, bool cv, bool tail) {
+  if (cv) {
+    const __half* r[9];
+    half_rows(p, j, r);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) cp_async16(&pw->pop[q][lane + 1], r[q] + i0);
+    if (lane == 0) {  // the word holding column i0 - 1 (periodic)
+      const int cl = (i0 == 0 ? p.nx - 1 : i0 - 1) & ~1;
+      cp_async4(&pw->pop[1][0].w, r[1] + cl);
+      cp_async4(&pw->pop[5][0].w, r[5] + cl);
+      cp_async4(&pw->pop[8][0].w, r[8] + cl);
+    }
+    if (lane == 31 || tail) {  // the word starting at column i0 + 8, or 0 at the row end
+      const int cr = tail ? 0 : i0 + 8;
+      cp_async4(&pw->pop[3][lane + 2].x, r[3] + cr);
+      cp_async4(&pw->pop[6][lane + 2].x, r[6] + cr);
+      cp_async4(&pw->pop[7][lane + 2].x, r[7] + cr);
+    }
+  }
+  cp_async_commit();
+}
+
+// The lane's staged codes after the pull along x, as binary16 words (four per
+// population: cells 0-1, 2-3, 4-5, 6-7).  lsel: the byte selector that takes the left
+// neighbour's code from its word (its high half; the low half where lane 0's halo word
+// starts at an odd row end, column nx - 1 of an odd nx); kend: the position of cell nx - 1
+// in the row-end lane's vector (8 elsewhere).  Slots of lanes past the row end hold stale
+// codes: only cells past the row end take them, and fused_row_paired zeroes those.
+__device__ __forceinline__ void pf_read_h8(const PfWarpH8* pw, int lane, uint32_t lsel, int kend,
+                                           uint4 (&w)[9]) {
+#pragma unroll
+  for (int q = 0; q < 9; ++q) w[q] = pw->pop[q][lane + 1];
+  // cx = +1 (q = 1, 5, 8): codes [left, c0 .. c6]
+#pragma unroll
+  for (int q : {1, 5, 8}) {
+    const uint32_t left = pw->pop[q][lane].w;
+    const uint4 v = w[q];
+    w[q] = make_uint4(__byte_perm(left, v.x, lsel), __byte_perm(v.x, v.y, 0x5432),
+                      __byte_perm(v.y, v.z, 0x5432), __byte_perm(v.z, v.w, 0x5432));
+  }
+  // cx = -1 (q = 3, 6, 7): codes [c1 .. c7, right]; cell nx - 1 takes column 0
+#pragma unroll
+  for (int q : {3, 6, 7}) {
+    const uint32_t right = pw->pop[q][lane + 2].x;
+    const uint4 v = w[q];
+    w[q] = make_uint4(__byte_perm(v.x, v.y, 0x5432), __byte_perm(v.y, v.z, 0x5432),
+                      __byte_perm(v.z, v.w, 0x5432), __byte_perm(v.w, right, 0x5432));
+    if (kend < 7) {  // a row end inside the vector (the row-end lane only)
+      const uint32_t c = right & 0xffffu;
+      auto patch = [&](uint32_t& wd, int t) {
+        if (kend == 2 * t) wd = (wd & 0xffff0000u) | c;
+        if (kend == 2 * t + 1) wd = (wd & 0x0000ffffu) | (c << 16);
+      };
+      patch(w[q].x, 0);
+      patch(w[q].y, 1);
+      patch(w[q].z, 2);
+      patch(w[q].w, 3);
+    }
+  }
+}
+
+// Decode the codes of one group of four cells (words lo and hi of each population).
+__device__ __forceinline__ void decode_h8(const StepParams<__half>& p, const uint4 (&w)[9],
+                                          bool upper, F2 (&f)[9][2]) {
+  const PairCodec<__half> c0(p.codec, 0), c1(p.codec, 1), c5(p.codec, 5);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    const PairCodec<__half>& c = q == 0 ? c0 : (q <= 4 ? c1 : c5);
+    const uint32_t lo = upper ? w[q].z : w[q].x, hi = upper ? w[q].w : w[q].y;
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
+    f[q][0] = fma2(pack2(a.x, a.y), c.inv, c.base);
+    f[q][1] = fma2(pack2(b.x, b.y), c.inv, c.base);
+  }
+}
+
+// Dynamic shared memory of step_kernel<S, MODE, ..., PF, VC>: the FP16 row prefetch slots
+// of the one-step {Kn, KL, neq} kernel (VC cells per lane), or 0.
+template <class S, int MODE, bool PF, int VC = Vec<S>::N>
 __host__ __device__ constexpr int step_prefetch_smem() {
-  return (PF && std::is_same<S, __half>::value && MODE == MODE_STD) ? kPfBytesH : 0;
+  return (PF && std::is_same<S, __half>::value && MODE == MODE_STD)
+             ? (VC == 8 ? kPfBytesH8 : kPfBytesH)
+             : 0;
 }
 
 // ---------------------------------------------------------------- the fused step ----
@@ -1490,27 +1631,35 @@ __host__ __device__ constexpr int step_prefetch_smem() {
 // STORE: collide and write the new populations (false: evaluation only).
 // Block (bx, by) of a lattice whose step grid is gx blocks wide: its rows, then (output
 // modes) its tile counts and its partial sums and counts in slot bid.  Called by every
-// thread of the CTA; the CTA's shared memory is free again when it returns.
+// thread of the CTA; the CTA's shared memory is free again when it returns.  VC: cells per
+// lane (the storage's vector width, or 8 for the FP16 {Kn, KL, neq} step with the row
+// prefetch, whose CTA rows are 256 columns).
 template <class S, int MODE, bool PULL, bool STORE, bool CG = false, bool AAR = false,
-          bool PREFETCH = false>
+          bool PREFETCH = false, int VC = Vec<S>::N>
 __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx, const int by,
                                            const int gx, double* part_sum, uint32_t* part_cnt) {
   using T = arith_t<S>;
   constexpr int V = Vec<S>::N;
   constexpr bool OUT = MODE != MODE_PLAIN;
+  // eight cells per lane: two groups of four on the paired FP16 row, staged by pf_issue_h8
+  constexpr bool kH8 = VC == 8;
+  static_assert(VC == V || (kH8 && std::is_same<S, __half>::value && MODE == MODE_STD &&
+                            PULL && STORE && PREFETCH && !AAR && !CG && KSS_ROW_PAIRED),
+                "eight cells per lane: the one-step FP16 {Kn, KL, neq} kernel only");
   const int lane = threadIdx.x & 31, warp = __shfl_sync(kFull, int(threadIdx.x >> 5), 0);
-  const int i0 = (bx * 32 + lane) * V;
+  const int i0 = (bx * 32 + lane) * VC;
   const bool cv = i0 < p.nx;
   const int j0 = by * p.tile * p.bands;
   const int j1 = min(j0 + p.tile * p.bands, p.ny);
   // (uniform over the CTA: every thread returns, before any barrier)
-  if (!bounds_ok(bx >= 0 && by >= 0 && bx < gx && bx * 32 * V < p.pitch && j0 < p.ny &&
+  if (!bounds_ok(bx >= 0 && by >= 0 && bx < gx && bx * 32 * VC < p.pitch && j0 < p.ny &&
                      p.bands >= 1 && p.bands <= kMaxBands && p.tile * p.bands <= 64,
                  p.err))
     return;
 
   __shared__ int s_tiles[2][kMaxBands][32];
-  __shared__ uint16_t s_dl[kWarps][kWarpDefer];  // each warp's deferred cells
+  constexpr int kDefer = kH8 ? kWarpDefer8 : kWarpDefer;
+  __shared__ uint16_t s_dl[kWarps][kDefer];  // each warp's deferred cells
   __shared__ uint32_t s_wn[kWarps];              // and their number
   __shared__ uint32_t s_cx[3];                   // their tags (refine, switch, nonpos)
   __shared__ Red<T> s_sum[kWarps][3];
@@ -1526,7 +1675,7 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
   uint32_t wn = 0;  // deferred cells gathered by this warp (warp-uniform)
   // tile = 2^tshift rows and columns, covered by lpt = 2^lshift lanes of V cells
   const int tshift = __ffs(p.tile) - 1;
-  const int lshift = tshift - (V == 4 ? 2 : (V == 2 ? 1 : 0));
+  const int lshift = tshift - (VC == 8 ? 3 : VC == 4 ? 2 : (VC == 2 ? 1 : 0));
   const int lpt = 1 << lshift;
 
   // row prefetch (see PfWarp): the warp's slots in dynamic shared memory, and the copies
@@ -1582,12 +1731,33 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
                                MODE != MODE_FULL && !AAR && PULL && V == 4;
   constexpr bool kHalfPF = kHalfPaired && PREFETCH && STORE;
   PfWarpH* const pwh = reinterpret_cast<PfWarpH*>(kss_dyn_smem) + warp;
-  if constexpr (kHalfPF) {
+  if constexpr (kHalfPF && !kH8) {
     if (j0 + warp < j1) pf_issue_half(p, pwh, j0 + warp, i0, lane, cv);
   }
+  PfWarpH8* const pw8 = reinterpret_cast<PfWarpH8*>(kss_dyn_smem) + warp;
+  const bool tail8 = cv && i0 + 8 >= p.nx;
+  const int kend = tail8 ? p.nx - 1 - i0 : 8;  // cell nx - 1 in the row-end lane's vector
+  // lane 0's left halo word: column nx - 1 sits in its low half at the seam of an odd nx
+  const uint32_t lsel = (i0 == 0 && (p.nx & 1)) ? 0x5410u : 0x5432u;
+  if constexpr (kH8) {
+    if (j0 + warp < j1) pf_issue_h8(p, pw8, j0 + warp, i0, lane, cv, tail8);
+  }
   for (int j = j0 + warp; j < j1; j += kWarps) {
-    uint32_t fbits;
-    if constexpr (kHalfPaired) {
+    uint32_t fbits, fbits2 = 0;  // flag bytes of cells 0-3 and (eight per lane) 4-7
+    if constexpr (kH8) {
+      uint4 w[9];
+      cp_async_wait_all();
+      __syncwarp();  // the neighbouring lanes' copies of this row are complete
+      pf_read_h8(pw8, lane, lsel, kend, w);
+      __syncwarp();  // the row's reads precede the copies of the next row into the slots
+      if (j + kWarps < j1) pf_issue_h8(p, pw8, j + kWarps, i0, lane, cv, tail8);
+      F2 f[9][2];
+      decode_h8(p, w, false, f);
+      fbits = fused_row_paired<S, MODE, STORE>(p, f, i0, j, cv, a_rho, a_jx, a_jy);
+      decode_h8(p, w, true, f);
+      fbits2 = fused_row_paired<S, MODE, STORE>(p, f, i0 + 4, j, i0 + 4 < p.nx, a_rho, a_jx,
+                                                a_jy);
+    } else if constexpr (kHalfPaired) {
       F2 f[9][2];
       uint2 w[9];
       uint32_t h[9];
@@ -1687,14 +1857,22 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
     fbits = fused_row<S, MODE, PULL, STORE, AAR, CG>(p, ft, i0, j, cv, a_rho, a_jx, a_jy, mbits);
     }
     if (OUT) {
-      n_ref += __popc(fbits & 0x01010101u);
-      n_sw += __popc(fbits & 0x02020202u);
-      n_np += __popc(fbits & 0x80808080u);
+      // (with eight cells per lane, the tags of cells 4-7 moved to bits no tag of cells
+      // 0-3 occupies, so one popcount counts both words)
+      const uint32_t fr = kH8 ? (fbits & 0x01010101u) | ((fbits2 & 0x01010101u) << 1)
+                              : fbits & 0x01010101u;
+      const uint32_t fs = kH8 ? (fbits & 0x02020202u) | ((fbits2 & 0x02020202u) >> 1)
+                              : fbits & 0x02020202u;
+      n_ref += __popc(fr);
+      n_sw += __popc(fs);
+      n_np += __popc(kH8 ? (fbits & 0x80808080u) | ((fbits2 & 0x80808080u) >> 1)
+                         : fbits & 0x80808080u);
     }
     // per-tile tag counts: this lane's cells all lie in tile (lane / lanes_per_tile);
     // tile and lanes per tile are powers of two (tile 8, 16, 32 or 64)
     if (OUT) {
-      int tr = __popc(fbits & 0x01010101u), ts = __popc(fbits & 0x02020202u);
+      int tr = __popc(fbits & 0x01010101u) + (kH8 ? __popc(fbits2 & 0x01010101u) : 0);
+      int ts = __popc(fbits & 0x02020202u) + (kH8 ? __popc(fbits2 & 0x02020202u) : 0);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         if (o < lpt) {
@@ -1711,9 +1889,9 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
       }
       if (MODE == MODE_STD) {
         // gather this row's deferred cells in the warp's region (CTA-local offsets)
-        const uint32_t dbits = fbits & 0x40404040u;
-        if (__any_sync(kFull, dbits != 0)) {
-          const int nd = __popc(dbits);
+        const uint32_t dbits = fbits & 0x40404040u, dbits2 = fbits2 & 0x40404040u;
+        if (__any_sync(kFull, (dbits | dbits2) != 0)) {
+          const int nd = __popc(dbits) + (kH8 ? __popc(dbits2) : 0);
           int incl = nd;
 #pragma unroll
           for (int o = 1; o < 32; o <<= 1) {
@@ -1721,11 +1899,11 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
             if (lane >= o) incl += v;
           }
           uint32_t slot = wn + uint32_t(incl - nd);
-          const int rowoff = (j - j0) * 32 * V + lane * V;
+          const int rowoff = (j - j0) * 32 * VC + lane * VC;
 #pragma unroll
-          for (int k = 0; k < V; ++k) {
-            if ((dbits >> (8 * k)) & 0x40u) {
-              if (bounds_ok(slot < uint32_t(kWarpDefer), p.err))
+          for (int k = 0; k < VC; ++k) {
+            if (((k < 4 ? dbits : dbits2) >> (8 * (k & 3))) & 0x40u) {
+              if (bounds_ok(slot < uint32_t(kDefer), p.err))
                 s_dl[warp][slot] = uint16_t(rowoff + k);
               ++slot;
             }
@@ -1771,8 +1949,8 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
         uint32_t w = 0, r = e;
         while (r >= s_wn[w]) r -= s_wn[w++];
         const int o = s_dl[w][r];
-        const int rl = o / (32 * V), cl = o - rl * (32 * V);
-        const int j = j0 + rl, i = bx * 32 * V + cl;
+        const int rl = o / (32 * VC), cl = o - rl * (32 * VC);
+        const int j = j0 + rl, i = bx * 32 * VC + cl;
         if (!bounds_ok(j < j1 && i < p.nx && rl / p.tile < kMaxBands && cl / p.tile < 32, p.err))
           continue;
         const uint32_t tags = fix_cell<S, PULL, CG>(p, pr, ps, i, j);
@@ -1791,7 +1969,7 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
       __syncthreads();
     }
   }
-  const int tpb = (32 * V) / p.tile;
+  const int tpb = (32 * VC) / p.tile;
   for (int t = threadIdx.x; t < tpb * p.bands; t += kThreads) {
     const int b = t / tpb, tl = t - b * tpb;
     const int tx = bx * tpb + tl, ty = by * p.bands + b;
@@ -1849,20 +2027,23 @@ __device__ __forceinline__ void ticket_and_finalize(const StepParams<S>& p, int 
 // One CTA per block (bx, by) of a grid gx blocks wide, nblocks in all.  PF: the FP16 row
 // prefetch (the launch then gives the kernel step_prefetch_smem bytes of dynamic shared
 // memory).
-template <class S, int MODE, bool PULL, bool STORE, bool AAR = false, bool PF = false>
+template <class S, int MODE, bool PULL, bool STORE, bool AAR = false, bool PF = false,
+          int VC = Vec<S>::N>
 __device__ __forceinline__ void step_cta(const StepParams<S>& p, const int bx, const int by,
                                          const int gx, const int nblocks) {
-  step_block<S, MODE, PULL, STORE, false, AAR, PF>(p, bx, by, gx, p.part_sum, p.part_cnt);
+  step_block<S, MODE, PULL, STORE, false, AAR, PF, VC>(p, bx, by, gx, p.part_sum, p.part_cnt);
   if (MODE != MODE_PLAIN) ticket_and_finalize<S>(p, nblocks, nblocks);
 }
 
 // AAR: the step with the two-relaxation collision in the region p.region (pull + store).
 
-template <class S, int MODE, bool PULL, bool STORE, bool AAR = false, bool PF = false>
-__global__ void __launch_bounds__(kThreads, step_min_blocks<S, MODE>())
+template <class S, int MODE, bool PULL, bool STORE, bool AAR = false, bool PF = false,
+          int VC = Vec<S>::N>
+__global__ void __launch_bounds__(kThreads, VC == 8 ? KSS_H8_MIN_BLOCKS
+                                                    : step_min_blocks<S, MODE>())
 step_kernel(const StepParams<S> p) {
-  step_cta<S, MODE, PULL, STORE, AAR, PF>(p, blockIdx.x, blockIdx.y, gridDim.x,
-                                          gridDim.x * gridDim.y);
+  step_cta<S, MODE, PULL, STORE, AAR, PF, VC>(p, blockIdx.x, blockIdx.y, gridDim.x,
+                                              gridDim.x * gridDim.y);
 }
 
 // The same step with a persistent grid: CTA c takes blocks c, c + gridDim.x, ... of the

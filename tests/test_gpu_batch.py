@@ -286,7 +286,9 @@ def test_multi_step_batch_equals_per_step_launches(prec, rows):
     """Every member an output step of the {Kn, KL, neq} set: kss_batch_step(n) runs all n
     steps as one cooperative launch (multi_step = 1) and must give, member by member, the
     results of one launch per step (multi_step = 0) bit for bit, and those of the member
-    stepped alone at its default CTA height."""
+    stepped alone at its default CTA height (a lone FP16-deviation lattice takes eight
+    cells per lane, CTA blocks 256 columns wide, so its conservation sums are added in
+    another order: equal within the rounding bound)."""
     specs = [dict(sp, output_every=1, tile=min(sp["tile"], 16)) for sp in SPECS]
     a = _batch(specs, prec)
     b = _batch(specs, prec)
@@ -300,7 +302,7 @@ def test_multi_step_batch_equals_per_step_launches(prec, rows):
             lat.step(n)
         for k in range(len(specs)):
             _assert_same(a[k], b[k])
-            _assert_same(a[k], singles[k], sums_exact=(rows == 32),
+            _assert_same(a[k], singles[k], sums_exact=(rows == 32 and prec != "fp16dev"),
                          prec="fp64" if prec == "fp64" else "fp32", nsteps=14)
     for lat in singles:
         lat.close()
