@@ -71,9 +71,6 @@ int resident_ctas() {
 #ifndef KSS_F16_CELLS8
 #define KSS_F16_CELLS8 1
 #endif
-#ifndef KSS_H8_ROWS
-#define KSS_H8_ROWS 64
-#endif
 
 template <int MODE>
 cudaError_t launch_step_mode(const StepParams<KSS_T>& p, dim3 grid, cudaStream_t stream) {
@@ -89,20 +86,21 @@ cudaError_t launch_step_mode(const StepParams<KSS_T>& p, dim3 grid, cudaStream_t
   }
   if constexpr (KSS_F16_PREFETCH && step_prefetch_smem<KSS_T, MODE, true>() > 0) {
     // FP16 deviations, {Kn, KL, neq}: the row prefetch, with its dynamic shared memory.
-    // Eight cells per lane: CTA blocks of 256 columns and at most KSS_H8_ROWS rows, where
+    // Eight cells per lane: CTA blocks of 256 columns and at most 8 rows per warp, where
     // that grid has no more blocks than the four-cell one (whose count sized the partial
     // sums)
     if constexpr (KSS_F16_CELLS8) {
-      const int rows8 = p.tile * p.bands < KSS_H8_ROWS ? p.tile * p.bands : KSS_H8_ROWS;
+      constexpr int NW = KSS_H8_WARPS, kRows = 8 * NW;  // at most 8 rows per warp
+      const int rows8 = p.tile * p.bands < kRows ? p.tile * p.bands : kRows;
       const dim3 g8(unsigned((p.nx + 255) / 256), unsigned((p.ny + rows8 - 1) / rows8));
       if (rows8 % p.tile == 0 && (long long)g8.x * g8.y <= nblocks) {
         StepParams<KSS_T> q = p;
         q.bands = rows8 / p.tile;
-        constexpr int dyn8 = step_prefetch_smem<KSS_T, MODE, true, 8>();
-        const cudaError_t e =
-            allow_dynamic_smem<step_kernel<KSS_T, MODE, true, true, false, true, 8>, dyn8>();
+        constexpr auto kern = step_kernel<KSS_T, MODE, true, true, false, true, 8, NW>;
+        constexpr int dyn8 = step_prefetch_smem<KSS_T, MODE, true, 8, NW>();
+        const cudaError_t e = allow_dynamic_smem<kern, dyn8>();
         if (e != cudaSuccess) return e;
-        step_kernel<KSS_T, MODE, true, true, false, true, 8><<<g8, kThreads, dyn8, stream>>>(q);
+        kern<<<g8, 32 * NW, dyn8, stream>>>(q);
         return cudaGetLastError();
       }
     }

@@ -68,8 +68,13 @@ namespace kss {
 #define KSS_F16_MIN_BLOCKS KSS_STEP_MIN_BLOCKS
 #endif
 //   KSS_H8_MIN_BLOCKS    the FP16 {Kn, KL, neq} step with eight cells per lane
+//   KSS_H8_WARPS         warps per CTA of that step (8; 4 takes five CTAs per SM at 96
+//                        registers, where the row spills: 0.672 vs 0.591 ms per 8192^2 step)
+#ifndef KSS_H8_WARPS
+#define KSS_H8_WARPS 8
+#endif
 #ifndef KSS_H8_MIN_BLOCKS
-#define KSS_H8_MIN_BLOCKS 2
+#define KSS_H8_MIN_BLOCKS (KSS_H8_WARPS == 4 ? 5 : 2)
 #endif
 
 // The knob of a step kernel with storage S and sensor set MODE.
@@ -1533,7 +1538,6 @@ __device__ __forceinline__ void pf_read_half(const StepParams<__half>& p, const 
 struct PfWarpH8 {
   uint4 pop[9][34];
 };
-constexpr int kPfBytesH8 = kWarps * int(sizeof(PfWarpH8));
 static_assert(sizeof(PfWarpH8) % 16 == 0, "16-byte aligned warp slots");
 
 // Copies of row j's codes for the lane at column i0 (committed as one group).  tail: the
@@ -1615,12 +1619,12 @@ __device__ __forceinline__ void decode_h8(const StepParams<__half>& p, const uin
   }
 }
 
-// Dynamic shared memory of step_kernel<S, MODE, ..., PF, VC>: the FP16 row prefetch slots
-// of the one-step {Kn, KL, neq} kernel (VC cells per lane), or 0.
-template <class S, int MODE, bool PF, int VC = Vec<S>::N>
+// Dynamic shared memory of step_kernel<S, MODE, ..., PF, VC, NW>: the FP16 row prefetch
+// slots of the one-step {Kn, KL, neq} kernel (VC cells per lane, NW warps), or 0.
+template <class S, int MODE, bool PF, int VC = Vec<S>::N, int NW = kWarps>
 __host__ __device__ constexpr int step_prefetch_smem() {
   return (PF && std::is_same<S, __half>::value && MODE == MODE_STD)
-             ? (VC == 8 ? kPfBytesH8 : kPfBytesH)
+             ? (VC == 8 ? NW * int(sizeof(PfWarpH8)) : kPfBytesH)
              : 0;
 }
 
@@ -1633,19 +1637,22 @@ __host__ __device__ constexpr int step_prefetch_smem() {
 // modes) its tile counts and its partial sums and counts in slot bid.  Called by every
 // thread of the CTA; the CTA's shared memory is free again when it returns.  VC: cells per
 // lane (the storage's vector width, or 8 for the FP16 {Kn, KL, neq} step with the row
-// prefetch, whose CTA rows are 256 columns).
+// prefetch, whose CTA rows are 256 columns).  NW: warps per CTA (8; the eight-cell kernel
+// may take fewer, at most 8 rows per warp).
 template <class S, int MODE, bool PULL, bool STORE, bool CG = false, bool AAR = false,
-          bool PREFETCH = false, int VC = Vec<S>::N>
+          bool PREFETCH = false, int VC = Vec<S>::N, int NW = kWarps>
 __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx, const int by,
                                            const int gx, double* part_sum, uint32_t* part_cnt) {
   using T = arith_t<S>;
   constexpr int V = Vec<S>::N;
   constexpr bool OUT = MODE != MODE_PLAIN;
+  constexpr int NT = 32 * NW;  // threads of the CTA
   // eight cells per lane: two groups of four on the paired FP16 row, staged by pf_issue_h8
   constexpr bool kH8 = VC == 8;
   static_assert(VC == V || (kH8 && std::is_same<S, __half>::value && MODE == MODE_STD &&
                             PULL && STORE && PREFETCH && !AAR && !CG && KSS_ROW_PAIRED),
                 "eight cells per lane: the one-step FP16 {Kn, KL, neq} kernel only");
+  static_assert(NW == kWarps || (kH8 && NW >= 1 && NW < kWarps), "warps per CTA");
   const int lane = threadIdx.x & 31, warp = __shfl_sync(kFull, int(threadIdx.x >> 5), 0);
   const int i0 = (bx * 32 + lane) * VC;
   const bool cv = i0 < p.nx;
@@ -1653,19 +1660,20 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
   const int j1 = min(j0 + p.tile * p.bands, p.ny);
   // (uniform over the CTA: every thread returns, before any barrier)
   if (!bounds_ok(bx >= 0 && by >= 0 && bx < gx && bx * 32 * VC < p.pitch && j0 < p.ny &&
-                     p.bands >= 1 && p.bands <= kMaxBands && p.tile * p.bands <= 64,
+                     p.bands >= 1 && p.bands <= kMaxBands && p.tile * p.bands <= 64 &&
+                     p.tile * p.bands <= 8 * NW,
                  p.err))
     return;
 
   __shared__ int s_tiles[2][kMaxBands][32];
   constexpr int kDefer = kH8 ? kWarpDefer8 : kWarpDefer;
-  __shared__ uint16_t s_dl[kWarps][kDefer];  // each warp's deferred cells
-  __shared__ uint32_t s_wn[kWarps];              // and their number
+  __shared__ uint16_t s_dl[NW][kDefer];  // each warp's deferred cells
+  __shared__ uint32_t s_wn[NW];              // and their number
   __shared__ uint32_t s_cx[3];                   // their tags (refine, switch, nonpos)
-  __shared__ Red<T> s_sum[kWarps][3];
-  __shared__ uint32_t s_cnt[kWarps][3];
+  __shared__ Red<T> s_sum[NW][3];
+  __shared__ uint32_t s_cnt[NW][3];
   if (OUT) {
-    for (int t = threadIdx.x; t < 2 * kMaxBands * 32; t += kThreads) (&s_tiles[0][0][0])[t] = 0;
+    for (int t = threadIdx.x; t < 2 * kMaxBands * 32; t += NT) (&s_tiles[0][0][0])[t] = 0;
     if (threadIdx.x < 3) s_cx[threadIdx.x] = 0;
     __syncthreads();
   }
@@ -1742,7 +1750,7 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
   if constexpr (kH8) {
     if (j0 + warp < j1) pf_issue_h8(p, pw8, j0 + warp, i0, lane, cv, tail8);
   }
-  for (int j = j0 + warp; j < j1; j += kWarps) {
+  for (int j = j0 + warp; j < j1; j += NW) {
     uint32_t fbits, fbits2 = 0;  // flag bytes of cells 0-3 and (eight per lane) 4-7
     if constexpr (kH8) {
       uint4 w[9];
@@ -1750,7 +1758,7 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
       __syncwarp();  // the neighbouring lanes' copies of this row are complete
       pf_read_h8(pw8, lane, lsel, kend, w);
       __syncwarp();  // the row's reads precede the copies of the next row into the slots
-      if (j + kWarps < j1) pf_issue_h8(p, pw8, j + kWarps, i0, lane, cv, tail8);
+      if (j + NW < j1) pf_issue_h8(p, pw8, j + NW, i0, lane, cv, tail8);
       F2 f[9][2];
       decode_h8(p, w, false, f);
       fbits = fused_row_paired<S, MODE, STORE>(p, f, i0, j, cv, a_rho, a_jx, a_jy);
@@ -1942,10 +1950,10 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
     // unchanged source populations, then their tags join the CTA's counts
     uint32_t total = 0;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) total += s_wn[w];
+    for (int w = 0; w < NW; ++w) total += s_wn[w];
     if (total) {
       const Pick3 pr(p.refine_s), ps(p.switch_s);
-      for (uint32_t e = threadIdx.x; e < total; e += kThreads) {
+      for (uint32_t e = threadIdx.x; e < total; e += NT) {
         uint32_t w = 0, r = e;
         while (r >= s_wn[w]) r -= s_wn[w++];
         const int o = s_dl[w][r];
@@ -1970,7 +1978,7 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
     }
   }
   const int tpb = (32 * VC) / p.tile;
-  for (int t = threadIdx.x; t < tpb * p.bands; t += kThreads) {
+  for (int t = threadIdx.x; t < tpb * p.bands; t += NT) {
     const int b = t / tpb, tl = t - b * tpb;
     const int tx = bx * tpb + tl, ty = by * p.bands + b;
     if (tx < p.ntx && ty < p.nty) {
@@ -1987,7 +1995,7 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
       c1 = s_cx[1];
       c2 = s_cx[2];
     }
-    for (int w = 0; w < kWarps; ++w) {
+    for (int w = 0; w < NW; ++w) {
       s0.add(s_sum[w][0]);
       s1.add(s_sum[w][1]);
       s2.add(s_sum[w][2]);
@@ -2007,7 +2015,7 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
 // After a CTA's last block: one ticket from the completion counter per CTA (nunits CTAs
 // in all); the CTA that takes the last one adds the nblocks per-block partials in block
 // order.  Called by every thread of the CTA.
-template <class S>
+template <class S, int NTHREADS = kThreads>
 __device__ __forceinline__ void ticket_and_finalize(const StepParams<S>& p, int nunits,
                                                     int nblocks) {
   __shared__ int s_last;
@@ -2021,29 +2029,30 @@ __device__ __forceinline__ void ticket_and_finalize(const StepParams<S>& p, int 
   if (!s_last) return;
   // ---- last CTA: add the per-block partials ----
   __threadfence();
-  finalize_partials<S, kThreads>(p, nblocks);
+  finalize_partials<S, NTHREADS>(p, nblocks);
 }
 
 // One CTA per block (bx, by) of a grid gx blocks wide, nblocks in all.  PF: the FP16 row
 // prefetch (the launch then gives the kernel step_prefetch_smem bytes of dynamic shared
 // memory).
 template <class S, int MODE, bool PULL, bool STORE, bool AAR = false, bool PF = false,
-          int VC = Vec<S>::N>
+          int VC = Vec<S>::N, int NW = kWarps>
 __device__ __forceinline__ void step_cta(const StepParams<S>& p, const int bx, const int by,
                                          const int gx, const int nblocks) {
-  step_block<S, MODE, PULL, STORE, false, AAR, PF, VC>(p, bx, by, gx, p.part_sum, p.part_cnt);
-  if (MODE != MODE_PLAIN) ticket_and_finalize<S>(p, nblocks, nblocks);
+  step_block<S, MODE, PULL, STORE, false, AAR, PF, VC, NW>(p, bx, by, gx, p.part_sum,
+                                                          p.part_cnt);
+  if (MODE != MODE_PLAIN) ticket_and_finalize<S, 32 * NW>(p, nblocks, nblocks);
 }
 
 // AAR: the step with the two-relaxation collision in the region p.region (pull + store).
 
 template <class S, int MODE, bool PULL, bool STORE, bool AAR = false, bool PF = false,
-          int VC = Vec<S>::N>
-__global__ void __launch_bounds__(kThreads, VC == 8 ? KSS_H8_MIN_BLOCKS
-                                                    : step_min_blocks<S, MODE>())
+          int VC = Vec<S>::N, int NW = kWarps>
+__global__ void __launch_bounds__(32 * NW, VC == 8 ? KSS_H8_MIN_BLOCKS
+                                                   : step_min_blocks<S, MODE>())
 step_kernel(const StepParams<S> p) {
-  step_cta<S, MODE, PULL, STORE, AAR, PF, VC>(p, blockIdx.x, blockIdx.y, gridDim.x,
-                                              gridDim.x * gridDim.y);
+  step_cta<S, MODE, PULL, STORE, AAR, PF, VC, NW>(p, blockIdx.x, blockIdx.y, gridDim.x,
+                                                  gridDim.x * gridDim.y);
 }
 
 // The same step with a persistent grid: CTA c takes blocks c, c + gridDim.x, ... of the
