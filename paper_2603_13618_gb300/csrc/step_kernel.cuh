@@ -1628,6 +1628,50 @@ __host__ __device__ constexpr int step_prefetch_smem() {
              : 0;
 }
 
+// The populations of row j's V-cell vectors at column i0 after the pull (loads of the nine
+// source rows, the halo values of the cx != 0 planes, the shifts along x): the direct-load
+// path of step_block, and one row of a plain step on its own (the adjoint's recomputation).
+template <class S, bool CG>
+__device__ __forceinline__ void pull_row(const StepParams<S>& p, int j, int i0, int lane,
+                                         bool cv, arith_t<S> (&ft)[9][Vec<S>::N]) {
+  using T = arith_t<S>;
+  constexpr int V = Vec<S>::N;
+  const S* base = p.src + (long long)j * p.pitch;
+  long long up, dn;  // rows j - 1 and j + 1
+  row_neighbours(p, j, up, dn);
+  // source rows of q = 0..8 (pull: row j - cy_q)
+  const S* r0 = base;
+  const S* r1 = base + 1 * p.plane;
+  const S* r2 = base + 2 * p.plane + up;
+  const S* r3 = base + 3 * p.plane;
+  const S* r4 = base + 4 * p.plane + dn;
+  const S* r5 = base + 5 * p.plane + up;
+  const S* r6 = base + 6 * p.plane + up;
+  const S* r7 = base + 7 * p.plane + dn;
+  const S* r8 = base + 8 * p.plane + dn;
+  pop_vload<S, V, CG>(r0 + i0, cv, ft[0], 0, p.codec);
+  pop_vload<S, V, CG>(r1 + i0, cv, ft[1], 1, p.codec);
+  pop_vload<S, V, CG>(r2 + i0, cv, ft[2], 2, p.codec);
+  pop_vload<S, V, CG>(r3 + i0, cv, ft[3], 3, p.codec);
+  pop_vload<S, V, CG>(r4 + i0, cv, ft[4], 4, p.codec);
+  pop_vload<S, V, CG>(r5 + i0, cv, ft[5], 5, p.codec);
+  pop_vload<S, V, CG>(r6 + i0, cv, ft[6], 6, p.codec);
+  pop_vload<S, V, CG>(r7 + i0, cv, ft[7], 7, p.codec);
+  pop_vload<S, V, CG>(r8 + i0, cv, ft[8], 8, p.codec);
+  const T h1 = decode<S>(load_left_halo<S, CG>(r1, i0, p.nx, lane, cv), 1, p.codec);
+  const T h5 = decode<S>(load_left_halo<S, CG>(r5, i0, p.nx, lane, cv), 5, p.codec);
+  const T h8 = decode<S>(load_left_halo<S, CG>(r8, i0, p.nx, lane, cv), 8, p.codec);
+  const T h3 = decode<S>(load_right_halo<S, V, CG>(r3, i0, p.nx, lane, cv), 3, p.codec);
+  const T h6 = decode<S>(load_right_halo<S, V, CG>(r6, i0, p.nx, lane, cv), 6, p.codec);
+  const T h7 = decode<S>(load_right_halo<S, V, CG>(r7, i0, p.nx, lane, cv), 7, p.codec);
+  assemble_from_left<T>(ft[1], h1, lane);
+  assemble_from_left<T>(ft[5], h5, lane);
+  assemble_from_left<T>(ft[8], h8, lane);
+  assemble_from_right<T>(ft[3], h3, i0, p.nx, lane);
+  assemble_from_right<T>(ft[6], h6, i0, p.nx, lane);
+  assemble_from_right<T>(ft[7], h7, i0, p.nx, lane);
+}
+
 // ---------------------------------------------------------------- the fused step ----
 // MODE:  MODE_PLAIN (stream + collide only), MODE_STD / MODE_FULL (plus sensors,
 //        flags, tile counts, sums).
@@ -1822,39 +1866,7 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
         if (cv && p.region) mbits = load_bytes<V>(p.region + (long long)j * p.pitch + i0);
       }
       if (PULL) {
-        long long up, dn;  // rows j - 1 and j + 1
-        row_neighbours(p, j, up, dn);
-        // source rows of q = 0..8 (pull: row j - cy_q)
-        const S* r0 = base;
-        const S* r1 = base + 1 * p.plane;
-        const S* r2 = base + 2 * p.plane + up;
-        const S* r3 = base + 3 * p.plane;
-        const S* r4 = base + 4 * p.plane + dn;
-        const S* r5 = base + 5 * p.plane + up;
-        const S* r6 = base + 6 * p.plane + up;
-        const S* r7 = base + 7 * p.plane + dn;
-        const S* r8 = base + 8 * p.plane + dn;
-        pop_vload<S, V, CG>(r0 + i0, cv, ft[0], 0, p.codec);
-        pop_vload<S, V, CG>(r1 + i0, cv, ft[1], 1, p.codec);
-        pop_vload<S, V, CG>(r2 + i0, cv, ft[2], 2, p.codec);
-        pop_vload<S, V, CG>(r3 + i0, cv, ft[3], 3, p.codec);
-        pop_vload<S, V, CG>(r4 + i0, cv, ft[4], 4, p.codec);
-        pop_vload<S, V, CG>(r5 + i0, cv, ft[5], 5, p.codec);
-        pop_vload<S, V, CG>(r6 + i0, cv, ft[6], 6, p.codec);
-        pop_vload<S, V, CG>(r7 + i0, cv, ft[7], 7, p.codec);
-        pop_vload<S, V, CG>(r8 + i0, cv, ft[8], 8, p.codec);
-        const T h1 = decode<S>(load_left_halo<S, CG>(r1, i0, p.nx, lane, cv), 1, p.codec);
-        const T h5 = decode<S>(load_left_halo<S, CG>(r5, i0, p.nx, lane, cv), 5, p.codec);
-        const T h8 = decode<S>(load_left_halo<S, CG>(r8, i0, p.nx, lane, cv), 8, p.codec);
-        const T h3 = decode<S>(load_right_halo<S, V, CG>(r3, i0, p.nx, lane, cv), 3, p.codec);
-        const T h6 = decode<S>(load_right_halo<S, V, CG>(r6, i0, p.nx, lane, cv), 6, p.codec);
-        const T h7 = decode<S>(load_right_halo<S, V, CG>(r7, i0, p.nx, lane, cv), 7, p.codec);
-        assemble_from_left<T>(ft[1], h1, lane);
-        assemble_from_left<T>(ft[5], h5, lane);
-        assemble_from_left<T>(ft[8], h8, lane);
-        assemble_from_right<T>(ft[3], h3, i0, p.nx, lane);
-        assemble_from_right<T>(ft[6], h6, i0, p.nx, lane);
-        assemble_from_right<T>(ft[7], h7, i0, p.nx, lane);
+        pull_row<S, CG>(p, j, i0, lane, cv, ft);
       } else {
 #pragma unroll
         for (int q = 0; q < 9; ++q)

@@ -74,8 +74,12 @@ def test_stored_state_round_trip_and_its_sensors(nx, ny, tile):
     lat.close()
 
 
+# (517 x 40: three 256-column blocks of the eight-cell step, an odd row end at the periodic
+# seam and in lane 0 of the last block; 300 x 33: the row-end lane's upper four cells lie
+# past the row end)
 @pytest.mark.parametrize("nx,ny,tile,tau", [(37, 21, 16, 0.7), (130, 67, 8, 0.55),
-                                            (1, 5, 8, 0.9), (256, 96, 16, 1.2)])
+                                            (1, 5, 8, 0.9), (256, 96, 16, 1.2),
+                                            (517, 40, 16, 0.8), (300, 33, 8, 0.6)])
 def test_one_step_against_the_oracle_codec(nx, ny, tile, tau):
     kss = _kss()
     X = _stored_state(nx, ny, seed=3 * nx + ny, tau=tau)
