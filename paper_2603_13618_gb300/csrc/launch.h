@@ -19,6 +19,19 @@ inline dim3 step_grid(int nx, int ny, int tile, int bands = 0) {
   return dim3((unsigned)((nx + cols - 1) / cols), (unsigned)((ny + rows - 1) / rows), 1u);
 }
 
+// Grid g of the FP16 {Kn, KL, neq} step with eight cells per lane (CTA blocks of 256
+// columns and at most 8 rows per warp of nw warps) for a lattice whose four-cell grid has
+// `bands` tile bands per CTA, and its bands per CTA; false where its rows are not whole
+// tiles or it would have more blocks than the four-cell grid (whose count sized the
+// partial sums).
+inline bool step_grid8(int nx, int ny, int tile, int bands, int nw, dim3& g, int& bands8) {
+  const int rows = tile * bands, rows8 = rows < 8 * nw ? rows : 8 * nw;
+  const dim3 g4 = step_grid<__half>(nx, ny, tile, bands);
+  g = dim3(unsigned((nx + 255) / 256), unsigned((ny + rows8 - 1) / rows8), 1u);
+  bands8 = rows8 / tile;
+  return rows8 % tile == 0 && (long long)g.x * g.y <= (long long)g4.x * g4.y;
+}
+
 // mode: MODE_PLAIN / MODE_STD / MODE_FULL; pull: stream first; store: collide + write.
 // Valid combinations: (any mode, pull, store) for steps; (STD/FULL, pull or not, no store)
 // for evaluation passes.

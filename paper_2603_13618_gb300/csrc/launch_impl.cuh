@@ -90,12 +90,12 @@ cudaError_t launch_step_mode(const StepParams<KSS_T>& p, dim3 grid, cudaStream_t
     // that grid has no more blocks than the four-cell one (whose count sized the partial
     // sums)
     if constexpr (KSS_F16_CELLS8) {
-      constexpr int NW = KSS_H8_WARPS, kRows = 8 * NW;  // at most 8 rows per warp
-      const int rows8 = p.tile * p.bands < kRows ? p.tile * p.bands : kRows;
-      const dim3 g8(unsigned((p.nx + 255) / 256), unsigned((p.ny + rows8 - 1) / rows8));
-      if (rows8 % p.tile == 0 && (long long)g8.x * g8.y <= nblocks) {
+      constexpr int NW = KSS_H8_WARPS;
+      dim3 g8;
+      int bands8 = 0;
+      if (step_grid8(p.nx, p.ny, p.tile, p.bands, NW, g8, bands8)) {
         StepParams<KSS_T> q = p;
-        q.bands = rows8 / p.tile;
+        q.bands = bands8;
         constexpr auto kern = step_kernel<KSS_T, MODE, true, true, false, true, 8, NW>;
         constexpr int dyn8 = step_prefetch_smem<KSS_T, MODE, true, 8, NW>();
         const cudaError_t e = allow_dynamic_smem<kern, dyn8>();
