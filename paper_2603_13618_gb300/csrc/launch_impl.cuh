@@ -84,7 +84,17 @@ cudaError_t launch_step_mode(const StepParams<KSS_T>& p, dim3 grid, cudaStream_t
       return cudaGetLastError();
     }
   }
-  if constexpr (KSS_F16_PREFETCH && step_prefetch_smem<KSS_T, MODE, true>() > 0) {
+  if constexpr (std::is_same<KSS_T, float>::value &&
+                step_prefetch_smem<KSS_T, MODE, true>() > 0) {
+    // FP32 {Kn, KL, neq} with the row prefetch (KSS_F32_ONESTEP_PREFETCH)
+    constexpr int dyn = step_prefetch_smem<KSS_T, MODE, true>();
+    const cudaError_t e = allow_dynamic_smem<step_kernel<KSS_T, MODE, true, true, false, true>, dyn>();
+    if (e != cudaSuccess) return e;
+    step_kernel<KSS_T, MODE, true, true, false, true><<<grid, kThreads, dyn, stream>>>(p);
+    return cudaGetLastError();
+  }
+  if constexpr (std::is_same<KSS_T, __half>::value && KSS_F16_PREFETCH &&
+                step_prefetch_smem<KSS_T, MODE, true>() > 0) {
     // FP16 deviations, {Kn, KL, neq}: the row prefetch, with its dynamic shared memory.
     // Eight cells per lane: CTA blocks of 256 columns and at most 8 rows per warp, where
     // that grid has no more blocks than the four-cell one (whose count sized the partial

@@ -1621,10 +1621,18 @@ __device__ __forceinline__ void decode_h8(const StepParams<__half>& p, const uin
 
 // Dynamic shared memory of step_kernel<S, MODE, ..., PF, VC, NW>: the FP16 row prefetch
 // slots of the one-step {Kn, KL, neq} kernel (VC cells per lane, NW warps), or 0.
+// FP32 one-step {Kn, KL, neq} launches with the row prefetch of the multi-step kernel
+// (KSS_F32_ONESTEP_PREFETCH; measured at two CTAs per SM with the paired row: 4096^2
+// 0.2165 vs 0.2248 ms per launch, 8192^2 0.7891 vs 0.8188 ms; 0 loads every row directly).
+#ifndef KSS_F32_ONESTEP_PREFETCH
+#define KSS_F32_ONESTEP_PREFETCH 1
+#endif
 template <class S, int MODE, bool PF, int VC = Vec<S>::N, int NW = kWarps>
 __host__ __device__ constexpr int step_prefetch_smem() {
   return (PF && std::is_same<S, __half>::value && MODE == MODE_STD)
              ? (VC == 8 ? NW * int(sizeof(PfWarpH8)) : kPfBytesH)
+         : (PF && KSS_F32_ONESTEP_PREFETCH && std::is_same<S, float>::value && MODE == MODE_STD)
+             ? kPfBytes
              : 0;
 }
 
@@ -1732,7 +1740,7 @@ __device__ __forceinline__ void step_block(const StepParams<S>& p, const int bx,
 
   // row prefetch (see PfWarp): the warp's slots in dynamic shared memory, and the copies
   // of row jj into them
-  constexpr bool PF = PREFETCH && CG && PULL && STORE && std::is_same<S, float>::value;
+  constexpr bool PF = PREFETCH && PULL && STORE && std::is_same<S, float>::value;
   extern __shared__ __align__(16) unsigned char kss_dyn_smem[];
   PfWarp* const pw = reinterpret_cast<PfWarp*>(kss_dyn_smem) + warp;
   auto pf_issue = [&](int jj) {
