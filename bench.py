@@ -907,33 +907,44 @@ def run_gpu(args):
 
     # end to end through the C ABI with host buffers: each step copies its input fields
     # from pinned host memory, runs one fused step and reads the flags, tile counts and
-    # stats back to pinned host memory
-    e2e = None
+    # stats back to pinned host memory.  The FP32 lattice's fields go in as FP32
+    # (kss_set_fields_f32: the same state as the same values in FP64, half the bytes over
+    # the host link); the leg with FP64 fields (kss_set_fields) is reported beside it.
+    e2e = e2e_fp64 = None
     if rank == 0 or world > 1:
+        import numpy as np
+
         pin = [torch.from_numpy(a).pin_memory() for a in (rho, ux, uy)]
+        pin32 = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory()
+                 for a in (rho, ux, uy)]
         fl = torch.empty((NY, NX), dtype=torch.uint8).pin_memory()
         tl = torch.empty((2, lat.nty, lat.ntx), dtype=torch.int32).pin_memory()
         ke = max(3, min(20, K // 10))
-        for _ in range(2):
-            lat.set_fields(*pin)
-            lat.step(1)
-            lat.read_flags(out=(fl, tl))
-            lat.read_stats()
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(ke):
-            lat.set_fields(*pin)
-            lat.step(1)
-            lat.read_flags(out=(fl, tl))
-            lat.read_stats()
-        barrier()
-        el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
-        h2d = 3 * 8 * cells
-        d2h = cells + 4 * 2 * lat.nty * lat.ntx + 8 * 3 + 8 * 3 + 8 * 3
-        e2e = {"value": whole_job_mlups(world, cells, ke, el * 1e3), "unit": "MLUPS",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "steps": ke, "calls_per_step": ["kss_set_fields(host)", "kss_step(1)",
-                                               "kss_read_flags(host)", "kss_read_stats"]}
+
+        def e2e_leg(fields, esize, call):
+            for _ in range(2):
+                lat.set_fields(*fields)
+                lat.step(1)
+                lat.read_flags(out=(fl, tl))
+                lat.read_stats()
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(ke):
+                lat.set_fields(*fields)
+                lat.step(1)
+                lat.read_flags(out=(fl, tl))
+                lat.read_stats()
+            barrier()
+            el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+            h2d = 3 * esize * cells
+            d2h = cells + 4 * 2 * lat.nty * lat.ntx + 8 * 3 + 8 * 3 + 8 * 3
+            return {"value": whole_job_mlups(world, cells, ke, el * 1e3), "unit": "MLUPS",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": ke,
+                    "calls_per_step": [call, "kss_step(1)", "kss_read_flags(host)",
+                                       "kss_read_stats"]}
+
+        e2e = e2e_leg(pin32, 4, "kss_set_fields_f32(host)")
+        e2e_fp64 = e2e_leg(pin, 8, "kss_set_fields(host)")
 
     # end to end for a caller that keeps the state on the device: K steps, each followed
     # by reading its flags, tile counts, KL field and sums back to pinned host memory
@@ -994,6 +1005,7 @@ def run_gpu(args):
             "single_step_launches": single,
             "cpu_baseline": base,
             "e2e": e2e,
+            "e2e_fp64_fields": e2e_fp64,
             "e2e_stepping": e2e_stepping,
             "tau_sweep": sweep,
             "gpu_launches": 1 if multi else K,

@@ -156,6 +156,13 @@ void kss_destroy(kss_lattice* lat);
  * rho, ux, uy: nx*ny doubles each.  Resets the step counter to 0. */
 int kss_set_fields(kss_lattice* lat, const double* rho, const double* ux, const double* uy,
                    int on_device);
+/* The same from FP32 fields (nx*ny floats each), for callers whose fields are single
+ * precision: half the bytes of kss_set_fields to move from the host.  A field value gives
+ * exactly the populations of the same value passed to kss_set_fields.  Host arrays that
+ * are page-locked are read in place over the host link; others go through the lattice's
+ * staging buffer.  Errors as kss_set_fields (KSS_ERR_ARG for a NULL field). */
+int kss_set_fields_f32(kss_lattice* lat, const float* rho, const float* ux, const float* uy,
+                       int on_device);
 
 /* Raw populations [9][ny][nx] (checkpoint / resume and tests).  Set resets the step
  * counter to 0; get returns the stored post-collision state f^n. */

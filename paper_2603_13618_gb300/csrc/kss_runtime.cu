@@ -258,14 +258,15 @@ __global__ void region_to_01_kernel(uint8_t* r, int pitch, int nx, int ny) {
 // kernels read directly over the host link, or nullptr for pageable memory.  Reading pinned
 // inputs in the consuming kernel skips the staging copy's round trip through HBM (4096^2
 // fields: 1.91 instead of 2.08 ms, both bound by the ~210 GB/s host link).
-const double* pinned_device_view(const double* host) {
+template <class E>
+const E* pinned_device_view(const E* host) {
   cudaPointerAttributes a{};
   if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
   if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
-  return static_cast<const double*>(a.devicePointer);
+  return static_cast<const E*>(a.devicePointer);
 }
 
 // Is step n (counted from the last set) an output step?
@@ -676,37 +677,61 @@ static int reset_after_set(kss_lattice* L) {
   return KSS_OK;
 }
 
-int kss_set_fields(kss_lattice* L, const double* rho, const double* ux, const double* uy,
-                   int on_device) {
+}  // extern "C"
+
+// kss_set_fields and kss_set_fields_f32: fields of element type E (double or float), read
+// in place from device or page-locked host memory, else through the staging buffer.
+namespace {
+template <class E>
+int set_fields_of(kss_lattice* L, const E* rho, const E* ux, const E* uy, int on_device) {
   int rc = enter(L);
   if (rc) return rc;
   if (!rho || !ux || !uy) return fail(L, KSS_ERR_ARG, "null field pointer");
   DeviceGuard g(L->device);
   const size_t n = size_t(L->cfg.nx) * L->cfg.ny;
-  const double *r = rho, *u = ux, *v = uy;
+  const E *r = rho, *u = ux, *v = uy;
   if (!on_device) {
     r = pinned_device_view(rho);
     u = pinned_device_view(ux);
     v = pinned_device_view(uy);
   }
   if (!on_device && !(r && u && v)) {
+    // (the staging buffer holds 3 n doubles: enough for 3 n elements of either type)
     if ((rc = ensure_staging(L, 3 * n))) return rc;
-    KSS_CUDA(L, cudaMemcpyAsync(L->staging, rho, n * 8, cudaMemcpyHostToDevice, L->stream));
-    KSS_CUDA(L, cudaMemcpyAsync(L->staging + n, ux, n * 8, cudaMemcpyHostToDevice, L->stream));
-    KSS_CUDA(L, cudaMemcpyAsync(L->staging + 2 * n, uy, n * 8, cudaMemcpyHostToDevice, L->stream));
-    r = L->staging;
-    u = L->staging + n;
-    v = L->staging + 2 * n;
+    E* st = reinterpret_cast<E*>(L->staging);
+    KSS_CUDA(L, cudaMemcpyAsync(st, rho, n * sizeof(E), cudaMemcpyHostToDevice, L->stream));
+    KSS_CUDA(L, cudaMemcpyAsync(st + n, ux, n * sizeof(E), cudaMemcpyHostToDevice, L->stream));
+    KSS_CUDA(L, cudaMemcpyAsync(st + 2 * n, uy, n * sizeof(E), cudaMemcpyHostToDevice, L->stream));
+    r = st;
+    u = st + n;
+    v = st + 2 * n;
   }
   const int nx = L->cfg.nx, ny = L->cfg.ny;
   KSS_CUDA(L, with_storage(L->cfg.precision, [&](auto tag) {
              using S = typename decltype(tag)::type;
-             return kss::launch_init_equilibrium<S>(r, u, v, static_cast<S*>(L->f[L->cur]),
-                                                    L->plane, L->pitch, nx, ny, codec_of<S>(L),
-                                                    L->stream);
+             S* const f = static_cast<S*>(L->f[L->cur]);
+             if constexpr (std::is_same<E, float>::value)
+               return kss::launch_init_equilibrium_f32<S>(r, u, v, f, L->plane, L->pitch, nx,
+                                                          ny, codec_of<S>(L), L->stream);
+             else
+               return kss::launch_init_equilibrium<S>(r, u, v, f, L->plane, L->pitch, nx, ny,
+                                                      codec_of<S>(L), L->stream);
            }));
   if (!on_device) KSS_CUDA(L, cudaStreamSynchronize(L->stream));
   return reset_after_set(L);
+}
+}  // namespace
+
+extern "C" {
+
+int kss_set_fields(kss_lattice* L, const double* rho, const double* ux, const double* uy,
+                   int on_device) {
+  return set_fields_of<double>(L, rho, ux, uy, on_device);
+}
+
+int kss_set_fields_f32(kss_lattice* L, const float* rho, const float* ux, const float* uy,
+                       int on_device) {
+  return set_fields_of<float>(L, rho, ux, uy, on_device);
 }
 
 int kss_set_populations(kss_lattice* L, const double* f, int on_device) {

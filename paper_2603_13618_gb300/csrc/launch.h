@@ -120,6 +120,10 @@ template <class S>
 cudaError_t launch_init_equilibrium(const double* rho, const double* ux, const double* uy,
                                     S* f, long long plane, int pitch, int nx, int ny,
                                     const codec_t<S>& codec, cudaStream_t stream);
+template <class S>
+cudaError_t launch_init_equilibrium_f32(const float* rho, const float* ux, const float* uy,
+                                        S* f, long long plane, int pitch, int nx, int ny,
+                                        const codec_t<S>& codec, cudaStream_t stream);
 
 template <class S>
 cudaError_t launch_moments(const S* f, long long plane, int pitch, int nx, int ny, double* rho,

@@ -329,7 +329,17 @@ template <>
 cudaError_t launch_init_equilibrium<KSS_T>(const double* rho, const double* ux, const double* uy,
                                            KSS_T* f, long long plane, int pitch, int nx, int ny,
                                            const codec_t<KSS_T>& codec, cudaStream_t stream) {
-  init_equilibrium_kernel<KSS_T><<<helper_grid(nx, ny), 256, 0, stream>>>(
+  init_equilibrium_kernel<KSS_T, double><<<helper_grid(nx, ny), 256, 0, stream>>>(
+      rho, ux, uy, f, plane, pitch, nx, ny, codec);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_init_equilibrium_f32<KSS_T>(const float* rho, const float* ux,
+                                               const float* uy, KSS_T* f, long long plane,
+                                               int pitch, int nx, int ny,
+                                               const codec_t<KSS_T>& codec, cudaStream_t stream) {
+  init_equilibrium_kernel<KSS_T, float><<<helper_grid(nx, ny), 256, 0, stream>>>(
       rho, ux, uy, f, plane, pitch, nx, ny, codec);
   return cudaGetLastError();
 }

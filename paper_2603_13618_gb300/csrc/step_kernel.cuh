@@ -2399,13 +2399,14 @@ __global__ void __launch_bounds__(256) fixup_kernel(const StepParams<S> p) {
 // The auxiliary kernels below run on a grid of (column blocks of 256) x (rows), rows
 // strided by gridDim.y: one row per CTA row, so no 64-bit division per element.
 
-// f := f^eq(rho, u) from dense FP64 fields, evaluated in the arithmetic type (the FP64
-// pipe is a small fraction of the FP32 one on this GPU, and an FP32 lattice keeps only
-// FP32 populations) and stored in S.
-template <class S>
-__global__ void init_equilibrium_kernel(const double* __restrict__ rho,
-                                        const double* __restrict__ ux,
-                                        const double* __restrict__ uy, S* __restrict__ f,
+// f := f^eq(rho, u) from dense FP64 (In = double) or FP32 (In = float) fields, evaluated in
+// the arithmetic type (the FP64 pipe is a small fraction of the FP32 one on this GPU, and
+// an FP32 lattice keeps only FP32 populations) and stored in S.  An FP32 field value gives
+// the populations of the same value passed as FP64.
+template <class S, class In>
+__global__ void init_equilibrium_kernel(const In* __restrict__ rho,
+                                        const In* __restrict__ ux,
+                                        const In* __restrict__ uy, S* __restrict__ f,
                                         long long plane, int pitch, int nx, int ny,
                                         const codec_t<S> codec) {
   using T = arith_t<S>;

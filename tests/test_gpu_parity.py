@@ -307,6 +307,48 @@ def test_pinned_host_inputs(prec):
     np.testing.assert_array_equal(out[1], out[0])
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16dev"])
+def test_fp32_fields(prec):
+    """kss_set_fields_f32: FP32 fields from pageable host, page-locked host and device memory
+    give the state of the same values passed as FP64, bit for bit, and so do three fused
+    steps from it (populations, flags, tile counts, counts, sums, the recorded field); on
+    an FP32 lattice the oracle's equilibrium of those values is within the FP32 rounding."""
+    import torch
+
+    kss = _kss()
+    nx, ny = 300, 77
+    rho, ux, uy = inputs.smooth_jump(nx, ny, seed=37, kmax=6)
+    f32 = [a.astype(np.float32) for a in (rho, ux, uy)]
+    f64 = [a.astype(np.float64) for a in f32]
+    lats = []
+    for fields in (f64, f32, [torch.from_numpy(a).pin_memory() for a in f32],
+                   [torch.from_numpy(a).cuda() for a in f32]):
+        lat = kss.Lattice(nx, ny, precision=prec, tau=0.7, record=("kl",))
+        lat.set_fields(*fields)
+        lats.append(lat)
+    torch.cuda.synchronize()
+    ref = lats[0]
+    want = ref.get_populations()
+    for lat in lats[1:]:
+        np.testing.assert_array_equal(lat.get_populations(), want)
+    if prec == "fp32":
+        feq = oracle.init_equilibrium(*f64)
+        assert np.max(np.abs(want - feq)) <= 8 * parity.UNIT_ROUNDOFF["fp32"] * np.max(feq)
+    for lat in lats:
+        lat.step(3)
+    fr, tr, cr = ref.read_flags()
+    for lat in lats[1:]:
+        np.testing.assert_array_equal(lat.get_populations(), ref.get_populations())
+        fl, tl, cl = lat.read_flags()
+        np.testing.assert_array_equal(fl, fr)
+        np.testing.assert_array_equal(tl, tr)
+        np.testing.assert_array_equal(cl, cr)
+        np.testing.assert_array_equal(lat.read_stats()[0], ref.read_stats()[0])
+        np.testing.assert_array_equal(lat.read_sensor("kl"), ref.read_sensor("kl"))
+    for lat in lats:
+        lat.close()
+
+
 def test_plain_steps_and_output_cadence():
     """output_every = 0 runs plain stream + collide; reads then evaluate on demand."""
     kss = _kss()
