@@ -186,9 +186,11 @@ __device__ __forceinline__ void adj_reduce(const AdjParams<T>& p, Acc<T>& s) {
 }
 
 // Replace the cells past the row end (padding of a ragged vector) by a positive rest
-// state, so that they stay finite; they are neither summed nor read by real cells.
+// state, so that they stay finite; they are neither summed nor read by real cells.  Only
+// the lanes that hold such cells take the branch (the others skip its selects).
 template <class T>
 __device__ __forceinline__ void adj_pad(T (&v)[9][kAdjV], int nvalid, T value) {
+  if (nvalid >= kAdjV) return;
 #pragma unroll
   for (int q = 0; q < 9; ++q)
 #pragma unroll
