@@ -115,7 +115,8 @@ def measured_peak():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during timing."""
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during timing (and, for
+    the headline, during about a second of the same untimed launches after it)."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -899,6 +900,12 @@ def run_gpu(args):
         e1.record(stream)
         barrier()
         t_host = time.perf_counter() - t_host
+        # (untimed) the same launches for about a second more, so that the clock samples
+        # of a short timed region are taken under its load rather than at idle
+        t_load = time.perf_counter()
+        while time.perf_counter() - t_load < 1.0:
+            lat.step(max(K, 20))
+            torch.cuda.synchronize()
     clocks = clk.summary()
     total_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     cells = NX * NY
